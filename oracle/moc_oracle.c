@@ -1,0 +1,646 @@
+/*
+ * Plain FP64 CPU oracle for the planar flat-source Method of Characteristics (MOC) on 2D
+ * triangle meshes.
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is the independent reference the CUDA library is checked
+ * against. Only the test suite, the package smoke check and the benchmark's CPU-baseline leg may
+ * build, load or call it. It shares no code, header, table or helper with the CUDA library.
+ *
+ * What it computes (each step cites the paper's section / equation):
+ *  - modular (cyclic) rays over the bounding box of the whole domain (Sec. 3.1, the modular ray
+ *    approach applied to the domain's bounding box rather than to pins or assemblies);
+ *  - ray-mesh intersection: per-ray segment lengths and element ids, computed once (Sec. 3.1).
+ *    Here every (ray, triangle) pair whose projections overlap is clipped exactly
+ *    (Cyrus-Beck half-plane clipping), and the pieces are sorted along the ray. This is a
+ *    deliberately different algorithm from the half-edge walk the library uses;
+ *  - the multigroup source of the element-wise equation (Eq. MGNTE / MGNTE_element, isotropic
+ *    scattering, L = 0): q = [sum_g' Sigma_s,g'->g phi_g' + chi_g/k sum_g' nuSigma_f,g' phi_g' + S_g]/(4 pi);
+ *  - the flat-source characteristic solution along each segment (Eq. MOC_sol):
+ *    psi_out = psi_in e^{-tau} + (q/Sigma_t)(1 - e^{-tau}), tau = Sigma_t * l / sin(theta_p);
+ *  - the scalar flux by angular integration over all discrete directions (Sec. 2.1, text after
+ *    Eq. MOC_sol): phi = 4 pi q/Sigma_t + sum_k W_k (psi_in - psi_out)_k / (Sigma_t A_i);
+ *  - k-eigenvalue power iteration (Alg. 1, "Perform MOC on the fine mesh", without the HFEM and
+ *    CMFD steps), one transport sweep per outer, Jacobi in energy and in boundary flux.
+ *
+ * Readings where the paper is silent (all also listed in the design notes):
+ *  - A azimuths cover [0, 2 pi); for the first quadrant phi_a = 2 pi (a + 1/2)/A,
+ *    nx = floor(W sin(phi_a)/delta) + 1, ny = floor(H cos(phi_a)/delta) + 1, corrected angle
+ *    atan(H nx/(W ny)), effective spacing (W/nx) sin(corrected angle); the other quadrants mirror it.
+ *    Ray starts sit at (i + 1/2) W/nx on the bottom edge and (j + 1/2) H/ny on the side edge.
+ *  - azimuthal weight of direction a: (phi_{a+1} - phi_{a-1})/(4 pi) over the sorted 2 pi set.
+ *  - direction weight W_{a,p} = 4 pi omega_a w_p delta_a sin(theta_p); polar weights cover one
+ *    hemisphere (2D symmetry psi(theta) = psi(pi - theta)).
+ *  - region area: the tracked area A_i = sum over the 2 pi set of omega_a delta_a (sum of l in i).
+ *  - pieces shorter than 1e-12 cm are dropped; a gap longer than 1e-9 cm along a ray (outside a
+ *    non-rectangular mesh) splits the ray into separate tracks with vacuum ends.
+ *  - reflective ends link to the ray end that starts at the same wall point with the mirrored
+ *    direction; vacuum ends have zero incoming flux.
+ *  - convergence: |k' - k| <= tol_k and max_i |f'_i - f_i|/f'_i <= tol_f over regions with
+ *    f'_i > 0, f_i = sum_g nuSigma_f,g phi_i,g, flux normalised to sum_i A_i f_i = 1.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <stdio.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_PI 3.14159265358979323846
+
+typedef struct {
+  /* mesh */
+  int n_vert, n_tri;
+  double *xy;      /* [V][2] */
+  int32_t *tri;    /* [R][3] */
+  int32_t *mat;    /* [R] */
+  double xmin, xmax, ymin, ymax;
+  int bc[4];       /* x-, x+, y-, y+ ; 0 vacuum 1 reflective */
+  /* quadrature */
+  int n_azim;      /* over 2 pi */
+  int n_dir;       /* n_azim/2 directions in [0, pi) */
+  double *phi_a, *delta_a, *omega_a;  /* [n_dir] */
+  int *nx_a, *ny_a;                    /* [n_dir] */
+  int n_polar;
+  double *sin_theta, *polar_w;        /* [P] */
+  /* tracks */
+  int64_t n_tracks, n_seg;
+  int32_t *track_dir;  /* [T] direction index */
+  double *track_xy;    /* [T][4] start x,y end x,y */
+  int64_t *seg_off;    /* [T+1] */
+  int32_t *seg_reg;    /* [S] */
+  double *seg_len;     /* [S] */
+  int64_t *link;       /* [T][2]: end (t,d) feeds incoming (t',d') encoded 2t'+d', -1 vacuum */
+  double *area;        /* [R] tracked area */
+  /* cross sections */
+  int n_mat, G;
+  double *st, *nsf, *chi, *ss;   /* [M][G], [M][G], [M][G], [M][G][G] */
+  double *ext;                    /* [R][G] fixed volumetric source or NULL */
+  /* state */
+  double *phi;      /* [R][G] */
+  double *q;        /* [R][G] source per steradian */
+  double *tally;    /* [R][G] */
+  double *psi_in;   /* [T][2][P][G] incoming angular flux */
+  double *psi_next; /* [T][2][P][G] */
+  double *leak;     /* [G] outgoing W*psi at vacuum ends during the last sweep */
+  double k;
+  int n_threads;
+  char err[256];
+} orc_t;
+
+static void *xcalloc(size_t n, size_t sz) {
+  void *p = calloc(n ? n : 1, sz);
+  if (!p) { fprintf(stderr, "oracle: out of memory\n"); abort(); }
+  return p;
+}
+
+const char *orc_error(orc_t *h) { return h->err; }
+
+void orc_destroy(orc_t *h) {
+  if (!h) return;
+  free(h->xy); free(h->tri); free(h->mat);
+  free(h->phi_a); free(h->delta_a); free(h->omega_a); free(h->nx_a); free(h->ny_a);
+  free(h->sin_theta); free(h->polar_w);
+  free(h->track_dir); free(h->track_xy); free(h->seg_off); free(h->seg_reg); free(h->seg_len);
+  free(h->link); free(h->area);
+  free(h->st); free(h->nsf); free(h->chi); free(h->ss); free(h->ext);
+  free(h->phi); free(h->q); free(h->tally); free(h->psi_in); free(h->psi_next); free(h->leak);
+  free(h);
+}
+
+/* ---------------------------------------------------------------- quadrature ---- */
+static int build_quadrature(orc_t *h, double spacing) {
+  int A = h->n_azim, nq = A / 4;
+  double W = h->xmax - h->xmin, H = h->ymax - h->ymin;
+  h->n_dir = A / 2;
+  h->phi_a = xcalloc(h->n_dir, sizeof(double));
+  h->delta_a = xcalloc(h->n_dir, sizeof(double));
+  h->omega_a = xcalloc(h->n_dir, sizeof(double));
+  h->nx_a = xcalloc(h->n_dir, sizeof(int));
+  h->ny_a = xcalloc(h->n_dir, sizeof(int));
+  for (int a = 0; a < nq; ++a) {
+    double phi = 2.0 * ORC_PI * (a + 0.5) / A;
+    int nx = (int)floor(W * sin(phi) / spacing) + 1;
+    int ny = (int)floor(H * cos(phi) / spacing) + 1;
+    double pc = atan((H * nx) / (W * ny));
+    double d = (W / nx) * sin(pc);
+    /* first quadrant direction a, second quadrant mirror at index n_dir-1-a */
+    h->phi_a[a] = pc; h->delta_a[a] = d; h->nx_a[a] = nx; h->ny_a[a] = ny;
+    int b = h->n_dir - 1 - a;
+    h->phi_a[b] = ORC_PI - pc; h->delta_a[b] = d; h->nx_a[b] = nx; h->ny_a[b] = ny;
+  }
+  /* full sorted set over [0, 2 pi): directions j and j + pi */
+  double *full = xcalloc(A, sizeof(double));
+  for (int j = 0; j < h->n_dir; ++j) { full[j] = h->phi_a[j]; full[j + h->n_dir] = h->phi_a[j] + ORC_PI; }
+  for (int j = 1; j < A; ++j)
+    if (!(full[j] > full[j - 1])) { snprintf(h->err, sizeof h->err, "azimuthal angles not increasing"); free(full); return -1; }
+  for (int j = 0; j < h->n_dir; ++j) {
+    double lo = (j == 0) ? full[A - 1] - 2.0 * ORC_PI : full[j - 1];
+    double hi = full[j + 1];
+    h->omega_a[j] = (hi - lo) / (4.0 * ORC_PI);
+  }
+  free(full);
+  return 0;
+}
+
+/* ---------------------------------------------------------------- tracks ---- */
+typedef struct { double s0, s1; int32_t tri; } piece_t;
+
+static int cmp_piece(const void *a, const void *b) {
+  const piece_t *x = a, *y = b;
+  if (x->s0 < y->s0) return -1;
+  if (x->s0 > y->s0) return 1;
+  return (x->tri < y->tri) ? -1 : (x->tri > y->tri);
+}
+
+typedef struct { double c; int idx; } offs_t;
+static int cmp_offs(const void *a, const void *b) {
+  const offs_t *x = a, *y = b;
+  return (x->c < y->c) ? -1 : (x->c > y->c);
+}
+
+/* Clip the line p0 + s u, s in [0, L], against CCW triangle (a, b, c). Returns 1 and the
+ * interval if the intersection has positive length. */
+static int clip_triangle(const double *p0, const double *u, double L, const double *v0,
+                         const double *v1, const double *v2, double *s_in, double *s_out) {
+  const double *V[3] = {v0, v1, v2};
+  double lo = 0.0, hi = L;
+  for (int e = 0; e < 3; ++e) {
+    const double *a = V[e], *b = V[(e + 1) % 3];
+    double nx = -(b[1] - a[1]), ny = b[0] - a[0];           /* inward normal for CCW */
+    double f0 = nx * (p0[0] - a[0]) + ny * (p0[1] - a[1]);  /* n.(p0 - a) */
+    double fu = nx * u[0] + ny * u[1];
+    if (fu == 0.0) {
+      /* ray parallel to this edge: outside if on the outer side; a ray running exactly along
+       * the edge belongs to the triangle on its left only */
+      if (f0 < 0.0) return 0;
+      if (f0 == 0.0 && (nx * (-u[1]) + ny * u[0]) <= 0.0) return 0;
+      continue;
+    }
+    double s = -f0 / fu;
+    if (fu > 0.0) { if (s > lo) lo = s; } else { if (s < hi) hi = s; }
+  }
+  if (hi - lo <= 0.0) return 0;
+  *s_in = lo; *s_out = hi;
+  return 1;
+}
+
+/* exit parameter of the ray p0 + s u from the box */
+static double box_exit(const orc_t *h, const double *p0, const double *u) {
+  double s = INFINITY;
+  if (u[0] > 0) s = fmin(s, (h->xmax - p0[0]) / u[0]);
+  if (u[0] < 0) s = fmin(s, (h->xmin - p0[0]) / u[0]);
+  if (u[1] > 0) s = fmin(s, (h->ymax - p0[1]) / u[1]);
+  if (u[1] < 0) s = fmin(s, (h->ymin - p0[1]) / u[1]);
+  return s;
+}
+
+/* wall id of a boundary point: 0 x-, 1 x+, 2 y-, 3 y+ ; -1 if interior */
+static int wall_of(const orc_t *h, double x, double y, double tol) {
+  if (fabs(x - h->xmin) <= tol) return 0;
+  if (fabs(x - h->xmax) <= tol) return 1;
+  if (fabs(y - h->ymin) <= tol) return 2;
+  if (fabs(y - h->ymax) <= tol) return 3;
+  return -1;
+}
+
+typedef struct { int key; double c; int64_t e; } inc_t;
+static int cmp_inc(const void *a, const void *b) {
+  const inc_t *x = a, *y = b;
+  if (x->key != y->key) return (x->key < y->key) ? -1 : 1;
+  if (x->c != y->c) return (x->c < y->c) ? -1 : 1;
+  return (x->e < y->e) ? -1 : (x->e > y->e);
+}
+
+static int build_tracks(orc_t *h) {
+  double W = h->xmax - h->xmin, H = h->ymax - h->ymin;
+  const double sliver = 1e-12, gap = 1e-9;
+  /* 1. rays over the bounding box, per direction */
+  int64_t n_rays = 0;
+  for (int j = 0; j < h->n_dir; ++j) n_rays += h->nx_a[j] + h->ny_a[j];
+  double *ray = xcalloc(n_rays * 5, sizeof(double));   /* x0 y0 ux uy L */
+  int32_t *ray_dir = xcalloc(n_rays, sizeof(int32_t));
+  int64_t r = 0;
+  for (int j = 0; j < h->n_dir; ++j) {
+    double ph = h->phi_a[j], u[2] = {cos(ph), sin(ph)};
+    int nx = h->nx_a[j], ny = h->ny_a[j];
+    for (int i = 0; i < nx; ++i) {        /* bottom edge starts */
+      double p0[2] = {h->xmin + (i + 0.5) * W / nx, h->ymin};
+      ray[5 * r] = p0[0]; ray[5 * r + 1] = p0[1]; ray[5 * r + 2] = u[0]; ray[5 * r + 3] = u[1];
+      ray[5 * r + 4] = box_exit(h, p0, u); ray_dir[r] = j; ++r;
+    }
+    for (int i = 0; i < ny; ++i) {        /* side edge starts: left for ux>0, right for ux<0 */
+      double p0[2] = {(u[0] > 0) ? h->xmin : h->xmax, h->ymin + (i + 0.5) * H / ny};
+      ray[5 * r] = p0[0]; ray[5 * r + 1] = p0[1]; ray[5 * r + 2] = u[0]; ray[5 * r + 3] = u[1];
+      ray[5 * r + 4] = box_exit(h, p0, u); ray_dir[r] = j; ++r;
+    }
+  }
+  /* 2. clip every (ray, triangle) pair whose projections on the ray normal overlap */
+  int64_t *cnt = xcalloc(n_rays, sizeof(int64_t));
+  int64_t *cap = xcalloc(n_rays, sizeof(int64_t));
+  piece_t **pcs = xcalloc(n_rays, sizeof(piece_t *));
+  int64_t r0 = 0;
+  for (int j = 0; j < h->n_dir; ++j) {
+    int nr = h->nx_a[j] + h->ny_a[j];
+    double ph = h->phi_a[j], nrm[2] = {-sin(ph), cos(ph)};
+    offs_t *off = xcalloc(nr, sizeof(offs_t));
+    for (int i = 0; i < nr; ++i) {
+      off[i].c = nrm[0] * ray[5 * (r0 + i)] + nrm[1] * ray[5 * (r0 + i) + 1];
+      off[i].idx = i;
+    }
+    qsort(off, nr, sizeof(offs_t), cmp_offs);
+    for (int t = 0; t < h->n_tri; ++t) {
+      const double *v[3];
+      double cmin = INFINITY, cmax = -INFINITY;
+      for (int k = 0; k < 3; ++k) {
+        v[k] = h->xy + 2 * (int64_t)h->tri[3 * t + k];
+        double c = nrm[0] * v[k][0] + nrm[1] * v[k][1];
+        if (c < cmin) cmin = c;
+        if (c > cmax) cmax = c;
+      }
+      /* first ray with offset >= cmin */
+      int lo = 0, hi = nr;
+      while (lo < hi) { int m = (lo + hi) / 2; if (off[m].c < cmin) lo = m + 1; else hi = m; }
+      for (int q = lo; q < nr && off[q].c <= cmax; ++q) {
+        int64_t rr = r0 + off[q].idx;
+        double s0, s1;
+        if (!clip_triangle(ray + 5 * rr, ray + 5 * rr + 2, ray[5 * rr + 4], v[0], v[1], v[2], &s0, &s1)) continue;
+        if (s1 - s0 < sliver) continue;
+        if (cnt[rr] == cap[rr]) {
+          cap[rr] = cap[rr] ? 2 * cap[rr] : 16;
+          pcs[rr] = realloc(pcs[rr], cap[rr] * sizeof(piece_t));
+          if (!pcs[rr]) abort();
+        }
+        pcs[rr][cnt[rr]].s0 = s0; pcs[rr][cnt[rr]].s1 = s1; pcs[rr][cnt[rr]].tri = t;
+        cnt[rr]++;
+      }
+    }
+    free(off);
+    r0 += nr;
+  }
+  /* 3. sort pieces along each ray; split at gaps into tracks */
+  int64_t n_tr = 0, n_sg = 0;
+  for (int64_t q = 0; q < n_rays; ++q) {
+    if (!cnt[q]) continue;
+    qsort(pcs[q], cnt[q], sizeof(piece_t), cmp_piece);
+    n_tr++;
+    for (int64_t k = 1; k < cnt[q]; ++k)
+      if (pcs[q][k].s0 - pcs[q][k - 1].s1 > gap) n_tr++;
+    n_sg += cnt[q];
+  }
+  h->n_tracks = n_tr; h->n_seg = n_sg;
+  h->track_dir = xcalloc(n_tr, sizeof(int32_t));
+  h->track_xy = xcalloc(4 * n_tr, sizeof(double));
+  h->seg_off = xcalloc(n_tr + 1, sizeof(int64_t));
+  h->seg_reg = xcalloc(n_sg, sizeof(int32_t));
+  h->seg_len = xcalloc(n_sg, sizeof(double));
+  int64_t t = 0, s = 0;
+  for (int64_t q = 0; q < n_rays; ++q) {
+    if (!cnt[q]) continue;
+    const double *p0 = ray + 5 * q, *u = ray + 5 * q + 2;
+    int64_t k = 0;
+    while (k < cnt[q]) {
+      int64_t k1 = k + 1;
+      while (k1 < cnt[q] && pcs[q][k1].s0 - pcs[q][k1 - 1].s1 <= gap) k1++;
+      h->track_dir[t] = ray_dir[q];
+      h->seg_off[t] = s;
+      double sa = pcs[q][k].s0, sb = pcs[q][k1 - 1].s1;
+      h->track_xy[4 * t] = p0[0] + sa * u[0]; h->track_xy[4 * t + 1] = p0[1] + sa * u[1];
+      h->track_xy[4 * t + 2] = p0[0] + sb * u[0]; h->track_xy[4 * t + 3] = p0[1] + sb * u[1];
+      for (int64_t m = k; m < k1; ++m) {
+        h->seg_reg[s] = pcs[q][m].tri;
+        h->seg_len[s] = pcs[q][m].s1 - pcs[q][m].s0;
+        s++;
+      }
+      t++;
+      k = k1;
+    }
+    free(pcs[q]);
+  }
+  h->seg_off[t] = s;
+  free(pcs); free(cnt); free(cap); free(ray); free(ray_dir);
+
+  /* 4. links: each outgoing end (t,d) -> the incoming end starting at the same wall point with
+   *    the mirrored direction, if that wall is reflective */
+  double tol = 1e-9 * fmax(W, H);
+  h->link = xcalloc(2 * h->n_tracks, sizeof(int64_t));
+  /* index incoming ends by (direction-in-2pi, wall, coordinate along the wall), sorted */
+  int64_t ne = 2 * h->n_tracks;
+  inc_t *inc = xcalloc(ne, sizeof(inc_t));
+  for (int64_t tt = 0; tt < h->n_tracks; ++tt) {
+    for (int d = 0; d < 2; ++d) {
+      /* incoming end of (tt,d): forward enters at the start point, backward at the end point */
+      double x = h->track_xy[4 * tt + (d ? 2 : 0)], y = h->track_xy[4 * tt + (d ? 3 : 1)];
+      int w = wall_of(h, x, y, tol);
+      int dir2pi = h->track_dir[tt] + d * h->n_dir;
+      inc[2 * tt + d].key = (w < 0) ? -1 : dir2pi * 4 + w;
+      inc[2 * tt + d].c = (w == 0 || w == 1) ? y : x;
+      inc[2 * tt + d].e = 2 * tt + d;
+    }
+  }
+  qsort(inc, ne, sizeof(inc_t), cmp_inc);
+  for (int64_t e = 0; e < ne; ++e) h->link[e] = -1;
+  for (int64_t tt = 0; tt < h->n_tracks; ++tt) {
+    for (int d = 0; d < 2; ++d) {
+      /* outgoing end of (tt,d): forward leaves at the end point, backward at the start point */
+      double x = h->track_xy[4 * tt + (d ? 0 : 2)], y = h->track_xy[4 * tt + (d ? 1 : 3)];
+      int w = wall_of(h, x, y, tol);
+      if (w < 0 || h->bc[w] == 0) continue;   /* interior gap end or vacuum wall */
+      double ph = h->phi_a[h->track_dir[tt]] + d * ORC_PI;
+      double ux = cos(ph), uy = sin(ph);
+      if (w <= 1) ux = -ux; else uy = -uy;
+      double pr = atan2(uy, ux);
+      if (pr < 0) pr += 2.0 * ORC_PI;
+      /* direction index (over 2 pi) of the reflected angle */
+      int best = -1; double bd = 1e300;
+      for (int j = 0; j < 2 * h->n_dir; ++j) {
+        double pj = h->phi_a[j % h->n_dir] + (j >= h->n_dir ? ORC_PI : 0.0);
+        double dd = fabs(pj - pr);
+        if (dd > ORC_PI) dd = 2.0 * ORC_PI - dd;
+        if (dd < bd) { bd = dd; best = j; }
+      }
+      if (bd > 1e-9) { snprintf(h->err, sizeof h->err, "reflected direction not in the set"); free(inc); return -1; }
+      int key = best * 4 + w;
+      double c = (w <= 1) ? y : x;
+      /* first entry with (key, coordinate) >= (key, c - tol) */
+      int64_t lo = 0, hi = ne;
+      while (lo < hi) {
+        int64_t m = (lo + hi) / 2;
+        if (inc[m].key < key || (inc[m].key == key && inc[m].c < c - tol)) lo = m + 1; else hi = m;
+      }
+      if (lo >= ne || inc[lo].key != key || fabs(inc[lo].c - c) > tol) {
+        snprintf(h->err, sizeof h->err, "no reflective partner for track %lld end %d", (long long)tt, d);
+        free(inc); return -1;
+      }
+      h->link[2 * tt + d] = inc[lo].e;
+    }
+  }
+  free(inc);
+  /* 5. tracked areas */
+  h->area = xcalloc(h->n_tri, sizeof(double));
+  for (int64_t tt = 0; tt < h->n_tracks; ++tt) {
+    int j = h->track_dir[tt];
+    double wgt = 2.0 * h->omega_a[j] * h->delta_a[j];
+    for (int64_t s2 = h->seg_off[tt]; s2 < h->seg_off[tt + 1]; ++s2) h->area[h->seg_reg[s2]] += wgt * h->seg_len[s2];
+  }
+  return 0;
+}
+
+orc_t *orc_create(int n_vert, const double *xy, int n_tri, const int32_t *tri, const int32_t *mat,
+                  const double *bbox, const int32_t *bc, int n_azim, double spacing, int n_polar,
+                  const double *sin_theta, const double *polar_w, char *err_out) {
+  orc_t *h = xcalloc(1, sizeof(orc_t));
+  h->n_vert = n_vert; h->n_tri = n_tri;
+  h->xy = xcalloc(2 * (size_t)n_vert, sizeof(double)); memcpy(h->xy, xy, 2 * (size_t)n_vert * sizeof(double));
+  h->tri = xcalloc(3 * (size_t)n_tri, sizeof(int32_t)); memcpy(h->tri, tri, 3 * (size_t)n_tri * sizeof(int32_t));
+  h->mat = xcalloc(n_tri, sizeof(int32_t)); memcpy(h->mat, mat, (size_t)n_tri * sizeof(int32_t));
+  h->xmin = bbox[0]; h->xmax = bbox[1]; h->ymin = bbox[2]; h->ymax = bbox[3];
+  for (int i = 0; i < 4; ++i) h->bc[i] = bc[i];
+  h->n_azim = n_azim; h->n_polar = n_polar;
+  h->sin_theta = xcalloc(n_polar, sizeof(double)); memcpy(h->sin_theta, sin_theta, n_polar * sizeof(double));
+  h->polar_w = xcalloc(n_polar, sizeof(double)); memcpy(h->polar_w, polar_w, n_polar * sizeof(double));
+  h->n_threads = 1;
+  h->k = 1.0;
+  if (n_azim < 4 || n_azim % 4 || spacing <= 0 || n_polar < 1) {
+    snprintf(err_out, 256, "bad quadrature arguments"); orc_destroy(h); return NULL;
+  }
+  if (build_quadrature(h, spacing) || build_tracks(h)) {
+    snprintf(err_out, 256, "%s", h->err); orc_destroy(h); return NULL;
+  }
+  return h;
+}
+
+void orc_set_threads(orc_t *h, int n) { h->n_threads = n > 0 ? n : 1; }
+
+void orc_counts(const orc_t *h, int64_t *n_tracks, int64_t *n_seg, int *n_dir) {
+  *n_tracks = h->n_tracks; *n_seg = h->n_seg; *n_dir = h->n_dir;
+}
+
+void orc_get_quadrature(const orc_t *h, double *phi, double *delta, double *omega, int32_t *nx, int32_t *ny) {
+  for (int j = 0; j < h->n_dir; ++j) {
+    phi[j] = h->phi_a[j]; delta[j] = h->delta_a[j]; omega[j] = h->omega_a[j];
+    nx[j] = h->nx_a[j]; ny[j] = h->ny_a[j];
+  }
+}
+
+void orc_get_tracks(const orc_t *h, int64_t *seg_off, int32_t *seg_reg, double *seg_len,
+                    int32_t *track_dir, double *track_xy, int64_t *link) {
+  memcpy(seg_off, h->seg_off, (h->n_tracks + 1) * sizeof(int64_t));
+  memcpy(seg_reg, h->seg_reg, h->n_seg * sizeof(int32_t));
+  memcpy(seg_len, h->seg_len, h->n_seg * sizeof(double));
+  memcpy(track_dir, h->track_dir, h->n_tracks * sizeof(int32_t));
+  memcpy(track_xy, h->track_xy, 4 * h->n_tracks * sizeof(double));
+  memcpy(link, h->link, 2 * h->n_tracks * sizeof(int64_t));
+}
+
+void orc_get_areas(const orc_t *h, double *area) { memcpy(area, h->area, h->n_tri * sizeof(double)); }
+
+/* ---------------------------------------------------------------- physics ---- */
+int orc_set_xs(orc_t *h, int n_mat, int G, const double *st, const double *nsf, const double *chi,
+               const double *ss) {
+  free(h->st); free(h->nsf); free(h->chi); free(h->ss);
+  free(h->phi); free(h->q); free(h->tally); free(h->psi_in); free(h->psi_next); free(h->leak);
+  free(h->ext); h->ext = NULL;
+  h->n_mat = n_mat; h->G = G;
+  h->st = xcalloc((size_t)n_mat * G, sizeof(double)); memcpy(h->st, st, (size_t)n_mat * G * sizeof(double));
+  h->nsf = xcalloc((size_t)n_mat * G, sizeof(double)); memcpy(h->nsf, nsf, (size_t)n_mat * G * sizeof(double));
+  h->chi = xcalloc((size_t)n_mat * G, sizeof(double)); memcpy(h->chi, chi, (size_t)n_mat * G * sizeof(double));
+  h->ss = xcalloc((size_t)n_mat * G * G, sizeof(double)); memcpy(h->ss, ss, (size_t)n_mat * G * G * sizeof(double));
+  for (int i = 0; i < h->n_tri; ++i)
+    if (h->mat[i] < 0 || h->mat[i] >= n_mat) { snprintf(h->err, sizeof h->err, "material id out of range"); return -1; }
+  size_t RG = (size_t)h->n_tri * G, PB = (size_t)h->n_tracks * 2 * h->n_polar * G;
+  h->phi = xcalloc(RG, sizeof(double));
+  h->q = xcalloc(RG, sizeof(double));
+  h->tally = xcalloc(RG, sizeof(double));
+  h->psi_in = xcalloc(PB, sizeof(double));
+  h->psi_next = xcalloc(PB, sizeof(double));
+  h->leak = xcalloc(G, sizeof(double));
+  for (size_t i = 0; i < RG; ++i) h->phi[i] = 1.0;
+  h->k = 1.0;
+  return 0;
+}
+
+void orc_set_fixed_source(orc_t *h, const double *S) {
+  free(h->ext); h->ext = NULL;
+  if (S) {
+    h->ext = xcalloc((size_t)h->n_tri * h->G, sizeof(double));
+    memcpy(h->ext, S, (size_t)h->n_tri * h->G * sizeof(double));
+  }
+}
+
+/* F = sum_i A_i sum_g nuSigma_f phi */
+static double fission_total(const orc_t *h, const double *phi) {
+  double F = 0.0;
+  for (int i = 0; i < h->n_tri; ++i) {
+    const double *nf = h->nsf + (size_t)h->mat[i] * h->G;
+    double f = 0.0;
+    for (int g = 0; g < h->G; ++g) f += nf[g] * phi[(size_t)i * h->G + g];
+    F += h->area[i] * f;
+  }
+  return F;
+}
+
+void orc_set_state(orc_t *h, const double *phi, double k, const double *psi) {
+  size_t RG = (size_t)h->n_tri * h->G, PB = (size_t)h->n_tracks * 2 * h->n_polar * h->G;
+  if (phi) memcpy(h->phi, phi, RG * sizeof(double)); else for (size_t i = 0; i < RG; ++i) h->phi[i] = 1.0;
+  if (psi) memcpy(h->psi_in, psi, PB * sizeof(double)); else memset(h->psi_in, 0, PB * sizeof(double));
+  h->k = k;
+}
+
+void orc_get_state(const orc_t *h, double *phi, double *k, double *psi) {
+  size_t RG = (size_t)h->n_tri * h->G, PB = (size_t)h->n_tracks * 2 * h->n_polar * h->G;
+  if (phi) memcpy(phi, h->phi, RG * sizeof(double));
+  if (k) *k = h->k;
+  if (psi) memcpy(psi, h->psi_in, PB * sizeof(double));
+}
+
+void orc_get_q(const orc_t *h, double *q) { memcpy(q, h->q, (size_t)h->n_tri * h->G * sizeof(double)); }
+void orc_get_tally(const orc_t *h, double *t) { memcpy(t, h->tally, (size_t)h->n_tri * h->G * sizeof(double)); }
+void orc_get_leakage(const orc_t *h, double *l) { memcpy(l, h->leak, h->G * sizeof(double)); }
+
+/* Eq. MGNTE_element source, isotropic (per steradian) */
+static void update_source(orc_t *h, int eigen) {
+  int G = h->G;
+  for (int i = 0; i < h->n_tri; ++i) {
+    int m = h->mat[i];
+    const double *ph = h->phi + (size_t)i * G;
+    double fis = 0.0;
+    for (int gp = 0; gp < G; ++gp) fis += h->nsf[(size_t)m * G + gp] * ph[gp];
+    for (int g = 0; g < G; ++g) {
+      double sc = 0.0;
+      for (int gp = 0; gp < G; ++gp) sc += h->ss[((size_t)m * G + gp) * G + g] * ph[gp];
+      double src = sc;
+      if (eigen) src += h->chi[(size_t)m * G + g] / h->k * fis;
+      if (h->ext) src += h->ext[(size_t)i * G + g];
+      h->q[(size_t)i * G + g] = src / (4.0 * ORC_PI);
+    }
+  }
+}
+
+/* One transport sweep of every track, both directions, every polar angle and group (Eq. MOC_sol),
+ * tallying W (psi_in - psi_out) per segment into its region; outgoing fluxes are routed to the
+ * linked incoming ends for the next sweep (Jacobi in boundary flux). */
+static void transport_sweep(orc_t *h) {
+  int G = h->G, P = h->n_polar;
+  size_t RG = (size_t)h->n_tri * G, PB = (size_t)h->n_tracks * 2 * P * G;
+  memset(h->tally, 0, RG * sizeof(double));
+  memset(h->psi_next, 0, PB * sizeof(double));
+  double *leak_g = xcalloc(G, sizeof(double));
+#pragma omp parallel for schedule(static) num_threads(h->n_threads)
+  for (int g = 0; g < G; ++g) {
+    double lk = 0.0;
+    for (int64_t t = 0; t < h->n_tracks; ++t) {
+      int j = h->track_dir[t];
+      int64_t s0 = h->seg_off[t], s1 = h->seg_off[t + 1];
+      for (int d = 0; d < 2; ++d) {
+        for (int p = 0; p < P; ++p) {
+          double Wt = 4.0 * ORC_PI * h->omega_a[j] * h->polar_w[p] * h->delta_a[j] * h->sin_theta[p];
+          double psi = h->psi_in[((size_t)(2 * t + d) * P + p) * G + g];
+          for (int64_t n = 0; n < s1 - s0; ++n) {
+            int64_t s = d ? (s1 - 1 - n) : (s0 + n);
+            int i = h->seg_reg[s];
+            double sig = h->st[(size_t)h->mat[i] * G + g];
+            double qi = h->q[(size_t)i * G + g];
+            double tau = sig * h->seg_len[s] / h->sin_theta[p];
+            double delta = (psi - qi / sig) * (-expm1(-tau));
+            h->tally[(size_t)i * G + g] += Wt * delta;
+            psi -= delta;
+          }
+          int64_t e = h->link[2 * t + d];
+          if (e >= 0) h->psi_next[((size_t)e * P + p) * G + g] = psi;
+          else lk += Wt * psi;
+        }
+      }
+    }
+    leak_g[g] = lk;
+  }
+  memcpy(h->leak, leak_g, G * sizeof(double));
+  free(leak_g);
+}
+
+/* scalar flux from source and tallies */
+static void finalize_flux(const orc_t *h, double *phi_new) {
+  int G = h->G;
+  for (int i = 0; i < h->n_tri; ++i) {
+    for (int g = 0; g < G; ++g) {
+      double sig = h->st[(size_t)h->mat[i] * G + g];
+      size_t ig = (size_t)i * G + g;
+      double v = 4.0 * ORC_PI * h->q[ig] / sig;
+      if (h->area[i] > 0.0) v += h->tally[ig] / (sig * h->area[i]);
+      phi_new[ig] = v;
+    }
+  }
+}
+
+/* One outer iteration: source, sweep, flux, and (eigen mode) k update + normalisation.
+ * Returns the residual. */
+double orc_outer(orc_t *h, int eigen) {
+  int G = h->G;
+  size_t RG = (size_t)h->n_tri * G, PB = (size_t)h->n_tracks * 2 * h->n_polar * G;
+  double *phi_new = xcalloc(RG, sizeof(double));
+  update_source(h, eigen);
+  transport_sweep(h);
+  finalize_flux(h, phi_new);
+  double resid = 0.0;
+  if (eigen) {
+    double F_old = fission_total(h, h->phi);
+    double F_new = fission_total(h, phi_new);
+    h->k = h->k * F_new / F_old;
+    for (size_t i = 0; i < RG; ++i) phi_new[i] /= F_new;
+    for (size_t i = 0; i < PB; ++i) h->psi_next[i] /= F_new;
+    for (int g = 0; g < G; ++g) h->leak[g] /= F_new;
+    for (int i = 0; i < h->n_tri; ++i) {
+      const double *nf = h->nsf + (size_t)h->mat[i] * G;
+      double fo = 0.0, fn = 0.0;
+      for (int g = 0; g < G; ++g) { fo += nf[g] * h->phi[(size_t)i * G + g] / F_old; fn += nf[g] * phi_new[(size_t)i * G + g]; }
+      if (fn > 0.0) { double r = fabs(fn - fo) / fn; if (r > resid) resid = r; }
+    }
+  } else {
+    for (size_t i = 0; i < RG; ++i)
+      if (phi_new[i] > 0.0) { double r = fabs(phi_new[i] - h->phi[i]) / phi_new[i]; if (r > resid) resid = r; }
+  }
+  memcpy(h->phi, phi_new, RG * sizeof(double));
+  double *tmp = h->psi_in; h->psi_in = h->psi_next; h->psi_next = tmp;
+  free(phi_new);
+  return resid;
+}
+
+/* Normalise the current state so that F = 1 (eigen mode). */
+void orc_normalise(orc_t *h) {
+  double F = fission_total(h, h->phi);
+  size_t RG = (size_t)h->n_tri * h->G, PB = (size_t)h->n_tracks * 2 * h->n_polar * h->G;
+  if (F > 0.0) {
+    for (size_t i = 0; i < RG; ++i) h->phi[i] /= F;
+    for (size_t i = 0; i < PB; ++i) h->psi_in[i] /= F;
+  }
+}
+
+/* Power iteration (eigen=1) or fixed-source iteration (eigen=0). Returns 0 if converged. */
+int orc_iterate(orc_t *h, int eigen, double tol_k, double tol_f, int max_outer, double *k_out,
+                int *n_out, double *resid_out) {
+  if (eigen) orc_normalise(h);
+  int n = 0;
+  double resid = INFINITY;
+  int conv = 0;
+  while (n < max_outer) {
+    double k_old = h->k;
+    resid = orc_outer(h, eigen);
+    n++;
+    if ((!eigen || fabs(h->k - k_old) <= tol_k) && resid <= tol_f) { conv = 1; break; }
+  }
+  *k_out = h->k; *n_out = n; *resid_out = resid;
+  return conv ? 0 : 1;
+}
+
+/* One flat-source characteristic along a sequence of segments, one group and polar angle:
+ * returns psi after each segment (used to pin Eq. MOC_sol against the exact path integral). */
+void orc_track_sweep(int n, const double *sig, const double *qr, const double *len, double sin_theta,
+                     double psi_in, double *psi_after) {
+  double psi = psi_in;
+  for (int k = 0; k < n; ++k) {
+    double tau = sig[k] * len[k] / sin_theta;
+    psi -= (psi - qr[k]) * (-expm1(-tau));
+    psi_after[k] = psi;
+  }
+}
