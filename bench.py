@@ -1,0 +1,286 @@
+"""Benchmark: MOC segment*polar*group updates/s on the 17x17 assembly workload (one GB300).
+
+A step is one outer iteration of the whole hot path: source update, transport sweep (tallies,
+boundary-flux links, own FP32 exponential), flux finalisation and the FP64 fission/k/residual
+reductions, on the seeded synthetic 17x17 assembly (39,304 triangles, 7 groups, 32 azimuths,
+TY-3 polar, 0.02 cm ray spacing). updates per step = 2 * segments * polar * groups.
+
+Prints one JSON line (rank 0). Under torchrun each rank runs an independent replica on its own
+GPU (the sweep has no data-path exchange); value = all ranks' updates / max time.
+`--impl reference` times the CPU oracle on the host cores instead (one oracle outer per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MOC segment*polar*group updates/s"
+UNIT = "updates/s"
+WORKLOAD = "17x17 assembly, 39,304 triangles, 7 groups, 32 azimuths, 3 polar (TY), ray spacing 0.02 cm"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(prob, outers: int = 2):
+    """The oracle as it stands on the host cores: `outers` outers of the full workload."""
+    import oracle
+
+    threads = min(os.cpu_count() or 1, prob.xs.n_groups)
+    o = oracle.Oracle.from_problem(prob, threads=threads)
+    o.normalise()
+    t0 = time.perf_counter()
+    for _ in range(outers):
+        o.outer(True)
+    dt = time.perf_counter() - t0
+    ups = 2 * o.n_segments * len(prob.sin_theta) * prob.xs.n_groups
+    return {"value": ups * outers / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{outers} oracle outers of the full workload (FP64, one thread per group), "
+                      f"{dt:.2f} s"}
+
+
+def run_reference(args, rank, world):
+    from paper_2607_01591_gb300 import workloads as W
+    import oracle
+
+    if rank != 0:
+        return
+    prob = W.assembly_problem()
+    threads = min(os.cpu_count() or 1, prob.xs.n_groups)
+    o = oracle.Oracle.from_problem(prob, threads=threads)
+    o.normalise()
+    ups = 2 * o.n_segments * len(prob.sin_theta) * prob.xs.n_groups
+    for _ in range(args.warmup):
+        o.outer(True)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.outer(True)
+    dt = time.perf_counter() - t0
+    v = ups * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded mesh and cross sections)",
+            "config": {"workload": WORKLOAD, "updates_per_step": ups},
+            "cpu_baseline": {"kind": "oracle", "cores": threads, "value": v, "unit": UNIT,
+                             "sample": f"{args.steps} oracle outers of the full workload after {args.warmup} warm-up"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_plain", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if args.warmup < 3:
+        args.warmup = 3
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2607_01591_gb300 import moc
+    from paper_2607_01591_gb300 import workloads as W
+    from paper_2607_01591_gb300.build import build
+
+    if world > 1:
+        dist.init_process_group("nccl", rank=rank, world_size=world)
+    torch.cuda.set_device(local)
+    if rank == 0 or world == 1:
+        build()
+    if world > 1:
+        dist.barrier()
+    moc.load_library()
+    prob = W.assembly_problem()
+    stream = torch.cuda.Stream(device=local)
+    m = moc.Moc.from_problem(prob, device=local, precision=args.precision, stream=stream.cuda_stream)
+    n_seg, ups, kpo = m.work()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{local}")
+
+    def timed_steps(mm, k, flush_l2=True):
+        evs = []
+        with torch.cuda.stream(stream):
+            for _ in range(k):
+                if flush_l2:
+                    flush.fill_(1.0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                mm.outer(1, read=False)
+                e1.record(stream)
+                evs.append((e0, e1))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs)
+
+    # warm-up (also builds the CUDA graphs)
+    timed_steps(m, args.warmup)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ms = timed_steps(m, args.steps)
+    torch.cuda.synchronize()
+    t = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{local}")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = ups * args.steps * world / (ms_max / 1e3)
+
+    # dominant kernel: the sweep, timed by CUDA events around each launch on its stream
+    m.enable_timing(True)
+    timed_steps(m, args.steps)
+    sweep_ms, n_sw = m.timing()
+    m.enable_timing(False)
+    sweep_avg_s = sweep_ms / n_sw / 1e3
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    # FP32 ALU peak: 152 SMs x 128 FP32 lanes x max SM clock (instructions/s, FMA = 1)
+    alu_peak = 152 * 128 * sm_max * 1e6
+    ops_per_update = 19
+    achieved = ops_per_update * ups / sweep_avg_s
+    seg_bytes = 8 if args.precision != "fp64" else 16
+    R, G, P = prob.mesh.n_tri, prob.xs.n_groups, len(prob.sin_theta)
+    T, _ = m.track_counts()
+    alg_bytes = seg_bytes * n_seg + R * 8 * (8 + 8) + 2 * T * 2 * P * G * 4
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+
+    # end to end through the public API with host buffers (H2D state, outer, D2H flux and k)
+    phi0, k0, psi0 = m.get_state(with_psi=True)
+    rs = 4 if args.precision != "fp64" else 8
+    h2d = R * ((G + 7) // 8 * 8) * rs + psi0.size * rs + 8 * 8
+    d2h = R * ((G + 7) // 8 * 8) * rs + 8 * 8 + 2 * prob.xs.n_mat * G * rs
+    for _ in range(2):
+        m.set_state(phi0, k0, psi0)
+        m.outer(1, read=False)
+        m.get_state()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        m.set_state(phi0, k0, psi0)
+        m.outer(1, read=False)
+        m.get_state()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device=f"cuda:{local}")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = ups * args.steps * world / float(te.item())
+
+    # FP64 mode on the same workload (context for the FP32 numbers)
+    fp64 = None
+    if args.precision != "fp64" and args.fp64_steps > 0:
+        m64 = moc.Moc.from_problem(prob, device=local, precision="fp64", stream=stream.cuda_stream)
+        timed_steps(m64, 2)
+        ms64 = timed_steps(m64, args.fp64_steps)
+        fp64 = {"value": ups * args.fp64_steps / (ms64 / 1e3), "ms_per_step": ms64 / args.fp64_steps}
+        m64.close()
+
+    if rank != 0:
+        return
+    cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(prob)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp32_plain": "f32", "fp64": "f64"}[args.precision],
+        "data": "synthetic (seeded mesh and cross sections shaped like the paper's lattice workloads)",
+        "config": {"workload": WORKLOAD, "precision": args.precision, "segments": n_seg, "tracks": T,
+                   "updates_per_step": ups, "l2": "flushed between steps (512 MiB write, untimed)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": alu_peak / 1e9, "unit": "Gop/s",
+                     "frac": achieved / alu_peak, "traffic": None,
+                     "kernel": "sweep_kernel", "avg_launch_ms": sweep_avg_s * 1e3,
+                     "ops_per_update": ops_per_update,
+                     "peak_note": "152 SMs x 128 FP32 lanes x max SM clock (derived; FMA counted as 1 op)",
+                     "hbm_frac_of_measured": alg_bytes / sweep_avg_s / 1e9 / hbm_peak,
+                     "alg_bytes_per_launch": alg_bytes},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": kpo * args.steps,
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+        "fp64": fp64,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

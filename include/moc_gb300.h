@@ -1,0 +1,181 @@
+/*
+ * moc_gb300.h -- C ABI of the GB300 (sm_103a) planar flat-source Method of Characteristics
+ * library: 2D unstructured triangle meshes, multigroup k-eigenvalue and fixed-source transport.
+ *
+ * The operations follow the paper "Verification and Performance Assessment of NuDEAL, a
+ * GPU-accelerated Deterministic Transport Framework on Unstructured Meshes":
+ *   - multigroup transport with isotropic scattering and fission source, Eq. (MGNTE) and its
+ *     element-wise form Eq. (MGNTE_element) (Sec. 2);
+ *   - each triangle is one flat source region (Sec. 2.1);
+ *   - characteristic solution along a segment, Eq. (MOC_sol) (Sec. 2.1);
+ *   - scalar flux by angular integration over all discrete directions (Sec. 2.1);
+ *   - half-edge mesh traversal, modular rays over the domain bounding box and ray-mesh
+ *     intersection precomputed once (Sec. 3.1);
+ *   - ray-centric GPU sweep over all rays and angles at once for isotropic scattering (Sec. 3.1);
+ *   - power iteration, the "Perform MOC" step of Alg. 1 without the HFEM/CMFD steps.
+ *
+ * Conventions for every entry point:
+ *   - Return value: MOC_OK (0) or a negative moc_status. A message for the last failure is kept
+ *     per context and returned by moc_last_error(). Nothing throws or aborts across the ABI.
+ *   - Host arrays passed in are owned by the caller, read during the call and copied; arrays
+ *     passed out are caller-allocated and written during the call.
+ *   - The context owns all device memory it allocates and frees it in moc_destroy().
+ *   - Calls on one context are not thread-safe; separate contexts are independent.
+ *   - Array layouts are C order. Regions are the triangles in input order; groups are
+ *     innermost. Track arrays use the library's track order (direction-major, see
+ *     moc_get_tracks()).
+ */
+#ifndef MOC_GB300_H
+#define MOC_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct moc_ctx moc_ctx;
+
+typedef enum {
+  MOC_OK = 0,
+  MOC_ERR_ARG = -1,            /* invalid argument (sizes, ids, non-finite or non-positive data) */
+  MOC_ERR_CUDA = -2,           /* a CUDA runtime call failed */
+  MOC_ERR_OOM = -3,            /* device allocation failed */
+  MOC_ERR_STATE = -4,          /* call out of order (e.g. sweep before tracks/XS), or no GPU */
+  MOC_ERR_NOT_CONVERGED = -5,  /* iteration limit reached before the tolerances were met */
+  MOC_ERR_NONFINITE = -6,      /* k or the flux became NaN/Inf */
+  MOC_ERR_GEOMETRY = -7        /* track generation failed (non-conforming mesh, lost walk) */
+} moc_status;
+
+/* Arithmetic of the sweep.
+ *   MOC_FP64       : FP64 sweep, FP64 exponential, FP64 tallies.
+ *   MOC_FP32       : FP32 sweep with the library's own FP32 evaluation of 1 - exp(-tau) and
+ *                    compensated FP32 region tallies (a TwoSum error term per atomic update,
+ *                    folded in FP64); FP64 source normalisation, k and norms.
+ *   MOC_FP32_PLAIN : as MOC_FP32 with plain FP32 atomic tallies (no compensation). */
+enum { MOC_FP64 = 0, MOC_FP32 = 1, MOC_FP32_PLAIN = 2 };
+
+/* Boundary conditions per wall of the bounding box (x-, x+, y-, y+). */
+enum { MOC_BC_VACUUM = 0, MOC_BC_REFLECTIVE = 1 };
+
+/* Create a context on CUDA device `device` (>= 0) with sweep arithmetic `precision`.
+ * `stream` is a cudaStream_t the context launches all work on (NULL: the context creates its
+ * own). device = -1 creates a host-only context: mesh, quadrature and track generation work;
+ * every call that needs the GPU returns MOC_ERR_STATE.  *out is NULL on failure. */
+int moc_create(moc_ctx **out, int device, int precision, void *stream);
+
+/* Free the context and all device memory it owns. NULL is allowed. */
+void moc_destroy(moc_ctx *ctx);
+
+/* Message of the last failed call on ctx (empty if none). Valid until the next call on ctx. */
+const char *moc_last_error(const moc_ctx *ctx);
+
+/* Triangle mesh (Sec. 3.1). xy: [n_vert][2] vertex coordinates (cm); tri: [n_tri][3] vertex
+ * ids, counter-clockwise; tri_material: [n_tri] material ids (checked in moc_set_xs); bbox:
+ * xmin, xmax, ymin, ymax of the domain's bounding box; bc: [4] MOC_BC_* for x-, x+, y-, y+.
+ * The mesh must be conforming (interior edges shared by exactly two triangles with opposite
+ * orientation). Reflective walls require the mesh to fill the box along that wall.
+ * Errors: MOC_ERR_ARG for bad sizes, ids, orientation or a non-conforming edge. */
+int moc_set_mesh(moc_ctx *ctx, int n_vert, const double *xy, int n_tri, const int32_t *tri,
+                 const int32_t *tri_material, const double *bbox, const int32_t *bc);
+
+/* Angular quadrature. n_azim: azimuthal angles over [0, 2 pi), a multiple of 4; ray_spacing
+ * (cm) > 0: the requested distance between parallel rays (the effective one is never larger);
+ * sin_theta, polar_w: [n_polar] polar angles of one hemisphere and their weights (sum 1).
+ * 1 <= n_polar <= 6. Errors: MOC_ERR_ARG. */
+int moc_set_quadrature(moc_ctx *ctx, int n_azim, double ray_spacing, int n_polar,
+                       const double *sin_theta, const double *polar_w);
+
+/* Lay down the modular (cyclic) rays over the bounding box, intersect them with the mesh by a
+ * half-edge walk, build the reflective links and the tracked region areas, and upload the
+ * segment data to the device (Sec. 3.1). Readings where the paper is silent: first-quadrant
+ * nominal angle 2 pi (a + 1/2)/n_azim, nx = floor(W sin/spacing) + 1, ny = floor(H cos/spacing)
+ * + 1, corrected angle atan(H nx / (W ny)), ray starts at (i + 1/2) W/nx and (j + 1/2) H/ny;
+ * pieces shorter than 1e-12 cm are dropped; a ray leaving a non-rectangular mesh and
+ * re-entering it starts a new track with vacuum inflow.
+ * Errors: MOC_ERR_STATE (no mesh/quadrature), MOC_ERR_GEOMETRY, MOC_ERR_OOM, MOC_ERR_CUDA. */
+int moc_generate_tracks(moc_ctx *ctx);
+
+/* Number of tracks and segments after moc_generate_tracks(). */
+int moc_get_track_counts(const moc_ctx *ctx, int64_t *n_tracks, int64_t *n_segments);
+
+/* Copy out the tracks (for inspection and tests). Track order: direction index j = 0 ..
+ * n_azim/2 - 1 (angles in [0, pi) ascending), for each the rays starting on the bottom edge
+ * (left to right) then on the side edge (bottom to top), each ray's tracks in order along it.
+ * seg_off: [T+1]; seg_region: [S]; seg_len: [S] (cm, 2D length); track_dir: [T];
+ * track_xy: [T][4] start x, y, end x, y; link: [T][2] for each track end (0: forward sweep's
+ * outgoing end at the track end, 1: backward sweep's at the start) the incoming end it feeds,
+ * encoded 2 t' + d', or -1 for vacuum. Any output pointer may be NULL. */
+int moc_get_tracks(const moc_ctx *ctx, int64_t *seg_off, int32_t *seg_region, double *seg_len,
+                   int32_t *track_dir, double *track_xy, int64_t *link);
+
+/* Quadrature after track generation: per direction j < n_azim/2 the corrected angle, the
+ * effective spacing and the azimuthal weight (weights of the 2 pi set sum to 1). */
+int moc_get_quadrature(const moc_ctx *ctx, double *phi, double *delta, double *omega);
+
+/* Tracked region areas [n_tri]: A_i = sum over the 2 pi set of omega_a delta_a (length in i). */
+int moc_get_region_areas(const moc_ctx *ctx, double *area);
+
+/* Multigroup cross sections per material (Eq. MGNTE): sigma_t, nu_sigma_f, chi: [n_mat][G];
+ * sigma_s: [n_mat][G_from][G_to] isotropic (P0) scattering. Requires sigma_t > 0, all data
+ * finite and >= 0, and every mesh material id < n_mat. Resets the state to phi = 1, k = 1,
+ * zero boundary flux, eigenvalue mode. Errors: MOC_ERR_ARG, MOC_ERR_STATE, MOC_ERR_OOM. */
+int moc_set_xs(moc_ctx *ctx, int n_mat, int G, const double *sigma_t, const double *nu_sigma_f,
+               const double *chi, const double *sigma_s);
+
+/* Fixed isotropic volumetric source S: [n_tri][G] (n/cm^3/s), switching the context to
+ * fixed-source mode (fission ignored, no normalisation); NULL returns to eigenvalue mode. */
+int moc_set_fixed_source(moc_ctx *ctx, const double *S);
+
+/* Set the iterate: phi [n_tri][G] (NULL: all ones), k, psi_bnd [T][2][n_polar][G] incoming
+ * angular flux per track end (NULL: zero). In eigenvalue mode the state is normalised so that
+ * sum_i A_i sum_g nuSigma_f phi = 1 before the next outer. */
+int moc_set_state(moc_ctx *ctx, const double *phi, double k, const double *psi_bnd);
+
+/* Read the iterate (normalised in eigenvalue mode). Any output may be NULL. Synchronises. */
+int moc_get_state(moc_ctx *ctx, double *phi, double *k, double *psi_bnd);
+
+/* Enqueue the source update of Eq. (MGNTE_element) from the current (phi, k). Asynchronous. */
+int moc_update_source(moc_ctx *ctx);
+
+/* Enqueue one transport sweep (Eq. MOC_sol over every track, both directions, every polar
+ * angle and group, tallies, boundary-flux links), the flux finalisation and the FP64 fission /
+ * residual reductions, using the source from the last moc_update_source(). Asynchronous. */
+int moc_sweep(moc_ctx *ctx);
+
+/* Enqueue n outer iterations (source update + sweep each). Asynchronous; k_out and resid_out
+ * (may be NULL) are read back with a synchronisation after the last outer. */
+int moc_outer(moc_ctx *ctx, int n, double *k_out, double *resid_out);
+
+/* Iterate until |k' - k| <= tol_k and the L-inf relative fission-source change <= tol_flux
+ * (fixed-source mode: the relative flux change <= tol_flux), or max_outer outers. Convergence
+ * is checked on the host every `check_every` outers (the outers in between run as one CUDA
+ * graph launch). Returns MOC_ERR_NOT_CONVERGED if max_outer is reached, MOC_ERR_NONFINITE if
+ * k or the residual is not finite. */
+int moc_power_iterate(moc_ctx *ctx, double tol_k, double tol_flux, int max_outer,
+                      int check_every, double *k_out, int *n_outer_out, double *resid_out);
+
+/* Timing of the sweep kernel, measured with CUDA events on the context's stream when enabled:
+ * enable != 0 starts recording (and resets the totals); the getter returns the summed sweep
+ * kernel time (ms) and the number of timed sweeps since. */
+int moc_enable_timing(moc_ctx *ctx, int enable);
+int moc_get_timing(moc_ctx *ctx, double *sweep_ms_total, int64_t *n_sweeps);
+
+/* Work counters: segments S, updates per sweep 2 S P G, and the number of kernels one outer
+ * launches. */
+int moc_get_work(const moc_ctx *ctx, int64_t *n_segments, int64_t *updates_per_sweep,
+                 int *kernels_per_outer);
+
+/* Evaluate the library's FP32 1 - exp(-tau) (the one the FP32 sweep uses) for n host values
+ * tau[i] >= 0 into out[i], on device `device`. Host buffers; synchronous. For checking the
+ * approximation error against an FP64 reference. Errors: MOC_ERR_ARG, MOC_ERR_CUDA. */
+int moc_eval_one_minus_exp_f32(int device, const float *tau, float *out, int64_t n);
+
+/* Wait for all work enqueued on the context's stream. */
+int moc_synchronize(moc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MOC_GB300_H */

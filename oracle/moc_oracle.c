@@ -485,6 +485,12 @@ void orc_set_state(orc_t *h, const double *phi, double k, const double *psi) {
   size_t RG = (size_t)h->n_tri * h->G, PB = (size_t)h->n_tracks * 2 * h->n_polar * h->G;
   if (phi) memcpy(h->phi, phi, RG * sizeof(double)); else for (size_t i = 0; i < RG; ++i) h->phi[i] = 1.0;
   if (psi) memcpy(h->psi_in, psi, PB * sizeof(double)); else memset(h->psi_in, 0, PB * sizeof(double));
+  /* vacuum boundary: an incoming end that no outgoing end feeds has zero inflow */
+  char *fed = xcalloc(2 * h->n_tracks, 1);
+  for (int64_t e = 0; e < 2 * h->n_tracks; ++e) if (h->link[e] >= 0) fed[h->link[e]] = 1;
+  size_t per = (size_t)h->n_polar * h->G;
+  for (int64_t e = 0; e < 2 * h->n_tracks; ++e) if (!fed[e]) memset(h->psi_in + e * per, 0, per * sizeof(double));
+  free(fed);
   h->k = k;
 }
 

@@ -1,0 +1,804 @@
+// C ABI of the GB300 MOC library: context, uploads, the outer-iteration driver and CUDA graphs.
+// See include/moc_gb300.h for the contract of every entry point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "moc_gb300.h"
+#include "moc_geom.h"
+#include "moc_kernels.cuh"
+
+using namespace moc;
+
+struct moc_ctx {
+  int device = -1;
+  int precision = MOC_FP64;
+  cudaStream_t stream = nullptr;      // all work is enqueued here
+  bool own_stream = false;
+  cudaStream_t cap_stream = nullptr;  // graphs are captured here (never the legacy stream)
+  std::string err;
+  Geometry geo;
+  // problem sizes
+  int G = 0, Gp = 0, P = 0, M = 0;
+  int64_t T = 0, S = 0;
+  std::vector<int64_t> perm;  // internal track -> external track
+  std::vector<int64_t> inv;   // external -> internal
+  // device data
+  void *d_seg = nullptr;
+  TrackRec *d_trk = nullptr;
+  int32_t *d_link = nullptr;
+  void *d_wgt = nullptr, *d_inv_sin = nullptr;
+  int32_t *d_mat = nullptr;
+  double *d_area = nullptr;
+  void *d_sig_t = nullptr, *d_nsf = nullptr, *d_chi = nullptr, *d_sig_s = nullptr;
+  void *d_xsq = nullptr, *d_phi = nullptr, *d_tsum = nullptr, *d_tcomp = nullptr;
+  void *d_psi[2] = {nullptr, nullptr};
+  double *d_fold = nullptr, *d_ext = nullptr, *d_part = nullptr, *d_scal = nullptr;
+  int cur = 0;          // psi buffer holding the incoming flux of the next sweep
+  bool eigen = true;
+  bool tracks_on_device = false, xs_set = false;
+  std::vector<double> h_ext;  // host copy of the fixed source (for re-upload)
+  // graphs: [parity of cur at launch]
+  cudaGraphExec_t graph2[2] = {nullptr, nullptr};
+  // timing
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+  double timed_ms = 0.0;
+  int64_t timed_n = 0;
+};
+
+namespace {
+
+size_t rsize(const moc_ctx *c) { return c->precision == MOC_FP64 ? sizeof(double) : sizeof(float); }
+int tally_mode(const moc_ctx *c) { return c->precision == MOC_FP32 ? 1 : 0; }
+
+int fail(moc_ctx *c, int code, const std::string &m) {
+  if (c) c->err = m;
+  return code;
+}
+
+#define CUDA_TRY(c, call)                                                                   \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return fail((c), e_ == cudaErrorMemoryAllocation ? MOC_ERR_OOM : MOC_ERR_CUDA,        \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                      \
+  } while (0)
+
+void dfree(void *&p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+template <typename T> void dfree(T *&p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+void drop_graphs(moc_ctx *c) {
+  for (auto &g : c->graph2)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+void free_problem(moc_ctx *c) {
+  drop_graphs(c);
+  dfree(c->d_xsq);
+  dfree(c->d_phi);
+  dfree(c->d_tsum);
+  dfree(c->d_tcomp);
+  dfree(c->d_psi[0]);
+  dfree(c->d_psi[1]);
+  dfree(c->d_fold);
+  dfree(c->d_ext);
+  dfree(c->d_part);
+  dfree(c->d_sig_t);
+  dfree(c->d_nsf);
+  dfree(c->d_chi);
+  dfree(c->d_sig_s);
+  c->xs_set = false;
+}
+
+void free_tracks(moc_ctx *c) {
+  free_problem(c);
+  dfree(c->d_seg);
+  dfree(c->d_trk);
+  dfree(c->d_link);
+  dfree(c->d_wgt);
+  dfree(c->d_inv_sin);
+  dfree(c->d_mat);
+  dfree(c->d_area);
+  c->tracks_on_device = false;
+}
+
+int need_gpu(moc_ctx *c) {
+  if (!c) return MOC_ERR_ARG;
+  if (c->device < 0) return fail(c, MOC_ERR_STATE, "host-only context: no GPU work possible");
+  return MOC_OK;
+}
+
+int need_ready(moc_ctx *c) {
+  int rc = need_gpu(c);
+  if (rc) return rc;
+  if (!c->tracks_on_device) return fail(c, MOC_ERR_STATE, "generate tracks first");
+  if (!c->xs_set) return fail(c, MOC_ERR_STATE, "set cross sections first");
+  return MOC_OK;
+}
+
+template <typename Real> std::vector<Real> to_real(const double *p, size_t n) {
+  std::vector<Real> v(n);
+  for (size_t i = 0; i < n; ++i) v[i] = (Real)p[i];
+  return v;
+}
+
+template <typename T> int upload(moc_ctx *c, T *&dst, const T *src, size_t n) {
+  CUDA_TRY(c, cudaMalloc((void **)&dst, std::max<size_t>(n, 1) * sizeof(T)));
+  if (n) CUDA_TRY(c, cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return MOC_OK;
+}
+
+// Upload tracks in the internal order: tracks sorted by segment count, longest first, so the
+// longest characteristic chains start first and neighbouring threads do similar work.
+template <typename Real> int upload_tracks(moc_ctx *c) {
+  const Geometry &g = c->geo;
+  const int64_t T = g.n_tracks(), S = g.n_segments();
+  c->T = T;
+  c->S = S;
+  c->P = g.n_polar;
+  c->perm.resize(T);
+  std::iota(c->perm.begin(), c->perm.end(), 0);
+  std::stable_sort(c->perm.begin(), c->perm.end(), [&](int64_t a, int64_t b) {
+    return (g.seg_off[a + 1] - g.seg_off[a]) > (g.seg_off[b + 1] - g.seg_off[b]);
+  });
+  c->inv.resize(T);
+  for (int64_t i = 0; i < T; ++i) c->inv[c->perm[i]] = i;
+  std::vector<TrackRec> trk(T);
+  std::vector<SegRec<Real>> seg(S);
+  std::vector<int32_t> link(2 * T);
+  int64_t o = 0;
+  for (int64_t i = 0; i < T; ++i) {
+    int64_t t = c->perm[i];
+    int64_t n = g.seg_off[t + 1] - g.seg_off[t];
+    trk[i].off = o;
+    trk[i].n = (int)n;
+    trk[i].dir = g.track_dir[t];
+    for (int64_t k = 0; k < n; ++k) {
+      SegRec<Real> r{};
+      r.r = g.seg_reg[g.seg_off[t] + k];
+      r.l = (Real)g.seg_len[g.seg_off[t] + k];
+      seg[o + k] = r;
+    }
+    o += n;
+    for (int d = 0; d < 2; ++d) {
+      int64_t e = g.link[2 * t + d];
+      link[2 * i + d] = (e < 0) ? -1 : (int32_t)(2 * c->inv[e >> 1] + (e & 1));
+    }
+  }
+  if (2 * T >= (int64_t)1 << 31) return fail(c, MOC_ERR_ARG, "too many tracks for 32-bit links");
+  std::vector<Real> wgt((size_t)g.n_dir * c->P), inv_sin(c->P);
+  for (int j = 0; j < g.n_dir; ++j)
+    for (int p = 0; p < c->P; ++p)
+      wgt[(size_t)j * c->P + p] = (Real)(kFourPi * g.omega[j] * g.polar_w[p] * g.delta[j] * g.sin_theta[p]);
+  for (int p = 0; p < c->P; ++p) inv_sin[p] = (Real)(1.0 / g.sin_theta[p]);
+  int rc;
+  SegRec<Real> *ds = nullptr;
+  if ((rc = upload(c, ds, seg.data(), seg.size()))) return rc;
+  c->d_seg = ds;
+  if ((rc = upload(c, c->d_trk, trk.data(), trk.size()))) return rc;
+  if ((rc = upload(c, c->d_link, link.data(), link.size()))) return rc;
+  Real *dw = nullptr, *di = nullptr;
+  if ((rc = upload(c, dw, wgt.data(), wgt.size()))) return rc;
+  c->d_wgt = dw;
+  if ((rc = upload(c, di, inv_sin.data(), inv_sin.size()))) return rc;
+  c->d_inv_sin = di;
+  if ((rc = upload(c, c->d_mat, g.mat.data(), g.mat.size()))) return rc;
+  if ((rc = upload(c, c->d_area, g.area.data(), g.area.size()))) return rc;
+  c->tracks_on_device = true;
+  return MOC_OK;
+}
+
+template <typename Real> int upload_xs(moc_ctx *c, int n_mat, int G, const double *st, const double *nsf,
+                                       const double *chi, const double *ss) {
+  const Geometry &g = c->geo;
+  const int R = g.n_tri;
+  c->G = G;
+  c->Gp = (G + 7) & ~7;
+  c->M = n_mat;
+  const int Gp = c->Gp;
+  int rc;
+  auto vst = to_real<Real>(st, (size_t)n_mat * G), vnsf = to_real<Real>(nsf, (size_t)n_mat * G),
+       vchi = to_real<Real>(chi, (size_t)n_mat * G), vss = to_real<Real>(ss, (size_t)n_mat * G * G);
+  Real *p1 = nullptr, *p2 = nullptr, *p3 = nullptr, *p4 = nullptr;
+  if ((rc = upload(c, p1, vst.data(), vst.size()))) return rc;
+  c->d_sig_t = p1;
+  if ((rc = upload(c, p2, vnsf.data(), vnsf.size()))) return rc;
+  c->d_nsf = p2;
+  if ((rc = upload(c, p3, vchi.data(), vchi.size()))) return rc;
+  c->d_chi = p3;
+  if ((rc = upload(c, p4, vss.data(), vss.size()))) return rc;
+  c->d_sig_s = p4;
+  // region pairs {Sigma_t, q/Sigma_t}; padding groups get Sigma_t = 1, q = 0
+  std::vector<typename Pair<Real>::T> xsq((size_t)R * Gp);
+  for (int r = 0; r < R; ++r)
+    for (int k = 0; k < Gp; ++k) {
+      typename Pair<Real>::T v;
+      v.x = (k < G) ? (Real)st[(size_t)g.mat[r] * G + k] : (Real)1;
+      v.y = 0;
+      xsq[(size_t)r * Gp + k] = v;
+    }
+  typename Pair<Real>::T *dx = nullptr;
+  if ((rc = upload(c, dx, xsq.data(), xsq.size()))) return rc;
+  c->d_xsq = dx;
+  const size_t RG = (size_t)R * Gp, PB = (size_t)c->T * 2 * c->P * G;
+  CUDA_TRY(c, cudaMalloc(&c->d_phi, RG * sizeof(Real)));
+  CUDA_TRY(c, cudaMalloc(&c->d_tsum, RG * sizeof(Real)));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_tsum, 0, RG * sizeof(Real), c->stream));
+  if (tally_mode(c) == 1) {
+    CUDA_TRY(c, cudaMalloc(&c->d_tcomp, RG * sizeof(Real)));
+    CUDA_TRY(c, cudaMemsetAsync(c->d_tcomp, 0, RG * sizeof(Real), c->stream));
+  }
+  for (int b = 0; b < 2; ++b) {
+    CUDA_TRY(c, cudaMalloc(&c->d_psi[b], std::max<size_t>(PB, 1) * sizeof(Real)));
+    CUDA_TRY(c, cudaMemsetAsync(c->d_psi[b], 0, std::max<size_t>(PB, 1) * sizeof(Real), c->stream));
+  }
+  CUDA_TRY(c, cudaMalloc(&c->d_fold, (size_t)R * sizeof(double)));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_fold, 0, (size_t)R * sizeof(double), c->stream));
+  const int nb = (R + 255) / 256;
+  CUDA_TRY(c, cudaMalloc(&c->d_part, (size_t)nb * 4 * sizeof(double)));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->xs_set = true;
+  return MOC_OK;
+}
+
+// state upload: phi [R][G] (NULL: ones) and psi [T][2][P][G] in external track order (NULL: 0)
+template <typename Real> int upload_state(moc_ctx *c, const double *phi, const double *psi) {
+  const int R = c->geo.n_tri, G = c->G, Gp = c->Gp, P = c->P;
+  std::vector<Real> hp((size_t)R * Gp, (Real)0);
+  for (int r = 0; r < R; ++r)
+    for (int g = 0; g < G; ++g) hp[(size_t)r * Gp + g] = (Real)(phi ? phi[(size_t)r * G + g] : 1.0);
+  const size_t per = (size_t)2 * P * G;
+  std::vector<Real> hpsi((size_t)c->T * per, (Real)0);
+  if (psi) {
+    // vacuum boundary: incoming ends that no outgoing end feeds keep zero inflow
+    std::vector<char> fed(2 * (size_t)c->T, 0);
+    for (int64_t e : c->geo.link)
+      if (e >= 0) fed[e] = 1;
+    const size_t half = per / 2;
+    for (int64_t t = 0; t < c->T; ++t)
+      for (int d = 0; d < 2; ++d) {
+        if (!fed[2 * t + d]) continue;
+        for (size_t q = 0; q < half; ++q)
+          hpsi[(size_t)c->inv[t] * per + d * half + q] = (Real)psi[(size_t)t * per + d * half + q];
+      }
+  }
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_phi, hp.data(), hp.size() * sizeof(Real), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_psi[c->cur], hpsi.data(), hpsi.size() * sizeof(Real), cudaMemcpyHostToDevice,
+                              c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return MOC_OK;
+}
+
+// ---------------------------------------------------------------------------------- launches
+template <typename Real> int launch_source(moc_ctx *c, cudaStream_t st) {
+  const int R = c->geo.n_tri;
+  size_t sm = (size_t)c->M * c->G * c->G * sizeof(Real);
+  if (sm > 48 * 1024) return fail(c, MOC_ERR_ARG, "scattering tables too large for shared memory (n_mat*G*G)");
+  source_kernel<Real><<<(R + 127) / 128, 128, sm, st>>>(
+      R, c->G, c->Gp, c->M, c->d_mat, (const Real *)c->d_sig_t, (const Real *)c->d_nsf, (const Real *)c->d_chi,
+      (const Real *)c->d_sig_s, c->d_ext, (Real *)c->d_phi, (typename Pair<Real>::T *)c->d_xsq, c->d_fold, c->d_scal,
+      c->eigen ? 1 : 0);
+  CUDA_TRY(c, cudaGetLastError());
+  return MOC_OK;
+}
+
+template <typename Real, int P, int TM> void sweep_launch(moc_ctx *c, cudaStream_t st) {
+  const long long n = (long long)c->T * 2 * c->G;
+  const int bs = 256;
+  const long long nb = (n + bs - 1) / bs;
+  sweep_kernel<Real, P, TM><<<(unsigned)nb, bs, 0, st>>>(
+      c->d_trk, (const SegRec<Real> *)c->d_seg, c->d_link, (const Real *)c->d_wgt, (const Real *)c->d_inv_sin,
+      (const typename Pair<Real>::T *)c->d_xsq, (Real *)c->d_tsum, (Real *)c->d_tcomp,
+      (const Real *)c->d_psi[c->cur], (Real *)c->d_psi[c->cur ^ 1], c->d_scal, n, c->G, c->Gp);
+}
+
+template <typename Real, int TM> int launch_sweep_p(moc_ctx *c, cudaStream_t st) {
+  switch (c->P) {
+    case 1: sweep_launch<Real, 1, TM>(c, st); break;
+    case 2: sweep_launch<Real, 2, TM>(c, st); break;
+    case 3: sweep_launch<Real, 3, TM>(c, st); break;
+    case 4: sweep_launch<Real, 4, TM>(c, st); break;
+    case 5: sweep_launch<Real, 5, TM>(c, st); break;
+    case 6: sweep_launch<Real, 6, TM>(c, st); break;
+    default: return fail(c, MOC_ERR_ARG, "unsupported polar count");
+  }
+  CUDA_TRY(c, cudaGetLastError());
+  return MOC_OK;
+}
+
+int launch_sweep(moc_ctx *c, cudaStream_t st) {
+  if (c->precision == MOC_FP64) return launch_sweep_p<double, 0>(c, st);
+  if (c->precision == MOC_FP32) return launch_sweep_p<float, 1>(c, st);
+  return launch_sweep_p<float, 0>(c, st);
+}
+
+template <typename Real> int launch_finalize_reduce(moc_ctx *c, cudaStream_t st) {
+  const int R = c->geo.n_tri;
+  const int nb = (R + 255) / 256;
+  if (tally_mode(c) == 1)
+    finalize_kernel<Real, 1><<<nb, 256, 0, st>>>(R, c->G, c->Gp, c->d_mat, (const Real *)c->d_nsf, c->d_area,
+                                                 (const typename Pair<Real>::T *)c->d_xsq, (Real *)c->d_tsum,
+                                                 (Real *)c->d_tcomp, (Real *)c->d_phi, c->d_fold, c->d_part,
+                                                 c->eigen ? 1 : 0);
+  else
+    finalize_kernel<Real, 0><<<nb, 256, 0, st>>>(R, c->G, c->Gp, c->d_mat, (const Real *)c->d_nsf, c->d_area,
+                                                 (const typename Pair<Real>::T *)c->d_xsq, (Real *)c->d_tsum,
+                                                 (Real *)c->d_tcomp, (Real *)c->d_phi, c->d_fold, c->d_part,
+                                                 c->eigen ? 1 : 0);
+  CUDA_TRY(c, cudaGetLastError());
+  reduce_kernel<<<1, 256, 0, st>>>(nb, c->d_part, c->d_scal, c->eigen ? 1 : 0);
+  CUDA_TRY(c, cudaGetLastError());
+  return MOC_OK;
+}
+
+int enqueue_source(moc_ctx *c, cudaStream_t st) {
+  return c->precision == MOC_FP64 ? launch_source<double>(c, st) : launch_source<float>(c, st);
+}
+
+// sweep + finalize + reduce; flips the boundary-flux buffer
+int enqueue_sweep(moc_ctx *c, cudaStream_t st, bool timed) {
+  int rc;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (timed) {
+    CUDA_TRY(c, cudaEventCreate(&e0));
+    CUDA_TRY(c, cudaEventCreate(&e1));
+    CUDA_TRY(c, cudaEventRecord(e0, st));
+  }
+  if ((rc = launch_sweep(c, st))) return rc;
+  if (timed) {
+    CUDA_TRY(c, cudaEventRecord(e1, st));
+    c->ev.push_back({e0, e1});
+  }
+  rc = c->precision == MOC_FP64 ? launch_finalize_reduce<double>(c, st) : launch_finalize_reduce<float>(c, st);
+  if (rc) return rc;
+  c->cur ^= 1;
+  return MOC_OK;
+}
+
+int enqueue_outer(moc_ctx *c, cudaStream_t st, bool timed) {
+  int rc = enqueue_source(c, st);
+  if (rc) return rc;
+  return enqueue_sweep(c, st, timed);
+}
+
+// Graph of two outers (the boundary-flux buffers swap twice, so the graph for a given starting
+// buffer can be relaunched any number of times).
+int get_graph(moc_ctx *c, cudaGraphExec_t &out) {
+  cudaGraphExec_t &ge = c->graph2[c->cur];
+  if (!ge) {
+    const int cur0 = c->cur;
+    CUDA_TRY(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_outer(c, c->cap_stream, false);
+    if (!rc) rc = enqueue_outer(c, c->cap_stream, false);
+    cudaGraph_t gr = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &gr);
+    c->cur = cur0;
+    if (rc) {
+      if (gr) cudaGraphDestroy(gr);
+      return rc;
+    }
+    if (e != cudaSuccess) return fail(c, MOC_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&ge, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) {
+      ge = nullptr;
+      return fail(c, MOC_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+  }
+  out = ge;
+  return MOC_OK;
+}
+
+int run_outers(moc_ctx *c, int n) {
+  int rc;
+  if (c->timing) {
+    for (int i = 0; i < n; ++i)
+      if ((rc = enqueue_outer(c, c->stream, true))) return rc;
+    return MOC_OK;
+  }
+  int pairs = n / 2;
+  for (int i = 0; i < pairs; ++i) {
+    cudaGraphExec_t ge;
+    if ((rc = get_graph(c, ge))) return rc;
+    CUDA_TRY(c, cudaGraphLaunch(ge, c->stream));
+    // two outers: the buffer parity is unchanged
+  }
+  if (n % 2)
+    if ((rc = enqueue_outer(c, c->stream, false))) return rc;
+  return MOC_OK;
+}
+
+int read_scalars(moc_ctx *c, double *s) {
+  CUDA_TRY(c, cudaMemcpyAsync(s, c->d_scal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return MOC_OK;
+}
+
+int reset_scalars(moc_ctx *c, double k, double scale) {
+  double s[S_COUNT] = {0};
+  s[S_K] = k;
+  s[S_KPREV] = k;
+  s[S_SCALE] = scale;
+  s[S_RESID] = INFINITY;
+  s[S_FISS] = 1.0 / scale;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_scal, s, sizeof s, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return MOC_OK;
+}
+
+// F = sum_i A_i sum_g nuSigma_f phi on the host (used to normalise a state set by the caller)
+double host_fission(const moc_ctx *c, const double *phi, const std::vector<double> &nsf) {
+  const Geometry &g = c->geo;
+  double F = 0.0;
+  for (int r = 0; r < g.n_tri; ++r) {
+    double f = 0.0;
+    for (int k = 0; k < c->G; ++k) f += nsf[(size_t)g.mat[r] * c->G + k] * (phi ? phi[(size_t)r * c->G + k] : 1.0);
+    F += g.area[r] * f;
+  }
+  return F;
+}
+
+}  // namespace
+
+// ====================================================================================== C ABI
+extern "C" {
+
+int moc_create(moc_ctx **out, int device, int precision, void *stream) {
+  if (!out) return MOC_ERR_ARG;
+  *out = nullptr;
+  if (precision != MOC_FP64 && precision != MOC_FP32 && precision != MOC_FP32_PLAIN) return MOC_ERR_ARG;
+  moc_ctx *c = new (std::nothrow) moc_ctx;
+  if (!c) return MOC_ERR_OOM;
+  c->device = device;
+  c->precision = precision;
+  if (device >= 0) {
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) {
+      if (stream) {
+        c->stream = (cudaStream_t)stream;
+      } else {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        c->own_stream = (e == cudaSuccess);
+      }
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_scal, S_COUNT * sizeof(double));
+    if (e != cudaSuccess) {
+      moc_destroy(c);
+      return MOC_ERR_CUDA;
+    }
+  }
+  *out = c;
+  return MOC_OK;
+}
+
+void moc_destroy(moc_ctx *c) {
+  if (!c) return;
+  if (c->device >= 0) {
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto &p : c->ev) {
+      cudaEventDestroy(p.first);
+      cudaEventDestroy(p.second);
+    }
+    free_tracks(c);
+    dfree(c->d_scal);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  }
+  delete c;
+}
+
+const char *moc_last_error(const moc_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+int moc_set_mesh(moc_ctx *c, int n_vert, const double *xy, int n_tri, const int32_t *tri, const int32_t *mat,
+                 const double *bbox, const int32_t *bc) {
+  if (!c) return MOC_ERR_ARG;
+  int rc = set_mesh(c->geo, n_vert, xy, n_tri, tri, mat, bbox, bc, c->err);
+  if (rc) return rc;
+  if (c->device >= 0) free_tracks(c);
+  return MOC_OK;
+}
+
+int moc_set_quadrature(moc_ctx *c, int n_azim, double spacing, int n_polar, const double *sin_theta,
+                       const double *polar_w) {
+  if (!c) return MOC_ERR_ARG;
+  int rc = set_quadrature(c->geo, n_azim, spacing, n_polar, sin_theta, polar_w, c->err);
+  if (rc) return rc;
+  if (c->device >= 0) free_tracks(c);
+  return MOC_OK;
+}
+
+int moc_generate_tracks(moc_ctx *c) {
+  if (!c) return MOC_ERR_ARG;
+  if (c->device >= 0) {
+    cudaSetDevice(c->device);
+    free_tracks(c);
+  }
+  int rc = generate_tracks(c->geo, c->err);
+  if (rc) return rc;
+  if (c->device < 0) return MOC_OK;
+  return c->precision == MOC_FP64 ? upload_tracks<double>(c) : upload_tracks<float>(c);
+}
+
+int moc_get_track_counts(const moc_ctx *c, int64_t *n_tracks, int64_t *n_segments) {
+  if (!c || !c->geo.has_tracks) return c ? MOC_ERR_STATE : MOC_ERR_ARG;
+  if (n_tracks) *n_tracks = c->geo.n_tracks();
+  if (n_segments) *n_segments = c->geo.n_segments();
+  return MOC_OK;
+}
+
+int moc_get_tracks(const moc_ctx *c, int64_t *seg_off, int32_t *seg_region, double *seg_len, int32_t *track_dir,
+                   double *track_xy, int64_t *link) {
+  if (!c || !c->geo.has_tracks) return c ? MOC_ERR_STATE : MOC_ERR_ARG;
+  const Geometry &g = c->geo;
+  if (seg_off) std::copy(g.seg_off.begin(), g.seg_off.end(), seg_off);
+  if (seg_region) std::copy(g.seg_reg.begin(), g.seg_reg.end(), seg_region);
+  if (seg_len) std::copy(g.seg_len.begin(), g.seg_len.end(), seg_len);
+  if (track_dir) std::copy(g.track_dir.begin(), g.track_dir.end(), track_dir);
+  if (track_xy) std::copy(g.track_xy.begin(), g.track_xy.end(), track_xy);
+  if (link) std::copy(g.link.begin(), g.link.end(), link);
+  return MOC_OK;
+}
+
+int moc_get_quadrature(const moc_ctx *c, double *phi, double *delta, double *omega) {
+  if (!c || !c->geo.has_tracks) return c ? MOC_ERR_STATE : MOC_ERR_ARG;
+  const Geometry &g = c->geo;
+  if (phi) std::copy(g.phi.begin(), g.phi.end(), phi);
+  if (delta) std::copy(g.delta.begin(), g.delta.end(), delta);
+  if (omega) std::copy(g.omega.begin(), g.omega.end(), omega);
+  return MOC_OK;
+}
+
+int moc_get_region_areas(const moc_ctx *c, double *area) {
+  if (!c || !c->geo.has_tracks || !area) return (!c || !area) ? MOC_ERR_ARG : MOC_ERR_STATE;
+  std::copy(c->geo.area.begin(), c->geo.area.end(), area);
+  return MOC_OK;
+}
+
+int moc_set_xs(moc_ctx *c, int n_mat, int G, const double *st, const double *nsf, const double *chi,
+               const double *ss) {
+  int rc = need_gpu(c);
+  if (rc) return rc;
+  if (!c->tracks_on_device) return fail(c, MOC_ERR_STATE, "set_xs: generate tracks first");
+  if (n_mat < 1 || G < 1 || G > 1024 || !st || !nsf || !chi || !ss) return fail(c, MOC_ERR_ARG, "set_xs: bad sizes");
+  for (int m : c->geo.mat)
+    if (m >= n_mat) return fail(c, MOC_ERR_ARG, "set_xs: a mesh material id is >= n_mat");
+  for (size_t i = 0; i < (size_t)n_mat * G; ++i) {
+    if (!(st[i] > 0.0) || !std::isfinite(st[i])) return fail(c, MOC_ERR_ARG, "set_xs: sigma_t must be finite and > 0");
+    if (!(nsf[i] >= 0.0) || !std::isfinite(nsf[i]) || !(chi[i] >= 0.0) || !std::isfinite(chi[i]))
+      return fail(c, MOC_ERR_ARG, "set_xs: nu_sigma_f and chi must be finite and >= 0");
+  }
+  for (size_t i = 0; i < (size_t)n_mat * G * G; ++i)
+    if (!(ss[i] >= 0.0) || !std::isfinite(ss[i])) return fail(c, MOC_ERR_ARG, "set_xs: sigma_s must be finite and >= 0");
+  cudaSetDevice(c->device);
+  free_problem(c);
+  c->h_ext.clear();
+  c->eigen = true;
+  c->cur = 0;
+  rc = c->precision == MOC_FP64 ? upload_xs<double>(c, n_mat, G, st, nsf, chi, ss)
+                                : upload_xs<float>(c, n_mat, G, st, nsf, chi, ss);
+  if (rc) return rc;
+  return moc_set_state(c, nullptr, 1.0, nullptr);
+}
+
+int moc_set_fixed_source(moc_ctx *c, const double *S) {
+  int rc = need_ready(c);
+  if (rc) return rc;
+  dfree(c->d_ext);
+  drop_graphs(c);
+  const size_t RG = (size_t)c->geo.n_tri * c->G;
+  if (!S) {
+    c->eigen = true;
+    return moc_set_state(c, nullptr, 1.0, nullptr);
+  }
+  for (size_t i = 0; i < RG; ++i)
+    if (!(S[i] >= 0.0) || !std::isfinite(S[i])) return fail(c, MOC_ERR_ARG, "set_fixed_source: S must be finite and >= 0");
+  if ((rc = upload(c, c->d_ext, S, RG))) return rc;
+  c->eigen = false;
+  return moc_set_state(c, nullptr, 1.0, nullptr);
+}
+
+int moc_set_state(moc_ctx *c, const double *phi, double k, const double *psi) {
+  int rc = need_ready(c);
+  if (rc) return rc;
+  if (!(k > 0.0) || !std::isfinite(k)) return fail(c, MOC_ERR_ARG, "set_state: k must be finite and > 0");
+  cudaSetDevice(c->device);
+  rc = c->precision == MOC_FP64 ? upload_state<double>(c, phi, psi) : upload_state<float>(c, phi, psi);
+  if (rc) return rc;
+  double scale = 1.0;
+  if (c->eigen) {
+    std::vector<double> nsf((size_t)c->M * c->G);
+    std::vector<unsigned char> tmp(nsf.size() * rsize(c));
+    CUDA_TRY(c, cudaMemcpy(tmp.data(), c->d_nsf, tmp.size(), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < nsf.size(); ++i)
+      nsf[i] = c->precision == MOC_FP64 ? ((double *)tmp.data())[i] : (double)((float *)tmp.data())[i];
+    double F = host_fission(c, phi, nsf);
+    if (!std::isfinite(F)) return fail(c, MOC_ERR_ARG, "set_state: the fission source of the state is not finite");
+    if (F > 0.0) scale = 1.0 / F;   // no fission at all: power iteration will report MOC_ERR_NONFINITE
+  }
+  return reset_scalars(c, k, scale);
+}
+
+int moc_get_state(moc_ctx *c, double *phi, double *k, double *psi) {
+  int rc = need_ready(c);
+  if (rc) return rc;
+  cudaSetDevice(c->device);
+  double s[S_COUNT];
+  if ((rc = read_scalars(c, s))) return rc;
+  const double scale = c->eigen ? s[S_SCALE] : 1.0;
+  const int R = c->geo.n_tri, G = c->G, Gp = c->Gp, P = c->P;
+  const size_t rs = rsize(c);
+  if (phi) {
+    std::vector<unsigned char> tmp((size_t)R * Gp * rs);
+    CUDA_TRY(c, cudaMemcpyAsync(tmp.data(), c->d_phi, tmp.size(), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    for (int r = 0; r < R; ++r)
+      for (int g = 0; g < G; ++g) {
+        size_t a = (size_t)r * Gp + g;
+        double v = c->precision == MOC_FP64 ? ((double *)tmp.data())[a] : (double)((float *)tmp.data())[a];
+        phi[(size_t)r * G + g] = v * scale;
+      }
+  }
+  if (k) *k = s[S_K];
+  if (psi) {
+    const size_t per = (size_t)2 * P * G;
+    std::vector<unsigned char> tmp((size_t)c->T * per * rs);
+    CUDA_TRY(c, cudaMemcpyAsync(tmp.data(), c->d_psi[c->cur], tmp.size(), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    for (int64_t t = 0; t < c->T; ++t) {
+      int64_t i = c->inv[t];
+      for (size_t q = 0; q < per; ++q) {
+        size_t a = (size_t)i * per + q;
+        double v = c->precision == MOC_FP64 ? ((double *)tmp.data())[a] : (double)((float *)tmp.data())[a];
+        psi[(size_t)t * per + q] = v * scale;
+      }
+    }
+  }
+  return MOC_OK;
+}
+
+int moc_update_source(moc_ctx *c) {
+  int rc = need_ready(c);
+  if (rc) return rc;
+  cudaSetDevice(c->device);
+  return enqueue_source(c, c->stream);
+}
+
+int moc_sweep(moc_ctx *c) {
+  int rc = need_ready(c);
+  if (rc) return rc;
+  cudaSetDevice(c->device);
+  return enqueue_sweep(c, c->stream, c->timing);
+}
+
+int moc_outer(moc_ctx *c, int n, double *k_out, double *resid_out) {
+  int rc = need_ready(c);
+  if (rc) return rc;
+  if (n < 0) return fail(c, MOC_ERR_ARG, "outer: n < 0");
+  cudaSetDevice(c->device);
+  if ((rc = run_outers(c, n))) return rc;
+  if (k_out || resid_out) {
+    double s[S_COUNT];
+    if ((rc = read_scalars(c, s))) return rc;
+    if (k_out) *k_out = s[S_K];
+    if (resid_out) *resid_out = s[S_RESID];
+    if (s[S_STATUS] != 0.0) return fail(c, MOC_ERR_NONFINITE, "outer: k or the residual is not finite");
+  }
+  return MOC_OK;
+}
+
+int moc_power_iterate(moc_ctx *c, double tol_k, double tol_flux, int max_outer, int check_every, double *k_out,
+                      int *n_outer_out, double *resid_out) {
+  int rc = need_ready(c);
+  if (rc) return rc;
+  if (max_outer < 1 || check_every < 1 || !(tol_flux >= 0.0)) return fail(c, MOC_ERR_ARG, "power_iterate: bad arguments");
+  cudaSetDevice(c->device);
+  int n = 0;
+  double s[S_COUNT] = {0};
+  bool conv = false;
+  while (n < max_outer) {
+    int m = std::min(check_every, max_outer - n);
+    // each reduce kernel keeps the k before its outer, so after m outers S_KPREV is the k
+    // before the last one
+    if ((rc = run_outers(c, m))) return rc;
+    n += m;
+    if ((rc = read_scalars(c, s))) return rc;
+    if (s[S_STATUS] != 0.0) return fail(c, MOC_ERR_NONFINITE, "power_iterate: k or the residual is not finite");
+    bool ok_k = !c->eigen || std::fabs(s[S_K] - s[S_KPREV]) <= tol_k;
+    if (ok_k && s[S_RESID] <= tol_flux) {
+      conv = true;
+      break;
+    }
+  }
+  if (k_out) *k_out = s[S_K];
+  if (n_outer_out) *n_outer_out = n;
+  if (resid_out) *resid_out = s[S_RESID];
+  return conv ? MOC_OK : fail(c, MOC_ERR_NOT_CONVERGED, "power_iterate: max_outer reached");
+}
+
+int moc_enable_timing(moc_ctx *c, int enable) {
+  int rc = need_gpu(c);
+  if (rc) return rc;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  for (auto &p : c->ev) {
+    cudaEventDestroy(p.first);
+    cudaEventDestroy(p.second);
+  }
+  c->ev.clear();
+  c->timed_ms = 0.0;
+  c->timed_n = 0;
+  c->timing = enable != 0;
+  return MOC_OK;
+}
+
+int moc_get_timing(moc_ctx *c, double *ms, int64_t *n) {
+  int rc = need_gpu(c);
+  if (rc) return rc;
+  cudaSetDevice(c->device);
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  for (auto &p : c->ev) {
+    float t = 0.f;
+    CUDA_TRY(c, cudaEventElapsedTime(&t, p.first, p.second));
+    c->timed_ms += t;
+    c->timed_n += 1;
+    cudaEventDestroy(p.first);
+    cudaEventDestroy(p.second);
+  }
+  c->ev.clear();
+  if (ms) *ms = c->timed_ms;
+  if (n) *n = c->timed_n;
+  return MOC_OK;
+}
+
+int moc_get_work(const moc_ctx *c, int64_t *n_segments, int64_t *updates, int *kernels) {
+  if (!c || !c->geo.has_tracks) return c ? MOC_ERR_STATE : MOC_ERR_ARG;
+  if (n_segments) *n_segments = c->geo.n_segments();
+  if (updates) *updates = 2 * c->geo.n_segments() * (int64_t)c->geo.n_polar * (int64_t)std::max(c->G, 0);
+  if (kernels) *kernels = 4;
+  return MOC_OK;
+}
+
+int moc_eval_one_minus_exp_f32(int device, const float *tau, float *out, int64_t n) {
+  if (device < 0 || n < 0 || (n > 0 && (!tau || !out))) return MOC_ERR_ARG;
+  if (n == 0) return MOC_OK;
+  if (cudaSetDevice(device) != cudaSuccess) return MOC_ERR_CUDA;
+  float *d = nullptr;
+  if (cudaMalloc(&d, 2 * (size_t)n * sizeof(float)) != cudaSuccess) return MOC_ERR_OOM;
+  cudaError_t e = cudaMemcpy(d, tau, (size_t)n * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    eval_exp_kernel<<<(unsigned)((n + 255) / 256), 256>>>(d, d + n, n);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(out, d + n, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  return e == cudaSuccess ? MOC_OK : MOC_ERR_CUDA;
+}
+
+int moc_synchronize(moc_ctx *c) {
+  int rc = need_gpu(c);
+  if (rc) return rc;
+  cudaSetDevice(c->device);
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return MOC_OK;
+}
+
+}  // extern "C"

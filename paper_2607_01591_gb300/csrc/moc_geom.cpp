@@ -1,0 +1,491 @@
+// Host-side geometry: half-edge mesh, cyclic modular rays over the bounding box, ray-mesh
+// intersection by half-edge walk, reflective links and tracked areas (Sec. 3.1 of the paper:
+// "HEDS" traversal, modular rays for the bounding box of the whole domain, segment data
+// computed once before the sweep).
+#include "moc_geom.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+
+#include "moc_gb300.h"
+
+namespace moc {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kSliver = 1e-12;     // pieces shorter than this (cm) are dropped
+constexpr double kVertexEps = 1e-12;  // an exit this close (cm) to a vertex crosses the vertex
+constexpr double kEventEps = 1e-9;    // entry events closer than this along a ray coincide
+
+inline double cross(double ax, double ay, double bx, double by) { return ax * by - ay * bx; }
+
+// Interval of the line p0 + s u inside CCW triangle t (Cyrus-Beck half-planes). A line running
+// exactly along an edge belongs to the triangle on its left. Returns false if empty.
+bool clip(const Geometry &g, int t, const double *p0, const double *u, double &lo, double &hi) {
+  lo = -INFINITY;
+  hi = INFINITY;
+  for (int k = 0; k < 3; ++k) {
+    const double *a = &g.xy[2 * (size_t)g.tri[3 * (size_t)t + k]];
+    const double *b = &g.xy[2 * (size_t)g.tri[3 * (size_t)t + (k + 1) % 3]];
+    double nx = -(b[1] - a[1]), ny = b[0] - a[0];  // inward normal of a CCW edge
+    double f0 = nx * (p0[0] - a[0]) + ny * (p0[1] - a[1]);
+    double fu = nx * u[0] + ny * u[1];
+    if (fu == 0.0) {
+      if (f0 < 0.0) return false;
+      if (f0 == 0.0 && (nx * (-u[1]) + ny * u[0]) <= 0.0) return false;
+      continue;
+    }
+    double s = -f0 / fu;
+    if (fu > 0.0) lo = std::max(lo, s);
+    else hi = std::min(hi, s);
+  }
+  return hi > lo;
+}
+
+struct Event {
+  double s;
+  int32_t he;   // boundary half-edge
+  double t;     // position along the half-edge
+};
+
+}  // namespace
+
+int set_mesh(Geometry &g, int n_vert, const double *xy, int n_tri, const int32_t *tri,
+             const int32_t *mat, const double *bbox, const int32_t *bc, std::string &err) {
+  if (n_vert < 3 || n_tri < 1 || !xy || !tri || !mat || !bbox || !bc) {
+    err = "set_mesh: bad sizes or NULL arrays";
+    return MOC_ERR_ARG;
+  }
+  if (!(bbox[1] > bbox[0]) || !(bbox[3] > bbox[2]) || !std::isfinite(bbox[0]) || !std::isfinite(bbox[1]) ||
+      !std::isfinite(bbox[2]) || !std::isfinite(bbox[3])) {
+    err = "set_mesh: bad bounding box";
+    return MOC_ERR_ARG;
+  }
+  for (int i = 0; i < 4; ++i)
+    if (bc[i] != MOC_BC_VACUUM && bc[i] != MOC_BC_REFLECTIVE) {
+      err = "set_mesh: boundary condition must be 0 (vacuum) or 1 (reflective)";
+      return MOC_ERR_ARG;
+    }
+  double tolb = 1e-9 * std::max(bbox[1] - bbox[0], bbox[3] - bbox[2]);
+  for (int v = 0; v < n_vert; ++v) {
+    double x = xy[2 * v], y = xy[2 * v + 1];
+    if (!std::isfinite(x) || !std::isfinite(y) || x < bbox[0] - tolb || x > bbox[1] + tolb || y < bbox[2] - tolb ||
+        y > bbox[3] + tolb) {
+      err = "set_mesh: vertex " + std::to_string(v) + " is not finite or lies outside the bounding box";
+      return MOC_ERR_ARG;
+    }
+  }
+  for (int t = 0; t < n_tri; ++t) {
+    for (int k = 0; k < 3; ++k)
+      if (tri[3 * t + k] < 0 || tri[3 * t + k] >= n_vert) {
+        err = "set_mesh: triangle " + std::to_string(t) + " has a vertex id out of range";
+        return MOC_ERR_ARG;
+      }
+    const double *a = xy + 2 * tri[3 * t], *b = xy + 2 * tri[3 * t + 1], *c = xy + 2 * tri[3 * t + 2];
+    if (!(cross(b[0] - a[0], b[1] - a[1], c[0] - a[0], c[1] - a[1]) > 0.0)) {
+      err = "set_mesh: triangle " + std::to_string(t) + " is degenerate or not counter-clockwise";
+      return MOC_ERR_ARG;
+    }
+    if (mat[t] < 0) {
+      err = "set_mesh: negative material id";
+      return MOC_ERR_ARG;
+    }
+  }
+  Geometry ng;
+  ng.n_vert = n_vert;
+  ng.n_tri = n_tri;
+  ng.xy.assign(xy, xy + 2 * (size_t)n_vert);
+  ng.tri.assign(tri, tri + 3 * (size_t)n_tri);
+  ng.mat.assign(mat, mat + n_tri);
+  for (int i = 0; i < 4; ++i) {
+    ng.bbox[i] = bbox[i];
+    ng.bc[i] = bc[i];
+  }
+  // half-edge twins by sorting undirected edge keys
+  size_t ne = 3 * (size_t)n_tri;
+  std::vector<std::pair<uint64_t, int32_t>> keys(ne);
+  for (size_t e = 0; e < ne; ++e) {
+    uint32_t a = (uint32_t)ng.tri[e], b = (uint32_t)ng.tri[(e / 3) * 3 + (e % 3 + 1) % 3];
+    uint64_t lo = std::min(a, b), hi = std::max(a, b);
+    keys[e] = {(lo << 32) | hi, (int32_t)e};
+  }
+  std::sort(keys.begin(), keys.end());
+  ng.twin.assign(ne, -1);
+  for (size_t i = 0; i < ne;) {
+    size_t j = i;
+    while (j < ne && keys[j].first == keys[i].first) ++j;
+    if (j - i > 2) {
+      err = "set_mesh: an edge is shared by more than two triangles";
+      return MOC_ERR_ARG;
+    }
+    if (j - i == 2) {
+      int32_t e0 = keys[i].second, e1 = keys[i + 1].second;
+      if (ng.tri[e0] == ng.tri[e1]) {
+        err = "set_mesh: neighbouring triangles have inconsistent orientation";
+        return MOC_ERR_ARG;
+      }
+      ng.twin[e0] = e1;
+      ng.twin[e1] = e0;
+    }
+    i = j;
+  }
+  // vertex -> incident triangles
+  ng.vt_off.assign(n_vert + 1, 0);
+  for (size_t e = 0; e < ne; ++e) ng.vt_off[ng.tri[e] + 1]++;
+  for (int v = 0; v < n_vert; ++v) ng.vt_off[v + 1] += ng.vt_off[v];
+  ng.vt_list.resize(ne);
+  std::vector<int32_t> fill(ng.vt_off.begin(), ng.vt_off.end() - 1);
+  for (size_t e = 0; e < ne; ++e) ng.vt_list[fill[ng.tri[e]]++] = (int32_t)(e / 3);
+  ng.has_mesh = true;
+  // keep a quadrature already set
+  ng.n_azim = g.n_azim;
+  ng.n_dir = g.n_dir;
+  ng.n_polar = g.n_polar;
+  ng.spacing = g.spacing;
+  ng.sin_theta = g.sin_theta;
+  ng.polar_w = g.polar_w;
+  ng.has_quad = g.has_quad;
+  g = std::move(ng);
+  return MOC_OK;
+}
+
+int set_quadrature(Geometry &g, int n_azim, double spacing, int n_polar, const double *sin_theta,
+                   const double *polar_w, std::string &err) {
+  if (n_azim < 4 || n_azim % 4 != 0 || !(spacing > 0.0) || !std::isfinite(spacing) || n_polar < 1 ||
+      n_polar > 6 || !sin_theta || !polar_w) {
+    err = "set_quadrature: n_azim must be a positive multiple of 4, spacing > 0, 1 <= n_polar <= 6";
+    return MOC_ERR_ARG;
+  }
+  double wsum = 0.0;
+  for (int p = 0; p < n_polar; ++p) {
+    if (!(sin_theta[p] > 0.0 && sin_theta[p] <= 1.0) || !(polar_w[p] > 0.0)) {
+      err = "set_quadrature: need 0 < sin_theta <= 1 and positive polar weights";
+      return MOC_ERR_ARG;
+    }
+    wsum += polar_w[p];
+  }
+  if (std::fabs(wsum - 1.0) > 1e-5) {
+    err = "set_quadrature: polar weights must sum to 1 over one hemisphere";
+    return MOC_ERR_ARG;
+  }
+  g.n_azim = n_azim;
+  g.n_dir = n_azim / 2;
+  g.spacing = spacing;
+  g.n_polar = n_polar;
+  g.sin_theta.assign(sin_theta, sin_theta + n_polar);
+  g.polar_w.assign(polar_w, polar_w + n_polar);
+  g.has_quad = true;
+  g.has_tracks = false;
+  return MOC_OK;
+}
+
+namespace {
+
+// Direction set over [0, pi) with the cyclic correction, and azimuthal weights over [0, 2 pi).
+int build_directions(Geometry &g, std::string &err) {
+  double W = g.bbox[1] - g.bbox[0], H = g.bbox[3] - g.bbox[2];
+  int nd = g.n_dir, nq = g.n_azim / 4;
+  g.phi.assign(nd, 0.0);
+  g.delta.assign(nd, 0.0);
+  g.omega.assign(nd, 0.0);
+  g.nx.assign(nd, 0);
+  g.ny.assign(nd, 0);
+  for (int a = 0; a < nq; ++a) {
+    double nominal = 2.0 * kPi * (a + 0.5) / g.n_azim;
+    int nx = (int)std::floor(W * std::sin(nominal) / g.spacing) + 1;
+    int ny = (int)std::floor(H * std::cos(nominal) / g.spacing) + 1;
+    double ph = std::atan((H * nx) / (W * ny));
+    double d = (W / nx) * std::sin(ph);
+    int b = nd - 1 - a;  // mirror image pi - phi in the second quadrant
+    g.phi[a] = ph;
+    g.phi[b] = kPi - ph;
+    g.delta[a] = g.delta[b] = d;
+    g.nx[a] = g.nx[b] = nx;
+    g.ny[a] = g.ny[b] = ny;
+  }
+  for (int j = 1; j < nd; ++j)
+    if (!(g.phi[j] > g.phi[j - 1])) {
+      err = "generate_tracks: corrected azimuthal angles are not increasing (ray spacing too coarse)";
+      return MOC_ERR_ARG;
+    }
+  // neighbours over the 2 pi set: angle j + pi has the same weight by point symmetry
+  for (int j = 0; j < nd; ++j) {
+    double prev = (j == 0) ? g.phi[nd - 1] - kPi : g.phi[j - 1];
+    double next = (j == nd - 1) ? g.phi[0] + kPi : g.phi[j + 1];
+    g.omega[j] = (next - prev) / (4.0 * kPi);
+  }
+  return MOC_OK;
+}
+
+double box_exit(const Geometry &g, const double *p, const double *u) {
+  double s = INFINITY;
+  if (u[0] > 0) s = std::min(s, (g.bbox[1] - p[0]) / u[0]);
+  if (u[0] < 0) s = std::min(s, (g.bbox[0] - p[0]) / u[0]);
+  if (u[1] > 0) s = std::min(s, (g.bbox[3] - p[1]) / u[1]);
+  if (u[1] < 0) s = std::min(s, (g.bbox[2] - p[1]) / u[1]);
+  return s;
+}
+
+struct Piece {
+  int32_t tri;
+  double len;
+};
+
+// Walk from triangle t0 (entered at s_start) along the ray until it leaves the mesh.
+// Returns the exit parameter, or NAN if the walk got lost.
+double walk(const Geometry &g, int t0, double s_start, const double *p0, const double *u, double L,
+            std::vector<Piece> &out) {
+  int T = t0, prev = -1;
+  double s_cur = s_start;
+  int64_t limit = 4 * (int64_t)g.n_tri + 64;
+  for (int64_t step = 0; step < limit; ++step) {
+    double lo, hi;
+    if (!clip(g, T, p0, u, lo, hi)) hi = s_cur;
+    hi = std::min(hi, L);
+    double l = hi - s_cur;
+    if (l > kSliver) out.push_back({T, l});
+    if (hi >= L) return L;
+    // leaving edge: smallest leaving parameter
+    int ex = -1;
+    double best = INFINITY;
+    for (int k = 0; k < 3; ++k) {
+      const double *a = &g.xy[2 * (size_t)g.tri[3 * (size_t)T + k]];
+      const double *b = &g.xy[2 * (size_t)g.tri[3 * (size_t)T + (k + 1) % 3]];
+      double nx = -(b[1] - a[1]), ny = b[0] - a[0];
+      double fu = nx * u[0] + ny * u[1];
+      if (fu >= 0.0) continue;
+      double s = -(nx * (p0[0] - a[0]) + ny * (p0[1] - a[1])) / fu;
+      if (s < best) {
+        best = s;
+        ex = k;
+      }
+    }
+    if (ex < 0) return NAN;
+    double P[2] = {p0[0] + hi * u[0], p0[1] + hi * u[1]};
+    int va = g.tri[3 * (size_t)T + ex], vb = g.tri[3 * (size_t)T + (ex + 1) % 3];
+    double da = std::hypot(P[0] - g.xy[2 * (size_t)va], P[1] - g.xy[2 * (size_t)va + 1]);
+    double db = std::hypot(P[0] - g.xy[2 * (size_t)vb], P[1] - g.xy[2 * (size_t)vb + 1]);
+    int he = 3 * T + ex;
+    int nxt = (g.twin[he] >= 0) ? g.twin[he] / 3 : -1;
+    int v = -1;
+    if (da <= kVertexEps || db <= kVertexEps) v = (da <= db) ? va : vb;
+    else if (nxt == prev && nxt >= 0) v = (da <= db) ? va : vb;   // no progress: resolve at the vertex
+    if (v < 0) {
+      if (nxt < 0) return hi;  // boundary edge: the ray leaves the mesh
+      prev = T;
+      T = nxt;
+      s_cur = hi;
+      continue;
+    }
+    // vertex crossing: the triangle of the vertex fan the ray continues into
+    int pick = -1;
+    double pick_hi = hi + kSliver;
+    for (int q = g.vt_off[v]; q < g.vt_off[v + 1]; ++q) {
+      int c = g.vt_list[q];
+      if (c == T) continue;
+      double lo2, hi2;
+      if (!clip(g, c, p0, u, lo2, hi2)) continue;
+      if (lo2 <= hi + kEventEps && hi2 > pick_hi) {
+        pick = c;
+        pick_hi = hi2;
+      }
+    }
+    if (pick < 0) return hi;  // leaves the mesh through a boundary vertex
+    prev = T;
+    T = pick;
+    s_cur = hi;
+  }
+  return NAN;
+}
+
+}  // namespace
+
+int generate_tracks(Geometry &g, std::string &err) {
+  if (!g.has_mesh || !g.has_quad) {
+    err = "generate_tracks: set the mesh and the quadrature first";
+    return MOC_ERR_STATE;
+  }
+  int rc = build_directions(g, err);
+  if (rc) return rc;
+  const double W = g.bbox[1] - g.bbox[0], H = g.bbox[3] - g.bbox[2];
+  const double tolw = 1e-9 * std::max(W, H);
+  std::vector<int32_t> bnd;
+  for (size_t e = 0; e < g.twin.size(); ++e)
+    if (g.twin[e] < 0) bnd.push_back((int32_t)e);
+
+  g.seg_off.assign(1, 0);
+  g.seg_reg.clear();
+  g.seg_len.clear();
+  g.track_dir.clear();
+  g.track_xy.clear();
+  std::vector<Piece> pieces;
+  for (int j = 0; j < g.n_dir; ++j) {
+    const double u[2] = {std::cos(g.phi[j]), std::sin(g.phi[j])};
+    const double nrm[2] = {-u[1], u[0]};
+    const int nr = g.nx[j] + g.ny[j];
+    std::vector<double> ray(3 * (size_t)nr);  // x0 y0 L
+    for (int i = 0; i < g.nx[j]; ++i) {
+      ray[3 * i] = g.bbox[0] + (i + 0.5) * W / g.nx[j];
+      ray[3 * i + 1] = g.bbox[2];
+    }
+    for (int i = 0; i < g.ny[j]; ++i) {
+      int r = g.nx[j] + i;
+      ray[3 * r] = (u[0] > 0) ? g.bbox[0] : g.bbox[1];
+      ray[3 * r + 1] = g.bbox[2] + (i + 0.5) * H / g.ny[j];
+    }
+    for (int r = 0; r < nr; ++r) ray[3 * r + 2] = box_exit(g, &ray[3 * r], u);
+    // rays sorted by their offset along the normal, to find the rays a boundary edge spans
+    std::vector<std::pair<double, int>> off(nr);
+    for (int r = 0; r < nr; ++r) off[r] = {nrm[0] * ray[3 * r] + nrm[1] * ray[3 * r + 1], r};
+    std::sort(off.begin(), off.end());
+    std::vector<std::vector<Event>> ev(nr);
+    for (int32_t he : bnd) {
+      int t = he / 3, k = he % 3;
+      const double *a = &g.xy[2 * (size_t)g.tri[3 * (size_t)t + k]];
+      const double *b = &g.xy[2 * (size_t)g.tri[3 * (size_t)t + (k + 1) % 3]];
+      double ca = nrm[0] * a[0] + nrm[1] * a[1], cb = nrm[0] * b[0] + nrm[1] * b[1];
+      double clo = std::min(ca, cb) - tolw, chi = std::max(ca, cb) + tolw;
+      auto it = std::lower_bound(off.begin(), off.end(), std::make_pair(clo, -1));
+      double dx = b[0] - a[0], dy = b[1] - a[1];
+      double den = cross(u[0], u[1], dx, dy);
+      if (den == 0.0) continue;  // parallel to the ray
+      for (; it != off.end() && it->first <= chi; ++it) {
+        int r = it->second;
+        const double *p0 = &ray[3 * r];
+        double ax = a[0] - p0[0], ay = a[1] - p0[1];
+        double s = cross(ax, ay, dx, dy) / den;
+        double tt = cross(ax, ay, u[0], u[1]) / den;
+        if (tt < -1e-12 || tt > 1.0 + 1e-12) continue;
+        if (s < -kEventEps || s > ray[3 * r + 2] - kEventEps) continue;
+        ev[r].push_back({s, he, tt});
+      }
+    }
+    for (int r = 0; r < nr; ++r) {
+      const double *p0 = &ray[3 * r];
+      const double L = ray[3 * r + 2];
+      std::sort(ev[r].begin(), ev[r].end(), [](const Event &x, const Event &y) { return x.s < y.s; });
+      double s_done = -INFINITY;
+      for (size_t q = 0; q < ev[r].size(); ++q) {
+        const Event &E = ev[r][q];
+        if (E.s <= s_done + kEventEps) continue;
+        // candidate start triangles: owners of the boundary edges hit here, and the vertex fans
+        // of edge endpoints hit
+        int best = -1;
+        double best_lo = 0, best_hi = E.s + kSliver;
+        for (size_t q2 = q; q2 < ev[r].size() && ev[r][q2].s <= E.s + kEventEps; ++q2) {
+          const Event &F = ev[r][q2];
+          int t = F.he / 3, k = F.he % 3;
+          int cands[1 + 64];
+          int nc = 0;
+          cands[nc++] = t;
+          int vs[2] = {-1, -1};
+          if (F.t < 1e-9) vs[0] = g.tri[3 * (size_t)t + k];
+          if (F.t > 1.0 - 1e-9) vs[1] = g.tri[3 * (size_t)t + (k + 1) % 3];
+          for (int vv : vs) {
+            if (vv < 0) continue;
+            for (int w = g.vt_off[vv]; w < g.vt_off[vv + 1] && nc < 65; ++w) cands[nc++] = g.vt_list[w];
+          }
+          for (int c = 0; c < nc; ++c) {
+            double lo, hi;
+            if (!clip(g, cands[c], p0, u, lo, hi)) continue;
+            hi = std::min(hi, L);
+            if (lo <= E.s + kEventEps && hi > best_hi) {
+              best = cands[c];
+              best_hi = hi;
+              best_lo = lo;
+            }
+          }
+        }
+        if (best < 0) continue;
+        pieces.clear();
+        double s0 = std::max(0.0, best_lo);
+        double s1 = walk(g, best, s0, p0, u, L, pieces);
+        if (std::isnan(s1)) {
+          char buf[160];
+          std::snprintf(buf, sizeof buf, "generate_tracks: half-edge walk lost on direction %d ray %d", j, r);
+          err = buf;
+          return MOC_ERR_GEOMETRY;
+        }
+        s_done = s1;
+        if (pieces.empty()) continue;
+        g.track_dir.push_back(j);
+        g.track_xy.push_back(p0[0] + s0 * u[0]);
+        g.track_xy.push_back(p0[1] + s0 * u[1]);
+        g.track_xy.push_back(p0[0] + s1 * u[0]);
+        g.track_xy.push_back(p0[1] + s1 * u[1]);
+        for (const Piece &p : pieces) {
+          g.seg_reg.push_back(p.tri);
+          g.seg_len.push_back(p.len);
+        }
+        g.seg_off.push_back((int64_t)g.seg_reg.size());
+      }
+    }
+  }
+  const int64_t T = g.n_tracks();
+  if (T == 0) {
+    err = "generate_tracks: no ray crosses the mesh";
+    return MOC_ERR_GEOMETRY;
+  }
+  // Reflective links, matched combinatorially: a wall point is identified by its wall and its
+  // slot index (i + 1/2) along the wall; reflection maps travel direction j (+ n_dir if
+  // reversed) to n_dir - 1 - j, keeping the sense on x walls and flipping it on y walls.
+  auto wall_slot = [&](double x, double y, int j, int &w, int64_t &slot) {
+    w = -1;
+    if (std::fabs(x - g.bbox[0]) <= tolw) w = 0;
+    else if (std::fabs(x - g.bbox[1]) <= tolw) w = 1;
+    else if (std::fabs(y - g.bbox[2]) <= tolw) w = 2;
+    else if (std::fabs(y - g.bbox[3]) <= tolw) w = 3;
+    if (w < 0) return false;
+    double pos = (w <= 1) ? (y - g.bbox[2]) * g.ny[j] / H : (x - g.bbox[0]) * g.nx[j] / W;
+    slot = (int64_t)std::llround(pos - 0.5);
+    double back = (w <= 1) ? g.bbox[2] + (slot + 0.5) * H / g.ny[j] : g.bbox[0] + (slot + 0.5) * W / g.nx[j];
+    return std::fabs(back - ((w <= 1) ? y : x)) <= tolw;
+  };
+  std::vector<std::pair<int64_t, int64_t>> incoming;  // key -> end code
+  incoming.reserve(2 * T);
+  for (int64_t t = 0; t < T; ++t) {
+    for (int d = 0; d < 2; ++d) {
+      double x = g.track_xy[4 * t + (d ? 2 : 0)], y = g.track_xy[4 * t + (d ? 3 : 1)];
+      int w;
+      int64_t slot;
+      if (!wall_slot(x, y, g.track_dir[t], w, slot)) continue;
+      int64_t a2 = g.track_dir[t] + d * g.n_dir;
+      incoming.push_back({((a2 * 4 + w) << 32) | slot, 2 * t + d});
+    }
+  }
+  std::sort(incoming.begin(), incoming.end());
+  g.link.assign(2 * T, -1);
+  for (int64_t t = 0; t < T; ++t) {
+    for (int d = 0; d < 2; ++d) {
+      double x = g.track_xy[4 * t + (d ? 0 : 2)], y = g.track_xy[4 * t + (d ? 1 : 3)];
+      int w;
+      int64_t slot;
+      if (!wall_slot(x, y, g.track_dir[t], w, slot)) continue;   // leaves through the mesh edge
+      if (g.bc[w] != MOC_BC_REFLECTIVE) continue;
+      int64_t j2 = g.n_dir - 1 - g.track_dir[t];
+      int64_t d2 = (w <= 1) ? d : 1 - d;
+      int64_t key = (((j2 + d2 * g.n_dir) * 4 + w) << 32) | slot;
+      auto it = std::lower_bound(incoming.begin(), incoming.end(), std::make_pair(key, (int64_t)-1));
+      if (it == incoming.end() || it->first != key) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "generate_tracks: no reflective partner for track %lld end %d",
+                      (long long)t, d);
+        err = buf;
+        return MOC_ERR_GEOMETRY;
+      }
+      g.link[2 * t + d] = it->second;
+    }
+  }
+  // tracked areas: both senses of each track count, with weight omega_j delta_j
+  g.area.assign(g.n_tri, 0.0);
+  for (int64_t t = 0; t < T; ++t) {
+    double w = 2.0 * g.omega[g.track_dir[t]] * g.delta[g.track_dir[t]];
+    for (int64_t s = g.seg_off[t]; s < g.seg_off[t + 1]; ++s) g.area[g.seg_reg[s]] += w * g.seg_len[s];
+  }
+  g.has_tracks = true;
+  return MOC_OK;
+}
+
+}  // namespace moc

@@ -1,0 +1,268 @@
+"""Thin ctypes binding of the C ABI in include/moc_gb300.h (argument marshalling only).
+
+Every step of the transport calculation runs in the CUDA library; this module converts numpy
+arrays to pointers, checks status codes and raises MocError with the library's message. There
+is no Python or CPU fallback: if the built library is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libmoc_gb300.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "moc_gb300.h")
+
+MOC_FP64, MOC_FP32, MOC_FP32_PLAIN = 0, 1, 2
+PRECISIONS = {"fp64": MOC_FP64, "fp32": MOC_FP32, "fp32_plain": MOC_FP32_PLAIN}
+STATUS = {0: "MOC_OK", -1: "MOC_ERR_ARG", -2: "MOC_ERR_CUDA", -3: "MOC_ERR_OOM", -4: "MOC_ERR_STATE",
+          -5: "MOC_ERR_NOT_CONVERGED", -6: "MOC_ERR_NONFINITE", -7: "MOC_ERR_GEOMETRY"}
+
+_d = ctypes.POINTER(ctypes.c_double)
+_i32 = ctypes.POINTER(ctypes.c_int32)
+_i64 = ctypes.POINTER(ctypes.c_int64)
+_vp = ctypes.c_void_p
+_lib = None
+_lock = threading.Lock()
+
+
+class MocError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def header_symbols() -> list:
+    """Names of the functions declared in include/moc_gb300.h."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char \*)\s*\*?\s*(moc_\w+)\s*\(", txt, re.M)))
+
+
+def load_library(path: Optional[str] = None):
+    """Load the built library (raises OSError/ImportError if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise ImportError(f"CUDA library not built: {p} is missing (run paper_2607_01591_gb300.build.build())")
+        lib = ctypes.CDLL(p)
+        sig = {
+            "moc_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, _vp]),
+            "moc_destroy": (None, [_vp]),
+            "moc_last_error": (ctypes.c_char_p, [_vp]),
+            "moc_set_mesh": (ctypes.c_int, [_vp, ctypes.c_int, _d, ctypes.c_int, _i32, _i32, _d, _i32]),
+            "moc_set_quadrature": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _d, _d]),
+            "moc_generate_tracks": (ctypes.c_int, [_vp]),
+            "moc_get_track_counts": (ctypes.c_int, [_vp, _i64, _i64]),
+            "moc_get_tracks": (ctypes.c_int, [_vp, _i64, _i32, _d, _i32, _d, _i64]),
+            "moc_get_quadrature": (ctypes.c_int, [_vp, _d, _d, _d]),
+            "moc_get_region_areas": (ctypes.c_int, [_vp, _d]),
+            "moc_set_xs": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _d, _d, _d, _d]),
+            "moc_set_fixed_source": (ctypes.c_int, [_vp, _d]),
+            "moc_set_state": (ctypes.c_int, [_vp, _d, ctypes.c_double, _d]),
+            "moc_get_state": (ctypes.c_int, [_vp, _d, _d, _d]),
+            "moc_update_source": (ctypes.c_int, [_vp]),
+            "moc_sweep": (ctypes.c_int, [_vp]),
+            "moc_outer": (ctypes.c_int, [_vp, ctypes.c_int, _d, _d]),
+            "moc_power_iterate": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                                 _d, ctypes.POINTER(ctypes.c_int), _d]),
+            "moc_enable_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
+            "moc_get_timing": (ctypes.c_int, [_vp, _d, _i64]),
+            "moc_get_work": (ctypes.c_int, [_vp, _i64, _i64, ctypes.POINTER(ctypes.c_int)]),
+            "moc_synchronize": (ctypes.c_int, [_vp]),
+            "moc_eval_one_minus_exp_f32": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_float),
+                                                          ctypes.POINTER(ctypes.c_float), ctypes.c_int64]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def _p(a, t):
+    return None if a is None else a.ctypes.data_as(t)
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32a(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def eval_one_minus_exp_f32(tau: np.ndarray, device: int = 0) -> np.ndarray:
+    """The library's FP32 1 - exp(-tau) evaluated on the GPU."""
+    lib = load_library()
+    tau = np.ascontiguousarray(tau, dtype=np.float32)
+    out = np.empty_like(tau)
+    fp = ctypes.POINTER(ctypes.c_float)
+    rc = lib.moc_eval_one_minus_exp_f32(int(device), tau.ctypes.data_as(fp), out.ctypes.data_as(fp), tau.size)
+    if rc != 0:
+        raise MocError(rc, "moc_eval_one_minus_exp_f32 failed")
+    return out
+
+
+class Moc:
+    """One transport problem on one GPU (device >= 0) or host-only geometry (device = -1)."""
+
+    def __init__(self, device: int = 0, precision: str = "fp32", stream: Optional[int] = None):
+        self._lib = load_library()
+        h = _vp()
+        self.precision = precision
+        rc = self._lib.moc_create(ctypes.byref(h), int(device), PRECISIONS[precision],
+                                  None if stream is None else _vp(stream))
+        if rc != 0:
+            raise MocError(rc, "moc_create failed")
+        self._h = h
+        self.device = device
+        self.G = 0
+        self.n_polar = 0
+        self.n_regions = 0
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.moc_destroy(h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int):
+        if rc != 0:
+            raise MocError(rc, self._lib.moc_last_error(self._h).decode())
+
+    # geometry -------------------------------------------------------------------------------
+    def set_mesh(self, mesh):
+        xy, tri, mat = _f64(mesh.xy), _i32a(mesh.tri), _i32a(mesh.mat)
+        bbox, bc = _f64(mesh.bbox), _i32a(mesh.bc)
+        self._check(self._lib.moc_set_mesh(self._h, xy.shape[0], _p(xy, _d), tri.shape[0], _p(tri, _i32),
+                                           _p(mat, _i32), _p(bbox, _d), _p(bc, _i32)))
+        self.n_regions = int(tri.shape[0])
+
+    def set_quadrature(self, n_azim: int, spacing: float, sin_theta, polar_w):
+        st, pw = _f64(sin_theta), _f64(polar_w)
+        self._check(self._lib.moc_set_quadrature(self._h, int(n_azim), float(spacing), st.shape[0], _p(st, _d),
+                                                 _p(pw, _d)))
+        self.n_polar = int(st.shape[0])
+
+    def generate_tracks(self):
+        self._check(self._lib.moc_generate_tracks(self._h))
+
+    def track_counts(self):
+        T, S = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self._lib.moc_get_track_counts(self._h, ctypes.byref(T), ctypes.byref(S)))
+        return T.value, S.value
+
+    def tracks(self) -> dict:
+        T, S = self.track_counts()
+        off, reg, ln = np.zeros(T + 1, np.int64), np.zeros(S, np.int32), np.zeros(S)
+        dr, xy, link = np.zeros(T, np.int32), np.zeros((T, 4)), np.zeros((T, 2), np.int64)
+        self._check(self._lib.moc_get_tracks(self._h, _p(off, _i64), _p(reg, _i32), _p(ln, _d), _p(dr, _i32),
+                                             _p(xy, _d), _p(link, _i64)))
+        return dict(seg_off=off, seg_region=reg, seg_len=ln, track_dir=dr, track_xy=xy, link=link)
+
+    def quadrature(self, n_dir: int) -> dict:
+        phi, delta, omega = np.zeros(n_dir), np.zeros(n_dir), np.zeros(n_dir)
+        self._check(self._lib.moc_get_quadrature(self._h, _p(phi, _d), _p(delta, _d), _p(omega, _d)))
+        return dict(phi=phi, delta=delta, omega=omega)
+
+    def areas(self) -> np.ndarray:
+        a = np.zeros(self.n_regions)
+        self._check(self._lib.moc_get_region_areas(self._h, _p(a, _d)))
+        return a
+
+    # physics --------------------------------------------------------------------------------
+    def set_xs(self, xs):
+        st, nsf, chi, ss = _f64(xs.sigma_t), _f64(xs.nu_sigma_f), _f64(xs.chi), _f64(xs.sigma_s)
+        M, G = st.shape
+        self._check(self._lib.moc_set_xs(self._h, M, G, _p(st, _d), _p(nsf, _d), _p(chi, _d), _p(ss, _d)))
+        self.G = G
+
+    def set_fixed_source(self, S):
+        S = _f64(S)
+        if S is not None:
+            assert S.shape == (self.n_regions, self.G)
+        self._check(self._lib.moc_set_fixed_source(self._h, _p(S, _d)))
+
+    def set_state(self, phi=None, k: float = 1.0, psi=None):
+        phi, psi = _f64(phi), _f64(psi)
+        if phi is not None:
+            assert phi.size == self.n_regions * self.G
+        if psi is not None:
+            T, _ = self.track_counts()
+            assert psi.size == T * 2 * self.n_polar * self.G
+        self._check(self._lib.moc_set_state(self._h, _p(phi, _d), float(k), _p(psi, _d)))
+
+    def get_state(self, with_psi: bool = False):
+        phi = np.zeros((self.n_regions, self.G))
+        k = ctypes.c_double()
+        psi = None
+        if with_psi:
+            T, _ = self.track_counts()
+            psi = np.zeros((T, 2, self.n_polar, self.G))
+        self._check(self._lib.moc_get_state(self._h, _p(phi, _d), ctypes.byref(k), _p(psi, _d)))
+        return (phi, k.value, psi) if with_psi else (phi, k.value)
+
+    def update_source(self):
+        self._check(self._lib.moc_update_source(self._h))
+
+    def sweep(self):
+        self._check(self._lib.moc_sweep(self._h))
+
+    def outer(self, n: int = 1, read: bool = True):
+        k, r = ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.moc_outer(self._h, int(n), ctypes.byref(k) if read else None,
+                                        ctypes.byref(r) if read else None))
+        return (k.value, r.value) if read else None
+
+    def power_iterate(self, tol_k: float = 1e-6, tol_flux: float = 1e-6, max_outer: int = 10000,
+                      check_every: int = 10, raise_on_fail: bool = True):
+        k, n, r = ctypes.c_double(), ctypes.c_int(), ctypes.c_double()
+        rc = self._lib.moc_power_iterate(self._h, float(tol_k), float(tol_flux), int(max_outer), int(check_every),
+                                         ctypes.byref(k), ctypes.byref(n), ctypes.byref(r))
+        if rc != 0 and (raise_on_fail or rc != -5):
+            self._check(rc)
+        return k.value, n.value, r.value, rc == 0
+
+    def enable_timing(self, on: bool = True):
+        self._check(self._lib.moc_enable_timing(self._h, 1 if on else 0))
+
+    def timing(self):
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        self._check(self._lib.moc_get_timing(self._h, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    def work(self):
+        s, u, k = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+        self._check(self._lib.moc_get_work(self._h, ctypes.byref(s), ctypes.byref(u), ctypes.byref(k)))
+        return s.value, u.value, k.value
+
+    def synchronize(self):
+        self._check(self._lib.moc_synchronize(self._h))
+
+    @classmethod
+    def from_problem(cls, prob, device: int = 0, precision: str = "fp32", stream=None, with_xs: bool = True):
+        m = cls(device, precision, stream)
+        m.set_mesh(prob.mesh)
+        m.set_quadrature(prob.n_azim, prob.ray_spacing, prob.sin_theta, prob.polar_w)
+        m.generate_tracks()
+        if with_xs and device >= 0:
+            m.set_xs(prob.xs)
+            if prob.fixed_source is not None:
+                m.set_fixed_source(prob.fixed_source)
+        return m

@@ -1,0 +1,95 @@
+"""C-ABI library: loads, exports every declared symbol, and its host-side geometry (half-edge
+walk segmentation, links, tracked areas) agrees with the oracle's clip-based segmentation.
+No GPU is needed: these use host-only contexts (device = -1)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2607_01591_gb300 import moc
+from paper_2607_01591_gb300 import workloads as W
+from paper_2607_01591_gb300.build import build
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build()
+    return moc.load_library()
+
+
+def test_library_exports_every_header_symbol(lib):
+    names = moc.header_symbols()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def _compare_tracks(prob):
+    m = moc.Moc.from_problem(prob, device=-1)
+    o = oracle.Oracle.from_problem(prob, with_xs=False)
+    a, b = m.tracks(), o.tracks()
+    assert m.track_counts() == (o.n_tracks, o.n_segments)
+    assert np.array_equal(a["seg_off"], b["seg_off"])
+    assert np.array_equal(a["seg_region"], b["seg_region"])
+    np.testing.assert_allclose(a["seg_len"], b["seg_len"], rtol=0, atol=1e-11)
+    assert np.array_equal(a["track_dir"], b["track_dir"])
+    np.testing.assert_allclose(a["track_xy"], b["track_xy"], rtol=0, atol=1e-11)
+    assert np.array_equal(a["link"], b["link"])
+    np.testing.assert_allclose(m.areas(), o.areas(), rtol=1e-11)
+    q1, q2 = m.quadrature(o.n_dir), o.quadrature()
+    for k in ("phi", "delta", "omega"):
+        np.testing.assert_allclose(q1[k], q2[k], rtol=1e-14)
+
+
+@pytest.mark.parametrize("case", ["pin", "pin_vacuum", "lattice3", "lattice3_mixed_bc", "grid", "hex7", "hex1"])
+def test_host_segmentation_matches_oracle(lib, case):
+    if case == "pin":
+        prob = W.pin_cell_problem()
+    elif case == "pin_vacuum":
+        prob = W.pin_cell_problem()
+        prob.mesh = W.with_bc(prob.mesh, (0, 0, 0, 0))
+    elif case == "lattice3":
+        prob = W.small_lattice_problem(3)
+    elif case == "lattice3_mixed_bc":
+        prob = W.small_lattice_problem(3, bc=(1, 0, 1, 0), n_azim=24, ray_spacing=0.03)
+    elif case == "grid":
+        prob = W.Problem(W.grid_mesh(5, 3, 2.0, 1.0), W.synthetic_xs(["fuel"], 2, 1), 8, 0.07)
+    elif case == "hex7":
+        prob = W.Problem(W.hex_core_mesh(n_sub=4, n_rings=1), W.synthetic_xs(["fuel", "fuel", "coolant"], 3, 1), 12, 0.3)
+    else:
+        prob = W.Problem(W.hex_core_mesh(n_sub=6, n_rings=0), W.synthetic_xs(["fuel", "fuel", "coolant"], 3, 1), 8, 0.2)
+    _compare_tracks(prob)
+
+
+def test_bad_inputs_are_rejected(lib):
+    m = moc.Moc(device=-1)
+    mesh = W.grid_mesh(2, 2, 1.0, 1.0)
+    bad = W.Mesh(mesh.xy, mesh.tri[:, ::-1].copy(), mesh.mat, mesh.bbox, mesh.bc)   # clockwise
+    with pytest.raises(moc.MocError) as e:
+        m.set_mesh(bad)
+    assert e.value.code == -1
+    bad2 = W.Mesh(mesh.xy, mesh.tri.copy(), mesh.mat, mesh.bbox, mesh.bc)
+    bad2.tri[0, 0] = 10_000
+    with pytest.raises(moc.MocError):
+        m.set_mesh(bad2)
+    # three triangles on one edge: not conforming
+    dup = W.Mesh(mesh.xy, np.concatenate([mesh.tri, mesh.tri[:1]]), np.concatenate([mesh.mat, mesh.mat[:1]]),
+                 mesh.bbox, mesh.bc)
+    with pytest.raises(moc.MocError):
+        m.set_mesh(dup)
+    m.set_mesh(mesh)
+    with pytest.raises(moc.MocError):
+        m.set_quadrature(6, 0.1, W.TY3_SIN_THETA, W.TY3_WEIGHT)       # not a multiple of 4
+    with pytest.raises(moc.MocError):
+        m.set_quadrature(8, 0.1, W.TY3_SIN_THETA, W.TY3_WEIGHT * 2)   # weights must sum to 1
+    with pytest.raises(moc.MocError) as e:
+        m.generate_tracks()                                            # no quadrature yet
+    assert e.value.code == -4
+    m.set_quadrature(8, 0.1, W.TY3_SIN_THETA, W.TY3_WEIGHT)
+    m.generate_tracks()
+    # GPU work on a host-only context is refused with a message, not a crash
+    with pytest.raises(moc.MocError) as e:
+        m.set_xs(W.synthetic_xs(["fuel"], 2, 1))
+    assert e.value.code == -4
+    assert "host-only" in str(e.value)

@@ -1,0 +1,204 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 CPU oracle on the same
+seeded inputs. Bars: FP64 mode |dk| <= 2 pcm and max relative region-flux error <= 1e-5
+(tighter where both sides run the same outers from the same state); FP32 modes are reported
+and held to looser bars that follow from FP32 arithmetic."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2607_01591_gb300 import moc
+from paper_2607_01591_gb300 import workloads as W
+from paper_2607_01591_gb300.build import build
+
+pytestmark = pytest.mark.gpu
+
+PCM = 1e-5
+NCPU = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build()
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300)))
+
+
+def _oracle(prob):
+    return oracle.Oracle.from_problem(prob, threads=min(NCPU, 16))
+
+
+def test_pin_cell_converged_fp64():
+    prob = W.pin_cell_problem()
+    o = _oracle(prob)
+    ko, no, _, conv = o.iterate(True, 1e-11, 1e-10, 20000)
+    assert conv
+    phio, _ = o.get_state()
+    m = moc.Moc.from_problem(prob, precision="fp64")
+    kg, ng, rg, convg = m.power_iterate(1e-11, 1e-10, 20000, check_every=1)
+    assert convg
+    phig, _ = m.get_state()
+    assert abs(kg - ko) <= 2 * PCM
+    assert _rel(phig, phio) <= 1e-5
+    # both iterate the same discrete operator: much closer than the bar, same outer count
+    assert abs(kg - ko) < 1e-9 and _rel(phig, phio) < 1e-8
+    assert ng == no
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_plain"])
+def test_same_outers_from_same_state(precision):
+    """Random flux, k and boundary flux on both sides; then 6 outers each, compared after every
+    outer (exercises every link, the normalisation and the k update)."""
+    prob = W.small_lattice_problem(3, bc=(1, 0, 1, 0), n_azim=24, ray_spacing=0.03)
+    o = _oracle(prob)
+    m = moc.Moc.from_problem(prob, precision=precision)
+    rng = np.random.default_rng(5)
+    T, _ = m.track_counts()
+    phi0 = rng.uniform(0.5, 1.5, (prob.mesh.n_tri, prob.xs.n_groups))
+    psi0 = rng.uniform(0.0, 0.2, (T, 2, 3, prob.xs.n_groups))
+    o.set_state(phi0, 1.1, psi0)
+    o.normalise()
+    m.set_state(phi0, 1.1, psi0)
+    tol_phi = {"fp64": 1e-11, "fp32": 2e-5, "fp32_plain": 5e-5}[precision]
+    tol_k = {"fp64": 1e-12, "fp32": 2e-6, "fp32_plain": 5e-6}[precision]
+    for it in range(6):
+        ro = o.outer(True)
+        kg, rg = m.outer(1)
+        phio, ko = o.get_state()
+        phig, kg2 = m.get_state()
+        assert kg == kg2
+        assert abs(kg - ko) <= tol_k, (it, kg, ko)
+        assert _rel(phig, phio) <= tol_phi, (it, _rel(phig, phio))
+        assert abs(rg - ro) <= max(1e-9, 10 * tol_phi) * max(1.0, ro), (it, rg, ro)
+
+
+def test_fixed_source_vacuum_fp64():
+    prob = W.pin_cell_problem()
+    prob.mesh = W.with_bc(prob.mesh, (0, 0, 0, 0))
+    xs = prob.xs
+    prob.xs = W.CrossSections(xs.sigma_t, np.zeros_like(xs.nu_sigma_f), xs.chi, xs.sigma_s)
+    S = np.zeros((prob.mesh.n_tri, 7))
+    S[prob.mesh.mat == 0, 0] = 1.0
+    prob.fixed_source = S
+    o = _oracle(prob)
+    o.set_state(np.zeros_like(S), 1.0, None)
+    _, no, _, conv = o.iterate(False, 0.0, 1e-12, 5000)
+    assert conv
+    m = moc.Moc.from_problem(prob, precision="fp64")
+    m.set_state(np.zeros_like(S), 1.0, None)
+    _, ng, _, convg = m.power_iterate(0.0, 1e-12, 5000, check_every=1)
+    assert convg and ng == no
+    assert _rel(m.get_state()[0], o.get_state()[0]) < 1e-9
+
+
+def test_fp32_converged_error_is_small():
+    prob = W.pin_cell_problem()
+    o = _oracle(prob)
+    ko, _, _, _ = o.iterate(True, 1e-10, 1e-10, 20000)
+    phio, _ = o.get_state()
+    errs = {}
+    for prec in ("fp32", "fp32_plain"):
+        m = moc.Moc.from_problem(prob, precision=prec)
+        kg, ng, _, conv = m.power_iterate(1e-7, 1e-6, 20000, check_every=5)
+        assert conv
+        errs[prec] = (abs(kg - ko), _rel(m.get_state()[0], phio))
+    assert errs["fp32"][0] < 0.5 * PCM and errs["fp32"][1] < 1e-4, errs
+
+
+def test_checkpoint_resume_reproduces_iterates():
+    prob = W.small_lattice_problem(3)
+    a = moc.Moc.from_problem(prob, precision="fp64")
+    a.outer(7)
+    phi, k, psi = a.get_state(with_psi=True)
+    a.outer(5)
+    ref = a.get_state()
+    b = moc.Moc.from_problem(prob, precision="fp64")
+    b.set_state(phi, k, psi)
+    b.outer(5)
+    got = b.get_state()
+    assert abs(got[1] - ref[1]) < 1e-13
+    assert _rel(got[0], ref[0]) < 1e-11
+
+
+def test_edge_cases():
+    # two triangles, one group, one polar angle, vacuum: smallest problem
+    mesh = W.grid_mesh(1, 1, 1.0, 1.0, bc=(0, 0, 0, 0))
+    xs = W.CrossSections(np.array([[0.5]]), np.array([[0.9]]), np.array([[1.0]]), np.array([[[0.2]]]))
+    prob = W.Problem(mesh, xs, 4, 0.3, sin_theta=np.array([0.8]), polar_w=np.array([1.0]))
+    o = _oracle(prob)
+    m = moc.Moc.from_problem(prob, precision="fp64")
+    for _ in range(4):
+        o.outer(True)
+        m.outer(1)
+    assert abs(m.get_state()[1] - o.get_state()[1]) < 1e-13
+    # many groups (not a multiple of the padding), several polar angles, hexagonal mesh with gaps
+    mesh = W.hex_core_mesh(n_sub=4, n_rings=1)
+    xs = W.synthetic_xs(["fuel", "fuel", "coolant"], 33, 9, sigt_range=(0.05, 0.6))
+    prob = W.Problem(mesh, xs, 12, 0.3)
+    o = _oracle(prob)
+    m = moc.Moc.from_problem(prob, precision="fp64")
+    for _ in range(3):
+        o.outer(True)
+        m.outer(1)
+    assert _rel(m.get_state()[0], o.get_state()[0]) < 1e-11
+    # no ray crosses a tiny mesh in the corner of a big box -> geometry error, no crash
+    tiny = W.grid_mesh(1, 1, 1e-3, 1e-3, bc=(0, 0, 0, 0))
+    tiny.bbox = (0.0, 10.0, 0.0, 10.0)
+    mm = moc.Moc(0, "fp64")
+    mm.set_mesh(tiny)
+    mm.set_quadrature(4, 1.0, W.TY3_SIN_THETA, W.TY3_WEIGHT)
+    with pytest.raises(moc.MocError) as e:
+        mm.generate_tracks()
+    assert e.value.code == -7
+
+
+def test_status_codes_without_faults():
+    prob = W.small_lattice_problem(3)
+    m = moc.Moc.from_problem(prob, precision="fp64")
+    k, n, r, conv = m.power_iterate(1e-14, 1e-14, 4, check_every=2, raise_on_fail=False)
+    assert not conv and n == 4
+    # eigenvalue mode without any fission: the k update is not finite -> status, not a fault
+    xs = prob.xs
+    m.set_xs(W.CrossSections(xs.sigma_t, np.zeros_like(xs.nu_sigma_f), xs.chi, xs.sigma_s))
+    with pytest.raises(moc.MocError) as e:
+        m.power_iterate(1e-6, 1e-6, 4, check_every=1)
+    assert e.value.code == -6
+
+
+def test_fp32_exponential_exhaustive():
+    """Every FP32 tau in [0, 80]: relative error of the library's 1 - exp(-tau) against FP64."""
+    lo = 0
+    hi = int(np.array(80.0, np.float32).view(np.int32))
+    worst = 0.0
+    chunk = 1 << 24
+    for start in range(lo, hi + 1, chunk):
+        bits = np.arange(start, min(start + chunk, hi + 1), dtype=np.int32)
+        tau = bits.view(np.float32)
+        got = moc.eval_one_minus_exp_f32(tau).astype(np.float64)
+        ref = -np.expm1(-tau.astype(np.float64))
+        nz = ref > 0
+        err = np.abs(got[nz] - ref[nz]) / ref[nz]
+        worst = max(worst, float(err.max()))
+    # stated bound: 3 ulp of FP32 (2^-23 ~ 1.19e-7 per ulp)
+    assert worst < 3 * 2.0 ** -23, worst
+    print(f"max relative error of FP32 1-exp(-tau) over [0, 80]: {worst:.3e} ({worst / 2**-23:.2f} ulp)")
+
+
+def test_assembly_full_size_fp64_and_fp32():
+    """17x17 assembly at full size: 20 outers from the default state, GPU vs oracle."""
+    prob = W.assembly_problem()
+    o = _oracle(prob)
+    o.normalise()
+    for _ in range(20):
+        o.outer(True)
+    phio, ko = o.get_state()
+    for prec, tk, tf in (("fp64", 2 * PCM, 1e-5), ("fp32", 2 * PCM, 2e-4)):
+        m = moc.Moc.from_problem(prob, precision=prec)
+        m.outer(20)
+        phig, kg = m.get_state()
+        print(prec, "dk", kg - ko, "max rel flux err", _rel(phig, phio))
+        assert abs(kg - ko) <= tk
+        assert _rel(phig, phio) <= tf
