@@ -89,6 +89,23 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """Largest value of x over all ranks (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Units all replicas processed divided by the slowest rank's time."""
+    return units_per_rank * world / seconds_max
+
+
 def cpu_baseline(prob, outers: int = 2):
     """The oracle as it stands on the host cores: `outers` outers of the full workload."""
     import oracle
@@ -196,11 +213,8 @@ def main():
     with ClockSampler(local) as clk:
         ms = timed_steps(m, args.steps)
     torch.cuda.synchronize()
-    t = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{local}")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = ups * args.steps * world / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms, world, f"cuda:{local}")
+    value = whole_job_rate(ups * args.steps, world, ms_max / 1e3)
 
     # dominant kernel: the sweep, timed by CUDA events around each launch on its stream
     m.enable_timing(True)
@@ -238,10 +252,7 @@ def main():
         m.outer(1, read=False)
         m.get_state()
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device=f"cuda:{local}")
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = ups * args.steps * world / float(te.item())
+    e2e_value = whole_job_rate(ups * args.steps, world, max_over_ranks(e2e_s, world, f"cuda:{local}"))
 
     # FP64 mode on the same workload (context for the FP32 numbers)
     fp64 = None
