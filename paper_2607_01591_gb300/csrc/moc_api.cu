@@ -161,9 +161,14 @@ template <typename Real> int upload_tracks(moc_ctx *c) {
   c->inv.resize(T);
   for (int64_t i = 0; i < T; ++i) c->inv[c->perm[i]] = i;
   std::vector<TrackRec> trk(T);
-  std::vector<SegRec<Real>> seg(S);
+  // two padding records at each end: the sweep's two-ahead prefetch reads them unconditionally
+  std::vector<SegRec<Real>> seg(S + 4);
+  for (int q = 0; q < 2; ++q) {
+    seg[q] = SegRec<Real>{};
+    seg[S + 2 + q] = SegRec<Real>{};
+  }
   std::vector<int32_t> link(2 * T);
-  int64_t o = 0;
+  int64_t o = 2;
   for (int64_t i = 0; i < T; ++i) {
     int64_t t = c->perm[i];
     int64_t n = g.seg_off[t + 1] - g.seg_off[t];
@@ -323,8 +328,38 @@ template <typename Real, int TM> int launch_sweep_p(moc_ctx *c, cudaStream_t st)
   return MOC_OK;
 }
 
+template <int GPT, int NACT, int TM> void chunk_launch(moc_ctx *c, cudaStream_t st, int lanes) {
+  const long long n = (long long)c->T * 2 * lanes;
+  const int bs = 64;
+  sweep_chunk_kernel<3, GPT, NACT, TM><<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(
+      c->d_trk, (const SegRec<float> *)c->d_seg, c->d_link, (const float *)c->d_wgt, (const float *)c->d_inv_sin,
+      (const float2 *)c->d_xsq, (float *)c->d_tsum, (float *)c->d_tcomp, (const float *)c->d_psi[c->cur],
+      (float *)c->d_psi[c->cur ^ 1], c->d_scal, n, c->G, c->Gp, lanes);
+}
+
+// FP32 with 3 polar angles: one thread per (track end, chunk of groups); G <= 8 in one chunk
+template <int TM> int launch_chunk(moc_ctx *c, cudaStream_t st) {
+  const int G = c->G;
+  switch (G) {
+    case 1: chunk_launch<4, 1, TM>(c, st, 1); break;
+    case 2: chunk_launch<4, 2, TM>(c, st, 1); break;
+    case 3: chunk_launch<4, 3, TM>(c, st, 1); break;
+    case 4: chunk_launch<4, 4, TM>(c, st, 1); break;
+    case 5: chunk_launch<8, 5, TM>(c, st, 1); break;
+    case 6: chunk_launch<8, 6, TM>(c, st, 1); break;
+    case 7: chunk_launch<8, 7, TM>(c, st, 1); break;
+    case 8: chunk_launch<8, 8, TM>(c, st, 1); break;
+    default: chunk_launch<4, 4, TM>(c, st, (G + 3) / 4); break;
+  }
+  CUDA_TRY(c, cudaGetLastError());
+  return MOC_OK;
+}
+
 int launch_sweep(moc_ctx *c, cudaStream_t st) {
   if (c->precision == MOC_FP64) return launch_sweep_p<double, 0>(c, st);
+  // many groups: one thread per chunk of 4 groups shares the per-segment cost; few groups: one
+  // thread per group keeps each lane's serial chain along a long track short
+  if (c->P == 3 && c->G > 8) return c->precision == MOC_FP32 ? launch_chunk<1>(c, st) : launch_chunk<0>(c, st);
   if (c->precision == MOC_FP32) return launch_sweep_p<float, 1>(c, st);
   return launch_sweep_p<float, 0>(c, st);
 }

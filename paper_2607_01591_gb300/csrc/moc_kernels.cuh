@@ -116,28 +116,23 @@ template <typename Real> struct Tally<0, Real> {
   __device__ __forceinline__ void flush(Real *) {}
 };
 template <> struct Tally<1, float> {
+  // The old value returned by this segment's atomic is turned into its TwoSum error one segment
+  // later, so the atomic's latency overlaps the next segment's arithmetic. The first call
+  // flushes a zero error to a valid address, which keeps the loop free of branches.
   float old = 0.f, x = 0.f;
   size_t addr = 0;
-  bool pending = false;
-  // The returned old value of this add is used one segment later, so the atomic's latency is
-  // hidden behind the next segment's arithmetic.
   __device__ __forceinline__ void add(float *sum, float *comp, size_t a, float v) {
-    float o = atomicAdd(sum + a, v);
+    const float o = atomicAdd(sum + a, v);
     flush(comp);
     old = o;
     x = v;
     addr = a;
-    pending = true;
   }
   __device__ __forceinline__ void flush(float *comp) {
-    if (pending) {
-      // TwoSum (Knuth): s = old + x exactly as the atomic unit rounded it; err = (old + x) - s
-      float s = old + x;
-      float bb = s - old;
-      float err = (old - (s - bb)) + (x - bb);
-      atomicAdd(comp + addr, err);
-      pending = false;
-    }
+    // TwoSum (Knuth): s = old + x as the atomic unit rounded it; err = (old + x) - s exactly
+    const float sm = old + x;
+    const float bb = sm - old;
+    atomicAdd(comp + addr, (old - (sm - bb)) + (x - bb));
   }
 };
 
@@ -164,17 +159,19 @@ __global__ void __launch_bounds__(256) sweep_kernel(
     w[p] = wgt[tr.dir * P + p];
     is[p] = inv_sin[p];
   }
-  const long long step = d ? -1 : 1;
-  long long s = d ? tr.off + tr.n - 1 : tr.off;
+  const int step = d ? -1 : 1;
+  // the segment array has two padding records at each end, so the two-ahead prefetch below
+  // never needs a bounds test (records past a track's end belong to a neighbour or the padding)
+  const SegRec<Real> *sp = seg + (d ? tr.off + tr.n - 1 : tr.off);
   Tally<TM, Real> tally;
-  const int N = tr.n;
-  SegRec<Real> sg0 = seg[s];
-  SegRec<Real> sg1 = (N > 1) ? seg[s + step] : sg0;
-  typename Pair<Real>::T xq0 = xsq[(size_t)sg0.r * Gp + g];
-  for (int n = 0; n < N; ++n, s += step) {
-    SegRec<Real> sg2 = (n + 2 < N) ? seg[s + 2 * step] : sg1;
-    typename Pair<Real>::T xq1 = (n + 1 < N) ? xsq[(size_t)sg1.r * Gp + g] : xq0;
-    const Real tau0 = xq0.x * sg0.l;
+  SegRec<Real> s0 = sp[0], s1 = sp[step];
+  typename Pair<Real>::T xq0 = xsq[(size_t)s0.r * Gp + g];
+  if constexpr (TM == 1) tally.addr = (size_t)s0.r * Gp + g;
+#pragma unroll 2
+  for (int n = 0; n < tr.n; ++n) {
+    const SegRec<Real> s2 = sp[2 * step];
+    const typename Pair<Real>::T xq1 = xsq[(size_t)s1.r * Gp + g];
+    const Real tau0 = xq0.x * s0.l;
     Real acc = 0;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
@@ -183,16 +180,134 @@ __global__ void __launch_bounds__(256) sweep_kernel(
       psi[p] -= dl;
       acc = fma(w[p], dl, acc);
     }
-    tally.add(tsum, tcomp, (size_t)sg0.r * Gp + g, acc);
-    sg0 = sg1;
-    sg1 = sg2;
+    tally.add(tsum, tcomp, (size_t)s0.r * Gp + g, acc);
+    s0 = s1;
+    s1 = s2;
     xq0 = xq1;
+    sp += step;
   }
   tally.flush(tcomp);
   const int e = link[td];
   if (e >= 0) {
 #pragma unroll
     for (int p = 0; p < P; ++p) psi_out[((long long)e * P + p) * G + g] = psi[p];
+  }
+}
+
+// FP32 sweep, one thread per (track, sense, chunk of GPT groups); the first NACT groups of the
+// chunk are computed (NACT < GPT only when G itself is smaller than the chunk, e.g. 7 of 8).
+// Region rows are read as GPT/2 128-bit loads of {Sigma_t, q/Sigma_t} pairs and the tallies are
+// added with GPT/4 float4 atomics, so the per-segment cost (segment record, addresses, loop,
+// atomics) is shared by P * NACT updates. The segment array carries two padding records at each
+// end, so the two-ahead prefetch never needs a bounds test.
+// TwoSum (Knuth): the exact rounding error (old + x) - fl(old + x) of each lane, where fl is the
+// round-to-nearest sum the atomic unit stored.
+__device__ __forceinline__ float4 two_sum_err(float4 o, float4 x) {
+  float4 e;
+  { const float sm = o.x + x.x, bb = sm - o.x; e.x = (o.x - (sm - bb)) + (x.x - bb); }
+  { const float sm = o.y + x.y, bb = sm - o.y; e.y = (o.y - (sm - bb)) + (x.y - bb); }
+  { const float sm = o.z + x.z, bb = sm - o.z; e.z = (o.z - (sm - bb)) + (x.z - bb); }
+  { const float sm = o.w + x.w, bb = sm - o.w; e.w = (o.w - (sm - bb)) + (x.w - bb); }
+  return e;
+}
+
+template <int GPT> struct Row {
+  float4 v[GPT / 2];
+};
+
+template <int P, int GPT, int NACT, int TM>
+__global__ void __launch_bounds__(64) sweep_chunk_kernel(
+    const TrackRec *__restrict__ trk, const SegRec<float> *__restrict__ seg, const int32_t *__restrict__ link,
+    const float *__restrict__ wgt, const float *__restrict__ inv_sin, const float2 *__restrict__ xsq,
+    float *__restrict__ tsum, float *__restrict__ tcomp, const float *__restrict__ psi_in,
+    float *__restrict__ psi_out, const double *__restrict__ scal, long long n_threads, int G, int Gp, int lanes) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n_threads) return;
+  const long long td = idx / lanes;
+  const int g0 = (int)(idx - td * lanes) * GPT;
+  const TrackRec tr = trk[td >> 1];
+  const int d = (int)(td & 1);
+  const float scale = (float)scal[S_SCALE];
+  float psi[NACT][P], w[P], is[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    w[p] = wgt[tr.dir * P + p];
+    is[p] = inv_sin[p];
+#pragma unroll
+    for (int k = 0; k < NACT; ++k)
+      psi[k][p] = (g0 + k < G) ? psi_in[(td * P + p) * G + g0 + k] * scale : 0.0f;
+  }
+  const int step = d ? -1 : 1;
+  const SegRec<float> *sp = seg + (d ? tr.off + tr.n - 1 : tr.off);
+  const float4 *rows = reinterpret_cast<const float4 *>(xsq + g0);
+  const int rstride = Gp / 2;  // float4 per region row
+  SegRec<float> s0 = sp[0], s1 = sp[step];
+  Row<GPT> r0, r1;
+#pragma unroll
+  for (int q = 0; q < GPT / 2; ++q) r0.v[q] = rows[(size_t)s0.r * rstride + q];
+  float4 *tsum4 = reinterpret_cast<float4 *>(tsum + g0);
+  float4 *tcomp4 = reinterpret_cast<float4 *>(tcomp + g0);
+  const int tstride = Gp / 4;
+  // compensated mode: the old values returned by this segment's atomics are turned into TwoSum
+  // errors one segment later, so the atomics' latency overlaps the next segment's arithmetic
+  float4 p_old[GPT / 4], p_x[GPT / 4];
+  size_t p_a = (size_t)s0.r * tstride;
+#pragma unroll
+  for (int q = 0; q < GPT / 4; ++q) {
+    p_old[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    p_x[q] = p_old[q];
+  }
+  for (int n = 0; n < tr.n; ++n) {
+    const SegRec<float> s2 = sp[2 * step];
+#pragma unroll
+    for (int q = 0; q < GPT / 2; ++q) r1.v[q] = rows[(size_t)s1.r * rstride + q];
+    float acc[GPT];
+#pragma unroll
+    for (int k = 0; k < GPT; ++k) acc[k] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < NACT; ++k) {
+      const float4 pr = r0.v[k / 2];
+      const float sig = (k & 1) ? pr.z : pr.x;
+      const float qr = (k & 1) ? pr.w : pr.y;
+      const float tau0 = sig * s0.l;
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const float F = one_minus_exp(tau0 * is[p]);
+        const float dl = (psi[k][p] - qr) * F;
+        psi[k][p] -= dl;
+        acc[k] = fmaf(w[p], dl, acc[k]);
+      }
+    }
+    const size_t a = (size_t)s0.r * tstride;
+#pragma unroll
+    for (int q = 0; q < GPT / 4; ++q) {
+      const float4 x = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+      if (TM == 1) {
+        const float4 o = atomicAdd(tsum4 + a + q, x);
+        atomicAdd(tcomp4 + p_a + q, two_sum_err(p_old[q], p_x[q]));
+        p_old[q] = o;
+        p_x[q] = x;
+      } else {
+        atomicAdd(tsum4 + a + q, x);
+      }
+    }
+    p_a = a;
+    s0 = s1;
+    s1 = s2;
+    r0 = r1;
+    sp += step;
+  }
+  if (TM == 1) {
+#pragma unroll
+    for (int q = 0; q < GPT / 4; ++q) atomicAdd(tcomp4 + p_a + q, two_sum_err(p_old[q], p_x[q]));
+  }
+  const int e = link[td];
+  if (e >= 0) {
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+#pragma unroll
+      for (int k = 0; k < NACT; ++k)
+        if (g0 + k < G) psi_out[((long long)e * P + p) * G + g0 + k] = psi[k][p];
   }
 }
 
