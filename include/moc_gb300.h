@@ -166,6 +166,24 @@ int moc_get_timing(moc_ctx *ctx, double *sweep_ms_total, int64_t *n_sweeps);
 int moc_get_work(const moc_ctx *ctx, int64_t *n_segments, int64_t *updates_per_sweep,
                  int *kernels_per_outer);
 
+/* Learned warm start, context side (the network itself is in moc_mlp.h). The paper has no
+ * counterpart; the cold start (flat flux, k = 1, zero boundary flux) remains the fallback.
+ *
+ * moc_ws_features: per-region network inputs feat_dev [n_tri][3 G + n_geo + n_glob] =
+ * (Sigma_t, nu Sigma_f, Sigma_a of the region's material) ++ geo_dev row ++ glob, built on the
+ * device from the cross sections set by moc_set_xs. geo_dev: device [n_tri][n_geo] (may be NULL
+ * when n_geo = 0); glob: host [n_glob]; feat_dev: device, caller-owned. Enqueued on the context's
+ * stream.
+ *
+ * moc_ws_apply: set the iterate from a prediction pred_dev [n_tri][G + 1] (device): phi = exp of
+ * the first G columns, k = area-weighted mean of the last column, incoming boundary flux of every
+ * linked track end = phi of the region at that end / (4 pi) for all polar angles, vacuum ends
+ * zero; then normalised as moc_set_state does. Enqueued on the context's stream; k_out (may be
+ * NULL) synchronises. Errors: MOC_ERR_STATE (no tracks/XS), MOC_ERR_ARG. */
+int moc_ws_features(moc_ctx *ctx, const float *geo_dev, int n_geo, const float *glob, int n_glob,
+                    float *feat_dev);
+int moc_ws_apply(moc_ctx *ctx, const float *pred_dev, double *k_out);
+
 /* Evaluate the library's FP32 1 - exp(-tau) (the one the FP32 sweep uses) for n host values
  * tau[i] >= 0 into out[i], on device `device`. Host buffers; synchronous. For checking the
  * approximation error against an FP64 reference. Errors: MOC_ERR_ARG, MOC_ERR_CUDA. */

@@ -19,7 +19,7 @@ OUT_DIR = os.path.join(HERE, "_lib")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmoc_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["moc_api.cu", "moc_geom.cpp"]
+SOURCES = ["moc_api.cu", "moc_mlp.cu", "moc_geom.cpp"]
 HEADERS = ["moc_kernels.cuh", "moc_geom.h", "exp_f32_coef.h"]
 
 
@@ -34,7 +34,7 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(INC, "moc_gb300.h")]
+    deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(INC, h) for h in os.listdir(INC)]
     return any(os.path.getmtime(d) > t for d in deps)
 
 

@@ -33,6 +33,7 @@ struct moc_ctx {
   void *d_seg = nullptr;
   TrackRec *d_trk = nullptr;
   int32_t *d_link = nullptr;
+  uint8_t *d_fed = nullptr;  // per internal track end: 1 if some outgoing end feeds it
   void *d_wgt = nullptr, *d_inv_sin = nullptr;
   int32_t *d_mat = nullptr;
   double *d_area = nullptr;
@@ -111,6 +112,7 @@ void free_tracks(moc_ctx *c) {
   dfree(c->d_seg);
   dfree(c->d_trk);
   dfree(c->d_link);
+  dfree(c->d_fed);
   dfree(c->d_wgt);
   dfree(c->d_inv_sin);
   dfree(c->d_mat);
@@ -161,14 +163,10 @@ template <typename Real> int upload_tracks(moc_ctx *c) {
   c->inv.resize(T);
   for (int64_t i = 0; i < T; ++i) c->inv[c->perm[i]] = i;
   std::vector<TrackRec> trk(T);
-  // two padding records at each end: the sweep's two-ahead prefetch reads them unconditionally
-  std::vector<SegRec<Real>> seg(S + 4);
-  for (int q = 0; q < 2; ++q) {
-    seg[q] = SegRec<Real>{};
-    seg[S + 2 + q] = SegRec<Real>{};
-  }
+  // kSegPad padding records at each end: the sweep's prefetch reads them unconditionally
+  std::vector<SegRec<Real>> seg(S + 2 * kSegPad, SegRec<Real>{});
   std::vector<int32_t> link(2 * T);
-  int64_t o = 2;
+  int64_t o = kSegPad;
   for (int64_t i = 0; i < T; ++i) {
     int64_t t = c->perm[i];
     int64_t n = g.seg_off[t + 1] - g.seg_off[t];
@@ -199,6 +197,10 @@ template <typename Real> int upload_tracks(moc_ctx *c) {
   c->d_seg = ds;
   if ((rc = upload(c, c->d_trk, trk.data(), trk.size()))) return rc;
   if ((rc = upload(c, c->d_link, link.data(), link.size()))) return rc;
+  std::vector<uint8_t> fed(2 * T, 0);
+  for (int32_t e : link)
+    if (e >= 0) fed[e] = 1;
+  if ((rc = upload(c, c->d_fed, fed.data(), fed.size()))) return rc;
   Real *dw = nullptr, *di = nullptr;
   if ((rc = upload(c, dw, wgt.data(), wgt.size()))) return rc;
   c->d_wgt = dw;
@@ -256,7 +258,7 @@ template <typename Real> int upload_xs(moc_ctx *c, int n_mat, int G, const doubl
   }
   CUDA_TRY(c, cudaMalloc(&c->d_fold, (size_t)R * sizeof(double)));
   CUDA_TRY(c, cudaMemsetAsync(c->d_fold, 0, (size_t)R * sizeof(double), c->stream));
-  const int nb = (R + 255) / 256;
+  const int nb = (R + 31) / 32;  // enough block partials for either finalize variant
   CUDA_TRY(c, cudaMalloc(&c->d_part, (size_t)nb * 4 * sizeof(double)));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   c->xs_set = true;
@@ -366,6 +368,24 @@ int launch_sweep(moc_ctx *c, cudaStream_t st) {
 
 template <typename Real> int launch_finalize_reduce(moc_ctx *c, cudaStream_t st) {
   const int R = c->geo.n_tri;
+  if (c->Gp == 8) {
+    // 8 lanes per region, 32 regions per block of 256 threads
+    const int nb8 = (R + 31) / 32;
+    if (tally_mode(c) == 1)
+      finalize8_kernel<Real, 1><<<nb8, 256, 0, st>>>(R, c->G, c->d_mat, (const Real *)c->d_nsf, c->d_area,
+                                                     (const typename Pair<Real>::T *)c->d_xsq, (Real *)c->d_tsum,
+                                                     (Real *)c->d_tcomp, (Real *)c->d_phi, c->d_fold, c->d_part,
+                                                     c->eigen ? 1 : 0);
+    else
+      finalize8_kernel<Real, 0><<<nb8, 256, 0, st>>>(R, c->G, c->d_mat, (const Real *)c->d_nsf, c->d_area,
+                                                     (const typename Pair<Real>::T *)c->d_xsq, (Real *)c->d_tsum,
+                                                     (Real *)c->d_tcomp, (Real *)c->d_phi, c->d_fold, c->d_part,
+                                                     c->eigen ? 1 : 0);
+    CUDA_TRY(c, cudaGetLastError());
+    reduce_kernel<<<1, 256, 0, st>>>(nb8, c->d_part, c->d_scal, c->eigen ? 1 : 0);
+    CUDA_TRY(c, cudaGetLastError());
+    return MOC_OK;
+  }
   const int nb = (R + 255) / 256;
   if (tally_mode(c) == 1)
     finalize_kernel<Real, 1><<<nb, 256, 0, st>>>(R, c->G, c->Gp, c->d_mat, (const Real *)c->d_nsf, c->d_area,
@@ -809,6 +829,79 @@ int moc_get_work(const moc_ctx *c, int64_t *n_segments, int64_t *updates, int *k
   if (n_segments) *n_segments = c->geo.n_segments();
   if (updates) *updates = 2 * c->geo.n_segments() * (int64_t)c->geo.n_polar * (int64_t)std::max(c->G, 0);
   if (kernels) *kernels = 4;
+  return MOC_OK;
+}
+
+}  // extern "C"
+
+namespace {
+template <typename Real> int ws_features_t(moc_ctx *c, const float *geo, int n_geo, const float *glob_dev, int n_glob,
+                                          float *feat) {
+  const int R = c->geo.n_tri;
+  ws_features_kernel<Real><<<(R + 255) / 256, 256, 0, c->stream>>>(R, c->G, n_geo, n_glob, c->d_mat,
+                                                                   (const Real *)c->d_sig_t, (const Real *)c->d_nsf,
+                                                                   (const Real *)c->d_sig_s, geo, glob_dev, feat);
+  CUDA_TRY(c, cudaGetLastError());
+  return MOC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int moc_ws_features(moc_ctx *c, const float *geo, int n_geo, const float *glob, int n_glob, float *feat) {
+  int rc = need_ready(c);
+  if (rc) return rc;
+  if (n_geo < 0 || n_glob < 0 || (n_geo > 0 && !geo) || (n_glob > 0 && !glob) || !feat)
+    return fail(c, MOC_ERR_ARG, "ws_features: bad arguments");
+  cudaSetDevice(c->device);
+  float *dglob = nullptr;
+  CUDA_TRY(c, cudaMalloc(&dglob, std::max(n_glob, 1) * sizeof(float)));
+  if (n_glob) CUDA_TRY(c, cudaMemcpyAsync(dglob, glob, n_glob * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  rc = c->precision == MOC_FP64 ? ws_features_t<double>(c, geo, n_geo, dglob, n_glob, feat)
+                                : ws_features_t<float>(c, geo, n_geo, dglob, n_glob, feat);
+  cudaStreamSynchronize(c->stream);
+  cudaFree(dglob);
+  return rc;
+}
+
+}  // extern "C"
+
+namespace {
+template <typename Real> int ws_apply_t(moc_ctx *c, const float *pred) {
+  const int R = c->geo.n_tri;
+  const int nb = (R + 255) / 256;
+  ws_apply_kernel<Real><<<nb, 256, 0, c->stream>>>(R, c->G, c->Gp, c->d_mat, (const Real *)c->d_nsf, c->d_area,
+                                                   pred, (Real *)c->d_phi, c->d_part);
+  CUDA_TRY(c, cudaGetLastError());
+  ws_reduce_kernel<<<1, 256, 0, c->stream>>>(nb, c->d_part, c->d_scal);
+  CUDA_TRY(c, cudaGetLastError());
+  const long long n = (long long)c->T * 2 * c->G;
+  ws_psi_kernel<Real><<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
+      n, c->P, c->G, c->Gp, c->d_trk, (const SegRec<Real> *)c->d_seg, c->d_fed, (const Real *)c->d_phi,
+      (Real *)c->d_psi[c->cur]);
+  CUDA_TRY(c, cudaGetLastError());
+  return MOC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int moc_ws_apply(moc_ctx *c, const float *pred, double *k_out) {
+  int rc = need_ready(c);
+  if (rc) return rc;
+  if (!pred) return fail(c, MOC_ERR_ARG, "ws_apply: NULL prediction");
+  if (!c->eigen) return fail(c, MOC_ERR_STATE, "ws_apply: eigenvalue mode only");
+  cudaSetDevice(c->device);
+  rc = c->precision == MOC_FP64 ? ws_apply_t<double>(c, pred) : ws_apply_t<float>(c, pred);
+  if (rc) return rc;
+  if (k_out) {
+    double s[S_COUNT];
+    if ((rc = read_scalars(c, s))) return rc;
+    *k_out = s[S_K];
+    if (s[S_STATUS] != 0.0) return fail(c, MOC_ERR_NONFINITE, "ws_apply: predicted k or flux not finite/positive");
+  }
   return MOC_OK;
 }
 

@@ -17,6 +17,7 @@
 namespace moc {
 
 constexpr double kFourPi = 12.566370614359172953850;
+constexpr int kSegPad = 4;  // padding records at each end of the segment array
 
 // scalar slots in device memory (double)
 enum Scal { S_K = 0, S_SCALE = 1, S_RESID = 2, S_FISS = 3, S_KPREV = 4, S_STATUS = 5, S_NOUTER = 6, S_COUNT = 8 };
@@ -116,23 +117,31 @@ template <typename Real> struct Tally<0, Real> {
   __device__ __forceinline__ void flush(Real *) {}
 };
 template <> struct Tally<1, float> {
-  // The old value returned by this segment's atomic is turned into its TwoSum error one segment
-  // later, so the atomic's latency overlaps the next segment's arithmetic. The first call
-  // flushes a zero error to a valid address, which keeps the loop free of branches.
-  float old = 0.f, x = 0.f;
-  size_t addr = 0;
+  // The old value returned by a segment's atomic is turned into its TwoSum error two segments
+  // later, so the atomic's round trip overlaps two segments of arithmetic. Both pending slots
+  // start as zero errors aimed at a valid address, which keeps the loop free of branches.
+  float oldA = 0.f, xA = 0.f, oldB = 0.f, xB = 0.f;
+  size_t aA = 0, aB = 0;
+  __device__ __forceinline__ static float err(float o, float x) {
+    // TwoSum (Knuth): s = o + x as the atomic unit rounded it; returns (o + x) - s exactly
+    const float sm = o + x;
+    const float bb = sm - o;
+    return (o - (sm - bb)) + (x - bb);
+  }
+  __device__ __forceinline__ void init(size_t a) { aA = aB = a; }
   __device__ __forceinline__ void add(float *sum, float *comp, size_t a, float v) {
     const float o = atomicAdd(sum + a, v);
-    flush(comp);
-    old = o;
-    x = v;
-    addr = a;
+    atomicAdd(comp + aB, err(oldB, xB));
+    oldB = oldA;
+    xB = xA;
+    aB = aA;
+    oldA = o;
+    xA = v;
+    aA = a;
   }
   __device__ __forceinline__ void flush(float *comp) {
-    // TwoSum (Knuth): s = old + x as the atomic unit rounded it; err = (old + x) - s exactly
-    const float sm = old + x;
-    const float bb = sm - old;
-    atomicAdd(comp + addr, (old - (sm - bb)) + (x - bb));
+    atomicAdd(comp + aB, err(oldB, xB));
+    atomicAdd(comp + aA, err(oldA, xA));
   }
 };
 
@@ -160,17 +169,18 @@ __global__ void __launch_bounds__(256) sweep_kernel(
     is[p] = inv_sin[p];
   }
   const int step = d ? -1 : 1;
-  // the segment array has two padding records at each end, so the two-ahead prefetch below
+  // the segment array has kSegPad padding records at each end, so the three-ahead prefetch below
   // never needs a bounds test (records past a track's end belong to a neighbour or the padding)
   const SegRec<Real> *sp = seg + (d ? tr.off + tr.n - 1 : tr.off);
   Tally<TM, Real> tally;
-  SegRec<Real> s0 = sp[0], s1 = sp[step];
+  SegRec<Real> s0 = sp[0], s1 = sp[step], s2 = sp[2 * step];
   typename Pair<Real>::T xq0 = xsq[(size_t)s0.r * Gp + g];
-  if constexpr (TM == 1) tally.addr = (size_t)s0.r * Gp + g;
+  typename Pair<Real>::T xq1 = xsq[(size_t)s1.r * Gp + g];
+  if constexpr (TM == 1) tally.init((size_t)s0.r * Gp + g);
 #pragma unroll 2
   for (int n = 0; n < tr.n; ++n) {
-    const SegRec<Real> s2 = sp[2 * step];
-    const typename Pair<Real>::T xq1 = xsq[(size_t)s1.r * Gp + g];
+    const SegRec<Real> s3 = sp[3 * step];
+    const typename Pair<Real>::T xq2 = xsq[(size_t)s2.r * Gp + g];
     const Real tau0 = xq0.x * s0.l;
     Real acc = 0;
 #pragma unroll
@@ -183,7 +193,9 @@ __global__ void __launch_bounds__(256) sweep_kernel(
     tally.add(tsum, tcomp, (size_t)s0.r * Gp + g, acc);
     s0 = s1;
     s1 = s2;
+    s2 = s3;
     xq0 = xq1;
+    xq1 = xq2;
     sp += step;
   }
   tally.flush(tcomp);
@@ -198,7 +210,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(
 // chunk are computed (NACT < GPT only when G itself is smaller than the chunk, e.g. 7 of 8).
 // Region rows are read as GPT/2 128-bit loads of {Sigma_t, q/Sigma_t} pairs and the tallies are
 // added with GPT/4 float4 atomics, so the per-segment cost (segment record, addresses, loop,
-// atomics) is shared by P * NACT updates. The segment array carries two padding records at each
+// atomics) is shared by P * NACT updates. The segment array carries kSegPad padding records at each
 // end, so the two-ahead prefetch never needs a bounds test.
 // TwoSum (Knuth): the exact rounding error (old + x) - fl(old + x) of each lane, where fl is the
 // round-to-nearest sum the atomic unit stored.
@@ -375,6 +387,80 @@ __global__ void __launch_bounds__(256) finalize_kernel(
   }
 }
 
+// Group-parallel variant for Gp = 8: 8 consecutive threads own one region (coalesced row
+// accesses); the region's fission rate is reduced across its 8 lanes with shuffles.
+template <typename Real, int TM>
+__global__ void __launch_bounds__(256) finalize8_kernel(
+    int R, int G, const int32_t *__restrict__ mat, const Real *__restrict__ nsf, const double *__restrict__ area,
+    const typename Pair<Real>::T *__restrict__ xsq, Real *__restrict__ tsum, Real *__restrict__ tcomp,
+    Real *__restrict__ phi, const double *__restrict__ fold, double *__restrict__ part, int eigen) {
+  __shared__ double s_sum[32], s_min[32], s_max[32], s_res[32];
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = tid >> 3, g = tid & 7;
+  const bool live = r < R;
+  double f = 0.0, res = 0.0, A = 0.0;
+  if (live) {
+    A = area[r];
+    const size_t a = (size_t)r * 8 + g;
+    const typename Pair<Real>::T v = xsq[a];
+    double t = (double)tsum[a];
+    tsum[a] = (Real)0;
+    if (TM == 1) {
+      t += (double)tcomp[a];
+      tcomp[a] = (Real)0;
+    }
+    if (g < G) {
+      double ph = kFourPi * (double)v.y;
+      if (A > 0.0) ph += t / ((double)v.x * A);
+      if (!eigen) {
+        const double old = (double)phi[a];
+        if (ph > 0.0) res = fabs(ph - old) / ph;
+      }
+      phi[a] = (Real)ph;
+      f = (double)nsf[mat[r] * G + g] * (double)(Real)ph;
+    }
+  }
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) {
+    f += __shfl_xor_sync(0xffffffffu, f, o);
+    res = fmax(res, __shfl_xor_sync(0xffffffffu, res, o));
+  }
+  double fsum = 0.0, rmin = INFINITY, rmax = -INFINITY;
+  if (live && g == 0) {
+    fsum = A * f;
+    if (eigen && f > 0.0) rmin = rmax = fold[r] / f;
+  }
+  // warp then block reduction (fixed order)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    fsum += __shfl_xor_sync(0xffffffffu, fsum, o);
+    rmin = fmin(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
+    rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    res = fmax(res, __shfl_xor_sync(0xffffffffu, res, o));
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    s_sum[w] = fsum;
+    s_min[w] = rmin;
+    s_max[w] = rmax;
+    s_res[w] = res;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, mn = INFINITY, mx = -INFINITY, rs = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      a += s_sum[k];
+      mn = fmin(mn, s_min[k]);
+      mx = fmax(mx, s_max[k]);
+      rs = fmax(rs, s_res[k]);
+    }
+    part[4 * blockIdx.x + 0] = a;
+    part[4 * blockIdx.x + 1] = mn;
+    part[4 * blockIdx.x + 2] = mx;
+    part[4 * blockIdx.x + 3] = rs;
+  }
+}
+
 // ----------------------------------------------------------------------------- reduce
 // One block of 256 threads, fixed reduction order (deterministic). k' = k F' (the flux the
 // source was built from is normalised to F = 1); scale = 1/F'; residual
@@ -424,6 +510,124 @@ __global__ void __launch_bounds__(256) reduce_kernel(int nb, const double *__res
     }
     scal[S_NOUTER] += 1.0;
   }
+}
+
+// ----------------------------------------------------------------------------- warm start
+// features: (Sigma_t, nuSigma_f, Sigma_a) of the region's material, geometry row, global vector
+template <typename Real>
+__global__ void ws_features_kernel(int R, int G, int n_geo, int n_glob, const int32_t *__restrict__ mat,
+                                   const Real *__restrict__ sig_t, const Real *__restrict__ nsf,
+                                   const Real *__restrict__ sig_s, const float *__restrict__ geo,
+                                   const float *__restrict__ glob, float *__restrict__ feat) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  const int m = mat[r];
+  const int nf = 3 * G + n_geo + n_glob;
+  float *f = feat + (size_t)r * nf;
+  for (int g = 0; g < G; ++g) {
+    double out = 0.0;
+    for (int h = 0; h < G; ++h) out += (double)sig_s[((size_t)m * G + g) * G + h];
+    f[g] = (float)sig_t[m * G + g];
+    f[G + g] = (float)nsf[m * G + g];
+    f[2 * G + g] = (float)((double)sig_t[m * G + g] - out);
+  }
+  for (int j = 0; j < n_geo; ++j) f[3 * G + j] = geo[(size_t)r * n_geo + j];
+  for (int j = 0; j < n_glob; ++j) f[3 * G + n_geo + j] = glob[j];
+}
+
+// phi = exp(pred[:, :G]); block partials of sum A f(phi), sum A pred[:, G], sum A
+template <typename Real>
+__global__ void __launch_bounds__(256) ws_apply_kernel(int R, int G, int Gp, const int32_t *__restrict__ mat,
+                                                       const Real *__restrict__ nsf, const double *__restrict__ area,
+                                                       const float *__restrict__ pred, Real *__restrict__ phi,
+                                                       double *__restrict__ part) {
+  __shared__ double s0[256], s1[256], s2[256];
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  double a = 0.0, b = 0.0, c = 0.0;
+  if (r < R) {
+    const int m = mat[r];
+    const double A = area[r];
+    double f = 0.0;
+    for (int g = 0; g < G; ++g) {
+      const Real v = (Real)exp((double)pred[(size_t)r * (G + 1) + g]);
+      phi[(size_t)r * Gp + g] = v;
+      f += (double)nsf[m * G + g] * (double)v;
+    }
+    a = A * f;
+    b = A * (double)pred[(size_t)r * (G + 1) + G];
+    c = A;
+  }
+  s0[threadIdx.x] = a;
+  s1[threadIdx.x] = b;
+  s2[threadIdx.x] = c;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) {
+      s0[threadIdx.x] += s0[threadIdx.x + k];
+      s1[threadIdx.x] += s1[threadIdx.x + k];
+      s2[threadIdx.x] += s2[threadIdx.x + k];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[4 * blockIdx.x + 0] = s0[0];
+    part[4 * blockIdx.x + 1] = s1[0];
+    part[4 * blockIdx.x + 2] = s2[0];
+    part[4 * blockIdx.x + 3] = 0.0;
+  }
+}
+
+// one block: F, area-weighted mean k; scalars reset for a fresh iteration
+__global__ void __launch_bounds__(256) ws_reduce_kernel(int nb, const double *__restrict__ part,
+                                                        double *__restrict__ scal) {
+  __shared__ double s0[256], s1[256], s2[256];
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    a += part[4 * i];
+    b += part[4 * i + 1];
+    c += part[4 * i + 2];
+  }
+  s0[threadIdx.x] = a;
+  s1[threadIdx.x] = b;
+  s2[threadIdx.x] = c;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) {
+      s0[threadIdx.x] += s0[threadIdx.x + k];
+      s1[threadIdx.x] += s1[threadIdx.x + k];
+      s2[threadIdx.x] += s2[threadIdx.x + k];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double F = s0[0];
+    const double k = s1[0] / s2[0];
+    scal[S_K] = k;
+    scal[S_KPREV] = k;
+    scal[S_SCALE] = (F > 0.0) ? 1.0 / F : 1.0;
+    scal[S_FISS] = F;
+    scal[S_RESID] = INFINITY;
+    scal[S_STATUS] = (isfinite(k) && k > 0.0 && isfinite(F)) ? 0.0 : 1.0;
+  }
+}
+
+// incoming boundary flux of each linked end (t, d) = phi(region at that end) / (4 pi)
+template <typename Real>
+__global__ void ws_psi_kernel(long long n, int P, int G, int Gp, const TrackRec *__restrict__ trk,
+                              const SegRec<Real> *__restrict__ seg, const uint8_t *__restrict__ fed,
+                              const Real *__restrict__ phi, Real *__restrict__ psi) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const long long td = idx / G;
+  const int g = (int)(idx - td * G);
+  const TrackRec tr = trk[td >> 1];
+  const int d = (int)(td & 1);
+  Real v = 0;
+  if (fed[td]) {
+    const int r = seg[d ? tr.off + tr.n - 1 : tr.off].r;
+    v = phi[(size_t)r * Gp + g] * (Real)(1.0 / kFourPi);
+  }
+  for (int p = 0; p < P; ++p) psi[(td * P + p) * G + g] = v;
 }
 
 }  // namespace moc

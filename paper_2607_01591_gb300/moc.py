@@ -16,7 +16,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libmoc_gb300.so")
-HEADER = os.path.join(os.path.dirname(HERE), "include", "moc_gb300.h")
+INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 MOC_FP64, MOC_FP32, MOC_FP32_PLAIN = 0, 1, 2
 PRECISIONS = {"fp64": MOC_FP64, "fp32": MOC_FP32, "fp32_plain": MOC_FP32_PLAIN}
@@ -38,9 +38,13 @@ class MocError(RuntimeError):
 
 
 def header_symbols() -> list:
-    """Names of the functions declared in include/moc_gb300.h."""
-    txt = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:int|void|const char \*)\s*\*?\s*(moc_\w+)\s*\(", txt, re.M)))
+    """Names of the functions declared in include/*.h."""
+    names = set()
+    for h in sorted(os.listdir(INCLUDE)):
+        if h.endswith(".h"):
+            txt = open(os.path.join(INCLUDE, h)).read()
+            names |= set(re.findall(r"^\s*(?:int|void|const char \*)\s*\*?\s*(moc_\w+)\s*\(", txt, re.M))
+    return sorted(names)
 
 
 def load_library(path: Optional[str] = None):
@@ -77,6 +81,21 @@ def load_library(path: Optional[str] = None):
             "moc_get_timing": (ctypes.c_int, [_vp, _d, _i64]),
             "moc_get_work": (ctypes.c_int, [_vp, _i64, _i64, ctypes.POINTER(ctypes.c_int)]),
             "moc_synchronize": (ctypes.c_int, [_vp]),
+            "moc_ws_features": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.c_int, _vp]),
+            "moc_ws_apply": (ctypes.c_int, [_vp, _vp, _d]),
+            "moc_mlp_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_int, ctypes.c_uint64]),
+            "moc_mlp_destroy": (None, [_vp]),
+            "moc_mlp_last_error": (ctypes.c_char_p, [_vp]),
+            "moc_mlp_dims": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), _i64]),
+            "moc_mlp_get_params": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float)]),
+            "moc_mlp_set_params": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float)]),
+            "moc_mlp_set_normalization": (ctypes.c_int, [_vp] + [ctypes.POINTER(ctypes.c_float)] * 4),
+            "moc_mlp_forward": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, _vp]),
+            "moc_mlp_train_step": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_float,
+                                                  ctypes.POINTER(ctypes.c_float), _vp]),
+            "moc_mlp_gradients": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_float),
+                                                 ctypes.POINTER(ctypes.c_float), _vp]),
             "moc_eval_one_minus_exp_f32": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_float),
                                                           ctypes.POINTER(ctypes.c_float), ctypes.c_int64]),
         }
@@ -99,6 +118,80 @@ def _f64(a):
 
 def _i32a(a):
     return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _ptr(x) -> int:
+    """Device address of a torch tensor (or an int address)."""
+    return int(x.data_ptr()) if hasattr(x, "data_ptr") else int(x)
+
+
+class Mlp:
+    """The warm-start network of include/moc_mlp.h (bf16 weights, FP32 accumulate, Adam)."""
+
+    def __init__(self, n_in: int, width: int = 256, n_out: int = 8, seed: int = 0, device: int = 0):
+        self._lib = load_library()
+        h = _vp()
+        rc = self._lib.moc_mlp_create(ctypes.byref(h), int(device), int(n_in), int(width), int(n_out), int(seed))
+        if rc != 0:
+            raise MocError(rc, "moc_mlp_create failed")
+        self._h = h
+        dims = (ctypes.c_int * 5)()
+        npar = ctypes.c_int64()
+        self._lib.moc_mlp_dims(h, dims, ctypes.byref(npar))
+        self.dims = list(dims)
+        self.n_params = npar.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.moc_mlp_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != 0:
+            raise MocError(rc, self._lib.moc_mlp_last_error(self._h).decode())
+
+    @staticmethod
+    def _fp(a):
+        return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+    def get_params(self) -> np.ndarray:
+        p = np.zeros(self.n_params, np.float32)
+        self._check(self._lib.moc_mlp_get_params(self._h, self._fp(p)))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.n_params
+        self._check(self._lib.moc_mlp_set_params(self._h, self._fp(p)))
+
+    def set_normalization(self, in_mean, in_std, out_mean, out_std):
+        a = [np.ascontiguousarray(v, dtype=np.float32) for v in (in_mean, in_std, out_mean, out_std)]
+        self.norm = a
+        self._check(self._lib.moc_mlp_set_normalization(self._h, *[self._fp(v) for v in a]))
+
+    def forward(self, x, y, n: int, stream=None):
+        self._check(self._lib.moc_mlp_forward(self._h, _vp(_ptr(x)), _vp(_ptr(y)), int(n),
+                                              None if stream is None else _vp(stream)))
+
+    def train_step(self, x, y, n: int, lr: float, stream=None, want_loss: bool = False):
+        loss = ctypes.c_float()
+        self._check(self._lib.moc_mlp_train_step(self._h, _vp(_ptr(x)), _vp(_ptr(y)), int(n), float(lr),
+                                                 ctypes.byref(loss) if want_loss else None,
+                                                 None if stream is None else _vp(stream)))
+        return loss.value if want_loss else None
+
+    def gradients(self, x, y, n: int, stream=None):
+        g = np.zeros(self.n_params, np.float32)
+        loss = ctypes.c_float()
+        self._check(self._lib.moc_mlp_gradients(self._h, _vp(_ptr(x)), _vp(_ptr(y)), int(n), self._fp(g),
+                                                ctypes.byref(loss), None if stream is None else _vp(stream)))
+        return g, loss.value
 
 
 def eval_one_minus_exp_f32(tau: np.ndarray, device: int = 0) -> np.ndarray:
@@ -254,6 +347,19 @@ class Moc:
 
     def synchronize(self):
         self._check(self._lib.moc_synchronize(self._h))
+
+    def ws_features(self, geo_ptr, n_geo: int, glob, feat_ptr):
+        """Per-region network inputs on the device (see moc_ws_features)."""
+        g = np.ascontiguousarray(glob, dtype=np.float32)
+        self._check(self._lib.moc_ws_features(self._h, _vp(_ptr(geo_ptr)) if n_geo else None, int(n_geo),
+                                              g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), g.size,
+                                              _vp(_ptr(feat_ptr))))
+
+    def ws_apply(self, pred_ptr) -> float:
+        """Set the iterate from a network prediction on the device (see moc_ws_apply)."""
+        k = ctypes.c_double()
+        self._check(self._lib.moc_ws_apply(self._h, _vp(_ptr(pred_ptr)), ctypes.byref(k)))
+        return k.value
 
     @classmethod
     def from_problem(cls, prob, device: int = 0, precision: str = "fp32", stream=None, with_xs: bool = True):

@@ -408,3 +408,37 @@ def test_thread_count_does_not_change_results():
             o.outer(True)
         res.append(o.get_state())
     assert np.array_equal(res[0][0], res[1][0]) and res[0][1] == res[1][1]
+
+
+# ------------------------------------------------------------------------------ warm-start network
+
+def test_mlp_oracle_gradient_matches_finite_differences():
+    from oracle import mlp_oracle as MO
+
+    rng = np.random.default_rng(0)
+    dims = [5, 8, 8, 8, 3]
+    n_par = sum(dims[l + 1] * dims[l] + dims[l + 1] for l in range(4))
+    p = rng.normal(0, 0.5, n_par)
+    x = rng.normal(0, 1, (7, 5))
+    y = rng.normal(0, 1, (7, 3))
+    norm = (rng.normal(0, 0.1, 5), rng.uniform(0.5, 2, 5), rng.normal(0, 0.1, 3), rng.uniform(0.5, 2, 3))
+    loss, g = MO.loss_and_grad(p, dims, x, y, norm, bf16=False)
+    h = 1e-6
+    fd = np.zeros(n_par)
+    for i in range(n_par):
+        pp, pm = p.copy(), p.copy()
+        pp[i] += h
+        pm[i] -= h
+        fd[i] = (MO.loss_and_grad(pp, dims, x, y, norm, bf16=False)[0] -
+                 MO.loss_and_grad(pm, dims, x, y, norm, bf16=False)[0]) / (2 * h)
+    np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-9)
+
+
+def test_bf16_rounding_is_round_to_nearest_even():
+    from oracle import mlp_oracle as MO
+
+    # 1 + 2^-8 lies exactly between bf16 neighbours 1 and 1 + 2^-7: ties go to even (1.0)
+    assert MO.round_bf16(np.float32(1.0 + 2 ** -8)) == 1.0
+    assert MO.round_bf16(np.float32(1.0 + 3 * 2 ** -8)) == 1.0 + 2 ** -6
+    assert MO.round_bf16(np.float32(1.0 + 2 ** -8 + 2 ** -20)) == 1.0 + 2 ** -7
+    assert MO.round_bf16(np.float32(-2.5)) == -2.5
