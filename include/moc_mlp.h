@@ -59,6 +59,23 @@ int moc_mlp_train_step(moc_mlp *net, const float *x_dev, const float *y_dev, int
 int moc_mlp_gradients(moc_mlp *net, const float *x_dev, const float *y_dev, int64_t n, float *grad_out,
                       float *loss_out, void *stream);
 
+/* Forward pass that allocates nothing, for callers that must not call cudaMalloc: code that runs
+ * while a stream is being captured into a CUDA graph (an allocation there breaks the capture),
+ * solvers that hand all device memory to their own pool up front and treat a driver allocation in
+ * the solve loop as an error, and latency-bound loops where an allocation's implicit device
+ * synchronisation is not acceptable. The paper has no counterpart.
+ *
+ * Same contract and result as moc_mlp_forward, except that the activations live in one fixed
+ * workspace of MOC_MLP_NOALLOC_FLOATS floats (8 MiB) that the library declares as a static
+ * device array: every GPU that loads the library holds it until the process exits. A call needs
+ * n * (dims[0] + 2 dims[1] + 2 dims[2] + 2 dims[3] + dims[4]) floats of it and returns MOC_ERR_ARG
+ * (touching nothing) when n is larger; split bigger batches. All calls on a device share the one
+ * array and it keeps the last call's contents, so calls whose GPU work overlaps (other streams,
+ * other threads) race and must be serialised by the caller. The first call on a device looks up
+ * the array's device address (no allocation) and should come before any stream capture. */
+#define MOC_MLP_NOALLOC_FLOATS (2u * 1024u * 1024u)
+int moc_mlp_forward_noalloc(moc_mlp *net, const float *x_dev, float *y_dev, int64_t n, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

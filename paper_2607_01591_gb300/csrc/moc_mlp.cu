@@ -498,3 +498,53 @@ int moc_mlp_gradients(moc_mlp *n, const float *x, const float *y, int64_t rows, 
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------ no-allocation
+// Workspace of moc_mlp_forward_noalloc: one fixed array per device, never allocated at run time.
+static __device__ __align__(256) float g_noalloc_ws[MOC_MLP_NOALLOC_FLOATS];
+
+namespace {
+constexpr int kMaxDevices = 64;
+float *g_noalloc_addr[kMaxDevices] = {};  // device address of g_noalloc_ws, looked up once per device
+}  // namespace
+
+extern "C" int moc_mlp_forward_noalloc(moc_mlp *n, const float *x, float *y, int64_t rows, void *stream) {
+  if (!n || rows < 0 || (rows > 0 && (!x || !y))) return MOC_ERR_ARG;
+  if (rows == 0) return MOC_OK;
+  if (n->device >= kMaxDevices) return mfail(n, MOC_ERR_ARG, "forward_noalloc: device index beyond the supported 64");
+  const int64_t per_row = (int64_t)n->dims[0] + 2 * n->dims[1] + 2 * n->dims[2] + 2 * n->dims[3] + n->dims[4];
+  if (rows > (int64_t)MOC_MLP_NOALLOC_FLOATS / per_row)
+    return mfail(n, MOC_ERR_ARG,
+                 "forward_noalloc: batch of " + std::to_string(rows) + " rows exceeds the fixed workspace (" +
+                     std::to_string((int64_t)MOC_MLP_NOALLOC_FLOATS / per_row) + " rows for this network)");
+  MLP_TRY(n, cudaSetDevice(n->device));
+  if (!g_noalloc_addr[n->device]) {
+    // host code cannot use the array's name as a device address: ask the runtime for it
+    float *p = nullptr;
+    MLP_TRY(n, cudaGetSymbolAddress((void **)&p, g_noalloc_ws));
+    g_noalloc_addr[n->device] = p;
+  }
+  // carve A0 | Z0 | A1 | Z1 | A2 | Z2 | A3 | Z3 out of the workspace
+  float *ws = g_noalloc_addr[n->device];
+  float *Aw[kLayers], *Zw[kLayers];
+  size_t o = 0;
+  for (int l = 0; l < kLayers; ++l) {
+    Aw[l] = ws + o;
+    o += (size_t)rows * n->dims[l];
+    Zw[l] = ws + o;
+    o += (size_t)rows * n->dims[l + 1];
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  normalize_kernel<<<grid1(rows * n->dims[0]), 256, 0, st>>>(rows, n->dims[0], x, n->in_mean, n->in_std, Aw[0]);
+  for (int l = 0; l < kLayers; ++l) {
+    const int din = n->dims[l], dout = n->dims[l + 1];
+    gemm<false, true, __nv_bfloat16>((int)rows, dout, din, Aw[l], din, n->Wh[l], din, Zw[l], dout, st);
+    const bool act = l < kLayers - 1;
+    bias_act_kernel<<<grid1(rows * dout), 256, 0, st>>>(rows, dout, Zw[l], n->b[l], act ? Aw[l + 1] : nullptr,
+                                                        act ? 1 : 0);
+  }
+  const int dlast = n->dims[kLayers];
+  denorm_kernel<<<grid1(rows * dlast), 256, 0, st>>>(rows, dlast, Zw[kLayers - 1], n->out_mean, n->out_std, y);
+  MLP_TRY(n, cudaGetLastError());
+  return MOC_OK;
+}

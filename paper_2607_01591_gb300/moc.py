@@ -96,6 +96,7 @@ def load_library(path: Optional[str] = None):
                                                   ctypes.POINTER(ctypes.c_float), _vp]),
             "moc_mlp_gradients": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_float),
                                                  ctypes.POINTER(ctypes.c_float), _vp]),
+            "moc_mlp_forward_noalloc": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, _vp]),
             "moc_eval_one_minus_exp_f32": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_float),
                                                           ctypes.POINTER(ctypes.c_float), ctypes.c_int64]),
         }
@@ -178,6 +179,11 @@ class Mlp:
     def forward(self, x, y, n: int, stream=None):
         self._check(self._lib.moc_mlp_forward(self._h, _vp(_ptr(x)), _vp(_ptr(y)), int(n),
                                               None if stream is None else _vp(stream)))
+
+    def forward_noalloc(self, x, y, n: int, stream=None):
+        """Forward pass in the library's fixed workspace; allocates nothing (moc_mlp_forward_noalloc)."""
+        self._check(self._lib.moc_mlp_forward_noalloc(self._h, _vp(_ptr(x)), _vp(_ptr(y)), int(n),
+                                                      None if stream is None else _vp(stream)))
 
     def train_step(self, x, y, n: int, lr: float, stream=None, want_loss: bool = False):
         loss = ctypes.c_float()
