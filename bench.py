@@ -26,7 +26,20 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MOC segment*polar*group updates/s"
 UNIT = "updates/s"
-WORKLOAD = "17x17 assembly, 39,304 triangles, 7 groups, 32 azimuths, 3 polar (TY), ray spacing 0.02 cm"
+WORKLOADS = {
+    "assembly": "17x17 assembly, 39,304 triangles, 7 groups, 32 azimuths, 3 polar (TY), ray spacing 0.02 cm",
+    "core": "3x3-assembly core + reflector, 608,804 triangles, 7 groups, 64 azimuths, 3 polar, ray spacing 0.01 cm",
+    "hexcore": "19-hexagon core, 1,507,650 triangles, 33 groups, 48 azimuths, 3 polar, ray spacing 0.02 cm",
+    "pin": "pin cell, 200 triangles, 7 groups, 16 azimuths, 3 polar, ray spacing 0.05 cm",
+}
+WORKLOAD = WORKLOADS["assembly"]
+
+
+def make_problem(name: str):
+    from paper_2607_01591_gb300 import workloads as W
+
+    return {"assembly": W.assembly_problem, "core": W.core_problem, "hexcore": W.hex_core_problem,
+            "pin": W.pin_cell_problem}[name]()
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -161,6 +174,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_plain", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--workload", default="assembly", choices=sorted(WORKLOADS))
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -185,7 +199,7 @@ def main():
     if world > 1:
         dist.barrier()
     moc.load_library()
-    prob = W.assembly_problem()
+    prob = make_problem(args.workload)
     stream = torch.cuda.Stream(device=local)
     m = moc.Moc.from_problem(prob, device=local, precision=args.precision, stream=stream.cuda_stream)
     n_seg, ups, kpo = m.work()
@@ -265,14 +279,14 @@ def main():
 
     if rank != 0:
         return
-    cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(prob)
+    cpu = None if args.no_cpu_baseline or world > 1 or args.workload != "assembly" else cpu_baseline(prob)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "fp32_plain": "f32", "fp64": "f64"}[args.precision],
         "data": "synthetic (seeded mesh and cross sections shaped like the paper's lattice workloads)",
-        "config": {"workload": WORKLOAD, "precision": args.precision, "segments": n_seg, "tracks": T,
+        "config": {"workload": WORKLOADS[args.workload], "precision": args.precision, "segments": n_seg, "tracks": T,
                    "updates_per_step": ups, "l2": "flushed between steps (512 MiB write, untimed)",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": alu_peak / 1e9, "unit": "Gop/s",

@@ -53,7 +53,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
             cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-I", INC, "-I", CSRC, "-Xcompiler", "-fPIC",
                    "-c", os.path.join(CSRC, src), "-o", obj]
         else:
-            cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-I", INC, "-I", CSRC, "-c", os.path.join(CSRC, src), "-o", obj]
+            cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-fopenmp", "-I", INC, "-I", CSRC, "-c", os.path.join(CSRC, src),
+                   "-o", obj]
         cmds.append(cmd)
 
     def run(cmd):
@@ -67,7 +68,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with ThreadPoolExecutor(len(cmds)) as ex:
         list(ex.map(run, cmds))
     tmp = LIB + f".{os.getpid()}.tmp"
-    run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-fPIC"])
+    run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-fPIC", "-lgomp"])
     os.replace(tmp, LIB)
     return LIB
 

@@ -44,7 +44,7 @@ struct moc_ctx {
   int cur = 0;          // psi buffer holding the incoming flux of the next sweep
   bool eigen = true;
   bool tracks_on_device = false, xs_set = false;
-  std::vector<double> h_ext;  // host copy of the fixed source (for re-upload)
+  std::vector<double> h_nsf;  // host copy of nu*Sigma_f [M][G] (normalising a caller's state)
   // graphs: [parity of cur at launch]
   cudaGraphExec_t graph2[2] = {nullptr, nullptr};
   // timing
@@ -308,7 +308,7 @@ template <typename Real> int launch_source(moc_ctx *c, cudaStream_t st) {
 
 template <typename Real, int P, int TM> void sweep_launch(moc_ctx *c, cudaStream_t st) {
   const long long n = (long long)c->T * 2 * c->G;
-  const int bs = 256;
+  const int bs = 128;  // matches the kernel's launch bounds (128 threads, 9 blocks per SM)
   const long long nb = (n + bs - 1) / bs;
   sweep_kernel<Real, P, TM><<<(unsigned)nb, bs, 0, st>>>(
       c->d_trk, (const SegRec<Real> *)c->d_seg, c->d_link, (const Real *)c->d_wgt, (const Real *)c->d_inv_sin,
@@ -645,8 +645,11 @@ int moc_set_xs(moc_ctx *c, int n_mat, int G, const double *st, const double *nsf
     if (!(ss[i] >= 0.0) || !std::isfinite(ss[i])) return fail(c, MOC_ERR_ARG, "set_xs: sigma_s must be finite and >= 0");
   cudaSetDevice(c->device);
   free_problem(c);
-  c->h_ext.clear();
   c->eigen = true;
+  // the device tables hold the values rounded to the sweep's type; normalise with the same
+  c->h_nsf.resize((size_t)n_mat * G);
+  for (size_t i = 0; i < c->h_nsf.size(); ++i)
+    c->h_nsf[i] = c->precision == MOC_FP64 ? nsf[i] : (double)(float)nsf[i];
   c->cur = 0;
   rc = c->precision == MOC_FP64 ? upload_xs<double>(c, n_mat, G, st, nsf, chi, ss)
                                 : upload_xs<float>(c, n_mat, G, st, nsf, chi, ss);
@@ -680,12 +683,7 @@ int moc_set_state(moc_ctx *c, const double *phi, double k, const double *psi) {
   if (rc) return rc;
   double scale = 1.0;
   if (c->eigen) {
-    std::vector<double> nsf((size_t)c->M * c->G);
-    std::vector<unsigned char> tmp(nsf.size() * rsize(c));
-    CUDA_TRY(c, cudaMemcpy(tmp.data(), c->d_nsf, tmp.size(), cudaMemcpyDeviceToHost));
-    for (size_t i = 0; i < nsf.size(); ++i)
-      nsf[i] = c->precision == MOC_FP64 ? ((double *)tmp.data())[i] : (double)((float *)tmp.data())[i];
-    double F = host_fission(c, phi, nsf);
+    double F = host_fission(c, phi, c->h_nsf);
     if (!std::isfinite(F)) return fail(c, MOC_ERR_ARG, "set_state: the fission source of the state is not finite");
     if (F > 0.0) scale = 1.0 / F;   // no fission at all: power iteration will report MOC_ERR_NONFINITE
   }

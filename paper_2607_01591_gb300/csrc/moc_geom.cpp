@@ -315,13 +315,20 @@ int generate_tracks(Geometry &g, std::string &err) {
   for (size_t e = 0; e < g.twin.size(); ++e)
     if (g.twin[e] < 0) bnd.push_back((int32_t)e);
 
-  g.seg_off.assign(1, 0);
-  g.seg_reg.clear();
-  g.seg_len.clear();
-  g.track_dir.clear();
-  g.track_xy.clear();
-  std::vector<Piece> pieces;
+  // Directions are walked independently (in parallel when OpenMP is on) and concatenated in
+  // direction order, so the result does not depend on the thread count.
+  struct DirOut {
+    std::vector<int32_t> reg;
+    std::vector<double> len, xy;
+    std::vector<int64_t> count;  // segments per track
+    std::string err;
+    int rc = 0;
+  };
+  std::vector<DirOut> outs(g.n_dir);
+#pragma omp parallel for schedule(dynamic, 1)
   for (int j = 0; j < g.n_dir; ++j) {
+    DirOut &D = outs[j];
+    std::vector<Piece> pieces;
     const double u[2] = {std::cos(g.phi[j]), std::sin(g.phi[j])};
     const double nrm[2] = {-u[1], u[0]};
     const int nr = g.nx[j] + g.ny[j];
@@ -355,14 +362,14 @@ int generate_tracks(Geometry &g, std::string &err) {
         int r = it->second;
         const double *p0 = &ray[3 * r];
         double ax = a[0] - p0[0], ay = a[1] - p0[1];
-        double s = cross(ax, ay, dx, dy) / den;
+        double sp = cross(ax, ay, dx, dy) / den;
         double tt = cross(ax, ay, u[0], u[1]) / den;
         if (tt < -1e-12 || tt > 1.0 + 1e-12) continue;
-        if (s < -kEventEps || s > ray[3 * r + 2] - kEventEps) continue;
-        ev[r].push_back({s, he, tt});
+        if (sp < -kEventEps || sp > ray[3 * r + 2] - kEventEps) continue;
+        ev[r].push_back({sp, he, tt});
       }
     }
-    for (int r = 0; r < nr; ++r) {
+    for (int r = 0; r < nr && D.rc == 0; ++r) {
       const double *p0 = &ray[3 * r];
       const double L = ray[3 * r + 2];
       std::sort(ev[r].begin(), ev[r].end(), [](const Event &x, const Event &y) { return x.s < y.s; });
@@ -405,23 +412,54 @@ int generate_tracks(Geometry &g, std::string &err) {
         if (std::isnan(s1)) {
           char buf[160];
           std::snprintf(buf, sizeof buf, "generate_tracks: half-edge walk lost on direction %d ray %d", j, r);
-          err = buf;
-          return MOC_ERR_GEOMETRY;
+          D.err = buf;
+          D.rc = MOC_ERR_GEOMETRY;
+          break;
         }
         s_done = s1;
         if (pieces.empty()) continue;
-        g.track_dir.push_back(j);
-        g.track_xy.push_back(p0[0] + s0 * u[0]);
-        g.track_xy.push_back(p0[1] + s0 * u[1]);
-        g.track_xy.push_back(p0[0] + s1 * u[0]);
-        g.track_xy.push_back(p0[1] + s1 * u[1]);
+        D.xy.push_back(p0[0] + s0 * u[0]);
+        D.xy.push_back(p0[1] + s0 * u[1]);
+        D.xy.push_back(p0[0] + s1 * u[0]);
+        D.xy.push_back(p0[1] + s1 * u[1]);
         for (const Piece &p : pieces) {
-          g.seg_reg.push_back(p.tri);
-          g.seg_len.push_back(p.len);
+          D.reg.push_back(p.tri);
+          D.len.push_back(p.len);
         }
-        g.seg_off.push_back((int64_t)g.seg_reg.size());
+        D.count.push_back((int64_t)pieces.size());
       }
     }
+  }
+  int64_t nt = 0, ns = 0;
+  for (int j = 0; j < g.n_dir; ++j) {
+    if (outs[j].rc) {
+      err = outs[j].err;
+      return outs[j].rc;
+    }
+    nt += (int64_t)outs[j].count.size();
+    ns += (int64_t)outs[j].reg.size();
+  }
+  g.seg_off.assign(1, 0);
+  g.seg_off.reserve(nt + 1);
+  g.seg_reg.clear();
+  g.seg_reg.reserve(ns);
+  g.seg_len.clear();
+  g.seg_len.reserve(ns);
+  g.track_dir.clear();
+  g.track_dir.reserve(nt);
+  g.track_xy.clear();
+  g.track_xy.reserve(4 * nt);
+  for (int j = 0; j < g.n_dir; ++j) {
+    DirOut &D = outs[j];
+    for (int64_t c : D.count) {
+      g.track_dir.push_back(j);
+      g.seg_off.push_back(g.seg_off.back() + c);
+    }
+    g.track_xy.insert(g.track_xy.end(), D.xy.begin(), D.xy.end());
+    g.seg_reg.insert(g.seg_reg.end(), D.reg.begin(), D.reg.end());
+    g.seg_len.insert(g.seg_len.end(), D.len.begin(), D.len.end());
+    std::vector<int32_t>().swap(D.reg);
+    std::vector<double>().swap(D.len);
   }
   const int64_t T = g.n_tracks();
   if (T == 0) {

@@ -51,8 +51,9 @@ __device__ __forceinline__ float one_minus_exp(float tau) {
   tau = fminf(tau, 80.0f);
   const float t = fmaf(tau, 1.44269504088896341f, 12582912.0f);  // 1.5*2^23: rounds to integer
   const float n = t - 12582912.0f;
-  float r = fmaf(n, -0.693145751953125f, tau);         // ln2 split: high part exact in n * hi
-  r = fmaf(n, -1.42860682030941723212e-6f, r);
+  // one FMA forms tau - n ln2 with a single rounding; the FP32 ln2 constant is off by 1.9e-9,
+  // i.e. n * 1.9e-9 in r, far below an ulp of the result for every n where 1 - e^-tau != 1
+  const float r = fmaf(n, -0.693147182464599609375f, tau);
   const float h = fmaf(fmaf(fmaf(fmaf(MOC_EXP_H4, r, MOC_EXP_H3), r, MOC_EXP_H2), r, MOC_EXP_H1), r, MOC_EXP_H0);
   const float p = fmaf(r * r, h, r);                   // 1 - exp(-r)
   const float sc = __int_as_float(0x3F800000 - (__float_as_int(t) << 23));  // 2^-n
@@ -113,23 +114,25 @@ __global__ void source_kernel(int R, int G, int Gp, int M, const int32_t *__rest
 // accumulated in a second array).
 template <int TM, typename Real> struct Tally;
 template <typename Real> struct Tally<0, Real> {
-  __device__ __forceinline__ void add(Real *sum, Real *, size_t a, Real x) { atomicAdd(sum + a, x); }
+  __device__ __forceinline__ void init(unsigned) {}
+  __device__ __forceinline__ void add(Real *sum, Real *, unsigned a, Real x) { atomicAdd(sum + a, x); }
   __device__ __forceinline__ void flush(Real *) {}
 };
 template <> struct Tally<1, float> {
   // The old value returned by a segment's atomic is turned into its TwoSum error two segments
   // later, so the atomic's round trip overlaps two segments of arithmetic. Both pending slots
-  // start as zero errors aimed at a valid address, which keeps the loop free of branches.
+  // start as zero errors aimed at a valid element, which keeps the loop free of branches.
+  // Element indices are 32-bit (R * Gp < 2^32) to keep the pending state small.
   float oldA = 0.f, xA = 0.f, oldB = 0.f, xB = 0.f;
-  size_t aA = 0, aB = 0;
+  unsigned aA = 0, aB = 0;
   __device__ __forceinline__ static float err(float o, float x) {
     // TwoSum (Knuth): s = o + x as the atomic unit rounded it; returns (o + x) - s exactly
     const float sm = o + x;
     const float bb = sm - o;
     return (o - (sm - bb)) + (x - bb);
   }
-  __device__ __forceinline__ void init(size_t a) { aA = aB = a; }
-  __device__ __forceinline__ void add(float *sum, float *comp, size_t a, float v) {
+  __device__ __forceinline__ void init(unsigned a) { aA = aB = a; }
+  __device__ __forceinline__ void add(float *sum, float *comp, unsigned a, float v) {
     const float o = atomicAdd(sum + a, v);
     atomicAdd(comp + aB, err(oldB, xB));
     oldB = oldA;
@@ -148,7 +151,7 @@ template <> struct Tally<1, float> {
 // One thread per (track, sense, group); polar angles held in registers; g fastest so the G
 // threads of one track end read one contiguous row of region data and hit one tally row.
 template <typename Real, int P, int TM>
-__global__ void __launch_bounds__(256) sweep_kernel(
+__global__ void __launch_bounds__(128, 9) sweep_kernel(
     const TrackRec *__restrict__ trk, const SegRec<Real> *__restrict__ seg, const int32_t *__restrict__ link,
     const Real *__restrict__ wgt, const Real *__restrict__ inv_sin,
     const typename Pair<Real>::T *__restrict__ xsq, Real *__restrict__ tsum, Real *__restrict__ tcomp,
@@ -176,7 +179,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(
   SegRec<Real> s0 = sp[0], s1 = sp[step], s2 = sp[2 * step];
   typename Pair<Real>::T xq0 = xsq[(size_t)s0.r * Gp + g];
   typename Pair<Real>::T xq1 = xsq[(size_t)s1.r * Gp + g];
-  if constexpr (TM == 1) tally.init((size_t)s0.r * Gp + g);
+  tally.init((unsigned)(s0.r * Gp + g));
 #pragma unroll 2
   for (int n = 0; n < tr.n; ++n) {
     const SegRec<Real> s3 = sp[3 * step];
@@ -190,7 +193,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(
       psi[p] -= dl;
       acc = fma(w[p], dl, acc);
     }
-    tally.add(tsum, tcomp, (size_t)s0.r * Gp + g, acc);
+    tally.add(tsum, tcomp, (unsigned)(s0.r * Gp + g), acc);
     s0 = s1;
     s1 = s2;
     s2 = s3;

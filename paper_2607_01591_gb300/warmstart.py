@@ -99,14 +99,18 @@ class WarmStart:
         self.pred = torch.empty((self.R, self.n_out), dtype=torch.float32, device=self.dev)
 
     # ------------------------------------------------------------------------------ data
-    def solve_reference(self, xs: W.CrossSections, tol: float = 1e-7, polish: int = 3):
-        """Converge in FP32, then finish with FP64 outers from that state: (phi, k)."""
+    def solve_reference(self, xs: W.CrossSections, polish: int = 3, tight: bool = False):
+        """Converge in FP32 (|dk| <= 1e-7, fission-source change <= 1e-6), then continue in FP64 from
+        that state: `polish` outers, or (tight) until |dk| <= 1e-10 and the change <= 1e-8."""
         self.ctx32.set_xs(xs)
-        self.ctx32.power_iterate(tol, 10 * tol, 20000, check_every=20, raise_on_fail=False)
+        self.ctx32.power_iterate(1e-7, 1e-6, 20000, check_every=20, raise_on_fail=False)
         phi, k, psi = self.ctx32.get_state(with_psi=True)
         self.ctx64.set_xs(xs)
         self.ctx64.set_state(phi, k, psi)
-        k64, _ = self.ctx64.outer(polish)
+        if tight:
+            self.ctx64.power_iterate(1e-10, 1e-8, 2000, check_every=5, raise_on_fail=False)
+        else:
+            self.ctx64.outer(polish)
         phi64, k64 = self.ctx64.get_state()
         return phi64, k64
 
@@ -217,7 +221,7 @@ def run(n_train: int, n_eval: int, n_eval_fp64: int, rows_per_instance: int, epo
     X, Y, ktr, t_data = ws.make_dataset(train, rows_per_instance, seed=1)
     losses, t_fit = ws.fit(X, Y, epochs=epochs)
     # reference k of held-out instances (same solve as the training data)
-    refs = [ws.solve_reference(xs, tol=1e-8) for xs in held]
+    refs = [ws.solve_reference(xs, tight=True) for xs in held]
     # ablation: start from the training-mean solution (mean log flux per region, mean k)
     mean_pred = torch.empty((ws.R, ws.n_out), dtype=torch.float32, device=ws.dev)
     acc = torch.zeros((ws.R, ws.n_out), dtype=torch.float64, device=ws.dev)
@@ -249,7 +253,7 @@ def run(n_train: int, n_eval: int, n_eval_fp64: int, rows_per_instance: int, epo
         "n_train": n_train, "n_eval": n_eval, "rows_per_instance": rows_per_instance, "epochs": epochs,
         "net": {"dims": ws.net.dims, "params": ws.net.n_params, "weights": "bf16 (FP32 master, Adam)"},
         "data_seconds": t_data, "fit_seconds": t_fit, "loss_first_last": [losses[0], losses[-1]],
-        "stop": "first outer with |k - k_ref| <= 5 pcm; k_ref from FP32 convergence to 1e-8 + 3 FP64 outers",
+        "stop": "first outer with |k - k_ref| <= 5 pcm; k_ref: FP32 to 1e-7, then FP64 to |dk| <= 1e-10",
         "cold_fp32": summ(res["cold_fp32"]), "warm_fp32": summ(res["warm_fp32"]),
         "mean_solution_fp32": summ(res["mean_fp32"]),
         "cold_fp64": summ(res["cold_fp64"]) if res["cold_fp64"] else None,

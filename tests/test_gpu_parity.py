@@ -202,3 +202,23 @@ def test_assembly_full_size_fp64_and_fp32():
         print(prec, "dk", kg - ko, "max rel flux err", _rel(phig, phio))
         assert abs(kg - ko) <= tk
         assert _rel(phig, phio) <= tf
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_plain"])
+def test_core_and_hex_geometries_reduced_quadrature(precision):
+    """The 3x3-assembly core (vacuum on two sides, 7 groups) and the 19-hexagon core (vacuum,
+    33 groups: the chunked FP32 kernel) at full mesh size with a coarse quadrature, 3 outers
+    from the default state, GPU vs oracle."""
+    tol = {"fp64": (1e-12, 1e-10), "fp32": (5e-6, 5e-5), "fp32_plain": (1e-5, 1e-4)}[precision]
+    for prob in (W.core_problem(), W.hex_core_problem()):
+        prob.n_azim, prob.ray_spacing = 8, 0.25
+        o = _oracle(prob)
+        o.normalise()
+        for _ in range(3):
+            o.outer(True)
+        phio, ko = o.get_state()
+        m = moc.Moc.from_problem(prob, precision=precision)
+        m.outer(3)
+        phig, kg = m.get_state()
+        assert abs(kg - ko) <= tol[0] * ko, (prob.name, kg, ko)
+        assert _rel(phig, phio) <= tol[1], (prob.name, _rel(phig, phio))
