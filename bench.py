@@ -41,6 +41,9 @@ def make_problem(name: str):
     return {"assembly": W.assembly_problem, "core": W.core_problem, "hexcore": W.hex_core_problem,
             "pin": W.pin_cell_problem}[name]()
 L2_FLUSH_BYTES = 512 << 20
+# DRAM bytes (read + write) per launch of the sweep kernel from one ncu capture of the current kernel
+# version on the assembly workload (profiles/sweep_kernel_assembly17.md); None for other workloads.
+SWEEP_DRAM_BYTES = {"assembly": 82.330112e6 + 2.306048e6}
 
 
 def _peaks():
@@ -290,7 +293,8 @@ def main():
                    "updates_per_step": ups, "l2": "flushed between steps (512 MiB write, untimed)",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": alu_peak / 1e9, "unit": "Gop/s",
-                     "frac": achieved / alu_peak, "traffic": None,
+                     "frac": achieved / alu_peak,
+                     "traffic": SWEEP_DRAM_BYTES.get(args.workload) if args.precision == "fp32" else None,
                      "kernel": "sweep_kernel", "avg_launch_ms": sweep_avg_s * 1e3,
                      "ops_per_update": ops_per_update,
                      "peak_note": "152 SMs x 128 FP32 lanes x max SM clock (derived; FMA counted as 1 op)",

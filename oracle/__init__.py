@@ -70,6 +70,10 @@ def _load():
         lib.orc_iterate.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_int, _d, ctypes.POINTER(ctypes.c_int), _d]
         lib.orc_track_sweep.argtypes = [ctypes.c_int, _d, _d, _d, ctypes.c_double, ctypes.c_double, _d]
+        lib.orc_sample_fixed_source.restype = ctypes.c_int
+        lib.orc_sample_fixed_source.argtypes = [ctypes.c_int, _d, ctypes.c_int, _i32, _i32, _d, _i32, ctypes.c_int,
+                                                ctypes.c_double, ctypes.c_int, _d, _d, ctypes.c_int, ctypes.c_int,
+                                                _d, _d, _d, _d, _d, ctypes.c_int, _i32, _d, _d]
         _lib = lib
         return lib
 
@@ -224,3 +228,24 @@ def track_sweep(sig, qr, length, sin_theta: float, psi_in: float) -> np.ndarray:
     lib.orc_track_sweep(sig.shape[0], _p(sig, _d), _p(qr, _d), _p(length, _d), float(sin_theta),
                         float(psi_in), _p(out, _d))
     return out
+
+
+def sample_fixed_source(mesh, n_azim, spacing, sin_theta, polar_w, xs, S, phi0, psi0, sample):
+    """Flux of the sampled regions after one fixed-source outer from (phi0, psi0), computed from
+    only the rays that cross them; also returns their tracked areas. Rectangular meshes only."""
+    lib = _load()
+    xy, tri, mat, bbox, bc = _f64(mesh.xy), _i32a(mesh.tri), _i32a(mesh.mat), _f64(mesh.bbox), _i32a(mesh.bc)
+    st_, pw = _f64(sin_theta), _f64(polar_w)
+    sig, ss = _f64(xs.sigma_t), _f64(xs.sigma_s)
+    S, phi0, psi0 = _f64(S), _f64(phi0), _f64(psi0)
+    sample = _i32a(sample)
+    G = sig.shape[1]
+    out = np.zeros((sample.size, G))
+    area = np.zeros(sample.size)
+    rc = lib.orc_sample_fixed_source(xy.shape[0], _p(xy, _d), tri.shape[0], _p(tri, _i32), _p(mat, _i32),
+                                     _p(bbox, _d), _p(bc, _i32), int(n_azim), float(spacing), st_.size, _p(st_, _d), _p(pw, _d),
+                                     sig.shape[0], G, _p(sig, _d), _p(ss, _d), _p(S, _d), _p(phi0, _d),
+                                     _p(psi0, _d), sample.size, _p(sample, _i32), _p(out, _d), _p(area, _d))
+    if rc != 0:
+        raise RuntimeError(f"oracle sample_fixed_source failed ({rc})")
+    return out, area

@@ -650,3 +650,161 @@ void orc_track_sweep(int n, const double *sig, const double *qr, const double *l
     psi_after[k] = psi;
   }
 }
+
+/* ------------------------------------------------------------------ sampled regions ---- */
+/* Scalar flux after one fixed-source outer (Q from phi0 and S, one sweep from psi0) for a sample of
+ * regions, without segmenting the whole problem: only rays crossing a sampled region are laid down
+ * and clipped (same laydown, clipping and weights as above, restated for a subset). For a
+ * rectangular mesh the ray index equals the track index of the full track list, so psi0 is indexed
+ * [ray][2][P][G]. Returns 0 on success. */
+typedef struct { double cmin, cmax; int t; } proj_t;
+static int cmp_proj(const void *a, const void *b) {
+  const proj_t *x = a, *y = b;
+  if (x->cmin != y->cmin) return (x->cmin < y->cmin) ? -1 : 1;
+  return (x->t < y->t) ? -1 : (x->t > y->t);
+}
+
+int orc_sample_fixed_source(int n_vert, const double *xy, int n_tri, const int32_t *tri, const int32_t *mat,
+                            const double *bbox, const int32_t *bc, int n_azim, double spacing, int n_polar, const double *sin_theta,
+                            const double *polar_w, int n_mat, int G, const double *st, const double *ss,
+                            const double *S, const double *phi0, const double *psi0, int n_sample,
+                            const int32_t *sample, double *phi_out, double *area_out) {
+  orc_t h0;
+  memset(&h0, 0, sizeof h0);
+  orc_t *h = &h0;
+  h->n_vert = n_vert; h->n_tri = n_tri; h->xy = (double *)xy; h->tri = (int32_t *)tri; h->mat = (int32_t *)mat;
+  h->xmin = bbox[0]; h->xmax = bbox[1]; h->ymin = bbox[2]; h->ymax = bbox[3];
+  h->n_azim = n_azim; h->n_polar = n_polar;
+  if (build_quadrature(h, spacing)) return -1;
+  double W = h->xmax - h->xmin, H = h->ymax - h->ymin;
+  /* sample lookup */
+  int *slot = xcalloc(n_tri, sizeof(int));
+  for (int i = 0; i < n_tri; ++i) slot[i] = -1;
+  for (int q = 0; q < n_sample; ++q) slot[sample[q]] = q;
+  double *tal = xcalloc((size_t)n_sample * G, sizeof(double));
+  double *area = xcalloc(n_sample, sizeof(double));
+  /* directions run in parallel, each into its own tally; the partial tallies are summed in
+   * direction order afterwards, so the result does not depend on the thread count */
+  int64_t *base = xcalloc(h->n_dir + 1, sizeof(int64_t));
+  for (int j = 0; j < h->n_dir; ++j) base[j + 1] = base[j] + h->nx_a[j] + h->ny_a[j];
+  double *tal_d = xcalloc((size_t)h->n_dir * n_sample * G, sizeof(double));
+  double *area_d = xcalloc((size_t)h->n_dir * n_sample, sizeof(double));
+  int fail = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int j = 0; j < h->n_dir; ++j) {
+    double *tal_j = tal_d + (size_t)j * n_sample * G, *area_j = area_d + (size_t)j * n_sample;
+    int64_t ray_base = base[j];
+    double ph = h->phi_a[j], u[2] = {cos(ph), sin(ph)}, nrm[2] = {-sin(ph), cos(ph)};
+    int nx = h->nx_a[j], ny = h->ny_a[j], nr = nx + ny;
+    /* offsets of all rays of this direction, and which rays cross a sampled region */
+    double *p0 = xcalloc(2 * (size_t)nr, sizeof(double));
+    for (int i = 0; i < nx; ++i) { p0[2 * i] = h->xmin + (i + 0.5) * W / nx; p0[2 * i + 1] = h->ymin; }
+    for (int i = 0; i < ny; ++i) { p0[2 * (nx + i)] = (u[0] > 0) ? h->xmin : h->xmax; p0[2 * (nx + i) + 1] = h->ymin + (i + 0.5) * H / ny; }
+    char *need = xcalloc(nr, 1);
+    for (int q = 0; q < n_sample; ++q) {
+      int t = sample[q];
+      double cmin = INFINITY, cmax = -INFINITY;
+      for (int k = 0; k < 3; ++k) {
+        const double *v = xy + 2 * (int64_t)tri[3 * t + k];
+        double c = nrm[0] * v[0] + nrm[1] * v[1];
+        if (c < cmin) cmin = c;
+        if (c > cmax) cmax = c;
+      }
+      for (int r = 0; r < nr; ++r) {
+        double c = nrm[0] * p0[2 * r] + nrm[1] * p0[2 * r + 1];
+        if (c >= cmin && c <= cmax) need[r] = 1;
+      }
+    }
+    /* triangle projection intervals of this direction, sorted, for the per-ray candidate search */
+    proj_t *pj = xcalloc(n_tri, sizeof(proj_t));
+    double wmax = 0.0;
+    for (int t = 0; t < n_tri; ++t) {
+      double cmin = INFINITY, cmax = -INFINITY;
+      for (int k = 0; k < 3; ++k) {
+        const double *v = xy + 2 * (int64_t)tri[3 * t + k];
+        double cc = nrm[0] * v[0] + nrm[1] * v[1];
+        if (cc < cmin) cmin = cc;
+        if (cc > cmax) cmax = cc;
+      }
+      pj[t].cmin = cmin; pj[t].cmax = cmax; pj[t].t = t;
+      if (cmax - cmin > wmax) wmax = cmax - cmin;
+    }
+    qsort(pj, n_tri, sizeof(proj_t), cmp_proj);
+    for (int r = 0; r < nr; ++r) {
+      if (!need[r]) continue;
+      double c = nrm[0] * p0[2 * r] + nrm[1] * p0[2 * r + 1];
+      double L = box_exit(h, p0 + 2 * r, u);
+      int cap = 64, cnt = 0;
+      piece_t *pc = xcalloc(cap, sizeof(piece_t));
+      int lo = 0, hi = n_tri;
+      while (lo < hi) { int m = (lo + hi) / 2; if (pj[m].cmin < c - wmax) lo = m + 1; else hi = m; }
+      for (int q2 = lo; q2 < n_tri && pj[q2].cmin <= c; ++q2) {
+        if (pj[q2].cmax < c) continue;
+        int t = pj[q2].t;
+        const double *v[3];
+        for (int k = 0; k < 3; ++k) v[k] = xy + 2 * (int64_t)tri[3 * t + k];
+        double s0, s1;
+        if (!clip_triangle(p0 + 2 * r, u, L, v[0], v[1], v[2], &s0, &s1)) continue;
+        if (s1 - s0 < 1e-12) continue;
+        if (cnt == cap) { cap *= 2; pc = realloc(pc, cap * sizeof(piece_t)); if (!pc) abort(); }
+        pc[cnt].s0 = s0; pc[cnt].s1 = s1; pc[cnt].tri = t; cnt++;
+      }
+      qsort(pc, cnt, sizeof(piece_t), cmp_piece);
+      for (int k = 1; k < cnt; ++k)
+        if (pc[k].s0 - pc[k - 1].s1 > 1e-9) fail = 1;   /* a gap: not a rectangular, box-filling mesh */
+      int64_t tr = ray_base + r;
+      for (int d = 0; d < 2; ++d) {
+        /* entry point of this sense; inflow through a vacuum wall is zero */
+        double ex = d ? p0[2 * r] + L * u[0] : p0[2 * r], ey = d ? p0[2 * r + 1] + L * u[1] : p0[2 * r + 1];
+        int w = wall_of(h, ex, ey, 1e-9 * fmax(W, H));
+        int vac = (w >= 0 && bc[w] == 0);
+        for (int p = 0; p < n_polar; ++p) {
+          double Wt = 4.0 * ORC_PI * h->omega_a[j] * polar_w[p] * h->delta_a[j] * sin_theta[p];
+          for (int g = 0; g < G; ++g) {
+            double psi = vac ? 0.0 : psi0[((size_t)(2 * tr + d) * n_polar + p) * G + g];
+            for (int n = 0; n < cnt; ++n) {
+              int k = d ? (cnt - 1 - n) : n;
+              int i = pc[k].tri, m = mat[i];
+              double sig = st[(size_t)m * G + g];
+              /* Eq. MGNTE_element source of region i from phi0 (fixed source, no fission) */
+              double sc = 0.0;
+              for (int gp = 0; gp < G; ++gp) sc += ss[((size_t)m * G + gp) * G + g] * phi0[(size_t)i * G + gp];
+              double qi = (sc + S[(size_t)i * G + g]) / (4.0 * ORC_PI);
+              double len = pc[k].s1 - pc[k].s0;
+              double delta = (psi - qi / sig) * (-expm1(-sig * len / sin_theta[p]));
+              if (slot[i] >= 0) tal_j[(size_t)slot[i] * G + g] += Wt * delta;
+              psi -= delta;
+            }
+          }
+        }
+      }
+      for (int n = 0; n < cnt; ++n)
+        if (slot[pc[n].tri] >= 0) area_j[slot[pc[n].tri]] += 2.0 * h->omega_a[j] * h->delta_a[j] * (pc[n].s1 - pc[n].s0);
+      free(pc);
+    }
+    free(pj);
+    free(need);
+    free(p0);
+  }
+  for (int j = 0; j < h->n_dir; ++j) {
+    for (size_t q = 0; q < (size_t)n_sample * G; ++q) tal[q] += tal_d[(size_t)j * n_sample * G + q];
+    for (int q = 0; q < n_sample; ++q) area[q] += area_d[(size_t)j * n_sample + q];
+  }
+  free(tal_d); free(area_d); free(base);
+  if (fail) { free(h->phi_a); free(h->delta_a); free(h->omega_a); free(h->nx_a); free(h->ny_a); free(slot); free(tal); free(area); return -2; }
+  for (int q = 0; q < n_sample; ++q) {
+    int i = sample[q], m = mat[i];
+    area_out[q] = area[q];
+    for (int g = 0; g < G; ++g) {
+      double sig = st[(size_t)m * G + g], sc = 0.0;
+      for (int gp = 0; gp < G; ++gp) sc += ss[((size_t)m * G + gp) * G + g] * phi0[(size_t)i * G + gp];
+      double qi = (sc + S[(size_t)i * G + g]) / (4.0 * ORC_PI);
+      double v = 4.0 * ORC_PI * qi / sig;
+      if (area[q] > 0.0) v += tal[(size_t)q * G + g] / (sig * area[q]);
+      phi_out[(size_t)q * G + g] = v;
+    }
+  }
+  free(h->phi_a); free(h->delta_a); free(h->omega_a); free(h->nx_a); free(h->ny_a);
+  free(slot); free(tal); free(area);
+  return 0;
+}

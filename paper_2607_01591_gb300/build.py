@@ -50,7 +50,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         obj = os.path.join(BUILD_DIR, src.replace(".", "_") + ".o")
         objs.append(obj)
         if src.endswith(".cu"):
-            cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-I", INC, "-I", CSRC, "-Xcompiler", "-fPIC",
+            cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-I", INC, "-I", CSRC, "-Xcompiler", "-fPIC,-fopenmp",
                    "-c", os.path.join(CSRC, src), "-o", obj]
         else:
             cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-fopenmp", "-I", INC, "-I", CSRC, "-c", os.path.join(CSRC, src),

@@ -41,10 +41,14 @@ struct moc_ctx {
   void *d_xsq = nullptr, *d_phi = nullptr, *d_tsum = nullptr, *d_tcomp = nullptr;
   void *d_psi[2] = {nullptr, nullptr};
   double *d_fold = nullptr, *d_ext = nullptr, *d_part = nullptr, *d_scal = nullptr;
+  void *d_inv_ta = nullptr;    // [R][Gp] 1/(Sigma_t A) in the sweep's type, 0 where the tracked area is 0
+  unsigned *d_ticket = nullptr;  // finalize's last-block counter (back to 0 after each launch)
   int cur = 0;          // psi buffer holding the incoming flux of the next sweep
   bool eigen = true;
   bool tracks_on_device = false, xs_set = false;
   std::vector<double> h_nsf;  // host copy of nu*Sigma_f [M][G] (normalising a caller's state)
+  void *h_stage = nullptr;    // pinned staging buffer for state transfers (grown on demand)
+  size_t h_stage_bytes = 0;
   // graphs: [parity of cur at launch]
   cudaGraphExec_t graph2[2] = {nullptr, nullptr};
   // timing
@@ -100,6 +104,8 @@ void free_problem(moc_ctx *c) {
   dfree(c->d_fold);
   dfree(c->d_ext);
   dfree(c->d_part);
+  dfree(c->d_inv_ta);
+  dfree(c->d_ticket);
   dfree(c->d_sig_t);
   dfree(c->d_nsf);
   dfree(c->d_chi);
@@ -144,6 +150,19 @@ template <typename T> int upload(moc_ctx *c, T *&dst, const T *src, size_t n) {
   CUDA_TRY(c, cudaMalloc((void **)&dst, std::max<size_t>(n, 1) * sizeof(T)));
   if (n) CUDA_TRY(c, cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return MOC_OK;
+}
+
+// Pinned host staging of at least `bytes` (reused across calls; freed in moc_destroy).
+int stage(moc_ctx *c, size_t bytes, unsigned char *&out) {
+  if (bytes > c->h_stage_bytes) {
+    if (c->h_stage) cudaFreeHost(c->h_stage);
+    c->h_stage = nullptr;
+    c->h_stage_bytes = 0;
+    CUDA_TRY(c, cudaHostAlloc(&c->h_stage, bytes, cudaHostAllocDefault));
+    c->h_stage_bytes = bytes;
+  }
+  out = (unsigned char *)c->h_stage;
   return MOC_OK;
 }
 
@@ -244,6 +263,22 @@ template <typename Real> int upload_xs(moc_ctx *c, int n_mat, int G, const doubl
   typename Pair<Real>::T *dx = nullptr;
   if ((rc = upload(c, dx, xsq.data(), xsq.size()))) return rc;
   c->d_xsq = dx;
+  // 1/(Sigma_t A) in FP64 from the Sigma_t the sweep uses (rounded to Real)
+  std::vector<double> inv_ta((size_t)R * Gp, 0.0);
+  for (int r = 0; r < R; ++r)
+    for (int k = 0; k < G; ++k) {
+      const double A = g.area[r];
+      const double sig = (double)(Real)st[(size_t)g.mat[r] * G + k];
+      inv_ta[(size_t)r * Gp + k] = (A > 0.0) ? 1.0 / (sig * A) : 0.0;
+    }
+  {
+    std::vector<Real> inv_r(inv_ta.begin(), inv_ta.end());
+    Real *di = nullptr;
+    if ((rc = upload(c, di, inv_r.data(), inv_r.size()))) return rc;
+    c->d_inv_ta = di;
+    const unsigned zero = 0;
+    if ((rc = upload(c, c->d_ticket, &zero, 1))) return rc;
+  }
   const size_t RG = (size_t)R * Gp, PB = (size_t)c->T * 2 * c->P * G;
   CUDA_TRY(c, cudaMalloc(&c->d_phi, RG * sizeof(Real)));
   CUDA_TRY(c, cudaMalloc(&c->d_tsum, RG * sizeof(Real)));
@@ -268,28 +303,62 @@ template <typename Real> int upload_xs(moc_ctx *c, int n_mat, int G, const doubl
 // state upload: phi [R][G] (NULL: ones) and psi [T][2][P][G] in external track order (NULL: 0)
 template <typename Real> int upload_state(moc_ctx *c, const double *phi, const double *psi) {
   const int R = c->geo.n_tri, G = c->G, Gp = c->Gp, P = c->P;
-  std::vector<Real> hp((size_t)R * Gp, (Real)0);
-  for (int r = 0; r < R; ++r)
-    for (int g = 0; g < G; ++g) hp[(size_t)r * Gp + g] = (Real)(phi ? phi[(size_t)r * G + g] : 1.0);
   const size_t per = (size_t)2 * P * G;
-  std::vector<Real> hpsi((size_t)c->T * per, (Real)0);
-  if (psi) {
-    // vacuum boundary: incoming ends that no outgoing end feeds keep zero inflow
-    std::vector<char> fed(2 * (size_t)c->T, 0);
+  const size_t nphi = (size_t)R * Gp, npsi = (size_t)c->T * per;
+  unsigned char *buf;
+  int rc = stage(c, (nphi + npsi) * sizeof(Real), buf);
+  if (rc) return rc;
+  Real *hp = (Real *)buf, *hpsi = hp + nphi;
+#pragma omp parallel for schedule(static)
+  for (int r = 0; r < R; ++r)
+    for (int g = 0; g < Gp; ++g) hp[(size_t)r * Gp + g] = (g < G) ? (Real)(phi ? phi[(size_t)r * G + g] : 1.0) : (Real)0;
+  // vacuum boundary: incoming ends that no outgoing end feeds keep zero inflow
+  std::vector<char> fed(2 * (size_t)c->T, 0);
+  if (psi)
     for (int64_t e : c->geo.link)
       if (e >= 0) fed[e] = 1;
-    const size_t half = per / 2;
-    for (int64_t t = 0; t < c->T; ++t)
-      for (int d = 0; d < 2; ++d) {
-        if (!fed[2 * t + d]) continue;
-        for (size_t q = 0; q < half; ++q)
-          hpsi[(size_t)c->inv[t] * per + d * half + q] = (Real)psi[(size_t)t * per + d * half + q];
+  const size_t half = per / 2;
+#pragma omp parallel for schedule(static)
+  for (int64_t t = 0; t < c->T; ++t)
+    for (int d = 0; d < 2; ++d) {
+      Real *dst = hpsi + (size_t)c->inv[t] * per + d * half;
+      if (!psi || !fed[2 * t + d]) {
+        for (size_t q = 0; q < half; ++q) dst[q] = (Real)0;
+      } else {
+        const double *src = psi + (size_t)t * per + d * half;
+        for (size_t q = 0; q < half; ++q) dst[q] = (Real)src[q];
       }
-  }
-  CUDA_TRY(c, cudaMemcpyAsync(c->d_phi, hp.data(), hp.size() * sizeof(Real), cudaMemcpyHostToDevice, c->stream));
-  CUDA_TRY(c, cudaMemcpyAsync(c->d_psi[c->cur], hpsi.data(), hpsi.size() * sizeof(Real), cudaMemcpyHostToDevice,
-                              c->stream));
+    }
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_phi, hp, nphi * sizeof(Real), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_psi[c->cur], hpsi, npsi * sizeof(Real), cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return MOC_OK;
+}
+
+template <typename Real> int download_state(moc_ctx *c, double scale, double *phi, double *psi) {
+  const int R = c->geo.n_tri, G = c->G, Gp = c->Gp, P = c->P;
+  const size_t per = (size_t)2 * P * G;
+  const size_t nphi = phi ? (size_t)R * Gp : 0, npsi = psi ? (size_t)c->T * per : 0;
+  unsigned char *buf;
+  int rc = stage(c, (nphi + npsi) * sizeof(Real) + 16, buf);
+  if (rc) return rc;
+  Real *hp = (Real *)buf, *hpsi = hp + nphi;
+  if (phi) CUDA_TRY(c, cudaMemcpyAsync(hp, c->d_phi, nphi * sizeof(Real), cudaMemcpyDeviceToHost, c->stream));
+  if (psi) CUDA_TRY(c, cudaMemcpyAsync(hpsi, c->d_psi[c->cur], npsi * sizeof(Real), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (phi) {
+#pragma omp parallel for schedule(static)
+    for (int r = 0; r < R; ++r)
+      for (int g = 0; g < G; ++g) phi[(size_t)r * G + g] = (double)hp[(size_t)r * Gp + g] * scale;
+  }
+  if (psi) {
+#pragma omp parallel for schedule(static)
+    for (int64_t t = 0; t < c->T; ++t) {
+      const Real *src = hpsi + (size_t)c->inv[t] * per;
+      double *dst = psi + (size_t)t * per;
+      for (size_t q = 0; q < per; ++q) dst[q] = (double)src[q] * scale;
+    }
+  }
   return MOC_OK;
 }
 
@@ -369,31 +438,31 @@ int launch_sweep(moc_ctx *c, cudaStream_t st) {
 template <typename Real> int launch_finalize_reduce(moc_ctx *c, cudaStream_t st) {
   const int R = c->geo.n_tri;
   if (c->Gp == 8) {
-    // 8 lanes per region, 32 regions per block of 256 threads
+    // 8 lanes per region, 32 regions per block of 256 threads; the last block also reduces
     const int nb8 = (R + 31) / 32;
     if (tally_mode(c) == 1)
-      finalize8_kernel<Real, 1><<<nb8, 256, 0, st>>>(R, c->G, c->d_mat, (const Real *)c->d_nsf, c->d_area,
-                                                     (const typename Pair<Real>::T *)c->d_xsq, (Real *)c->d_tsum,
-                                                     (Real *)c->d_tcomp, (Real *)c->d_phi, c->d_fold, c->d_part,
-                                                     c->eigen ? 1 : 0);
+      finalize8_kernel<Real, 1><<<nb8, 256, 0, st>>>(
+          R, c->G, c->d_mat, (const Real *)c->d_nsf, (const Real *)c->d_inv_ta, (const typename Pair<Real>::T *)c->d_xsq,
+          (Real *)c->d_tsum, (Real *)c->d_tcomp, (Real *)c->d_phi, c->d_fold, c->d_area, c->d_part, c->d_ticket,
+          c->d_scal, c->eigen ? 1 : 0);
     else
-      finalize8_kernel<Real, 0><<<nb8, 256, 0, st>>>(R, c->G, c->d_mat, (const Real *)c->d_nsf, c->d_area,
-                                                     (const typename Pair<Real>::T *)c->d_xsq, (Real *)c->d_tsum,
-                                                     (Real *)c->d_tcomp, (Real *)c->d_phi, c->d_fold, c->d_part,
-                                                     c->eigen ? 1 : 0);
-    CUDA_TRY(c, cudaGetLastError());
-    reduce_kernel<<<1, 256, 0, st>>>(nb8, c->d_part, c->d_scal, c->eigen ? 1 : 0);
+      finalize8_kernel<Real, 0><<<nb8, 256, 0, st>>>(
+          R, c->G, c->d_mat, (const Real *)c->d_nsf, (const Real *)c->d_inv_ta, (const typename Pair<Real>::T *)c->d_xsq,
+          (Real *)c->d_tsum, (Real *)c->d_tcomp, (Real *)c->d_phi, c->d_fold, c->d_area, c->d_part, c->d_ticket,
+          c->d_scal, c->eigen ? 1 : 0);
     CUDA_TRY(c, cudaGetLastError());
     return MOC_OK;
   }
   const int nb = (R + 255) / 256;
   if (tally_mode(c) == 1)
     finalize_kernel<Real, 1><<<nb, 256, 0, st>>>(R, c->G, c->Gp, c->d_mat, (const Real *)c->d_nsf, c->d_area,
+                                                 (const Real *)c->d_inv_ta,
                                                  (const typename Pair<Real>::T *)c->d_xsq, (Real *)c->d_tsum,
                                                  (Real *)c->d_tcomp, (Real *)c->d_phi, c->d_fold, c->d_part,
                                                  c->eigen ? 1 : 0);
   else
     finalize_kernel<Real, 0><<<nb, 256, 0, st>>>(R, c->G, c->Gp, c->d_mat, (const Real *)c->d_nsf, c->d_area,
+                                                 (const Real *)c->d_inv_ta,
                                                  (const typename Pair<Real>::T *)c->d_xsq, (Real *)c->d_tsum,
                                                  (Real *)c->d_tcomp, (Real *)c->d_phi, c->d_fold, c->d_part,
                                                  c->eigen ? 1 : 0);
@@ -555,6 +624,7 @@ void moc_destroy(moc_ctx *c) {
     }
     free_tracks(c);
     dfree(c->d_scal);
+    if (c->h_stage) cudaFreeHost(c->h_stage);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   }
@@ -697,33 +767,11 @@ int moc_get_state(moc_ctx *c, double *phi, double *k, double *psi) {
   double s[S_COUNT];
   if ((rc = read_scalars(c, s))) return rc;
   const double scale = c->eigen ? s[S_SCALE] : 1.0;
-  const int R = c->geo.n_tri, G = c->G, Gp = c->Gp, P = c->P;
-  const size_t rs = rsize(c);
-  if (phi) {
-    std::vector<unsigned char> tmp((size_t)R * Gp * rs);
-    CUDA_TRY(c, cudaMemcpyAsync(tmp.data(), c->d_phi, tmp.size(), cudaMemcpyDeviceToHost, c->stream));
-    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    for (int r = 0; r < R; ++r)
-      for (int g = 0; g < G; ++g) {
-        size_t a = (size_t)r * Gp + g;
-        double v = c->precision == MOC_FP64 ? ((double *)tmp.data())[a] : (double)((float *)tmp.data())[a];
-        phi[(size_t)r * G + g] = v * scale;
-      }
-  }
   if (k) *k = s[S_K];
-  if (psi) {
-    const size_t per = (size_t)2 * P * G;
-    std::vector<unsigned char> tmp((size_t)c->T * per * rs);
-    CUDA_TRY(c, cudaMemcpyAsync(tmp.data(), c->d_psi[c->cur], tmp.size(), cudaMemcpyDeviceToHost, c->stream));
-    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    for (int64_t t = 0; t < c->T; ++t) {
-      int64_t i = c->inv[t];
-      for (size_t q = 0; q < per; ++q) {
-        size_t a = (size_t)i * per + q;
-        double v = c->precision == MOC_FP64 ? ((double *)tmp.data())[a] : (double)((float *)tmp.data())[a];
-        psi[(size_t)t * per + q] = v * scale;
-      }
-    }
+  if (phi || psi) {
+    rc = c->precision == MOC_FP64 ? download_state<double>(c, scale, phi, psi)
+                                  : download_state<float>(c, scale, phi, psi);
+    if (rc) return rc;
   }
   return MOC_OK;
 }
@@ -826,7 +874,7 @@ int moc_get_work(const moc_ctx *c, int64_t *n_segments, int64_t *updates, int *k
   if (!c || !c->geo.has_tracks) return c ? MOC_ERR_STATE : MOC_ERR_ARG;
   if (n_segments) *n_segments = c->geo.n_segments();
   if (updates) *updates = 2 * c->geo.n_segments() * (int64_t)c->geo.n_polar * (int64_t)std::max(c->G, 0);
-  if (kernels) *kernels = 4;
+  if (kernels) *kernels = (c->Gp == 8) ? 3 : 4;
   return MOC_OK;
 }
 

@@ -333,7 +333,8 @@ __global__ void __launch_bounds__(64) sweep_chunk_kernel(
 template <typename Real, int TM>
 __global__ void __launch_bounds__(256) finalize_kernel(
     int R, int G, int Gp, const int32_t *__restrict__ mat, const Real *__restrict__ nsf,
-    const double *__restrict__ area, const typename Pair<Real>::T *__restrict__ xsq, Real *__restrict__ tsum,
+    const double *__restrict__ area, const Real *__restrict__ inv_ta,
+    const typename Pair<Real>::T *__restrict__ xsq, Real *__restrict__ tsum,
     Real *__restrict__ tcomp, Real *__restrict__ phi, const double *__restrict__ fold,
     double *__restrict__ part, int eigen) {
   __shared__ double s_sum[256], s_min[256], s_max[256], s_res[256];
@@ -352,8 +353,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(
         t += (double)tcomp[a];
         tcomp[a] = (Real)0;
       }
-      double ph = kFourPi * (double)v.y;
-      if (A > 0.0) ph += t / ((double)v.x * A);
+      const double ph = fma(t, (double)inv_ta[a], kFourPi * (double)v.y);
       if (!eigen) {
         const double old = (double)phi[a];
         if (ph > 0.0) res = fmax(res, fabs(ph - old) / ph);
@@ -390,37 +390,45 @@ __global__ void __launch_bounds__(256) finalize_kernel(
   }
 }
 
+__device__ __forceinline__ void reduce_partials(int nb, const double *__restrict__ part, double *__restrict__ scal,
+                                                int eigen);
+
 // Group-parallel variant for Gp = 8: 8 consecutive threads own one region (coalesced row
-// accesses); the region's fission rate is reduced across its 8 lanes with shuffles.
+// accesses). Per region and group the arithmetic is in the sweep's type (FP32 mode: the
+// compensation is folded by one FP32 add, i.e. the compensated sum rounded once, and phi is stored
+// in FP32 anyway); FP64 is used for A_i f_i and every reduction. The last block to finish (atomic
+// ticket after a memory fence; no waiting) reduces all block partials, so no separate reduce
+// launch is needed. 1/(Sigma_t A) is precomputed (no division per region and group).
 template <typename Real, int TM>
 __global__ void __launch_bounds__(256) finalize8_kernel(
-    int R, int G, const int32_t *__restrict__ mat, const Real *__restrict__ nsf, const double *__restrict__ area,
+    int R, int G, const int32_t *__restrict__ mat, const Real *__restrict__ nsf, const Real *__restrict__ inv_ta,
     const typename Pair<Real>::T *__restrict__ xsq, Real *__restrict__ tsum, Real *__restrict__ tcomp,
-    Real *__restrict__ phi, const double *__restrict__ fold, double *__restrict__ part, int eigen) {
-  __shared__ double s_sum[32], s_min[32], s_max[32], s_res[32];
+    Real *__restrict__ phi, const double *__restrict__ fold, const double *__restrict__ area,
+    double *__restrict__ part, unsigned *__restrict__ ticket, double *__restrict__ scal, int eigen) {
+  __shared__ double l_sum[32], l_min[32], l_max[32], l_res[32];
+  __shared__ bool last;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = tid >> 3, g = tid & 7;
   const bool live = r < R;
-  double f = 0.0, res = 0.0, A = 0.0;
+  Real f = 0;
+  double res = 0.0;
   if (live) {
-    A = area[r];
     const size_t a = (size_t)r * 8 + g;
     const typename Pair<Real>::T v = xsq[a];
-    double t = (double)tsum[a];
+    Real t = tsum[a];
     tsum[a] = (Real)0;
     if (TM == 1) {
-      t += (double)tcomp[a];
+      t += tcomp[a];
       tcomp[a] = (Real)0;
     }
     if (g < G) {
-      double ph = kFourPi * (double)v.y;
-      if (A > 0.0) ph += t / ((double)v.x * A);
+      const Real ph = fma(t, inv_ta[a], (Real)kFourPi * v.y);
       if (!eigen) {
-        const double old = (double)phi[a];
-        if (ph > 0.0) res = fabs(ph - old) / ph;
+        const Real old = phi[a];
+        if (ph > (Real)0) res = (double)(fabs(ph - old) / ph);
       }
-      phi[a] = (Real)ph;
-      f = (double)nsf[mat[r] * G + g] * (double)(Real)ph;
+      phi[a] = ph;
+      f = nsf[mat[r] * G + g] * ph;
     }
   }
 #pragma unroll
@@ -428,48 +436,51 @@ __global__ void __launch_bounds__(256) finalize8_kernel(
     f += __shfl_xor_sync(0xffffffffu, f, o);
     res = fmax(res, __shfl_xor_sync(0xffffffffu, res, o));
   }
-  double fsum = 0.0, rmin = INFINITY, rmax = -INFINITY;
   if (live && g == 0) {
-    fsum = A * f;
-    if (eigen && f > 0.0) rmin = rmax = fold[r] / f;
-  }
-  // warp then block reduction (fixed order)
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    fsum += __shfl_xor_sync(0xffffffffu, fsum, o);
-    rmin = fmin(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
-    rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-    res = fmax(res, __shfl_xor_sync(0xffffffffu, res, o));
-  }
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) {
-    s_sum[w] = fsum;
-    s_min[w] = rmin;
-    s_max[w] = rmax;
-    s_res[w] = res;
+    const int q = threadIdx.x >> 3;
+    l_sum[q] = area[r] * (double)f;
+    const bool fis = eigen && f > (Real)0;
+    const double rho = fis ? (double)((Real)fold[r] / f) : 0.0;
+    l_min[q] = fis ? rho : INFINITY;
+    l_max[q] = fis ? rho : -INFINITY;
+    l_res[q] = res;
+  } else if (!live && g == 0) {
+    const int q = threadIdx.x >> 3;
+    l_sum[q] = 0.0;
+    l_min[q] = INFINITY;
+    l_max[q] = -INFINITY;
+    l_res[q] = 0.0;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     double a = 0.0, mn = INFINITY, mx = -INFINITY, rs = 0.0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-      a += s_sum[k];
-      mn = fmin(mn, s_min[k]);
-      mx = fmax(mx, s_max[k]);
-      rs = fmax(rs, s_res[k]);
+    for (int q = 0; q < (int)(blockDim.x >> 3); ++q) {
+      a += l_sum[q];
+      mn = fmin(mn, l_min[q]);
+      mx = fmax(mx, l_max[q]);
+      rs = fmax(rs, l_res[q]);
     }
     part[4 * blockIdx.x + 0] = a;
     part[4 * blockIdx.x + 1] = mn;
     part[4 * blockIdx.x + 2] = mx;
     part[4 * blockIdx.x + 3] = rs;
+    __threadfence();
+    last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    reduce_partials(gridDim.x, part, scal, eigen);
+    if (threadIdx.x == 0) *ticket = 0u;
   }
 }
 
 // ----------------------------------------------------------------------------- reduce
-// One block of 256 threads, fixed reduction order (deterministic). k' = k F' (the flux the
-// source was built from is normalised to F = 1); scale = 1/F'; residual
-// max_i |f'_i/F' - fold_i| / (f'_i/F') = max(|1 - F' rho_min|, |1 - F' rho_max|).
-__global__ void __launch_bounds__(256) reduce_kernel(int nb, const double *__restrict__ part,
-                                                     double *__restrict__ scal, int eigen) {
+// Final reduction of the block partials by one block of 256 threads in a fixed order
+// (deterministic): k' = k F' (the flux the source was built from is normalised to F = 1);
+// scale = 1/F'; residual max_i |f'_i/F' - fold_i| / (f'_i/F') = max(|1 - F' rho_min|, |1 - F' rho_max|).
+__device__ __forceinline__ void reduce_partials(int nb, const double *__restrict__ part, double *__restrict__ scal,
+                                                int eigen) {
   __shared__ double s_sum[256], s_min[256], s_max[256], s_res[256];
   double a = 0.0, mn = INFINITY, mx = -INFINITY, rs = 0.0;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {
@@ -513,6 +524,11 @@ __global__ void __launch_bounds__(256) reduce_kernel(int nb, const double *__res
     }
     scal[S_NOUTER] += 1.0;
   }
+}
+
+__global__ void __launch_bounds__(256) reduce_kernel(int nb, const double *__restrict__ part,
+                                                     double *__restrict__ scal, int eigen) {
+  reduce_partials(nb, part, scal, eigen);
 }
 
 // ----------------------------------------------------------------------------- warm start

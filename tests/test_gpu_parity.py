@@ -222,3 +222,32 @@ def test_core_and_hex_geometries_reduced_quadrature(precision):
         phig, kg = m.get_state()
         assert abs(kg - ko) <= tol[0] * ko, (prob.name, kg, ko)
         assert _rel(phig, phio) <= tol[1], (prob.name, _rel(phig, phio))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_core_full_size_sampled_regions(precision):
+    """The 3x3-assembly core at full size (64 azimuths, 0.01 cm: 4.7e8 segments) in the launch
+    configuration bench.py times: one fixed-source outer from a random state on the GPU, checked
+    region by region against the oracle, which sweeps only the rays crossing the sampled regions."""
+    prob = W.core_problem()
+    xs = W.CrossSections(prob.xs.sigma_t, np.zeros_like(prob.xs.nu_sigma_f), prob.xs.chi, prob.xs.sigma_s)
+    R, G = prob.mesh.n_tri, xs.n_groups
+    rng = np.random.default_rng(17)
+    S = rng.uniform(0.0, 1.0, (R, G))
+    phi0 = rng.uniform(0.5, 1.5, (R, G))
+    m = moc.Moc.from_problem(prob, precision=precision, with_xs=False)
+    T, _ = m.track_counts()
+    psi0 = rng.uniform(0.0, 0.2, (T, 2, 3, G))
+    m.set_xs(xs)
+    m.set_fixed_source(S)
+    m.set_state(phi0, 1.0, psi0)
+    m.outer(1)
+    phig, _ = m.get_state()
+    m.close()
+    # regions spread over fuel, clad, moderator and reflector, plus the smallest ones
+    by_mat = [rng.choice(np.nonzero(prob.mesh.mat == k)[0], 5, replace=False) for k in range(7)]
+    sample = np.unique(np.concatenate(by_mat + [np.argsort(prob.mesh.areas())[:5]]))
+    ref, area = oracle.sample_fixed_source(prob.mesh, prob.n_azim, prob.ray_spacing, prob.sin_theta,
+                                           prob.polar_w, xs, S, phi0, psi0, sample)
+    tol = 1e-10 if precision == "fp64" else 2e-5
+    assert _rel(phig[sample], ref) <= tol, _rel(phig[sample], ref)
