@@ -139,6 +139,34 @@ def cpu_baseline(prob, outers: int = 2):
                       f"{dt:.2f} s"}
 
 
+def time_to_converged_k(moc, prob, device, stream, pcm: float = 5.0):
+    """Wall time and outers of the cold-start power iteration until |k - k_ref| <= pcm * 1e-5."""
+    import torch
+
+    ref32 = moc.Moc.from_problem(prob, device=device, precision="fp32", stream=stream.cuda_stream)
+    ref32.power_iterate(1e-7, 1e-6, 20000, check_every=20, raise_on_fail=False)
+    phi, k, psi = ref32.get_state(with_psi=True)
+    ref64 = moc.Moc.from_problem(prob, device=device, precision="fp64", stream=stream.cuda_stream)
+    ref64.set_state(phi, k, psi)
+    k_ref, _, _, _ = ref64.power_iterate(1e-10, 1e-8, 5000, check_every=5, raise_on_fail=False)
+    out = {"k_ref": k_ref, "criterion": f"|k - k_ref| <= {pcm} pcm",
+           "k_ref_from": "FP32 to |dk| <= 1e-7, continued in FP64 to |dk| <= 1e-10"}
+    for name, ctx in (("cold_fp32", ref32), ("cold_fp64", ref64)):
+        ctx.set_xs(prob.xs)
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        n = 0
+        while n < 20000:
+            k, _ = ctx.outer(1)
+            n += 1
+            if abs(k - k_ref) <= pcm * 1e-5:
+                break
+        out[name] = {"ms": (time.perf_counter() - t0) * 1e3, "outers": n}
+    ref32.close()
+    ref64.close()
+    return out
+
+
 def run_reference(args, rank, world):
     from paper_2607_01591_gb300 import workloads as W
     import oracle
@@ -178,6 +206,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--workload", default="assembly", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-time-to-k", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -280,6 +309,12 @@ def main():
         fp64 = {"value": ups * args.fp64_steps / (ms64 / 1e3), "ms_per_step": ms64 / args.fp64_steps}
         m64.close()
 
+    # time to converged k: outers from the cold start until |k - k_ref| <= 5 pcm, k_ref from FP32
+    # convergence continued in FP64 to |dk| <= 1e-10 (same workload, same stream)
+    time_to_k = None
+    if not args.no_time_to_k and args.workload == "assembly":
+        time_to_k = time_to_converged_k(moc, prob, local, stream)
+
     if rank != 0:
         return
     cpu = None if args.no_cpu_baseline or world > 1 or args.workload != "assembly" else cpu_baseline(prob)
@@ -305,6 +340,7 @@ def main():
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
         "fp64": fp64,
+        "time_to_k": time_to_k,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

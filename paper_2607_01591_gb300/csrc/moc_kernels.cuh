@@ -56,7 +56,9 @@ __device__ __forceinline__ float one_minus_exp(float tau) {
   const float r = fmaf(n, -0.693147182464599609375f, tau);
   const float h = fmaf(fmaf(fmaf(fmaf(MOC_EXP_H4, r, MOC_EXP_H3), r, MOC_EXP_H2), r, MOC_EXP_H1), r, MOC_EXP_H0);
   const float p = fmaf(r * r, h, r);                   // 1 - exp(-r)
-  const float sc = __int_as_float(0x3F800000 - (__float_as_int(t) << 23));  // 2^-n
+  // 2^-n from the bits of t (0x4B400000 + n): 0x3F800000 - n * 2^23 as one unsigned (wrapping)
+  // multiply-add: (0x4B400000 + n) * (2^32 - 2^23) = -n * 2^23 modulo 2^32
+  const float sc = __uint_as_float((unsigned)__float_as_int(t) * 0xFF800000u + 0x3F800000u);
   return fmaf(sc, p, 1.0f - sc);
 }
 
@@ -88,14 +90,14 @@ __global__ void source_kernel(int R, int G, int Gp, int M, const int32_t *__rest
   const Real inv_k = eigen ? (Real)(1.0 / scal[S_K]) : (Real)0;
   Real *ph = phi + (size_t)r * Gp;
   Real fis = 0;
-  double fis_d = 0.0;
   for (int g = 0; g < G; ++g) {
     Real v = ph[g] * scale;
     ph[g] = v;
     fis += nsf[m * G + g] * v;
-    fis_d += (double)nsf[m * G + g] * (double)v;
   }
-  if (eigen) fold[r] = fis_d;
+  // normalised fission rate of the region, in the sweep's type (the FP64 pipe is kept for the
+  // global sums)
+  if (eigen) fold[r] = (double)fis;
   const Real *ss = s_ss + (size_t)m * G * G;
   const Real inv4pi = (Real)(1.0 / kFourPi);
   for (int g = 0; g < G; ++g) {
@@ -405,13 +407,15 @@ __global__ void __launch_bounds__(256) finalize8_kernel(
     const typename Pair<Real>::T *__restrict__ xsq, Real *__restrict__ tsum, Real *__restrict__ tcomp,
     Real *__restrict__ phi, const double *__restrict__ fold, const double *__restrict__ area,
     double *__restrict__ part, unsigned *__restrict__ ticket, double *__restrict__ scal, int eigen) {
-  __shared__ double l_sum[32], l_min[32], l_max[32], l_res[32];
+  __shared__ double l_sum[32];
+  __shared__ Real l_min[32], l_max[32], l_res[32];
   __shared__ bool last;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = tid >> 3, g = tid & 7;
   const bool live = r < R;
-  Real f = 0;
-  double res = 0.0;
+  // everything per region and group stays in the sweep's type: the FP64 pipe is reserved for
+  // A_i f_i and the block totals
+  Real f = 0, res = 0;
   if (live) {
     const size_t a = (size_t)r * 8 + g;
     const typename Pair<Real>::T v = xsq[a];
@@ -425,35 +429,31 @@ __global__ void __launch_bounds__(256) finalize8_kernel(
       const Real ph = fma(t, inv_ta[a], (Real)kFourPi * v.y);
       if (!eigen) {
         const Real old = phi[a];
-        if (ph > (Real)0) res = (double)(fabs(ph - old) / ph);
+        if (ph > (Real)0) res = fabs(ph - old) / ph;
       }
       phi[a] = ph;
       f = nsf[mat[r] * G + g] * ph;
     }
   }
 #pragma unroll
-  for (int o = 4; o > 0; o >>= 1) {
-    f += __shfl_xor_sync(0xffffffffu, f, o);
-    res = fmax(res, __shfl_xor_sync(0xffffffffu, res, o));
+  for (int o = 4; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+  if (!eigen) {
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) res = fmax(res, __shfl_xor_sync(0xffffffffu, res, o));
   }
-  if (live && g == 0) {
+  if (g == 0) {
     const int q = threadIdx.x >> 3;
-    l_sum[q] = area[r] * (double)f;
-    const bool fis = eigen && f > (Real)0;
-    const double rho = fis ? (double)((Real)fold[r] / f) : 0.0;
-    l_min[q] = fis ? rho : INFINITY;
-    l_max[q] = fis ? rho : -INFINITY;
+    const bool fis = live && eigen && f > (Real)0;
+    const Real rho = fis ? (Real)fold[r] / f : (Real)0;
+    l_sum[q] = live ? area[r] * (double)f : 0.0;
+    l_min[q] = fis ? rho : (Real)INFINITY;
+    l_max[q] = fis ? rho : (Real)-INFINITY;
     l_res[q] = res;
-  } else if (!live && g == 0) {
-    const int q = threadIdx.x >> 3;
-    l_sum[q] = 0.0;
-    l_min[q] = INFINITY;
-    l_max[q] = -INFINITY;
-    l_res[q] = 0.0;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double a = 0.0, mn = INFINITY, mx = -INFINITY, rs = 0.0;
+    double a = 0.0;
+    Real mn = (Real)INFINITY, mx = (Real)-INFINITY, rs = 0;
     for (int q = 0; q < (int)(blockDim.x >> 3); ++q) {
       a += l_sum[q];
       mn = fmin(mn, l_min[q]);
@@ -461,9 +461,9 @@ __global__ void __launch_bounds__(256) finalize8_kernel(
       rs = fmax(rs, l_res[q]);
     }
     part[4 * blockIdx.x + 0] = a;
-    part[4 * blockIdx.x + 1] = mn;
-    part[4 * blockIdx.x + 2] = mx;
-    part[4 * blockIdx.x + 3] = rs;
+    part[4 * blockIdx.x + 1] = (double)mn;
+    part[4 * blockIdx.x + 2] = (double)mx;
+    part[4 * blockIdx.x + 3] = (double)rs;
     __threadfence();
     last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
   }
