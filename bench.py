@@ -150,9 +150,17 @@ def time_to_converged_k(moc, prob, device, stream, pcm: float = 5.0):
     ref64.set_state(phi, k, psi)
     k_ref, _, _, _ = ref64.power_iterate(1e-10, 1e-8, 5000, check_every=5, raise_on_fail=False)
     out = {"k_ref": k_ref, "criterion": f"|k - k_ref| <= {pcm} pcm",
-           "k_ref_from": "FP32 to |dk| <= 1e-7, continued in FP64 to |dk| <= 1e-10"}
-    for name, ctx in (("cold_fp32", ref32), ("cold_fp64", ref64)):
+           "k_ref_from": "FP32 to |dk| <= 1e-7, continued in FP64 to |dk| <= 1e-10",
+           "cmfd": "pin-pitch (1.26 cm) coarse cells, 6 coarse power iterations x 6 Jacobi sweeps per outer"}
+    from paper_2607_01591_gb300 import workloads as W
+
+    cell, n_cells = W.grid_cells(prob.mesh, 1.26)
+    runs = (("cold_fp32", ref32, False), ("cold_fp64", ref64, False), ("cold_fp32_cmfd", ref32, True),
+            ("cold_fp64_cmfd", ref64, True))
+    for name, ctx, accel in runs:
         ctx.set_xs(prob.xs)
+        if accel:
+            ctx.set_cmfd(cell, n_cells, 6, 6)
         torch.cuda.synchronize(device)
         t0 = time.perf_counter()
         n = 0

@@ -123,6 +123,19 @@ int moc_get_region_areas(const moc_ctx *ctx, double *area);
 int moc_set_xs(moc_ctx *ctx, int n_mat, int G, const double *sigma_t, const double *nu_sigma_f,
                const double *chi, const double *sigma_s);
 
+/* Coarse-mesh finite difference (CMFD) acceleration of the power iteration (Alg. 1: CMFD on a
+ * coarse mesh from the MOC surface currents, then the fine MOC solution updated with the
+ * accelerated result). cell: [n_tri] coarse cell (0 .. n_cells-1) of every region, any partition
+ * of the triangles; NULL switches the acceleration off. Partial-current form: the sweep tallies,
+ * per pair of cells and direction, W * psi at every crossing between them and the outgoing
+ * current at vacuum ends; each cell's balance uses flux-volume homogenised cross sections and
+ * coefficients J/phi that reproduce the MOC currents, so the converged MOC solution is unchanged.
+ * After each outer the coarse eigenproblem is iterated n_outer times (Gauss-Seidel in energy,
+ * n_inner Jacobi sweeps per group), then phi and the incoming boundary flux are scaled by the
+ * coarse/fine flux ratio of their cell and k becomes the coarse k. Eigenvalue mode only; must be
+ * called after moc_set_xs (which switches it off). Errors: MOC_ERR_ARG, MOC_ERR_STATE. */
+int moc_set_cmfd(moc_ctx *ctx, const int32_t *cell, int n_cells, int n_outer, int n_inner);
+
 /* Fixed isotropic volumetric source S: [n_tri][G] (n/cm^3/s), switching the context to
  * fixed-source mode (fission ignored, no normalisation); NULL returns to eigenvalue mode. */
 int moc_set_fixed_source(moc_ctx *ctx, const double *S);

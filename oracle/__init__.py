@@ -58,6 +58,8 @@ def _load():
         lib.orc_set_xs.restype = ctypes.c_int
         lib.orc_set_xs.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _d, _d, _d, _d]
         lib.orc_set_fixed_source.argtypes = [ctypes.c_void_p, _d]
+        lib.orc_set_cmfd.restype = ctypes.c_int
+        lib.orc_set_cmfd.argtypes = [ctypes.c_void_p, _i32, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         lib.orc_set_state.argtypes = [ctypes.c_void_p, _d, ctypes.c_double, _d]
         lib.orc_get_state.argtypes = [ctypes.c_void_p, _d, _d, _d]
         lib.orc_get_q.argtypes = [ctypes.c_void_p, _d]
@@ -174,6 +176,15 @@ class Oracle:
             S = _f64(S)
             assert S.shape == (self.n_regions, self.G)
             self._lib.orc_set_fixed_source(self._h, _p(S, _d))
+
+    def set_cmfd(self, cell=None, n_cells: int = 0, n_outer: int = 6, n_inner: int = 6):
+        """Coarse-mesh acceleration on cells `cell` [R] (None disables); call after set_xs."""
+        if cell is None:
+            self._lib.orc_set_cmfd(self._h, None, 0, 0, 0)
+            return
+        c = _i32a(cell)
+        self._lib.orc_set_cmfd(self._h, _p(c, _i32), int(n_cells), int(n_outer), int(n_inner))
+        self._cell = c
 
     def set_state(self, phi=None, k: float = 1.0, psi=None):
         pp = None if phi is None else _f64(phi)

@@ -86,6 +86,12 @@ typedef struct {
   double *leak;     /* [G] outgoing W*psi at vacuum ends during the last sweep */
   double k;
   int n_threads;
+  /* coarse-mesh finite difference acceleration (Alg. 1), partial-current form */
+  int cmfd, n_cells, n_if, cm_outer, cm_inner;
+  int32_t *cell;      /* [R] */
+  uint64_t *pairs;    /* [n_if] sorted (min cell << 32 | max cell) */
+  double *cur;        /* [2 n_if][G]: slot 2e a->b (a the lower id), 2e+1 b->a */
+  double *cleak;      /* [n_cells][G] outgoing current at vacuum ends */
   char err[256];
 } orc_t;
 
@@ -106,6 +112,7 @@ void orc_destroy(orc_t *h) {
   free(h->link); free(h->area);
   free(h->st); free(h->nsf); free(h->chi); free(h->ss); free(h->ext);
   free(h->phi); free(h->q); free(h->tally); free(h->psi_in); free(h->psi_next); free(h->leak);
+  free(h->cell); free(h->pairs); free(h->cur); free(h->cleak);
   free(h);
 }
 
@@ -436,12 +443,28 @@ void orc_get_tracks(const orc_t *h, int64_t *seg_off, int32_t *seg_reg, double *
 
 void orc_get_areas(const orc_t *h, double *area) { memcpy(area, h->area, h->n_tri * sizeof(double)); }
 
+/* ---------------------------------------------------------------- CMFD set-up ---- */
+static int cmp_u64(const void *a, const void *b) {
+  uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+  return (x < y) ? -1 : (x > y);
+}
+
+/* slot of the current from cell a to cell b */
+static int64_t cmfd_slot(const orc_t *h, int a, int b) {
+  uint64_t lo = (uint64_t)(a < b ? a : b), hi = (uint64_t)(a < b ? b : a), key = (lo << 32) | hi;
+  int64_t l = 0, r = h->n_if;
+  while (l < r) { int64_t m = (l + r) / 2; if (h->pairs[m] < key) l = m + 1; else r = m; }
+  return 2 * l + (a > b ? 1 : 0);
+}
+
 /* ---------------------------------------------------------------- physics ---- */
 int orc_set_xs(orc_t *h, int n_mat, int G, const double *st, const double *nsf, const double *chi,
                const double *ss) {
   free(h->st); free(h->nsf); free(h->chi); free(h->ss);
   free(h->phi); free(h->q); free(h->tally); free(h->psi_in); free(h->psi_next); free(h->leak);
   free(h->ext); h->ext = NULL;
+  free(h->cell); free(h->pairs); free(h->cur); free(h->cleak);
+  h->cell = NULL; h->pairs = NULL; h->cur = NULL; h->cleak = NULL; h->cmfd = 0;
   h->n_mat = n_mat; h->G = G;
   h->st = xcalloc((size_t)n_mat * G, sizeof(double)); memcpy(h->st, st, (size_t)n_mat * G * sizeof(double));
   h->nsf = xcalloc((size_t)n_mat * G, sizeof(double)); memcpy(h->nsf, nsf, (size_t)n_mat * G * sizeof(double));
@@ -458,6 +481,38 @@ int orc_set_xs(orc_t *h, int n_mat, int G, const double *st, const double *nsf, 
   h->leak = xcalloc(G, sizeof(double));
   for (size_t i = 0; i < RG; ++i) h->phi[i] = 1.0;
   h->k = 1.0;
+  return 0;
+}
+
+/* Enable the acceleration on the coarse cells `cell` [R] (NULL disables). Interfaces are the
+ * pairs of cells that consecutive segments of some track cross between. Call after orc_set_xs. */
+int orc_set_cmfd(orc_t *h, const int32_t *cell, int n_cells, int n_outer, int n_inner) {
+  free(h->cell); free(h->pairs); free(h->cur); free(h->cleak);
+  h->cell = NULL; h->pairs = NULL; h->cur = NULL; h->cleak = NULL; h->cmfd = 0;
+  if (!cell) return 0;
+  h->cell = xcalloc(h->n_tri, sizeof(int32_t));
+  memcpy(h->cell, cell, h->n_tri * sizeof(int32_t));
+  int64_t np = 0;
+  for (int64_t t = 0; t < h->n_tracks; ++t)
+    for (int64_t s2 = h->seg_off[t]; s2 + 1 < h->seg_off[t + 1]; ++s2)
+      if (cell[h->seg_reg[s2]] != cell[h->seg_reg[s2 + 1]]) np++;
+  uint64_t *pr = xcalloc(np, sizeof(uint64_t));
+  np = 0;
+  for (int64_t t = 0; t < h->n_tracks; ++t)
+    for (int64_t s2 = h->seg_off[t]; s2 + 1 < h->seg_off[t + 1]; ++s2) {
+      int a = cell[h->seg_reg[s2]], b = cell[h->seg_reg[s2 + 1]];
+      if (a == b) continue;
+      uint64_t lo = (uint64_t)(a < b ? a : b), hi = (uint64_t)(a < b ? b : a);
+      pr[np++] = (lo << 32) | hi;
+    }
+  qsort(pr, np, sizeof(uint64_t), cmp_u64);
+  int64_t nu = 0;
+  for (int64_t k = 0; k < np; ++k) if (nu == 0 || pr[k] != pr[nu - 1]) pr[nu++] = pr[k];
+  h->pairs = pr; h->n_if = (int)nu;
+  h->n_cells = n_cells; h->cm_outer = n_outer; h->cm_inner = n_inner;
+  h->cur = xcalloc(2 * (size_t)nu * h->G, sizeof(double));
+  h->cleak = xcalloc((size_t)(n_cells > 1 ? n_cells : 1) * h->G, sizeof(double));
+  h->cmfd = 1;
   return 0;
 }
 
@@ -532,6 +587,10 @@ static void transport_sweep(orc_t *h) {
   size_t RG = (size_t)h->n_tri * G, PB = (size_t)h->n_tracks * 2 * P * G;
   memset(h->tally, 0, RG * sizeof(double));
   memset(h->psi_next, 0, PB * sizeof(double));
+  if (h->cmfd) {
+    memset(h->cur, 0, 2 * (size_t)h->n_if * G * sizeof(double));
+    memset(h->cleak, 0, (size_t)h->n_cells * G * sizeof(double));
+  }
   double *leak_g = xcalloc(G, sizeof(double));
 #pragma omp parallel for schedule(static) num_threads(h->n_threads)
   for (int g = 0; g < G; ++g) {
@@ -552,10 +611,22 @@ static void transport_sweep(orc_t *h) {
             double delta = (psi - qi / sig) * (-expm1(-tau));
             h->tally[(size_t)i * G + g] += Wt * delta;
             psi -= delta;
+            if (h->cmfd && n + 1 < s1 - s0) {
+              /* partial current W psi into the next cell along the track, if the cell changes */
+              int64_t sn = d ? (s - 1) : (s + 1);
+              int a = h->cell[i], b = h->cell[h->seg_reg[sn]];
+              if (a != b) h->cur[(size_t)cmfd_slot(h, a, b) * G + g] += Wt * psi;
+            }
           }
           int64_t e = h->link[2 * t + d];
           if (e >= 0) h->psi_next[((size_t)e * P + p) * G + g] = psi;
-          else lk += Wt * psi;
+          else {
+            lk += Wt * psi;
+            if (h->cmfd) {
+              int64_t s_last = d ? s0 : (s1 - 1);
+              h->cleak[(size_t)h->cell[h->seg_reg[s_last]] * G + g] += Wt * psi;
+            }
+          }
         }
       }
     }
@@ -577,6 +648,125 @@ static void finalize_flux(const orc_t *h, double *phi_new) {
       phi_new[ig] = v;
     }
   }
+}
+
+/* The coarse step on the normalised new flux phi_new (currents already divided by the same
+ * normalisation): homogenise per cell, coarse balance with partial-current coefficients, a fixed
+ * number of coarse power iterations (Gauss-Seidel in energy, Jacobi in space), then scale phi_new
+ * and the boundary flux for the next sweep by the coarse/fine ratio of their cell and take the
+ * coarse k. */
+static void cmfd_step(orc_t *h, double *phi_new) {
+  int G = h->G, N = h->n_cells, P = h->n_polar;
+  double *cphi = xcalloc((size_t)N * G, sizeof(double)), *TV = xcalloc((size_t)N * G, sizeof(double));
+  double *FV = xcalloc((size_t)N * G, sizeof(double)), *CH = xcalloc((size_t)N * G, sizeof(double));
+  double *SV = xcalloc((size_t)N * G * G, sizeof(double)), *V = xcalloc(N, sizeof(double));
+  /* homogenisation, regions of each cell in ascending order */
+  for (int r = 0; r < h->n_tri; ++r) {
+    int i = h->cell[r], m = h->mat[r];
+    double A = h->area[r], f = 0.0;
+    V[i] += A;
+    for (int g = 0; g < G; ++g) f += h->nsf[(size_t)m * G + g] * phi_new[(size_t)r * G + g];
+    for (int g = 0; g < G; ++g) {
+      double a = A * phi_new[(size_t)r * G + g];
+      cphi[(size_t)i * G + g] += a;
+      TV[(size_t)i * G + g] += h->st[(size_t)m * G + g] * a;
+      FV[(size_t)i * G + g] += h->nsf[(size_t)m * G + g] * a;
+      CH[(size_t)i * G + g] += h->chi[(size_t)m * G + g] * A * f;
+      for (int gg = 0; gg < G; ++gg) SV[((size_t)i * G + g) * G + gg] += h->ss[((size_t)m * G + g) * G + gg] * a;
+    }
+  }
+  for (int i = 0; i < N; ++i) {
+    double chs = 0.0;
+    for (int g = 0; g < G; ++g) chs += CH[(size_t)i * G + g];
+    for (int g = 0; g < G; ++g) {
+      size_t x = (size_t)i * G + g;
+      double raw = cphi[x];
+      if (raw > 0.0) {
+        TV[x] = TV[x] * V[i] / raw;
+        FV[x] = FV[x] * V[i] / raw;
+        for (int gg = 0; gg < G; ++gg) SV[x * G + gg] = SV[x * G + gg] * V[i] / raw;
+      } else {
+        TV[x] = FV[x] = 0.0;
+        for (int gg = 0; gg < G; ++gg) SV[x * G + gg] = 0.0;
+      }
+      cphi[x] = (V[i] > 0.0) ? raw / V[i] : 0.0;
+      CH[x] = (chs > 0.0) ? CH[x] / chs : 0.0;
+    }
+  }
+  /* coefficients: out of cell i through interface e (cell i side s): D = J(out)/phi_i; in: J(in)/phi_j */
+  double *diag = xcalloc((size_t)N * G, sizeof(double));
+  double *phic = xcalloc((size_t)N * G, sizeof(double)), *phin = xcalloc(N, sizeof(double));
+  double *fis = xcalloc(N, sizeof(double));
+  for (int i = 0; i < N; ++i)
+    for (int g = 0; g < G; ++g) {
+      size_t x = (size_t)i * G + g;
+      double pi = cphi[x], dg = TV[x] - SV[x * G + g];
+      if (pi > 0.0) dg += h->cleak[x] / pi;
+      diag[x] = dg;
+      phic[x] = pi;
+    }
+  for (int e = 0; e < h->n_if; ++e) {
+    int a = (int)(h->pairs[e] >> 32), b = (int)(h->pairs[e] & 0xffffffffu);
+    for (int g = 0; g < G; ++g) {
+      double pa = cphi[(size_t)a * G + g], pb = cphi[(size_t)b * G + g];
+      if (pa > 0.0) diag[(size_t)a * G + g] += h->cur[(size_t)(2 * e) * G + g] / pa;
+      if (pb > 0.0) diag[(size_t)b * G + g] += h->cur[(size_t)(2 * e + 1) * G + g] / pb;
+    }
+  }
+  double kc = h->k;
+  for (int it = 0; it < h->cm_outer; ++it) {
+    double F_old = 0.0;
+    for (int i = 0; i < N; ++i) {
+      double f = 0.0;
+      for (int g = 0; g < G; ++g) f += FV[(size_t)i * G + g] * phic[(size_t)i * G + g];
+      fis[i] = f;
+      F_old += f;
+    }
+    for (int g = 0; g < G; ++g) {
+      for (int j = 0; j < h->cm_inner; ++j) {
+        for (int i = 0; i < N; ++i) {
+          size_t x = (size_t)i * G + g;
+          double rhs = CH[x] * fis[i] / kc;
+          for (int gg = 0; gg < G; ++gg)
+            if (gg != g) rhs += SV[((size_t)i * G + gg) * G + g] * phic[(size_t)i * G + gg];
+          phin[i] = rhs;
+        }
+        for (int e = 0; e < h->n_if; ++e) {
+          int a = (int)(h->pairs[e] >> 32), b = (int)(h->pairs[e] & 0xffffffffu);
+          double pa = cphi[(size_t)a * G + g], pb = cphi[(size_t)b * G + g];
+          /* inflow into a from b: J(b->a)/phi_b * phic_b, and into b from a */
+          if (pb > 0.0) phin[a] += h->cur[(size_t)(2 * e + 1) * G + g] / pb * phic[(size_t)b * G + g];
+          if (pa > 0.0) phin[b] += h->cur[(size_t)(2 * e) * G + g] / pa * phic[(size_t)a * G + g];
+        }
+        for (int i = 0; i < N; ++i) {
+          size_t x = (size_t)i * G + g;
+          phic[x] = (diag[x] > 0.0) ? phin[i] / diag[x] : 0.0;
+        }
+      }
+    }
+    double F_new = 0.0;
+    for (int i = 0; i < N; ++i)
+      for (int g = 0; g < G; ++g) F_new += FV[(size_t)i * G + g] * phic[(size_t)i * G + g];
+    if (F_new > 0.0 && F_old > 0.0) kc = kc * F_new / F_old;
+  }
+  /* prolongation of the flux and of the incoming boundary flux of the next sweep */
+  for (int r = 0; r < h->n_tri; ++r)
+    for (int g = 0; g < G; ++g) {
+      size_t x = (size_t)h->cell[r] * G + g;
+      double ratio = (cphi[x] > 0.0 && phic[x] > 0.0) ? phic[x] / cphi[x] : 1.0;
+      phi_new[(size_t)r * G + g] *= ratio;
+    }
+  for (int64_t t = 0; t < h->n_tracks; ++t)
+    for (int d = 0; d < 2; ++d) {
+      int r = h->seg_reg[d ? h->seg_off[t + 1] - 1 : h->seg_off[t]];
+      for (int g = 0; g < G; ++g) {
+        size_t x = (size_t)h->cell[r] * G + g;
+        double ratio = (cphi[x] > 0.0 && phic[x] > 0.0) ? phic[x] / cphi[x] : 1.0;
+        for (int p = 0; p < P; ++p) h->psi_next[((size_t)(2 * t + d) * P + p) * G + g] *= ratio;
+      }
+    }
+  h->k = kc;
+  free(cphi); free(TV); free(FV); free(CH); free(SV); free(V); free(diag); free(phic); free(phin); free(fis);
 }
 
 /* One outer iteration: source, sweep, flux, and (eigen mode) k update + normalisation.
@@ -601,6 +791,15 @@ double orc_outer(orc_t *h, int eigen) {
       double fo = 0.0, fn = 0.0;
       for (int g = 0; g < G; ++g) { fo += nf[g] * h->phi[(size_t)i * G + g] / F_old; fn += nf[g] * phi_new[(size_t)i * G + g]; }
       if (fn > 0.0) { double r = fabs(fn - fo) / fn; if (r > resid) resid = r; }
+    }
+    if (h->cmfd) {
+      /* currents in the same normalisation as phi_new */
+      for (size_t x = 0; x < 2 * (size_t)h->n_if * G; ++x) h->cur[x] /= F_new;
+      for (size_t x = 0; x < (size_t)h->n_cells * G; ++x) h->cleak[x] /= F_new;
+      cmfd_step(h, phi_new);
+      double F2 = fission_total(h, phi_new);
+      for (size_t i = 0; i < RG; ++i) phi_new[i] /= F2;
+      for (size_t i = 0; i < PB; ++i) h->psi_next[i] /= F2;
     }
   } else {
     for (size_t i = 0; i < RG; ++i)

@@ -12,6 +12,7 @@
 
 #include "moc_gb300.h"
 #include "moc_geom.h"
+#include "moc_cmfd.cuh"
 #include "moc_kernels.cuh"
 
 using namespace moc;
@@ -47,6 +48,18 @@ struct moc_ctx {
   bool eigen = true;
   bool tracks_on_device = false, xs_set = false;
   std::vector<double> h_nsf;  // host copy of nu*Sigma_f [M][G] (normalising a caller's state)
+  // CMFD acceleration (off unless moc_set_cmfd was called)
+  bool cmfd = false;
+  int n_cells = 0, n_if = 0, cm_outer = 0, cm_inner = 0;
+  int32_t *d_xing = nullptr, *d_cell = nullptr;
+  int32_t *d_cif_off = nullptr, *d_cif = nullptr, *d_if_cells = nullptr, *d_nbr = nullptr;
+  size_t cm_smem = 0;  // dynamic shared memory of the coarse solve (0: its working set stays in global memory)
+  void *d_cur = nullptr, *d_leak = nullptr, *d_cphi = nullptr, *d_TV = nullptr, *d_SV = nullptr, *d_FV = nullptr;
+  void *d_CHI = nullptr, *d_din = nullptr, *d_diag = nullptr, *d_phic = nullptr, *d_phin = nullptr, *d_fis = nullptr;
+  void *d_ratio = nullptr, *d_phio = nullptr, *d_src = nullptr;
+  double *d_psum = nullptr, *d_vol = nullptr;  // [N][M][G] flux sums, [N] cell areas
+  double *d_cpart = nullptr;
+  unsigned *d_cticket = nullptr;
   void *h_stage = nullptr;    // pinned staging buffer for state transfers (grown on demand)
   size_t h_stage_bytes = 0;
   // graphs: [parity of cur at launch]
@@ -93,7 +106,38 @@ void drop_graphs(moc_ctx *c) {
     }
 }
 
+void free_cmfd(moc_ctx *c) {
+  drop_graphs(c);
+  dfree(c->d_xing);
+  dfree(c->d_cell);
+  dfree(c->d_cif_off);
+  dfree(c->d_cif);
+  dfree(c->d_if_cells);
+  dfree(c->d_nbr);
+  dfree(c->d_cur);
+  dfree(c->d_leak);
+  dfree(c->d_cphi);
+  dfree(c->d_TV);
+  dfree(c->d_SV);
+  dfree(c->d_FV);
+  dfree(c->d_CHI);
+  dfree(c->d_din);
+  dfree(c->d_diag);
+  dfree(c->d_phic);
+  dfree(c->d_phin);
+  dfree(c->d_fis);
+  dfree(c->d_ratio);
+  dfree(c->d_phio);
+  dfree(c->d_src);
+  dfree(c->d_psum);
+  dfree(c->d_vol);
+  dfree(c->d_cpart);
+  dfree(c->d_cticket);
+  c->cmfd = false;
+}
+
 void free_problem(moc_ctx *c) {
+  free_cmfd(c);
   drop_graphs(c);
   dfree(c->d_xsq);
   dfree(c->d_phi);
@@ -426,7 +470,35 @@ template <int TM> int launch_chunk(moc_ctx *c, cudaStream_t st) {
   return MOC_OK;
 }
 
+template <typename Real, int P, int TM> void sweep_cmfd_launch(moc_ctx *c, cudaStream_t st) {
+  const long long n = (long long)c->T * 2 * c->G;
+  CmfdDev<Real> cm{c->d_xing, c->d_cell, (Real *)c->d_cur, (Real *)c->d_leak};
+  sweep_cmfd_kernel<Real, P, TM><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(
+      c->d_trk, (const SegRec<Real> *)c->d_seg, c->d_link, (const Real *)c->d_wgt, (const Real *)c->d_inv_sin,
+      (const typename Pair<Real>::T *)c->d_xsq, (Real *)c->d_tsum, (Real *)c->d_tcomp,
+      (const Real *)c->d_psi[c->cur], (Real *)c->d_psi[c->cur ^ 1], c->d_scal, n, c->G, c->Gp, cm);
+}
+
+template <typename Real, int TM> int launch_sweep_cmfd_p(moc_ctx *c, cudaStream_t st) {
+  switch (c->P) {
+    case 1: sweep_cmfd_launch<Real, 1, TM>(c, st); break;
+    case 2: sweep_cmfd_launch<Real, 2, TM>(c, st); break;
+    case 3: sweep_cmfd_launch<Real, 3, TM>(c, st); break;
+    case 4: sweep_cmfd_launch<Real, 4, TM>(c, st); break;
+    case 5: sweep_cmfd_launch<Real, 5, TM>(c, st); break;
+    case 6: sweep_cmfd_launch<Real, 6, TM>(c, st); break;
+    default: return fail(c, MOC_ERR_ARG, "unsupported polar count");
+  }
+  CUDA_TRY(c, cudaGetLastError());
+  return MOC_OK;
+}
+
 int launch_sweep(moc_ctx *c, cudaStream_t st) {
+  if (c->cmfd) {
+    if (c->precision == MOC_FP64) return launch_sweep_cmfd_p<double, 0>(c, st);
+    if (c->precision == MOC_FP32) return launch_sweep_cmfd_p<float, 1>(c, st);
+    return launch_sweep_cmfd_p<float, 0>(c, st);
+  }
   if (c->precision == MOC_FP64) return launch_sweep_p<double, 0>(c, st);
   // many groups: one thread per chunk of 4 groups shares the per-segment cost; few groups: one
   // thread per group keeps each lane's serial chain along a long track short
@@ -476,6 +548,40 @@ int enqueue_source(moc_ctx *c, cudaStream_t st) {
   return c->precision == MOC_FP64 ? launch_source<double>(c, st) : launch_source<float>(c, st);
 }
 
+// CMFD after finalize: homogenise, coarse solve, prolong phi and the incoming boundary flux
+template <typename Real> int launch_cmfd(moc_ctx *c, cudaStream_t st) {
+  const int N = c->n_cells, G = c->G, R = c->geo.n_tri;
+  CUDA_TRY(c, cudaMemsetAsync(c->d_psum, 0, (size_t)N * c->M * G * sizeof(double), st));
+  const long long nrg = (long long)R * G;
+  cmfd_flux_sums_kernel<Real><<<(unsigned)((nrg + 255) / 256), 256, 0, st>>>(R, G, c->Gp, c->M, c->d_cell, c->d_mat,
+                                                                          c->d_area, (const Real *)c->d_phi,
+                                                                          c->d_psum);
+  cmfd_coeff_kernel<Real><<<(N * G + 127) / 128, 128, 0, st>>>(
+      N, G, c->M, c->d_psum, c->d_vol, (const Real *)c->d_sig_t, (const Real *)c->d_nsf, (const Real *)c->d_chi,
+      (const Real *)c->d_sig_s, (Real *)c->d_cphi, (Real *)c->d_TV, (Real *)c->d_SV, (Real *)c->d_FV,
+      (Real *)c->d_CHI);
+  CUDA_TRY(c, cudaGetLastError());
+  CmfdTopo t{N, G, c->Gp, 2 * c->n_if, c->d_nbr, c->d_cif_off, c->d_cif, c->d_if_cells};
+  auto solve = c->cm_smem ? cmfd_solve_kernel<Real, true> : cmfd_solve_kernel<Real, false>;
+  solve<<<1, 1024, c->cm_smem, st>>>(t, (Real *)c->d_cur, (Real *)c->d_leak, (const Real *)c->d_cphi,
+                                             (const Real *)c->d_TV, (const Real *)c->d_SV, (const Real *)c->d_FV,
+                                             (const Real *)c->d_CHI, (Real *)c->d_din, (Real *)c->d_diag,
+                                             (Real *)c->d_phic, (Real *)c->d_phin, (Real *)c->d_phio,
+                                             (Real *)c->d_src, (Real *)c->d_fis,
+                                             (Real *)c->d_ratio, c->d_scal, c->cm_outer, c->cm_inner);
+  CUDA_TRY(c, cudaGetLastError());
+  cmfd_prolong_kernel<Real><<<(R + 255) / 256, 256, 0, st>>>(R, G, c->Gp, c->d_cell, c->d_mat, (const Real *)c->d_nsf,
+                                                             c->d_area, (const Real *)c->d_ratio, (Real *)c->d_phi,
+                                                             c->d_cpart, c->d_cticket, c->d_scal);
+  CUDA_TRY(c, cudaGetLastError());
+  const long long n = (long long)c->T * 2 * G;
+  cmfd_psi_kernel<Real><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+      n, c->P, G, c->d_trk, (const SegRec<Real> *)c->d_seg, c->d_fed, c->d_cell, (const Real *)c->d_ratio,
+      (Real *)c->d_psi[c->cur]);
+  CUDA_TRY(c, cudaGetLastError());
+  return MOC_OK;
+}
+
 // sweep + finalize + reduce; flips the boundary-flux buffer
 int enqueue_sweep(moc_ctx *c, cudaStream_t st, bool timed) {
   int rc;
@@ -493,7 +599,8 @@ int enqueue_sweep(moc_ctx *c, cudaStream_t st, bool timed) {
   rc = c->precision == MOC_FP64 ? launch_finalize_reduce<double>(c, st) : launch_finalize_reduce<float>(c, st);
   if (rc) return rc;
   c->cur ^= 1;
-  return MOC_OK;
+  if (c->cmfd) rc = c->precision == MOC_FP64 ? launch_cmfd<double>(c, st) : launch_cmfd<float>(c, st);
+  return rc;
 }
 
 int enqueue_outer(moc_ctx *c, cudaStream_t st, bool timed) {
@@ -727,6 +834,137 @@ int moc_set_xs(moc_ctx *c, int n_mat, int G, const double *st, const double *nsf
   return moc_set_state(c, nullptr, 1.0, nullptr);
 }
 
+int moc_set_cmfd(moc_ctx *c, const int32_t *cell, int n_cells, int n_outer, int n_inner) {
+  int rc = need_ready(c);
+  if (rc) return rc;
+  cudaSetDevice(c->device);
+  free_cmfd(c);
+  if (!cell) return MOC_OK;
+  const Geometry &g = c->geo;
+  const int R = g.n_tri, G = c->G;
+  if (n_cells < 1 || n_outer < 1 || n_inner < 1) return fail(c, MOC_ERR_ARG, "set_cmfd: bad sizes or iteration counts");
+  for (int r = 0; r < R; ++r)
+    if (cell[r] < 0 || cell[r] >= n_cells) return fail(c, MOC_ERR_ARG, "set_cmfd: cell id out of range");
+  // interfaces: pairs of cells that consecutive segments of some track cross between
+  std::vector<uint64_t> pairs;
+  const int64_t T = g.n_tracks();
+  for (int64_t t = 0; t < T; ++t)
+    for (int64_t q = g.seg_off[t]; q + 1 < g.seg_off[t + 1]; ++q) {
+      const uint32_t a = (uint32_t)cell[g.seg_reg[q]], b = (uint32_t)cell[g.seg_reg[q + 1]];
+      if (a != b) pairs.push_back(((uint64_t)std::min(a, b) << 32) | std::max(a, b));
+    }
+  std::sort(pairs.begin(), pairs.end());
+  pairs.erase(std::unique(pairs.begin(), pairs.end()), pairs.end());
+  const int n_if = (int)pairs.size();
+  auto iface = [&](uint32_t a, uint32_t b) {
+    const uint64_t key = ((uint64_t)std::min(a, b) << 32) | std::max(a, b);
+    return (int)(std::lower_bound(pairs.begin(), pairs.end(), key) - pairs.begin());
+  };
+  // crossing code of the boundary after each segment (forward order), laid out like the
+  // uploaded segment array (internal track order, kSegPad padding records at each end)
+  std::vector<int32_t> xing(c->S + 2 * kSegPad, -1);
+  int64_t o = kSegPad;
+  for (int64_t i = 0; i < T; ++i) {
+    const int64_t t = c->perm[i];
+    for (int64_t q = g.seg_off[t]; q < g.seg_off[t + 1]; ++q, ++o) {
+      if (q + 1 == g.seg_off[t + 1]) continue;
+      const uint32_t a = (uint32_t)cell[g.seg_reg[q]], b = (uint32_t)cell[g.seg_reg[q + 1]];
+      if (a != b) xing[o] = 2 * iface(a, b) + (a > b ? 1 : 0);
+    }
+  }
+  // incidences: each interface appears in the lists of both its cells, in interface order
+  std::vector<int32_t> cif_off(n_cells + 1, 0), cif(2 * (size_t)n_if), if_cells(2 * (size_t)n_if);
+  for (int e = 0; e < n_if; ++e) {
+    const int a = (int)(pairs[e] >> 32), b = (int)(pairs[e] & 0xffffffffu);
+    if_cells[2 * e] = a;
+    if_cells[2 * e + 1] = b;
+    cif_off[a + 1]++;
+    cif_off[b + 1]++;
+  }
+  for (int i = 0; i < n_cells; ++i) cif_off[i + 1] += cif_off[i];
+  {
+    std::vector<int32_t> fill(cif_off.begin(), cif_off.end() - 1);
+    for (int e = 0; e < n_if; ++e) {
+      cif[fill[if_cells[2 * e]]++] = (e << 1) | 0;
+      cif[fill[if_cells[2 * e + 1]]++] = (e << 1) | 1;
+    }
+  }
+  std::vector<int32_t> nbr(2 * (size_t)n_if);
+  for (size_t q = 0; q < nbr.size(); ++q) nbr[q] = if_cells[2 * (cif[q] >> 1) + ((cif[q] & 1) ^ 1)];
+  std::vector<int32_t> cellv(cell, cell + R);
+  if ((rc = upload(c, c->d_xing, xing.data(), xing.size()))) return rc;
+  if ((rc = upload(c, c->d_cell, cellv.data(), cellv.size()))) return rc;
+  if ((rc = upload(c, c->d_cif_off, cif_off.data(), cif_off.size()))) return rc;
+  if ((rc = upload(c, c->d_cif, cif.data(), cif.size()))) return rc;
+  if ((rc = upload(c, c->d_if_cells, if_cells.data(), if_cells.size()))) return rc;
+  if ((rc = upload(c, c->d_nbr, nbr.data(), nbr.size()))) return rc;
+  const size_t rs = rsize(c), Gp = c->Gp, N = n_cells;
+  auto alloc0 = [&](void *&ptr, size_t bytes) -> int {
+    CUDA_TRY(c, cudaMalloc(&ptr, std::max<size_t>(bytes, 8)));
+    CUDA_TRY(c, cudaMemsetAsync(ptr, 0, std::max<size_t>(bytes, 8), c->stream));
+    return MOC_OK;
+  };
+  if ((rc = alloc0(c->d_cur, 2 * (size_t)n_if * Gp * rs))) return rc;
+  if ((rc = alloc0(c->d_leak, N * Gp * rs))) return rc;
+  if ((rc = alloc0(c->d_cphi, N * G * rs))) return rc;
+  if ((rc = alloc0(c->d_TV, N * G * rs))) return rc;
+  if ((rc = alloc0(c->d_SV, N * G * G * rs))) return rc;
+  if ((rc = alloc0(c->d_FV, N * G * rs))) return rc;
+  if ((rc = alloc0(c->d_CHI, N * G * rs))) return rc;
+  // one more group's worth of din and one more vector of phio: the per-group working set of the
+  // coarse solve when it does not fit in shared memory
+  if ((rc = alloc0(c->d_din, 2 * (size_t)n_if * (G + 1) * rs))) return rc;
+  if ((rc = alloc0(c->d_diag, N * G * rs))) return rc;
+  if ((rc = alloc0(c->d_phic, N * G * rs))) return rc;
+  if ((rc = alloc0(c->d_phin, N * rs))) return rc;
+  if ((rc = alloc0(c->d_phio, 2 * N * rs))) return rc;
+  if ((rc = alloc0(c->d_src, N * rs))) return rc;
+  {
+    void *ps = nullptr, *pv = nullptr;
+    if ((rc = alloc0(ps, N * (size_t)c->M * G * sizeof(double)))) return rc;
+    c->d_psum = (double *)ps;
+    std::vector<double> vol(N, 0.0);
+    for (int r = 0; r < R; ++r) vol[cell[r]] += g.area[r];
+    if ((rc = alloc0(pv, N * sizeof(double)))) return rc;
+    c->d_vol = (double *)pv;
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_vol, vol.data(), N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  }
+  if ((rc = alloc0(c->d_fis, N * rs))) return rc;
+  if ((rc = alloc0(c->d_ratio, N * G * rs))) return rc;
+  void *cp = nullptr, *ct = nullptr;
+  if ((rc = alloc0(cp, ((size_t)R + 255) / 256 * sizeof(double)))) return rc;
+  c->d_cpart = (double *)cp;
+  if ((rc = alloc0(ct, sizeof(unsigned)))) return rc;
+  c->d_cticket = (unsigned *)ct;
+  // the coarse solve's per-group working set in shared memory when it fits (next to the kernel's
+  // 8 KB reduction buffer): src, diag and two iterates per cell, one coefficient per entry, the
+  // entry offsets and neighbours
+  {
+    const size_t ne = 2 * (size_t)n_if;
+    const size_t need = (4 * N + ne) * rs + (N + 1 + ne) * sizeof(int32_t);
+    int dev_max = 0;
+    CUDA_TRY(c, cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    c->cm_smem = 0;
+    if (need + 8192 + 1024 <= (size_t)dev_max) {
+      if (c->precision == MOC_FP64)
+        CUDA_TRY(c, cudaFuncSetAttribute(cmfd_solve_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)need));
+      else
+        CUDA_TRY(c, cudaFuncSetAttribute(cmfd_solve_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)need));
+      c->cm_smem = need;
+    }
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->n_cells = n_cells;
+  c->n_if = n_if;
+  c->cm_outer = n_outer;
+  c->cm_inner = n_inner;
+  c->cmfd = true;
+  drop_graphs(c);
+  return MOC_OK;
+}
+
 int moc_set_fixed_source(moc_ctx *c, const double *S) {
   int rc = need_ready(c);
   if (rc) return rc;
@@ -737,6 +975,7 @@ int moc_set_fixed_source(moc_ctx *c, const double *S) {
     c->eigen = true;
     return moc_set_state(c, nullptr, 1.0, nullptr);
   }
+  if (c->cmfd) return fail(c, MOC_ERR_STATE, "set_fixed_source: CMFD acceleration is for eigenvalue mode only");
   for (size_t i = 0; i < RG; ++i)
     if (!(S[i] >= 0.0) || !std::isfinite(S[i])) return fail(c, MOC_ERR_ARG, "set_fixed_source: S must be finite and >= 0");
   if ((rc = upload(c, c->d_ext, S, RG))) return rc;
@@ -874,7 +1113,7 @@ int moc_get_work(const moc_ctx *c, int64_t *n_segments, int64_t *updates, int *k
   if (!c || !c->geo.has_tracks) return c ? MOC_ERR_STATE : MOC_ERR_ARG;
   if (n_segments) *n_segments = c->geo.n_segments();
   if (updates) *updates = 2 * c->geo.n_segments() * (int64_t)c->geo.n_polar * (int64_t)std::max(c->G, 0);
-  if (kernels) *kernels = (c->Gp == 8) ? 3 : 4;
+  if (kernels) *kernels = ((c->Gp == 8) ? 3 : 4) + (c->cmfd ? 5 : 0);
   return MOC_OK;
 }
 

@@ -555,3 +555,17 @@ def one_material(mesh: Mesh) -> Mesh:
 def with_bc(mesh: Mesh, bc) -> Mesh:
     """Copy of `mesh` with other boundary conditions."""
     return Mesh(mesh.xy.copy(), mesh.tri.copy(), mesh.mat.copy(), mesh.bbox, tuple(int(b) for b in bc), mesh.name)
+
+
+def grid_cells(mesh: Mesh, size: float):
+    """Coarse cells for acceleration: each triangle goes to the square of side `size` (over the
+    bounding box) that contains its centroid; empty squares are dropped. Returns (cell [n_tri],
+    n_cells)."""
+    c = mesh.centroids()
+    xmin, xmax, ymin, ymax = mesh.bbox
+    nx = max(1, int(math.ceil((xmax - xmin) / size - 1e-9)))
+    i = np.clip(np.floor((c[:, 0] - xmin) / size).astype(np.int64), 0, nx - 1)
+    j = np.clip(np.floor((c[:, 1] - ymin) / size).astype(np.int64), 0, 10 ** 9)
+    key = j * nx + i
+    uniq, inv = np.unique(key, return_inverse=True)
+    return inv.astype(np.int32), int(uniq.size)

@@ -273,3 +273,43 @@ def test_fp32_kernel_variants(precision, n_polar, G):
     phig, kg = m.get_state()
     assert abs(kg - ko) <= 5e-6 * ko, (kg, ko)
     assert _rel(phig, phio) <= 1e-4, _rel(phig, phio)
+
+
+def test_cmfd_outers_match_oracle_fp64():
+    """Accelerated outers from the same random state, GPU FP64 vs oracle, compared after each."""
+    prob = W.small_lattice_problem(3, bc=(1, 0, 1, 0), n_azim=24, ray_spacing=0.03)
+    cell, nc = W.grid_cells(prob.mesh, 1.26)
+    o = _oracle(prob)
+    o.set_cmfd(cell, nc, 5, 4)
+    m = moc.Moc.from_problem(prob, precision="fp64")
+    m.set_cmfd(cell, nc, 5, 4)
+    rng = np.random.default_rng(8)
+    T, _ = m.track_counts()
+    phi0 = rng.uniform(0.5, 1.5, (prob.mesh.n_tri, prob.xs.n_groups))
+    psi0 = rng.uniform(0.0, 0.2, (T, 2, 3, prob.xs.n_groups))
+    o.set_state(phi0, 1.1, psi0)
+    o.normalise()
+    m.set_state(phi0, 1.1, psi0)
+    for it in range(5):
+        o.outer(True)
+        kg, _ = m.outer(1)
+        phio, ko = o.get_state()
+        phig, _ = m.get_state()
+        assert abs(kg - ko) <= 1e-10 * ko, (it, kg, ko)
+        assert _rel(phig, phio) <= 1e-9, (it, _rel(phig, phio))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_cmfd_converges_to_the_unaccelerated_solution(precision):
+    prob = W.small_lattice_problem(5, bc=(1, 0, 1, 0), n_azim=16, ray_spacing=0.04)
+    cell, nc = W.grid_cells(prob.mesh, 1.26)
+    ref = moc.Moc.from_problem(prob, precision="fp64")
+    kr, nr, _, cr = ref.power_iterate(1e-11, 1e-10, 50000, check_every=10)
+    m = moc.Moc.from_problem(prob, precision=precision)
+    m.set_cmfd(cell, nc, 6, 6)
+    tol = (1e-10, 1e-9) if precision == "fp64" else (1e-7, 1e-6)
+    k, n, _, c = m.power_iterate(tol[0], tol[1], 50000, check_every=1)
+    assert cr and c
+    assert n < nr / 2, (n, nr)
+    assert abs(k - kr) <= (1e-9 if precision == "fp64" else 2e-6) * kr
+    assert _rel(m.get_state()[0], ref.get_state()[0]) <= (1e-7 if precision == "fp64" else 1e-4)

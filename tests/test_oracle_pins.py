@@ -442,3 +442,38 @@ def test_bf16_rounding_is_round_to_nearest_even():
     assert MO.round_bf16(np.float32(1.0 + 3 * 2 ** -8)) == 1.0 + 2 ** -6
     assert MO.round_bf16(np.float32(1.0 + 2 ** -8 + 2 ** -20)) == 1.0 + 2 ** -7
     assert MO.round_bf16(np.float32(-2.5)) == -2.5
+
+
+# ------------------------------------------------------------------------------ CMFD acceleration
+
+@pytest.mark.parametrize("bc", [(1, 1, 1, 1), (1, 0, 1, 0)])
+def test_cmfd_keeps_the_converged_solution_and_needs_fewer_outers(bc):
+    """The partial-current coarse balance reproduces the MOC currents, so the accelerated power
+    iteration converges to the unaccelerated solution, in fewer outers."""
+    prob = W.small_lattice_problem(3, bc=bc, n_azim=16, ray_spacing=0.05)
+    cell, nc = W.grid_cells(prob.mesh, 1.26)
+    a = oracle.Oracle.from_problem(prob, threads=4)
+    ka, na, _, ca = a.iterate(True, 1e-12, 1e-11, 20000)
+    b = oracle.Oracle.from_problem(prob, threads=4)
+    b.set_cmfd(cell, nc, 6, 6)
+    kb, nb, _, cb = b.iterate(True, 1e-12, 1e-11, 20000)
+    assert ca and cb
+    assert abs(ka - kb) < 1e-10
+    np.testing.assert_allclose(b.get_state()[0], a.get_state()[0], rtol=1e-8)
+    assert nb < na / 2, (na, nb)
+
+
+def test_cmfd_step_is_consistent_at_the_fixed_point():
+    """From a converged unaccelerated state one accelerated outer leaves k and the flux unchanged:
+    any error in the currents, homogenisation or coefficients would move them."""
+    prob = W.small_lattice_problem(3, bc=(1, 0, 1, 0), n_azim=16, ray_spacing=0.05)
+    cell, nc = W.grid_cells(prob.mesh, 1.26)
+    o = oracle.Oracle.from_problem(prob, threads=4)
+    o.iterate(True, 1e-13, 1e-12, 20000)
+    phi, k, psi = o.get_state(with_psi=True)
+    o.set_cmfd(cell, nc, 8, 8)
+    o.set_state(phi, k, psi)
+    o.outer(True)
+    phi2, k2 = o.get_state()
+    assert abs(k2 - k) < 1e-10
+    np.testing.assert_allclose(phi2, phi, rtol=1e-9)
