@@ -151,7 +151,7 @@ def time_to_converged_k(moc, prob, device, stream, pcm: float = 5.0):
     k_ref, _, _, _ = ref64.power_iterate(1e-10, 1e-8, 5000, check_every=5, raise_on_fail=False)
     out = {"k_ref": k_ref, "criterion": f"|k - k_ref| <= {pcm} pcm",
            "k_ref_from": "FP32 to |dk| <= 1e-7, continued in FP64 to |dk| <= 1e-10",
-           "cmfd": "pin-pitch (1.26 cm) coarse cells, 6 coarse power iterations x 6 Jacobi sweeps per outer"}
+           "cmfd": "pin-pitch (1.26 cm) coarse cells; per outer 6 coarse power iterations, 6 Gauss-Seidel sweeps per group"}
     from paper_2607_01591_gb300 import workloads as W
 
     cell, n_cells = W.grid_cells(prob.mesh, 1.26)

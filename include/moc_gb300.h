@@ -127,14 +127,20 @@ int moc_set_xs(moc_ctx *ctx, int n_mat, int G, const double *sigma_t, const doub
  * coarse mesh from the MOC surface currents, then the fine MOC solution updated with the
  * accelerated result). cell: [n_tri] coarse cell (0 .. n_cells-1) of every region, any partition
  * of the triangles; NULL switches the acceleration off. Partial-current form: the sweep tallies,
- * per pair of cells and direction, W * psi at every crossing between them and the outgoing
- * current at vacuum ends; each cell's balance uses flux-volume homogenised cross sections and
+ * per pair of cells and direction, W * psi at every crossing between them, and per cell the net
+ * current through the domain boundary (out at every track end, in at every track start, vacuum and
+ * reflective walls alike); each cell's balance uses flux-volume homogenised cross sections and
  * coefficients J/phi that reproduce the MOC currents, so the converged MOC solution is unchanged.
- * After each outer the coarse eigenproblem is iterated n_outer times (Gauss-Seidel in energy,
- * n_inner Jacobi sweeps per group), then phi and the incoming boundary flux are scaled by the
- * coarse/fine flux ratio of their cell and k becomes the coarse k. Eigenvalue mode only; must be
- * called after moc_set_xs (which switches it off). Errors: MOC_ERR_ARG, MOC_ERR_STATE. */
-int moc_set_cmfd(moc_ctx *ctx, const int32_t *cell, int n_cells, int n_outer, int n_inner);
+ * After each outer the coarse eigenproblem is iterated n_outer times (Gauss-Seidel in energy;
+ * per group n_inner over-relaxed Gauss-Seidel sweeps with factor omega in (0, 2), over a greedy
+ * colouring of the cells in ascending id, one colour at a time), then phi and the incoming
+ * boundary flux are scaled by the coarse/fine flux ratio of their cell and k becomes the coarse
+ * k. Eigenvalue mode only; must be called after moc_set_xs (which switches it off). The coarse
+ * solve runs in one thread block; its per-group working set is kept in shared memory when it
+ * fits in what the device allows a block after 9 KB (FP32: 16 bytes per cell and 6 per interface
+ * side, e.g. the 4,624 cells of a 68 x 68 grid), else in global memory. Errors: MOC_ERR_ARG,
+ * MOC_ERR_STATE. */
+int moc_set_cmfd(moc_ctx *ctx, const int32_t *cell, int n_cells, int n_outer, int n_inner, double omega);
 
 /* Fixed isotropic volumetric source S: [n_tri][G] (n/cm^3/s), switching the context to
  * fixed-source mode (fission ignored, no normalisation); NULL returns to eigenvalue mode. */

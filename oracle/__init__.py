@@ -32,7 +32,7 @@ def build(force: bool = False) -> str:
     os.makedirs(os.path.dirname(_OUT), exist_ok=True)
     if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
         tmp = _OUT + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-std=c11",
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _OUT)
     return _OUT
@@ -59,7 +59,7 @@ def _load():
         lib.orc_set_xs.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _d, _d, _d, _d]
         lib.orc_set_fixed_source.argtypes = [ctypes.c_void_p, _d]
         lib.orc_set_cmfd.restype = ctypes.c_int
-        lib.orc_set_cmfd.argtypes = [ctypes.c_void_p, _i32, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        lib.orc_set_cmfd.argtypes = [ctypes.c_void_p, _i32, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double]
         lib.orc_set_state.argtypes = [ctypes.c_void_p, _d, ctypes.c_double, _d]
         lib.orc_get_state.argtypes = [ctypes.c_void_p, _d, _d, _d]
         lib.orc_get_q.argtypes = [ctypes.c_void_p, _d]
@@ -177,13 +177,15 @@ class Oracle:
             assert S.shape == (self.n_regions, self.G)
             self._lib.orc_set_fixed_source(self._h, _p(S, _d))
 
-    def set_cmfd(self, cell=None, n_cells: int = 0, n_outer: int = 6, n_inner: int = 6):
-        """Coarse-mesh acceleration on cells `cell` [R] (None disables); call after set_xs."""
+    def set_cmfd(self, cell=None, n_cells: int = 0, n_outer: int = 6, n_inner: int = 6, omega: float = 1.0):
+        """Coarse-mesh acceleration on cells `cell` [R] (None disables); call after set_xs. Each
+        outer runs n_outer coarse power iterations with n_inner over-relaxed (omega) sweeps per
+        group."""
         if cell is None:
-            self._lib.orc_set_cmfd(self._h, None, 0, 0, 0)
+            self._lib.orc_set_cmfd(self._h, None, 0, 0, 0, 1.0)
             return
         c = _i32a(cell)
-        self._lib.orc_set_cmfd(self._h, _p(c, _i32), int(n_cells), int(n_outer), int(n_inner))
+        self._lib.orc_set_cmfd(self._h, _p(c, _i32), int(n_cells), int(n_outer), int(n_inner), float(omega))
         self._cell = c
 
     def set_state(self, phi=None, k: float = 1.0, psi=None):

@@ -87,11 +87,16 @@ typedef struct {
   double k;
   int n_threads;
   /* coarse-mesh finite difference acceleration (Alg. 1), partial-current form */
-  int cmfd, n_cells, n_if, cm_outer, cm_inner;
+  int cmfd, n_cells, n_if, cm_outer, cm_inner, n_colors;
+  double cm_omega;    /* over-relaxation factor of the coarse sweeps */
   int32_t *cell;      /* [R] */
+  int32_t *color;     /* [n_cells] greedy colouring: no two cells of one interface share a colour */
+  int32_t *nb_off, *nb_cell, *nb_in;  /* per cell, its neighbours in interface order and the
+                                         slot of the current from each neighbour into it */
   uint64_t *pairs;    /* [n_if] sorted (min cell << 32 | max cell) */
   double *cur;        /* [2 n_if][G]: slot 2e a->b (a the lower id), 2e+1 b->a */
-  double *cleak;      /* [n_cells][G] outgoing current at vacuum ends */
+  double *cleak;      /* [n_cells][G] net current out of the domain boundary: out at every track end
+                         (vacuum or reflective) minus in at every track start */
   char err[256];
 } orc_t;
 
@@ -112,7 +117,8 @@ void orc_destroy(orc_t *h) {
   free(h->link); free(h->area);
   free(h->st); free(h->nsf); free(h->chi); free(h->ss); free(h->ext);
   free(h->phi); free(h->q); free(h->tally); free(h->psi_in); free(h->psi_next); free(h->leak);
-  free(h->cell); free(h->pairs); free(h->cur); free(h->cleak);
+  free(h->cell); free(h->pairs); free(h->cur); free(h->cleak); free(h->color);
+  free(h->nb_off); free(h->nb_cell); free(h->nb_in);
   free(h);
 }
 
@@ -463,8 +469,10 @@ int orc_set_xs(orc_t *h, int n_mat, int G, const double *st, const double *nsf, 
   free(h->st); free(h->nsf); free(h->chi); free(h->ss);
   free(h->phi); free(h->q); free(h->tally); free(h->psi_in); free(h->psi_next); free(h->leak);
   free(h->ext); h->ext = NULL;
-  free(h->cell); free(h->pairs); free(h->cur); free(h->cleak);
-  h->cell = NULL; h->pairs = NULL; h->cur = NULL; h->cleak = NULL; h->cmfd = 0;
+  free(h->cell); free(h->pairs); free(h->cur); free(h->cleak); free(h->color);
+  free(h->nb_off); free(h->nb_cell); free(h->nb_in);
+  h->cell = NULL; h->pairs = NULL; h->cur = NULL; h->cleak = NULL; h->color = NULL; h->cmfd = 0;
+  h->nb_off = h->nb_cell = h->nb_in = NULL;
   h->n_mat = n_mat; h->G = G;
   h->st = xcalloc((size_t)n_mat * G, sizeof(double)); memcpy(h->st, st, (size_t)n_mat * G * sizeof(double));
   h->nsf = xcalloc((size_t)n_mat * G, sizeof(double)); memcpy(h->nsf, nsf, (size_t)n_mat * G * sizeof(double));
@@ -485,10 +493,15 @@ int orc_set_xs(orc_t *h, int n_mat, int G, const double *st, const double *nsf, 
 }
 
 /* Enable the acceleration on the coarse cells `cell` [R] (NULL disables). Interfaces are the
- * pairs of cells that consecutive segments of some track cross between. Call after orc_set_xs. */
-int orc_set_cmfd(orc_t *h, const int32_t *cell, int n_cells, int n_outer, int n_inner) {
-  free(h->cell); free(h->pairs); free(h->cur); free(h->cleak);
-  h->cell = NULL; h->pairs = NULL; h->cur = NULL; h->cleak = NULL; h->cmfd = 0;
+ * pairs of cells that consecutive segments of some track cross between. Cells are coloured
+ * greedily in ascending id (each takes the smallest colour none of its lower-id neighbours has),
+ * so cells of one colour share no interface and their over-relaxed updates are independent.
+ * Call after orc_set_xs. */
+int orc_set_cmfd(orc_t *h, const int32_t *cell, int n_cells, int n_outer, int n_inner, double omega) {
+  free(h->cell); free(h->pairs); free(h->cur); free(h->cleak); free(h->color);
+  free(h->nb_off); free(h->nb_cell); free(h->nb_in);
+  h->cell = NULL; h->pairs = NULL; h->cur = NULL; h->cleak = NULL; h->color = NULL; h->cmfd = 0;
+  h->nb_off = h->nb_cell = h->nb_in = NULL;
   if (!cell) return 0;
   h->cell = xcalloc(h->n_tri, sizeof(int32_t));
   memcpy(h->cell, cell, h->n_tri * sizeof(int32_t));
@@ -512,6 +525,40 @@ int orc_set_cmfd(orc_t *h, const int32_t *cell, int n_cells, int n_outer, int n_
   h->n_cells = n_cells; h->cm_outer = n_outer; h->cm_inner = n_inner;
   h->cur = xcalloc(2 * (size_t)nu * h->G, sizeof(double));
   h->cleak = xcalloc((size_t)(n_cells > 1 ? n_cells : 1) * h->G, sizeof(double));
+  h->cm_omega = omega;
+  /* neighbour lists */
+  h->nb_off = xcalloc((size_t)n_cells + 1, sizeof(int32_t));
+  h->nb_cell = xcalloc(2 * (size_t)nu + 1, sizeof(int32_t));
+  h->nb_in = xcalloc(2 * (size_t)nu + 1, sizeof(int32_t));
+  for (int e = 0; e < h->n_if; ++e) {
+    h->nb_off[(int)(h->pairs[e] >> 32) + 1]++;
+    h->nb_off[(int)(h->pairs[e] & 0xffffffffu) + 1]++;
+  }
+  for (int i = 0; i < n_cells; ++i) h->nb_off[i + 1] += h->nb_off[i];
+  int32_t *fill = xcalloc((size_t)n_cells + 1, sizeof(int32_t));
+  for (int e = 0; e < h->n_if; ++e) {
+    int a = (int)(h->pairs[e] >> 32), b = (int)(h->pairs[e] & 0xffffffffu);
+    /* slot 2e runs a -> b, slot 2e + 1 runs b -> a */
+    int qa = h->nb_off[a] + fill[a]++, qb = h->nb_off[b] + fill[b]++;
+    h->nb_cell[qa] = b; h->nb_in[qa] = 2 * e + 1;
+    h->nb_cell[qb] = a; h->nb_in[qb] = 2 * e;
+  }
+  free(fill);
+  /* greedy colouring over the interface graph */
+  h->color = xcalloc(n_cells > 1 ? n_cells : 1, sizeof(int32_t));
+  int *used = xcalloc((size_t)n_cells + 1, sizeof(int));  /* used[c] == i + 1: colour c taken for cell i */
+  h->n_colors = 0;
+  for (int i = 0; i < n_cells; ++i) {
+    for (int q = h->nb_off[i]; q < h->nb_off[i + 1]; ++q) {
+      int j = h->nb_cell[q];
+      if (j < i) used[h->color[j]] = i + 1;
+    }
+    int c = 0;
+    while (used[c] == i + 1) ++c;
+    h->color[i] = c;
+    if (c + 1 > h->n_colors) h->n_colors = c + 1;
+  }
+  free(used);
   h->cmfd = 1;
   return 0;
 }
@@ -602,6 +649,11 @@ static void transport_sweep(orc_t *h) {
         for (int p = 0; p < P; ++p) {
           double Wt = 4.0 * ORC_PI * h->omega_a[j] * h->polar_w[p] * h->delta_a[j] * h->sin_theta[p];
           double psi = h->psi_in[((size_t)(2 * t + d) * P + p) * G + g];
+          if (h->cmfd) {
+            /* current entering the domain at this start (zero at vacuum starts) */
+            int64_t s_first = d ? (s1 - 1) : s0;
+            h->cleak[(size_t)h->cell[h->seg_reg[s_first]] * G + g] -= Wt * psi;
+          }
           for (int64_t n = 0; n < s1 - s0; ++n) {
             int64_t s = d ? (s1 - 1 - n) : (s0 + n);
             int i = h->seg_reg[s];
@@ -620,12 +672,11 @@ static void transport_sweep(orc_t *h) {
           }
           int64_t e = h->link[2 * t + d];
           if (e >= 0) h->psi_next[((size_t)e * P + p) * G + g] = psi;
-          else {
-            lk += Wt * psi;
-            if (h->cmfd) {
-              int64_t s_last = d ? s0 : (s1 - 1);
-              h->cleak[(size_t)h->cell[h->seg_reg[s_last]] * G + g] += Wt * psi;
-            }
+          else lk += Wt * psi;
+          if (h->cmfd) {
+            /* current leaving the domain at this end, vacuum or reflective */
+            int64_t s_last = d ? s0 : (s1 - 1);
+            h->cleak[(size_t)h->cell[h->seg_reg[s_last]] * G + g] += Wt * psi;
           }
         }
       }
@@ -652,7 +703,8 @@ static void finalize_flux(const orc_t *h, double *phi_new) {
 
 /* The coarse step on the normalised new flux phi_new (currents already divided by the same
  * normalisation): homogenise per cell, coarse balance with partial-current coefficients, a fixed
- * number of coarse power iterations (Gauss-Seidel in energy, Jacobi in space), then scale phi_new
+ * number of coarse power iterations (Gauss-Seidel in energy, over-relaxed Gauss-Seidel sweeps in
+ * space, colour by colour), then scale phi_new
  * and the boundary flux for the next sweep by the coarse/fine ratio of their cell and take the
  * coarse k. */
 static void cmfd_step(orc_t *h, double *phi_new) {
@@ -695,7 +747,7 @@ static void cmfd_step(orc_t *h, double *phi_new) {
   }
   /* coefficients: out of cell i through interface e (cell i side s): D = J(out)/phi_i; in: J(in)/phi_j */
   double *diag = xcalloc((size_t)N * G, sizeof(double));
-  double *phic = xcalloc((size_t)N * G, sizeof(double)), *phin = xcalloc(N, sizeof(double));
+  double *phic = xcalloc((size_t)N * G, sizeof(double));
   double *fis = xcalloc(N, sizeof(double));
   for (int i = 0; i < N; ++i)
     for (int g = 0; g < G; ++g) {
@@ -723,24 +775,24 @@ static void cmfd_step(orc_t *h, double *phi_new) {
       F_old += f;
     }
     for (int g = 0; g < G; ++g) {
+      /* n_inner over-relaxed Gauss-Seidel sweeps, colour by colour (cells of one colour are
+       * independent): x_i <- x_i + omega (rhs_i / diag_i - x_i), rhs_i = fission and other groups'
+       * scattering into g + inflow from the neighbours at their current values */
       for (int j = 0; j < h->cm_inner; ++j) {
-        for (int i = 0; i < N; ++i) {
-          size_t x = (size_t)i * G + g;
-          double rhs = CH[x] * fis[i] / kc;
-          for (int gg = 0; gg < G; ++gg)
-            if (gg != g) rhs += SV[((size_t)i * G + gg) * G + g] * phic[(size_t)i * G + gg];
-          phin[i] = rhs;
-        }
-        for (int e = 0; e < h->n_if; ++e) {
-          int a = (int)(h->pairs[e] >> 32), b = (int)(h->pairs[e] & 0xffffffffu);
-          double pa = cphi[(size_t)a * G + g], pb = cphi[(size_t)b * G + g];
-          /* inflow into a from b: J(b->a)/phi_b * phic_b, and into b from a */
-          if (pb > 0.0) phin[a] += h->cur[(size_t)(2 * e + 1) * G + g] / pb * phic[(size_t)b * G + g];
-          if (pa > 0.0) phin[b] += h->cur[(size_t)(2 * e) * G + g] / pa * phic[(size_t)a * G + g];
-        }
-        for (int i = 0; i < N; ++i) {
-          size_t x = (size_t)i * G + g;
-          phic[x] = (diag[x] > 0.0) ? phin[i] / diag[x] : 0.0;
+        for (int c = 0; c < h->n_colors; ++c) {
+          for (int i = 0; i < N; ++i) {
+            if (h->color[i] != c) continue;
+            size_t x = (size_t)i * G + g;
+            double rhs = CH[x] * fis[i] / kc;
+            for (int gg = 0; gg < G; ++gg)
+              if (gg != g) rhs += SV[((size_t)i * G + gg) * G + g] * phic[(size_t)i * G + gg];
+            for (int q = h->nb_off[i]; q < h->nb_off[i + 1]; ++q) {
+              int nb = h->nb_cell[q];
+              double pn = cphi[(size_t)nb * G + g];
+              if (pn > 0.0) rhs += h->cur[(size_t)h->nb_in[q] * G + g] / pn * phic[(size_t)nb * G + g];
+            }
+            if (diag[x] > 0.0) phic[x] += h->cm_omega * (rhs / diag[x] - phic[x]);
+          }
         }
       }
     }
@@ -766,7 +818,7 @@ static void cmfd_step(orc_t *h, double *phi_new) {
       }
     }
   h->k = kc;
-  free(cphi); free(TV); free(FV); free(CH); free(SV); free(V); free(diag); free(phic); free(phin); free(fis);
+  free(cphi); free(TV); free(FV); free(CH); free(SV); free(V); free(diag); free(phic); free(fis);
 }
 
 /* One outer iteration: source, sweep, flux, and (eigen mode) k update + normalisation.

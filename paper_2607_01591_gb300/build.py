@@ -53,7 +53,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-I", INC, "-I", CSRC, "-Xcompiler", "-fPIC,-fopenmp",
                    "-c", os.path.join(CSRC, src), "-o", obj]
         else:
-            cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-fopenmp", "-I", INC, "-I", CSRC, "-c", os.path.join(CSRC, src),
+            cmd = ["g++", "-O2", "-ffp-contract=off", "-std=c++17", "-fPIC", "-fopenmp", "-I", INC, "-I", CSRC, "-c", os.path.join(CSRC, src),
                    "-o", obj]
         cmds.append(cmd)
 

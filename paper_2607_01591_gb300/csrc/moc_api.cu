@@ -50,10 +50,13 @@ struct moc_ctx {
   std::vector<double> h_nsf;  // host copy of nu*Sigma_f [M][G] (normalising a caller's state)
   // CMFD acceleration (off unless moc_set_cmfd was called)
   bool cmfd = false;
-  int n_cells = 0, n_if = 0, cm_outer = 0, cm_inner = 0;
-  int32_t *d_xing = nullptr, *d_cell = nullptr;
-  int32_t *d_cif_off = nullptr, *d_cif = nullptr, *d_if_cells = nullptr, *d_nbr = nullptr;
+  int n_cells = 0, n_if = 0, cm_outer = 0, cm_inner = 0, cm_colors = 0;
+  double cm_omega = 1.0;
+  int32_t *d_xoff = nullptr, *d_cell = nullptr;
+  int2 *d_xent = nullptr;
+  int32_t *d_cif_off = nullptr, *d_cif = nullptr, *d_if_cells = nullptr, *d_nbr = nullptr, *d_coff = nullptr;
   size_t cm_smem = 0;  // dynamic shared memory of the coarse solve (0: its working set stays in global memory)
+  bool cm_idx16 = false;  // neighbour ids staged as 16-bit
   void *d_cur = nullptr, *d_leak = nullptr, *d_cphi = nullptr, *d_TV = nullptr, *d_SV = nullptr, *d_FV = nullptr;
   void *d_CHI = nullptr, *d_din = nullptr, *d_diag = nullptr, *d_phic = nullptr, *d_phin = nullptr, *d_fis = nullptr;
   void *d_ratio = nullptr, *d_phio = nullptr, *d_src = nullptr;
@@ -108,12 +111,14 @@ void drop_graphs(moc_ctx *c) {
 
 void free_cmfd(moc_ctx *c) {
   drop_graphs(c);
-  dfree(c->d_xing);
+  dfree(c->d_xoff);
+  dfree(c->d_xent);
   dfree(c->d_cell);
   dfree(c->d_cif_off);
   dfree(c->d_cif);
   dfree(c->d_if_cells);
   dfree(c->d_nbr);
+  dfree(c->d_coff);
   dfree(c->d_cur);
   dfree(c->d_leak);
   dfree(c->d_cphi);
@@ -419,24 +424,25 @@ template <typename Real> int launch_source(moc_ctx *c, cudaStream_t st) {
   return MOC_OK;
 }
 
-template <typename Real, int P, int TM> void sweep_launch(moc_ctx *c, cudaStream_t st) {
+template <typename Real, int P, int TM, bool CM> void sweep_launch(moc_ctx *c, cudaStream_t st) {
   const long long n = (long long)c->T * 2 * c->G;
   const int bs = 128;  // matches the kernel's launch bounds (128 threads, 9 blocks per SM)
   const long long nb = (n + bs - 1) / bs;
-  sweep_kernel<Real, P, TM><<<(unsigned)nb, bs, 0, st>>>(
+  CmfdDev<Real> cm{c->d_xoff, c->d_xent, c->d_cell, (double *)c->d_cur, (double *)c->d_leak};
+  sweep_kernel<Real, P, TM, CM><<<(unsigned)nb, bs, 0, st>>>(
       c->d_trk, (const SegRec<Real> *)c->d_seg, c->d_link, (const Real *)c->d_wgt, (const Real *)c->d_inv_sin,
       (const typename Pair<Real>::T *)c->d_xsq, (Real *)c->d_tsum, (Real *)c->d_tcomp,
-      (const Real *)c->d_psi[c->cur], (Real *)c->d_psi[c->cur ^ 1], c->d_scal, n, c->G, c->Gp);
+      (const Real *)c->d_psi[c->cur], (Real *)c->d_psi[c->cur ^ 1], c->d_scal, n, c->G, c->Gp, cm);
 }
 
-template <typename Real, int TM> int launch_sweep_p(moc_ctx *c, cudaStream_t st) {
+template <typename Real, int TM, bool CM> int launch_sweep_p(moc_ctx *c, cudaStream_t st) {
   switch (c->P) {
-    case 1: sweep_launch<Real, 1, TM>(c, st); break;
-    case 2: sweep_launch<Real, 2, TM>(c, st); break;
-    case 3: sweep_launch<Real, 3, TM>(c, st); break;
-    case 4: sweep_launch<Real, 4, TM>(c, st); break;
-    case 5: sweep_launch<Real, 5, TM>(c, st); break;
-    case 6: sweep_launch<Real, 6, TM>(c, st); break;
+    case 1: sweep_launch<Real, 1, TM, CM>(c, st); break;
+    case 2: sweep_launch<Real, 2, TM, CM>(c, st); break;
+    case 3: sweep_launch<Real, 3, TM, CM>(c, st); break;
+    case 4: sweep_launch<Real, 4, TM, CM>(c, st); break;
+    case 5: sweep_launch<Real, 5, TM, CM>(c, st); break;
+    case 6: sweep_launch<Real, 6, TM, CM>(c, st); break;
     default: return fail(c, MOC_ERR_ARG, "unsupported polar count");
   }
   CUDA_TRY(c, cudaGetLastError());
@@ -470,41 +476,18 @@ template <int TM> int launch_chunk(moc_ctx *c, cudaStream_t st) {
   return MOC_OK;
 }
 
-template <typename Real, int P, int TM> void sweep_cmfd_launch(moc_ctx *c, cudaStream_t st) {
-  const long long n = (long long)c->T * 2 * c->G;
-  CmfdDev<Real> cm{c->d_xing, c->d_cell, (Real *)c->d_cur, (Real *)c->d_leak};
-  sweep_cmfd_kernel<Real, P, TM><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(
-      c->d_trk, (const SegRec<Real> *)c->d_seg, c->d_link, (const Real *)c->d_wgt, (const Real *)c->d_inv_sin,
-      (const typename Pair<Real>::T *)c->d_xsq, (Real *)c->d_tsum, (Real *)c->d_tcomp,
-      (const Real *)c->d_psi[c->cur], (Real *)c->d_psi[c->cur ^ 1], c->d_scal, n, c->G, c->Gp, cm);
-}
-
-template <typename Real, int TM> int launch_sweep_cmfd_p(moc_ctx *c, cudaStream_t st) {
-  switch (c->P) {
-    case 1: sweep_cmfd_launch<Real, 1, TM>(c, st); break;
-    case 2: sweep_cmfd_launch<Real, 2, TM>(c, st); break;
-    case 3: sweep_cmfd_launch<Real, 3, TM>(c, st); break;
-    case 4: sweep_cmfd_launch<Real, 4, TM>(c, st); break;
-    case 5: sweep_cmfd_launch<Real, 5, TM>(c, st); break;
-    case 6: sweep_cmfd_launch<Real, 6, TM>(c, st); break;
-    default: return fail(c, MOC_ERR_ARG, "unsupported polar count");
-  }
-  CUDA_TRY(c, cudaGetLastError());
-  return MOC_OK;
-}
-
 int launch_sweep(moc_ctx *c, cudaStream_t st) {
   if (c->cmfd) {
-    if (c->precision == MOC_FP64) return launch_sweep_cmfd_p<double, 0>(c, st);
-    if (c->precision == MOC_FP32) return launch_sweep_cmfd_p<float, 1>(c, st);
-    return launch_sweep_cmfd_p<float, 0>(c, st);
+    if (c->precision == MOC_FP64) return launch_sweep_p<double, 0, true>(c, st);
+    if (c->precision == MOC_FP32) return launch_sweep_p<float, 1, true>(c, st);
+    return launch_sweep_p<float, 0, true>(c, st);
   }
-  if (c->precision == MOC_FP64) return launch_sweep_p<double, 0>(c, st);
+  if (c->precision == MOC_FP64) return launch_sweep_p<double, 0, false>(c, st);
   // many groups: one thread per chunk of 4 groups shares the per-segment cost; few groups: one
   // thread per group keeps each lane's serial chain along a long track short
   if (c->P == 3 && c->G > 8) return c->precision == MOC_FP32 ? launch_chunk<1>(c, st) : launch_chunk<0>(c, st);
-  if (c->precision == MOC_FP32) return launch_sweep_p<float, 1>(c, st);
-  return launch_sweep_p<float, 0>(c, st);
+  if (c->precision == MOC_FP32) return launch_sweep_p<float, 1, false>(c, st);
+  return launch_sweep_p<float, 0, false>(c, st);
 }
 
 template <typename Real> int launch_finalize_reduce(moc_ctx *c, cudaStream_t st) {
@@ -561,22 +544,23 @@ template <typename Real> int launch_cmfd(moc_ctx *c, cudaStream_t st) {
       (const Real *)c->d_sig_s, (Real *)c->d_cphi, (Real *)c->d_TV, (Real *)c->d_SV, (Real *)c->d_FV,
       (Real *)c->d_CHI);
   CUDA_TRY(c, cudaGetLastError());
-  CmfdTopo t{N, G, c->Gp, 2 * c->n_if, c->d_nbr, c->d_cif_off, c->d_cif, c->d_if_cells};
-  auto solve = c->cm_smem ? cmfd_solve_kernel<Real, true> : cmfd_solve_kernel<Real, false>;
-  solve<<<1, 1024, c->cm_smem, st>>>(t, (Real *)c->d_cur, (Real *)c->d_leak, (const Real *)c->d_cphi,
-                                             (const Real *)c->d_TV, (const Real *)c->d_SV, (const Real *)c->d_FV,
-                                             (const Real *)c->d_CHI, (Real *)c->d_din, (Real *)c->d_diag,
-                                             (Real *)c->d_phic, (Real *)c->d_phin, (Real *)c->d_phio,
-                                             (Real *)c->d_src, (Real *)c->d_fis,
-                                             (Real *)c->d_ratio, c->d_scal, c->cm_outer, c->cm_inner);
+  CmfdTopo t{N, G, c->Gp, 2 * c->n_if, c->cm_colors, c->d_nbr, c->d_cif_off, c->d_cif, c->d_if_cells, c->d_coff};
+  auto solve = !c->cm_smem ? cmfd_solve_kernel<Real, false, int32_t>
+               : c->cm_idx16 ? cmfd_solve_kernel<Real, true, uint16_t> : cmfd_solve_kernel<Real, true, int32_t>;
+  solve<<<1, 1024, c->cm_smem, st>>>(t, (double *)c->d_cur, (double *)c->d_leak, (const Real *)c->d_cphi,
+                                     (const Real *)c->d_TV, (const Real *)c->d_SV, (const Real *)c->d_FV,
+                                     (const Real *)c->d_CHI, (Real *)c->d_din, (Real *)c->d_diag,
+                                     (Real *)c->d_phic, (Real *)c->d_phin, (Real *)c->d_phio,
+                                     (Real *)c->d_src, (Real *)c->d_fis, (Real *)c->d_ratio, c->d_scal,
+                                     c->cm_outer, c->cm_inner, (Real)c->cm_omega);
   CUDA_TRY(c, cudaGetLastError());
-  cmfd_prolong_kernel<Real><<<(R + 255) / 256, 256, 0, st>>>(R, G, c->Gp, c->d_cell, c->d_mat, (const Real *)c->d_nsf,
+  cmfd_prolong_kernel<Real><<<(R + 255) / 256, 256, 0, st>>>(R, G, c->Gp, N, c->d_cell, c->d_mat, (const Real *)c->d_nsf,
                                                              c->d_area, (const Real *)c->d_ratio, (Real *)c->d_phi,
                                                              c->d_cpart, c->d_cticket, c->d_scal);
   CUDA_TRY(c, cudaGetLastError());
   const long long n = (long long)c->T * 2 * G;
   cmfd_psi_kernel<Real><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-      n, c->P, G, c->d_trk, (const SegRec<Real> *)c->d_seg, c->d_fed, c->d_cell, (const Real *)c->d_ratio,
+      n, c->P, G, N, c->d_trk, (const SegRec<Real> *)c->d_seg, c->d_fed, c->d_cell, (const Real *)c->d_ratio,
       (Real *)c->d_psi[c->cur]);
   CUDA_TRY(c, cudaGetLastError());
   return MOC_OK;
@@ -834,43 +818,91 @@ int moc_set_xs(moc_ctx *c, int n_mat, int G, const double *st, const double *nsf
   return moc_set_state(c, nullptr, 1.0, nullptr);
 }
 
-int moc_set_cmfd(moc_ctx *c, const int32_t *cell, int n_cells, int n_outer, int n_inner) {
+int moc_set_cmfd(moc_ctx *c, const int32_t *cell_in, int n_cells, int n_outer, int n_inner, double omega) {
   int rc = need_ready(c);
   if (rc) return rc;
   cudaSetDevice(c->device);
   free_cmfd(c);
-  if (!cell) return MOC_OK;
+  if (!cell_in) return MOC_OK;
   const Geometry &g = c->geo;
   const int R = g.n_tri, G = c->G;
   if (n_cells < 1 || n_outer < 1 || n_inner < 1) return fail(c, MOC_ERR_ARG, "set_cmfd: bad sizes or iteration counts");
+  if (!(omega > 0.0 && omega < 2.0)) return fail(c, MOC_ERR_ARG, "set_cmfd: omega must lie in (0, 2)");
   for (int r = 0; r < R; ++r)
-    if (cell[r] < 0 || cell[r] >= n_cells) return fail(c, MOC_ERR_ARG, "set_cmfd: cell id out of range");
-  // interfaces: pairs of cells that consecutive segments of some track cross between
-  std::vector<uint64_t> pairs;
+    if (cell_in[r] < 0 || cell_in[r] >= n_cells) return fail(c, MOC_ERR_ARG, "set_cmfd: cell id out of range");
   const int64_t T = g.n_tracks();
-  for (int64_t t = 0; t < T; ++t)
-    for (int64_t q = g.seg_off[t]; q + 1 < g.seg_off[t + 1]; ++q) {
-      const uint32_t a = (uint32_t)cell[g.seg_reg[q]], b = (uint32_t)cell[g.seg_reg[q + 1]];
-      if (a != b) pairs.push_back(((uint64_t)std::min(a, b) << 32) | std::max(a, b));
+  // interfaces: pairs of cells that consecutive segments of some track cross between
+  auto find_pairs = [&](const int32_t *cell) {
+    std::vector<uint64_t> pr;
+    for (int64_t t = 0; t < T; ++t)
+      for (int64_t q = g.seg_off[t]; q + 1 < g.seg_off[t + 1]; ++q) {
+        const uint32_t a = (uint32_t)cell[g.seg_reg[q]], b = (uint32_t)cell[g.seg_reg[q + 1]];
+        if (a != b) pr.push_back(((uint64_t)std::min(a, b) << 32) | std::max(a, b));
+      }
+    std::sort(pr.begin(), pr.end());
+    pr.erase(std::unique(pr.begin(), pr.end()), pr.end());
+    return pr;
+  };
+  std::vector<uint64_t> pairs = find_pairs(cell_in);
+  // greedy colouring in ascending cell id (smallest colour none of the lower-id neighbours has),
+  // then cells renumbered colour by colour (ascending id within a colour), so the over-relaxed
+  // sweeps update one contiguous range of independent cells per colour
+  std::vector<int32_t> adj_off(n_cells + 1, 0), adj((size_t)2 * pairs.size());
+  for (uint64_t p : pairs) {
+    adj_off[(p >> 32) + 1]++;
+    adj_off[(p & 0xffffffffu) + 1]++;
+  }
+  for (int i = 0; i < n_cells; ++i) adj_off[i + 1] += adj_off[i];
+  {
+    std::vector<int32_t> fill(adj_off.begin(), adj_off.end() - 1);
+    for (uint64_t p : pairs) {
+      const int a = (int)(p >> 32), b = (int)(p & 0xffffffffu);
+      adj[fill[a]++] = b;
+      adj[fill[b]++] = a;
     }
+  }
+  std::vector<int32_t> color(n_cells, 0), used(n_cells + 1, -1);
+  int n_colors = 0;
+  for (int i = 0; i < n_cells; ++i) {
+    for (int q = adj_off[i]; q < adj_off[i + 1]; ++q)
+      if (adj[q] < i) used[color[adj[q]]] = i;
+    int col = 0;
+    while (used[col] == i) ++col;
+    color[i] = col;
+    n_colors = std::max(n_colors, col + 1);
+  }
+  std::vector<int32_t> coff(n_colors + 1, 0), newid(n_cells);
+  for (int i = 0; i < n_cells; ++i) coff[color[i] + 1]++;
+  for (int k = 0; k < n_colors; ++k) coff[k + 1] += coff[k];
+  {
+    std::vector<int32_t> fill(coff.begin(), coff.end() - 1);
+    for (int i = 0; i < n_cells; ++i) newid[i] = fill[color[i]]++;
+  }
+  std::vector<int32_t> cellv(R);
+  for (int r = 0; r < R; ++r) cellv[r] = newid[cell_in[r]];
+  const int32_t *cell = cellv.data();
+  for (uint64_t &p : pairs) {
+    const uint32_t a = (uint32_t)newid[p >> 32], b = (uint32_t)newid[p & 0xffffffffu];
+    p = ((uint64_t)std::min(a, b) << 32) | std::max(a, b);
+  }
   std::sort(pairs.begin(), pairs.end());
-  pairs.erase(std::unique(pairs.begin(), pairs.end()), pairs.end());
   const int n_if = (int)pairs.size();
   auto iface = [&](uint32_t a, uint32_t b) {
     const uint64_t key = ((uint64_t)std::min(a, b) << 32) | std::max(a, b);
     return (int)(std::lower_bound(pairs.begin(), pairs.end(), key) - pairs.begin());
   };
-  // crossing code of the boundary after each segment (forward order), laid out like the
-  // uploaded segment array (internal track order, kSegPad padding records at each end)
-  std::vector<int32_t> xing(c->S + 2 * kSegPad, -1);
-  int64_t o = kSegPad;
+  // coarse boundaries crossed by each track, in internal track order and along the track:
+  // {segment p after which the boundary lies (forward numbering), 2 * interface + (a > b)}
+  std::vector<int32_t> xoff(T + 1, 0);
+  std::vector<int2> xent;
   for (int64_t i = 0; i < T; ++i) {
     const int64_t t = c->perm[i];
-    for (int64_t q = g.seg_off[t]; q < g.seg_off[t + 1]; ++q, ++o) {
-      if (q + 1 == g.seg_off[t + 1]) continue;
+    for (int64_t q = g.seg_off[t]; q + 1 < g.seg_off[t + 1]; ++q) {
       const uint32_t a = (uint32_t)cell[g.seg_reg[q]], b = (uint32_t)cell[g.seg_reg[q + 1]];
-      if (a != b) xing[o] = 2 * iface(a, b) + (a > b ? 1 : 0);
+      if (a != b) xent.push_back(make_int2((int)(q - g.seg_off[t]), 2 * iface(a, b) + (a > b ? 1 : 0)));
     }
+    if (xent.size() > (size_t)INT32_MAX) return fail(c, MOC_ERR_ARG, "set_cmfd: too many coarse-boundary crossings");
+    xoff[i + 1] = (int32_t)xent.size();
   }
   // incidences: each interface appears in the lists of both its cells, in interface order
   std::vector<int32_t> cif_off(n_cells + 1, 0), cif(2 * (size_t)n_if), if_cells(2 * (size_t)n_if);
@@ -891,33 +923,34 @@ int moc_set_cmfd(moc_ctx *c, const int32_t *cell, int n_cells, int n_outer, int 
   }
   std::vector<int32_t> nbr(2 * (size_t)n_if);
   for (size_t q = 0; q < nbr.size(); ++q) nbr[q] = if_cells[2 * (cif[q] >> 1) + ((cif[q] & 1) ^ 1)];
-  std::vector<int32_t> cellv(cell, cell + R);
-  if ((rc = upload(c, c->d_xing, xing.data(), xing.size()))) return rc;
+  if ((rc = upload(c, c->d_xoff, xoff.data(), xoff.size()))) return rc;
+  if ((rc = upload(c, c->d_xent, xent.data(), xent.size()))) return rc;
   if ((rc = upload(c, c->d_cell, cellv.data(), cellv.size()))) return rc;
   if ((rc = upload(c, c->d_cif_off, cif_off.data(), cif_off.size()))) return rc;
   if ((rc = upload(c, c->d_cif, cif.data(), cif.size()))) return rc;
   if ((rc = upload(c, c->d_if_cells, if_cells.data(), if_cells.size()))) return rc;
   if ((rc = upload(c, c->d_nbr, nbr.data(), nbr.size()))) return rc;
+  if ((rc = upload(c, c->d_coff, coff.data(), coff.size()))) return rc;
   const size_t rs = rsize(c), Gp = c->Gp, N = n_cells;
   auto alloc0 = [&](void *&ptr, size_t bytes) -> int {
     CUDA_TRY(c, cudaMalloc(&ptr, std::max<size_t>(bytes, 8)));
     CUDA_TRY(c, cudaMemsetAsync(ptr, 0, std::max<size_t>(bytes, 8), c->stream));
     return MOC_OK;
   };
-  if ((rc = alloc0(c->d_cur, 2 * (size_t)n_if * Gp * rs))) return rc;
-  if ((rc = alloc0(c->d_leak, N * Gp * rs))) return rc;
+  if ((rc = alloc0(c->d_cur, 2 * (size_t)n_if * Gp * sizeof(double)))) return rc;
+  if ((rc = alloc0(c->d_leak, N * Gp * sizeof(double)))) return rc;
   if ((rc = alloc0(c->d_cphi, N * G * rs))) return rc;
   if ((rc = alloc0(c->d_TV, N * G * rs))) return rc;
   if ((rc = alloc0(c->d_SV, N * G * G * rs))) return rc;
   if ((rc = alloc0(c->d_FV, N * G * rs))) return rc;
   if ((rc = alloc0(c->d_CHI, N * G * rs))) return rc;
-  // one more group's worth of din and one more vector of phio: the per-group working set of the
-  // coarse solve when it does not fit in shared memory
+  // one more group's worth of din: the per-group coefficients of the coarse solve when its working
+  // set does not fit in shared memory (phin, phio and src hold the iterate, 1/diagonal, source)
   if ((rc = alloc0(c->d_din, 2 * (size_t)n_if * (G + 1) * rs))) return rc;
   if ((rc = alloc0(c->d_diag, N * G * rs))) return rc;
   if ((rc = alloc0(c->d_phic, N * G * rs))) return rc;
   if ((rc = alloc0(c->d_phin, N * rs))) return rc;
-  if ((rc = alloc0(c->d_phio, 2 * N * rs))) return rc;
+  if ((rc = alloc0(c->d_phio, N * rs))) return rc;
   if ((rc = alloc0(c->d_src, N * rs))) return rc;
   {
     void *ps = nullptr, *pv = nullptr;
@@ -937,21 +970,23 @@ int moc_set_cmfd(moc_ctx *c, const int32_t *cell, int n_cells, int n_outer, int 
   if ((rc = alloc0(ct, sizeof(unsigned)))) return rc;
   c->d_cticket = (unsigned *)ct;
   // the coarse solve's per-group working set in shared memory when it fits (next to the kernel's
-  // 8 KB reduction buffer): src, diag and two iterates per cell, one coefficient per entry, the
-  // entry offsets and neighbours
+  // 8 KB reduction buffer): source, 1/diagonal and iterate per cell, one coefficient per entry,
+  // the entry offsets, and the neighbour ids (16-bit when the cell count allows)
   {
     const size_t ne = 2 * (size_t)n_if;
-    const size_t need = (4 * N + ne) * rs + (N + 1 + ne) * sizeof(int32_t);
+    const bool idx16 = n_cells <= 65535;
+    const size_t need = (3 * N + ne) * rs + (N + 1) * sizeof(int32_t) + ne * (idx16 ? 2 : 4);
     int dev_max = 0;
     CUDA_TRY(c, cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     c->cm_smem = 0;
+    c->cm_idx16 = idx16;
     if (need + 8192 + 1024 <= (size_t)dev_max) {
+      const void *fn;
       if (c->precision == MOC_FP64)
-        CUDA_TRY(c, cudaFuncSetAttribute(cmfd_solve_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)need));
+        fn = idx16 ? (const void *)cmfd_solve_kernel<double, true, uint16_t> : (const void *)cmfd_solve_kernel<double, true, int32_t>;
       else
-        CUDA_TRY(c, cudaFuncSetAttribute(cmfd_solve_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)need));
+        fn = idx16 ? (const void *)cmfd_solve_kernel<float, true, uint16_t> : (const void *)cmfd_solve_kernel<float, true, int32_t>;
+      CUDA_TRY(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
       c->cm_smem = need;
     }
   }
@@ -960,6 +995,8 @@ int moc_set_cmfd(moc_ctx *c, const int32_t *cell, int n_cells, int n_outer, int 
   c->n_if = n_if;
   c->cm_outer = n_outer;
   c->cm_inner = n_inner;
+  c->cm_omega = omega;
+  c->cm_colors = n_colors;
   c->cmfd = true;
   drop_graphs(c);
   return MOC_OK;

@@ -150,15 +150,37 @@ template <> struct Tally<1, float> {
   }
 };
 
+// Coarse-mesh current tallies of the CMFD acceleration (used when the sweep's CM flag is set).
+template <typename Real> struct CmfdDev {
+  // coarse-cell boundaries crossed by each track (internal track order), sorted along the track:
+  // entries xoff[t] .. xoff[t+1]-1, each {p, code}: the boundary between the track's segments p and
+  // p+1 (forward numbering), code = 2 * interface + (1 when forward travel leaves the interface's
+  // higher cell)
+  const int32_t *xoff;  // [T+1]
+  const int2 *xent;     // [crossings]
+  const int32_t *cell;  // [R] coarse cell of each region
+  // FP64 in every precision: a coarse boundary sums thousands of crossings, and FP32 rounding of
+  // those sums (different in every sweep, atomics reorder them) would make the coarse operator
+  // inconsistent with the fine solution and keep the iteration from settling
+  double *cur;          // [2 n_if][Gp] partial currents per interface and direction
+  double *leak;         // [N][Gp] net current out of the domain boundary: out at every track end
+                        // (vacuum or reflective) minus in at every track start. Reflective walls
+                        // cancel only at convergence; leaving them out lets the accelerated
+                        // iteration settle on a point that is not the transport solution
+};
+
 // One thread per (track, sense, group); polar angles held in registers; g fastest so the G
 // threads of one track end read one contiguous row of region data and hit one tally row.
-template <typename Real, int P, int TM>
-__global__ void __launch_bounds__(128, 9) sweep_kernel(
+// CM: also tally the partial current W psi at every coarse-cell boundary the track crosses and
+// the current through the domain boundary at both ends (CMFD). The crossing list is read one
+// entry ahead of use, so its loads stay off the per-segment critical path.
+template <typename Real, int P, int TM, bool CM>
+__global__ void __launch_bounds__(128, CM ? 8 : 9) sweep_kernel(
     const TrackRec *__restrict__ trk, const SegRec<Real> *__restrict__ seg, const int32_t *__restrict__ link,
     const Real *__restrict__ wgt, const Real *__restrict__ inv_sin,
     const typename Pair<Real>::T *__restrict__ xsq, Real *__restrict__ tsum, Real *__restrict__ tcomp,
     const Real *__restrict__ psi_in, Real *__restrict__ psi_out, const double *__restrict__ scal,
-    long long n_threads, int G, int Gp) {
+    long long n_threads, int G, int Gp, CmfdDev<Real> cm) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n_threads) return;
   const long long td = idx / G;
@@ -177,6 +199,24 @@ __global__ void __launch_bounds__(128, 9) sweep_kernel(
   // the segment array has kSegPad padding records at each end, so the three-ahead prefetch below
   // never needs a bounds test (records past a track's end belong to a neighbour or the padding)
   const SegRec<Real> *sp = seg + (d ? tr.off + tr.n - 1 : tr.off);
+  // crossing entries in travel order: E_k = xent[d ? hi-1-k : lo+k]; the tally for E_k happens after
+  // travel step d ? n - 2 - p : p. cx is the next entry, nx the one after it (already loaded).
+  int xk = 0, xm = 0, xlo = 0, xhi = 0, xt = 0x7fffffff;
+  int2 cx = make_int2(0, -1), nx = make_int2(0, -1);
+  if (CM) {
+    xlo = cm.xoff[td >> 1];
+    xhi = cm.xoff[(td >> 1) + 1];
+    xm = xhi - xlo;
+    if (xm > 0) cx = cm.xent[d ? xhi - 1 : xlo];
+    if (xm > 1) nx = cm.xent[d ? xhi - 2 : xlo + 1];
+    if (xm > 0) xt = d ? tr.n - 2 - cx.x : cx.x;
+  }
+  if (CM && tr.n > 0) {
+    Real j = 0;
+#pragma unroll
+    for (int p = 0; p < P; ++p) j = fma(w[p], psi[p], j);
+    if (j != (Real)0) atomicAdd(cm.leak + (size_t)cm.cell[sp->r] * Gp + g, -(double)j);
+  }
   Tally<TM, Real> tally;
   SegRec<Real> s0 = sp[0], s1 = sp[step], s2 = sp[2 * step];
   typename Pair<Real>::T xq0 = xsq[(size_t)s0.r * Gp + g];
@@ -196,6 +236,17 @@ __global__ void __launch_bounds__(128, 9) sweep_kernel(
       acc = fma(w[p], dl, acc);
     }
     tally.add(tsum, tcomp, (unsigned)(s0.r * Gp + g), acc);
+    if (CM && n == xt) {
+      // partial current into the next cell; backward travel crosses the boundary the other way
+      Real j = 0;
+#pragma unroll
+      for (int p = 0; p < P; ++p) j = fma(w[p], psi[p], j);
+      atomicAdd(cm.cur + (size_t)(cx.y ^ d) * Gp + g, (double)j);
+      ++xk;
+      cx = nx;
+      xt = (xk < xm) ? (d ? tr.n - 2 - cx.x : cx.x) : 0x7fffffff;
+      if (xk + 1 < xm) nx = cm.xent[d ? xhi - 2 - xk : xlo + 1 + xk];
+    }
     s0 = s1;
     s1 = s2;
     s2 = s3;
@@ -208,6 +259,12 @@ __global__ void __launch_bounds__(128, 9) sweep_kernel(
   if (e >= 0) {
 #pragma unroll
     for (int p = 0; p < P; ++p) psi_out[((long long)e * P + p) * G + g] = psi[p];
+  }
+  if (CM && tr.n > 0) {
+    Real j = 0;
+#pragma unroll
+    for (int p = 0; p < P; ++p) j = fma(w[p], psi[p], j);
+    atomicAdd(cm.leak + (size_t)cm.cell[sp[-step].r] * Gp + g, (double)j);
   }
 }
 

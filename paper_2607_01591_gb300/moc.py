@@ -81,7 +81,7 @@ def load_library(path: Optional[str] = None):
             "moc_get_timing": (ctypes.c_int, [_vp, _d, _i64]),
             "moc_get_work": (ctypes.c_int, [_vp, _i64, _i64, ctypes.POINTER(ctypes.c_int)]),
             "moc_synchronize": (ctypes.c_int, [_vp]),
-            "moc_set_cmfd": (ctypes.c_int, [_vp, _i32, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+            "moc_set_cmfd": (ctypes.c_int, [_vp, _i32, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double]),
             "moc_ws_features": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.c_int, _vp]),
             "moc_ws_apply": (ctypes.c_int, [_vp, _vp, _d]),
             "moc_mlp_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -299,14 +299,16 @@ class Moc:
             assert S.shape == (self.n_regions, self.G)
         self._check(self._lib.moc_set_fixed_source(self._h, _p(S, _d)))
 
-    def set_cmfd(self, cell=None, n_cells: int = 0, n_outer: int = 6, n_inner: int = 6):
-        """CMFD acceleration on the coarse cells `cell` [n_tri] (None switches it off)."""
+    def set_cmfd(self, cell=None, n_cells: int = 0, n_outer: int = 6, n_inner: int = 6, omega: float = 1.0):
+        """CMFD acceleration on the coarse cells `cell` [n_tri] (None switches it off): per outer,
+        n_outer coarse power iterations with n_inner over-relaxed (omega) sweeps per group."""
         if cell is None:
-            self._check(self._lib.moc_set_cmfd(self._h, None, 0, 0, 0))
+            self._check(self._lib.moc_set_cmfd(self._h, None, 0, 0, 0, 1.0))
             return
         cell = _i32a(cell)
         assert cell.size == self.n_regions
-        self._check(self._lib.moc_set_cmfd(self._h, _p(cell, _i32), int(n_cells), int(n_outer), int(n_inner)))
+        self._check(self._lib.moc_set_cmfd(self._h, _p(cell, _i32), int(n_cells), int(n_outer), int(n_inner),
+                                           float(omega)))
 
     def set_state(self, phi=None, k: float = 1.0, psi=None):
         phi, psi = _f64(phi), _f64(psi)

@@ -275,14 +275,16 @@ def test_fp32_kernel_variants(precision, n_polar, G):
     assert _rel(phig, phio) <= 1e-4, _rel(phig, phio)
 
 
-def test_cmfd_outers_match_oracle_fp64():
-    """Accelerated outers from the same random state, GPU FP64 vs oracle, compared after each."""
+@pytest.mark.parametrize("cell_size,omega", [(1.26, 1.0), (1.26, 1.6), (0.63, 1.4)])
+def test_cmfd_outers_match_oracle_fp64(cell_size, omega):
+    """Accelerated outers from the same random state, GPU FP64 vs oracle, compared after each
+    (Gauss-Seidel and over-relaxed coarse sweeps; pin and half-pin cells)."""
     prob = W.small_lattice_problem(3, bc=(1, 0, 1, 0), n_azim=24, ray_spacing=0.03)
-    cell, nc = W.grid_cells(prob.mesh, 1.26)
+    cell, nc = W.grid_cells(prob.mesh, cell_size)
     o = _oracle(prob)
-    o.set_cmfd(cell, nc, 5, 4)
+    o.set_cmfd(cell, nc, 5, 4, omega)
     m = moc.Moc.from_problem(prob, precision="fp64")
-    m.set_cmfd(cell, nc, 5, 4)
+    m.set_cmfd(cell, nc, 5, 4, omega)
     rng = np.random.default_rng(8)
     T, _ = m.track_counts()
     phi0 = rng.uniform(0.5, 1.5, (prob.mesh.n_tri, prob.xs.n_groups))
@@ -313,3 +315,24 @@ def test_cmfd_converges_to_the_unaccelerated_solution(precision):
     assert n < nr / 2, (n, nr)
     assert abs(k - kr) <= (1e-9 if precision == "fp64" else 2e-6) * kr
     assert _rel(m.get_state()[0], ref.get_state()[0]) <= (1e-7 if precision == "fp64" else 1e-4)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_cmfd_reflector_core_converges_to_the_oracle(precision):
+    """One assembly with the reflector band, pin-size coarse cells, reflective -x/-y: the
+    accelerated GPU iteration converges to the oracle's accelerated limit, which the oracle pins
+    as a fixed point of the plain transport iteration."""
+    xs = W.synthetic_xs(["fuel", "fuel", "fuel", "fuel", "clad", "moderator", "reflector"], 7, 4,
+                        fuel_scales=[1.0, 0.95, 1.05, 0.9])
+    prob = W.Problem(W.core_mesh(1), xs, 16, 0.2, tol=1e-6, name="core1", seed=4)
+    cell, nc = W.grid_cells(prob.mesh, 1.26)
+    o = _oracle(prob)
+    o.set_cmfd(cell, nc, 20, 20)
+    ko, _, _, co = o.iterate(True, 1e-11, 1e-9, 80)
+    m = moc.Moc.from_problem(prob, precision=precision)
+    m.set_cmfd(cell, nc, 20, 20)
+    tol = (1e-11, 1e-9) if precision == "fp64" else (1e-7, 2e-6)
+    k, n, r, c = m.power_iterate(tol[0], tol[1], 400, check_every=1)
+    assert co and c, (n, r)
+    assert abs(k - ko) <= (1e-9 if precision == "fp64" else 2e-6) * ko, (k, ko)
+    assert _rel(m.get_state()[0], o.get_state()[0]) <= (1e-7 if precision == "fp64" else 1e-4)
