@@ -139,28 +139,37 @@ def cpu_baseline(prob, outers: int = 2):
                       f"{dt:.2f} s"}
 
 
-def time_to_converged_k(moc, prob, device, stream, pcm: float = 5.0):
-    """Wall time and outers of the cold-start power iteration until |k - k_ref| <= pcm * 1e-5."""
+def time_to_converged_k(moc, prob, device, stream, cmfd, plain: bool = True, pcm: float = 5.0):
+    """Wall time and outers of the cold-start power iteration until |k - k_ref| <= pcm * 1e-5, in
+    FP32 and FP64, plain (when `plain`) and CMFD-accelerated with cmfd = (cell size, coarse power
+    iterations, sweeps per group, omega). k_ref: FP32 to |dk| <= 1e-7 continued in FP64 to
+    |dk| <= 1e-10, accelerated when the plain iteration is not run (the accelerated limit is the
+    transport solution)."""
     import torch
+    from paper_2607_01591_gb300 import workloads as W
 
+    cell, n_cells = W.grid_cells(prob.mesh, cmfd[0])
+    accel = lambda ctx: ctx.set_cmfd(cell, n_cells, cmfd[1], cmfd[2], cmfd[3])
     ref32 = moc.Moc.from_problem(prob, device=device, precision="fp32", stream=stream.cuda_stream)
-    ref32.power_iterate(1e-7, 1e-6, 20000, check_every=20, raise_on_fail=False)
-    phi, k, psi = ref32.get_state(with_psi=True)
     ref64 = moc.Moc.from_problem(prob, device=device, precision="fp64", stream=stream.cuda_stream)
+    if not plain:
+        accel(ref32)
+        accel(ref64)
+    ref32.power_iterate(1e-7, 1e-6, 20000, check_every=20 if plain else 2, raise_on_fail=False)
+    phi, k, psi = ref32.get_state(with_psi=True)
     ref64.set_state(phi, k, psi)
     k_ref, _, _, _ = ref64.power_iterate(1e-10, 1e-8, 5000, check_every=5, raise_on_fail=False)
     out = {"k_ref": k_ref, "criterion": f"|k - k_ref| <= {pcm} pcm",
-           "k_ref_from": "FP32 to |dk| <= 1e-7, continued in FP64 to |dk| <= 1e-10",
-           "cmfd": "pin-pitch (1.26 cm) coarse cells; per outer 6 coarse power iterations, 6 Gauss-Seidel sweeps per group"}
-    from paper_2607_01591_gb300 import workloads as W
-
-    cell, n_cells = W.grid_cells(prob.mesh, 1.26)
-    runs = (("cold_fp32", ref32, False), ("cold_fp64", ref64, False), ("cold_fp32_cmfd", ref32, True),
-            ("cold_fp64_cmfd", ref64, True))
-    for name, ctx, accel in runs:
+           "k_ref_from": "FP32 to |dk| <= 1e-7, continued in FP64 to |dk| <= 1e-10"
+                         + ("" if plain else " (CMFD-accelerated)"),
+           "cmfd": f"{cmfd[0]} cm square coarse cells ({n_cells}); per outer {cmfd[1]} coarse power iterations, "
+                   f"{cmfd[2]} Gauss-Seidel sweeps per group, over-relaxation {cmfd[3]}"}
+    runs = ((("cold_fp32", ref32, False), ("cold_fp64", ref64, False)) if plain else ()) + \
+        (("cold_fp32_cmfd", ref32, True), ("cold_fp64_cmfd", ref64, True))
+    for name, ctx, acc in runs:
         ctx.set_xs(prob.xs)
-        if accel:
-            ctx.set_cmfd(cell, n_cells, 6, 6)
+        if acc:
+            accel(ctx)
         torch.cuda.synchronize(device)
         t0 = time.perf_counter()
         n = 0
@@ -215,7 +224,14 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--workload", default="assembly", choices=sorted(WORKLOADS))
     ap.add_argument("--no-time-to-k", action="store_true")
+    ap.add_argument("--cmfd", default=None, metavar="SIZE,NOUT,NIN,OMEGA",
+                    help="time CMFD-accelerated outers (square coarse cells of SIZE cm); also the "
+                         "parameters of the accelerated time-to-k runs")
     args = ap.parse_args()
+    cm_default = {"assembly": "1.26,6,6,1.0", "core": "1.26,80,3,1.5", "hexcore": "2.52,10,5,1.0",
+                  "pin": "0.63,6,6,1.0"}[args.workload]
+    cmp = (args.cmfd or cm_default).split(",")
+    cmfd = (float(cmp[0]), int(cmp[1]), int(cmp[2]), float(cmp[3]))
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -242,6 +258,9 @@ def main():
     prob = make_problem(args.workload)
     stream = torch.cuda.Stream(device=local)
     m = moc.Moc.from_problem(prob, device=local, precision=args.precision, stream=stream.cuda_stream)
+    if args.cmfd:
+        cm_cell, cm_n = W.grid_cells(prob.mesh, cmfd[0])
+        m.set_cmfd(cm_cell, cm_n, cmfd[1], cmfd[2], cmfd[3])
     n_seg, ups, kpo = m.work()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{local}")
 
@@ -320,8 +339,8 @@ def main():
     # time to converged k: outers from the cold start until |k - k_ref| <= 5 pcm, k_ref from FP32
     # convergence continued in FP64 to |dk| <= 1e-10 (same workload, same stream)
     time_to_k = None
-    if not args.no_time_to_k and args.workload == "assembly":
-        time_to_k = time_to_converged_k(moc, prob, local, stream)
+    if not args.no_time_to_k and args.workload in ("assembly", "core"):
+        time_to_k = time_to_converged_k(moc, prob, local, stream, cmfd, plain=args.workload == "assembly")
 
     if rank != 0:
         return
@@ -334,10 +353,12 @@ def main():
         "data": "synthetic (seeded mesh and cross sections shaped like the paper's lattice workloads)",
         "config": {"workload": WORKLOADS[args.workload], "precision": args.precision, "segments": n_seg, "tracks": T,
                    "updates_per_step": ups, "l2": "flushed between steps (512 MiB write, untimed)",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   "cmfd": (f"each step one CMFD-accelerated outer: {cmfd[0]} cm cells, {cmfd[1]} coarse power "
+                            f"iterations x {cmfd[2]} sweeps per group, omega {cmfd[3]}") if args.cmfd else None},
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": alu_peak / 1e9, "unit": "Gop/s",
                      "frac": achieved / alu_peak,
-                     "traffic": SWEEP_DRAM_BYTES.get(args.workload) if args.precision == "fp32" else None,
+                     "traffic": SWEEP_DRAM_BYTES.get(args.workload) if args.precision == "fp32" and not args.cmfd else None,
                      "kernel": "sweep_kernel", "avg_launch_ms": sweep_avg_s * 1e3,
                      "ops_per_update": ops_per_update,
                      "peak_note": "152 SMs x 128 FP32 lanes x max SM clock (derived; FMA counted as 1 op)",
