@@ -96,6 +96,15 @@ int moc_set_quadrature(moc_ctx *ctx, int n_azim, double ray_spacing, int n_polar
  * Errors: MOC_ERR_STATE (no mesh/quadrature), MOC_ERR_GEOMETRY, MOC_ERR_OOM, MOC_ERR_CUDA. */
 int moc_generate_tracks(moc_ctx *ctx);
 
+/* Same as moc_generate_tracks, with the ray-mesh intersection (the half-edge walk of every ray,
+ * Sec. 3.1) run on the context's GPU, one thread per ray in a counting pass and a filling pass;
+ * ray laydown, boundary-entry events, links and areas stay on the host. The device walk uses the
+ * host walk's code and IEEE double arithmetic without contracted multiply-adds, so tracks and
+ * segments are bit-identical to moc_generate_tracks (areas, summed from the same segments, are
+ * too). For fast re-tracking of large meshes. walk_ms (may be NULL) gets the device time of the
+ * two passes. Errors: as moc_generate_tracks; MOC_ERR_STATE on a host-only context. */
+int moc_generate_tracks_device(moc_ctx *ctx, double *walk_ms);
+
 /* Number of tracks and segments after moc_generate_tracks(). */
 int moc_get_track_counts(const moc_ctx *ctx, int64_t *n_tracks, int64_t *n_segments);
 

@@ -19,8 +19,10 @@ OUT_DIR = os.path.join(HERE, "_lib")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmoc_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["moc_api.cu", "moc_mlp.cu", "moc_geom.cpp"]
-HEADERS = ["moc_kernels.cuh", "moc_geom.h", "exp_f32_coef.h"]
+SOURCES = ["moc_api.cu", "moc_mlp.cu", "moc_track.cu", "moc_geom.cpp"]
+HEADERS = ["moc_kernels.cuh", "moc_cmfd.cuh", "moc_geom.h", "moc_walk.h", "moc_track.h", "exp_f32_coef.h"]
+# the device walk must round every double multiply and add separately, like the host build
+NO_FMA = {"moc_track.cu"}
 
 
 def _nvcc() -> str:
@@ -50,7 +52,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         obj = os.path.join(BUILD_DIR, src.replace(".", "_") + ".o")
         objs.append(obj)
         if src.endswith(".cu"):
-            cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-I", INC, "-I", CSRC, "-Xcompiler", "-fPIC,-fopenmp",
+            cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-I", INC, "-I", CSRC, "-Xcompiler",
+                   "-fPIC,-fopenmp,-ffp-contract=off", *(["--fmad=false"] if src in NO_FMA else []),
                    "-c", os.path.join(CSRC, src), "-o", obj]
         else:
             cmd = ["g++", "-O2", "-ffp-contract=off", "-std=c++17", "-fPIC", "-fopenmp", "-I", INC, "-I", CSRC, "-c", os.path.join(CSRC, src),

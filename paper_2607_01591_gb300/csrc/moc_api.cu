@@ -13,6 +13,7 @@
 #include "moc_gb300.h"
 #include "moc_geom.h"
 #include "moc_cmfd.cuh"
+#include "moc_track.h"
 #include "moc_kernels.cuh"
 
 using namespace moc;
@@ -751,6 +752,19 @@ int moc_generate_tracks(moc_ctx *c) {
   int rc = generate_tracks(c->geo, c->err);
   if (rc) return rc;
   if (c->device < 0) return MOC_OK;
+  return c->precision == MOC_FP64 ? upload_tracks<double>(c) : upload_tracks<float>(c);
+}
+
+int moc_generate_tracks_device(moc_ctx *c, double *walk_ms) {
+  if (!c) return MOC_ERR_ARG;
+  if (c->device < 0) return fail(c, MOC_ERR_STATE, "generate_tracks_device: the context has no device");
+  cudaSetDevice(c->device);
+  free_tracks(c);
+  DeviceWalkCtx wc{c->device, c->stream, 0.0};
+  const Walker w{device_walk, &wc};
+  int rc = generate_tracks(c->geo, c->err, &w);
+  if (rc) return rc;
+  if (walk_ms) *walk_ms = wc.walk_ms;
   return c->precision == MOC_FP64 ? upload_tracks<double>(c) : upload_tracks<float>(c);
 }
 

@@ -1,7 +1,7 @@
 // Host-side geometry: half-edge mesh, cyclic modular rays over the bounding box, ray-mesh
-// intersection by half-edge walk, reflective links and tracked areas (Sec. 3.1 of the paper:
-// "HEDS" traversal, modular rays for the bounding box of the whole domain, segment data
-// computed once before the sweep).
+// intersection by half-edge walk (moc_walk.h, run here or on the device), reflective links and
+// tracked areas (Sec. 3.1 of the paper: half-edge traversal of the mesh, modular rays over the
+// bounding box of the whole domain, segments computed once before any sweep).
 #include "moc_geom.h"
 
 #include <algorithm>
@@ -15,40 +15,8 @@ namespace moc {
 namespace {
 
 constexpr double kPi = 3.14159265358979323846;
-constexpr double kSliver = 1e-12;     // pieces shorter than this (cm) are dropped
-constexpr double kVertexEps = 1e-12;  // an exit this close (cm) to a vertex crosses the vertex
-constexpr double kEventEps = 1e-9;    // entry events closer than this along a ray coincide
 
 inline double cross(double ax, double ay, double bx, double by) { return ax * by - ay * bx; }
-
-// Interval of the line p0 + s u inside CCW triangle t (Cyrus-Beck half-planes). A line running
-// exactly along an edge belongs to the triangle on its left. Returns false if empty.
-bool clip(const Geometry &g, int t, const double *p0, const double *u, double &lo, double &hi) {
-  lo = -INFINITY;
-  hi = INFINITY;
-  for (int k = 0; k < 3; ++k) {
-    const double *a = &g.xy[2 * (size_t)g.tri[3 * (size_t)t + k]];
-    const double *b = &g.xy[2 * (size_t)g.tri[3 * (size_t)t + (k + 1) % 3]];
-    double nx = -(b[1] - a[1]), ny = b[0] - a[0];  // inward normal of a CCW edge
-    double f0 = nx * (p0[0] - a[0]) + ny * (p0[1] - a[1]);
-    double fu = nx * u[0] + ny * u[1];
-    if (fu == 0.0) {
-      if (f0 < 0.0) return false;
-      if (f0 == 0.0 && (nx * (-u[1]) + ny * u[0]) <= 0.0) return false;
-      continue;
-    }
-    double s = -f0 / fu;
-    if (fu > 0.0) lo = std::max(lo, s);
-    else hi = std::min(hi, s);
-  }
-  return hi > lo;
-}
-
-struct Event {
-  double s;
-  int32_t he;   // boundary half-edge
-  double t;     // position along the half-edge
-};
 
 }  // namespace
 
@@ -228,81 +196,32 @@ double box_exit(const Geometry &g, const double *p, const double *u) {
   return s;
 }
 
-struct Piece {
-  int32_t tri;
-  double len;
-};
-
-// Walk from triangle t0 (entered at s_start) along the ray until it leaves the mesh.
-// Returns the exit parameter, or NAN if the walk got lost.
-double walk(const Geometry &g, int t0, double s_start, const double *p0, const double *u, double L,
-            std::vector<Piece> &out) {
-  int T = t0, prev = -1;
-  double s_cur = s_start;
-  int64_t limit = 4 * (int64_t)g.n_tri + 64;
-  for (int64_t step = 0; step < limit; ++step) {
-    double lo, hi;
-    if (!clip(g, T, p0, u, lo, hi)) hi = s_cur;
-    hi = std::min(hi, L);
-    double l = hi - s_cur;
-    if (l > kSliver) out.push_back({T, l});
-    if (hi >= L) return L;
-    // leaving edge: smallest leaving parameter
-    int ex = -1;
-    double best = INFINITY;
-    for (int k = 0; k < 3; ++k) {
-      const double *a = &g.xy[2 * (size_t)g.tri[3 * (size_t)T + k]];
-      const double *b = &g.xy[2 * (size_t)g.tri[3 * (size_t)T + (k + 1) % 3]];
-      double nx = -(b[1] - a[1]), ny = b[0] - a[0];
-      double fu = nx * u[0] + ny * u[1];
-      if (fu >= 0.0) continue;
-      double s = -(nx * (p0[0] - a[0]) + ny * (p0[1] - a[1])) / fu;
-      if (s < best) {
-        best = s;
-        ex = k;
-      }
-    }
-    if (ex < 0) return NAN;
-    double P[2] = {p0[0] + hi * u[0], p0[1] + hi * u[1]};
-    int va = g.tri[3 * (size_t)T + ex], vb = g.tri[3 * (size_t)T + (ex + 1) % 3];
-    double da = std::hypot(P[0] - g.xy[2 * (size_t)va], P[1] - g.xy[2 * (size_t)va + 1]);
-    double db = std::hypot(P[0] - g.xy[2 * (size_t)vb], P[1] - g.xy[2 * (size_t)vb + 1]);
-    int he = 3 * T + ex;
-    int nxt = (g.twin[he] >= 0) ? g.twin[he] / 3 : -1;
-    int v = -1;
-    if (da <= kVertexEps || db <= kVertexEps) v = (da <= db) ? va : vb;
-    else if (nxt == prev && nxt >= 0) v = (da <= db) ? va : vb;   // no progress: resolve at the vertex
-    if (v < 0) {
-      if (nxt < 0) return hi;  // boundary edge: the ray leaves the mesh
-      prev = T;
-      T = nxt;
-      s_cur = hi;
-      continue;
-    }
-    // vertex crossing: the triangle of the vertex fan the ray continues into
-    int pick = -1;
-    double pick_hi = hi + kSliver;
-    for (int q = g.vt_off[v]; q < g.vt_off[v + 1]; ++q) {
-      int c = g.vt_list[q];
-      if (c == T) continue;
-      double lo2, hi2;
-      if (!clip(g, c, p0, u, lo2, hi2)) continue;
-      if (lo2 <= hi + kEventEps && hi2 > pick_hi) {
-        pick = c;
-        pick_hi = hi2;
-      }
-    }
-    if (pick < 0) return hi;  // leaves the mesh through a boundary vertex
-    prev = T;
-    T = pick;
-    s_cur = hi;
-  }
-  return NAN;
+walkdef::MeshView mesh_view(const Geometry &g) {
+  return walkdef::MeshView{g.xy.data(), g.tri.data(), g.twin.data(), g.vt_off.data(), g.vt_list.data(), g.n_tri};
 }
+
+// Host emitter of the walk: pieces and tracks appended to one direction's output.
+struct HostEmit {
+  WalkResult *out;
+  const double *p0, *u;
+  int dir;
+  void piece(int t, double l) {
+    out->seg_reg.push_back(t);
+    out->seg_len.push_back(l);
+  }
+  void track(double s0, double s1, int64_t n) {
+    out->track_dir.push_back(dir);
+    out->track_xy.push_back(p0[0] + s0 * u[0]);
+    out->track_xy.push_back(p0[1] + s0 * u[1]);
+    out->track_xy.push_back(p0[0] + s1 * u[0]);
+    out->track_xy.push_back(p0[1] + s1 * u[1]);
+    out->seg_count.push_back(n);
+  }
+};
 
 }  // namespace
 
-int generate_tracks(Geometry &g, std::string &err) {
+int generate_tracks(Geometry &g, std::string &err, const Walker *walker) {
   if (!g.has_mesh || !g.has_quad) {
     err = "generate_tracks: set the mesh and the quadrature first";
     return MOC_ERR_STATE;
@@ -315,24 +234,29 @@ int generate_tracks(Geometry &g, std::string &err) {
   for (size_t e = 0; e < g.twin.size(); ++e)
     if (g.twin[e] < 0) bnd.push_back((int32_t)e);
 
-  // Directions are walked independently (in parallel when OpenMP is on) and concatenated in
+  // Rays of every direction (cyclic laydown over the bounding box) and, per ray, the boundary
+  // edges it crosses, found by projecting each boundary edge onto the direction's normal.
+  // Directions are processed independently (in parallel when OpenMP is on) and concatenated in
   // direction order, so the result does not depend on the thread count.
-  struct DirOut {
-    std::vector<int32_t> reg;
-    std::vector<double> len, xy;
-    std::vector<int64_t> count;  // segments per track
-    std::string err;
-    int rc = 0;
+  struct DirRays {
+    std::vector<double> ray;  // x0 y0 L
+    std::vector<std::vector<walkdef::Event>> ev;
   };
-  std::vector<DirOut> outs(g.n_dir);
+  std::vector<DirRays> dr(g.n_dir);
+  RayBatch rb;
+  rb.u.resize(2 * (size_t)g.n_dir);
+  for (int j = 0; j < g.n_dir; ++j) {
+    rb.u[2 * j] = std::cos(g.phi[j]);
+    rb.u[2 * j + 1] = std::sin(g.phi[j]);
+  }
 #pragma omp parallel for schedule(dynamic, 1)
   for (int j = 0; j < g.n_dir; ++j) {
-    DirOut &D = outs[j];
-    std::vector<Piece> pieces;
-    const double u[2] = {std::cos(g.phi[j]), std::sin(g.phi[j])};
+    DirRays &D = dr[j];
+    const double u[2] = {rb.u[2 * j], rb.u[2 * j + 1]};
     const double nrm[2] = {-u[1], u[0]};
     const int nr = g.nx[j] + g.ny[j];
-    std::vector<double> ray(3 * (size_t)nr);  // x0 y0 L
+    std::vector<double> &ray = D.ray;
+    ray.resize(3 * (size_t)nr);
     for (int i = 0; i < g.nx[j]; ++i) {
       ray[3 * i] = g.bbox[0] + (i + 0.5) * W / g.nx[j];
       ray[3 * i + 1] = g.bbox[2];
@@ -347,7 +271,8 @@ int generate_tracks(Geometry &g, std::string &err) {
     std::vector<std::pair<double, int>> off(nr);
     for (int r = 0; r < nr; ++r) off[r] = {nrm[0] * ray[3 * r] + nrm[1] * ray[3 * r + 1], r};
     std::sort(off.begin(), off.end());
-    std::vector<std::vector<Event>> ev(nr);
+    std::vector<std::vector<walkdef::Event>> &ev = D.ev;
+    ev.resize(nr);
     for (int32_t he : bnd) {
       int t = he / 3, k = he % 3;
       const double *a = &g.xy[2 * (size_t)g.tri[3 * (size_t)t + k]];
@@ -365,102 +290,87 @@ int generate_tracks(Geometry &g, std::string &err) {
         double sp = cross(ax, ay, dx, dy) / den;
         double tt = cross(ax, ay, u[0], u[1]) / den;
         if (tt < -1e-12 || tt > 1.0 + 1e-12) continue;
-        if (sp < -kEventEps || sp > ray[3 * r + 2] - kEventEps) continue;
-        ev[r].push_back({sp, he, tt});
+        if (sp < -walkdef::kEventEps || sp > ray[3 * r + 2] - walkdef::kEventEps) continue;
+        ev[r].push_back(walkdef::Event{sp, he, 0, tt});
       }
     }
-    for (int r = 0; r < nr && D.rc == 0; ++r) {
-      const double *p0 = &ray[3 * r];
-      const double L = ray[3 * r + 2];
-      std::sort(ev[r].begin(), ev[r].end(), [](const Event &x, const Event &y) { return x.s < y.s; });
-      double s_done = -INFINITY;
-      for (size_t q = 0; q < ev[r].size(); ++q) {
-        const Event &E = ev[r][q];
-        if (E.s <= s_done + kEventEps) continue;
-        // candidate start triangles: owners of the boundary edges hit here, and the vertex fans
-        // of edge endpoints hit
-        int best = -1;
-        double best_lo = 0, best_hi = E.s + kSliver;
-        for (size_t q2 = q; q2 < ev[r].size() && ev[r][q2].s <= E.s + kEventEps; ++q2) {
-          const Event &F = ev[r][q2];
-          int t = F.he / 3, k = F.he % 3;
-          int cands[1 + 64];
-          int nc = 0;
-          cands[nc++] = t;
-          int vs[2] = {-1, -1};
-          if (F.t < 1e-9) vs[0] = g.tri[3 * (size_t)t + k];
-          if (F.t > 1.0 - 1e-9) vs[1] = g.tri[3 * (size_t)t + (k + 1) % 3];
-          for (int vv : vs) {
-            if (vv < 0) continue;
-            for (int w = g.vt_off[vv]; w < g.vt_off[vv + 1] && nc < 65; ++w) cands[nc++] = g.vt_list[w];
-          }
-          for (int c = 0; c < nc; ++c) {
-            double lo, hi;
-            if (!clip(g, cands[c], p0, u, lo, hi)) continue;
-            hi = std::min(hi, L);
-            if (lo <= E.s + kEventEps && hi > best_hi) {
-              best = cands[c];
-              best_hi = hi;
-              best_lo = lo;
-            }
-          }
-        }
-        if (best < 0) continue;
-        pieces.clear();
-        double s0 = std::max(0.0, best_lo);
-        double s1 = walk(g, best, s0, p0, u, L, pieces);
-        if (std::isnan(s1)) {
-          char buf[160];
-          std::snprintf(buf, sizeof buf, "generate_tracks: half-edge walk lost on direction %d ray %d", j, r);
-          D.err = buf;
-          D.rc = MOC_ERR_GEOMETRY;
+    for (int r = 0; r < nr; ++r)
+      std::sort(ev[r].begin(), ev[r].end(), [](const walkdef::Event &x, const walkdef::Event &y) { return x.s < y.s; });
+  }
+  // flatten, direction-major
+  int64_t n_rays = 0, n_ev = 0;
+  for (int j = 0; j < g.n_dir; ++j) {
+    n_rays += (int64_t)dr[j].ev.size();
+    for (auto &e : dr[j].ev) n_ev += (int64_t)e.size();
+  }
+  rb.p0.reserve(2 * n_rays);
+  rb.len.reserve(n_rays);
+  rb.dir.reserve(n_rays);
+  rb.ev_off.assign(1, 0);
+  rb.ev_off.reserve(n_rays + 1);
+  rb.ev.reserve(n_ev);
+  for (int j = 0; j < g.n_dir; ++j) {
+    DirRays &D = dr[j];
+    for (size_t r = 0; r < D.ev.size(); ++r) {
+      rb.p0.push_back(D.ray[3 * r]);
+      rb.p0.push_back(D.ray[3 * r + 1]);
+      rb.len.push_back(D.ray[3 * r + 2]);
+      rb.dir.push_back(j);
+      rb.ev.insert(rb.ev.end(), D.ev[r].begin(), D.ev[r].end());
+      rb.ev_off.push_back((int64_t)rb.ev.size());
+    }
+    DirRays().ray.swap(D.ray);
+    std::vector<std::vector<walkdef::Event>>().swap(D.ev);
+  }
+  // the walk
+  WalkResult wr;
+  if (walker) {
+    rc = walker->run(walker->ctx, g, rb, wr, err);
+    if (rc) return rc;
+  } else {
+    std::vector<int64_t> dir_ray(g.n_dir + 1, 0);
+    for (int64_t r = 0; r < n_rays; ++r) dir_ray[rb.dir[r] + 1]++;
+    for (int j = 0; j < g.n_dir; ++j) dir_ray[j + 1] += dir_ray[j];
+    std::vector<WalkResult> outs(g.n_dir);
+    std::vector<int64_t> lost(g.n_dir, -1);
+    const walkdef::MeshView mv = mesh_view(g);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int j = 0; j < g.n_dir; ++j) {
+      for (int64_t r = dir_ray[j]; r < dir_ray[j + 1]; ++r) {
+        HostEmit em{&outs[j], &rb.p0[2 * r], &rb.u[2 * j], j};
+        if (walkdef::trace_ray(mv, &rb.p0[2 * r], &rb.u[2 * j], rb.len[r], rb.ev.data() + rb.ev_off[r],
+                               rb.ev_off[r + 1] - rb.ev_off[r], em)) {
+          lost[j] = r;
           break;
         }
-        s_done = s1;
-        if (pieces.empty()) continue;
-        D.xy.push_back(p0[0] + s0 * u[0]);
-        D.xy.push_back(p0[1] + s0 * u[1]);
-        D.xy.push_back(p0[0] + s1 * u[0]);
-        D.xy.push_back(p0[1] + s1 * u[1]);
-        for (const Piece &p : pieces) {
-          D.reg.push_back(p.tri);
-          D.len.push_back(p.len);
-        }
-        D.count.push_back((int64_t)pieces.size());
       }
     }
-  }
-  int64_t nt = 0, ns = 0;
-  for (int j = 0; j < g.n_dir; ++j) {
-    if (outs[j].rc) {
-      err = outs[j].err;
-      return outs[j].rc;
+    for (int j = 0; j < g.n_dir; ++j)
+      if (lost[j] >= 0) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "generate_tracks: half-edge walk lost on direction %d ray %lld", j,
+                      (long long)(lost[j] - dir_ray[j]));
+        err = buf;
+        return MOC_ERR_GEOMETRY;
+      }
+    for (int j = 0; j < g.n_dir; ++j) {
+      WalkResult &o = outs[j];
+      wr.track_dir.insert(wr.track_dir.end(), o.track_dir.begin(), o.track_dir.end());
+      wr.track_xy.insert(wr.track_xy.end(), o.track_xy.begin(), o.track_xy.end());
+      wr.seg_count.insert(wr.seg_count.end(), o.seg_count.begin(), o.seg_count.end());
+      wr.seg_reg.insert(wr.seg_reg.end(), o.seg_reg.begin(), o.seg_reg.end());
+      wr.seg_len.insert(wr.seg_len.end(), o.seg_len.begin(), o.seg_len.end());
+      WalkResult().seg_reg.swap(o.seg_reg);
+      std::vector<double>().swap(o.seg_len);
     }
-    nt += (int64_t)outs[j].count.size();
-    ns += (int64_t)outs[j].reg.size();
   }
   g.seg_off.assign(1, 0);
-  g.seg_off.reserve(nt + 1);
-  g.seg_reg.clear();
-  g.seg_reg.reserve(ns);
-  g.seg_len.clear();
-  g.seg_len.reserve(ns);
-  g.track_dir.clear();
-  g.track_dir.reserve(nt);
-  g.track_xy.clear();
-  g.track_xy.reserve(4 * nt);
-  for (int j = 0; j < g.n_dir; ++j) {
-    DirOut &D = outs[j];
-    for (int64_t c : D.count) {
-      g.track_dir.push_back(j);
-      g.seg_off.push_back(g.seg_off.back() + c);
-    }
-    g.track_xy.insert(g.track_xy.end(), D.xy.begin(), D.xy.end());
-    g.seg_reg.insert(g.seg_reg.end(), D.reg.begin(), D.reg.end());
-    g.seg_len.insert(g.seg_len.end(), D.len.begin(), D.len.end());
-    std::vector<int32_t>().swap(D.reg);
-    std::vector<double>().swap(D.len);
-  }
+  g.seg_off.reserve(wr.seg_count.size() + 1);
+  for (int64_t c : wr.seg_count) g.seg_off.push_back(g.seg_off.back() + c);
+  g.track_dir.swap(wr.track_dir);
+  g.track_xy.swap(wr.track_xy);
+  g.seg_reg.swap(wr.seg_reg);
+  g.seg_len.swap(wr.seg_len);
   const int64_t T = g.n_tracks();
   if (T == 0) {
     err = "generate_tracks: no ray crosses the mesh";

@@ -5,6 +5,8 @@
 #include <string>
 #include <vector>
 
+#include "moc_walk.h"
+
 namespace moc {
 
 struct Geometry {
@@ -41,11 +43,41 @@ struct Geometry {
   int64_t n_segments() const { return (int64_t)seg_reg.size(); }
 };
 
+// All rays of all directions (direction-major) with their boundary-entry events, the input of the
+// half-edge walk (moc_walk.h).
+struct RayBatch {
+  std::vector<double> p0;       // [n_rays][2] start point (on the bounding box)
+  std::vector<double> len;      // [n_rays] parameter where the ray leaves the bounding box
+  std::vector<int32_t> dir;     // [n_rays] direction index
+  std::vector<double> u;        // [n_dir][2] unit direction
+  std::vector<int64_t> ev_off;  // [n_rays+1] events of each ray, sorted by s
+  std::vector<walkdef::Event> ev;
+  int64_t n_rays() const { return (int64_t)dir.size(); }
+};
+
+// What the walk produced, in ray order (tracks of one ray in walk order).
+struct WalkResult {
+  std::vector<int32_t> track_dir;  // [T]
+  std::vector<double> track_xy;    // [T][4]
+  std::vector<int64_t> seg_count;  // [T]
+  std::vector<int32_t> seg_reg;    // [S]
+  std::vector<double> seg_len;     // [S]
+};
+
+// A walk run elsewhere (the device): fills `out` from `rays` for the mesh of `g`; returns 0 or a
+// negative moc_status with a message in err.
+struct Walker {
+  int (*run)(void *ctx, const Geometry &g, const RayBatch &rays, WalkResult &out, std::string &err);
+  void *ctx;
+};
+
 // Each returns 0 on success or a negative moc_status with a message in err.
 int set_mesh(Geometry &g, int n_vert, const double *xy, int n_tri, const int32_t *tri,
              const int32_t *mat, const double *bbox, const int32_t *bc, std::string &err);
 int set_quadrature(Geometry &g, int n_azim, double spacing, int n_polar, const double *sin_theta,
                    const double *polar_w, std::string &err);
-int generate_tracks(Geometry &g, std::string &err);
+// Ray laydown, segmentation, links, tracked areas. The walk runs on the host (OpenMP over
+// directions) unless `walker` is given.
+int generate_tracks(Geometry &g, std::string &err, const Walker *walker = nullptr);
 
 }  // namespace moc

@@ -64,6 +64,7 @@ def load_library(path: Optional[str] = None):
             "moc_set_mesh": (ctypes.c_int, [_vp, ctypes.c_int, _d, ctypes.c_int, _i32, _i32, _d, _i32]),
             "moc_set_quadrature": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _d, _d]),
             "moc_generate_tracks": (ctypes.c_int, [_vp]),
+            "moc_generate_tracks_device": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
             "moc_get_track_counts": (ctypes.c_int, [_vp, _i64, _i64]),
             "moc_get_tracks": (ctypes.c_int, [_vp, _i64, _i32, _d, _i32, _d, _i64]),
             "moc_get_quadrature": (ctypes.c_int, [_vp, _d, _d, _d]),
@@ -263,6 +264,13 @@ class Moc:
     def generate_tracks(self):
         self._check(self._lib.moc_generate_tracks(self._h))
 
+    def generate_tracks_device(self) -> float:
+        """Tracks with the half-edge walk on the GPU (bit-identical to generate_tracks); returns the
+        device time of the walk in ms."""
+        ms = ctypes.c_double()
+        self._check(self._lib.moc_generate_tracks_device(self._h, ctypes.byref(ms)))
+        return ms.value
+
     def track_counts(self):
         T, S = ctypes.c_int64(), ctypes.c_int64()
         self._check(self._lib.moc_get_track_counts(self._h, ctypes.byref(T), ctypes.byref(S)))
@@ -380,11 +388,15 @@ class Moc:
         return k.value
 
     @classmethod
-    def from_problem(cls, prob, device: int = 0, precision: str = "fp32", stream=None, with_xs: bool = True):
+    def from_problem(cls, prob, device: int = 0, precision: str = "fp32", stream=None, with_xs: bool = True,
+                     device_tracking: bool = False):
         m = cls(device, precision, stream)
         m.set_mesh(prob.mesh)
         m.set_quadrature(prob.n_azim, prob.ray_spacing, prob.sin_theta, prob.polar_w)
-        m.generate_tracks()
+        if device_tracking:
+            m.generate_tracks_device()
+        else:
+            m.generate_tracks()
         if with_xs and device >= 0:
             m.set_xs(prob.xs)
             if prob.fixed_source is not None:

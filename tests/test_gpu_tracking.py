@@ -1,0 +1,58 @@
+"""Segmentation on the GPU (moc_generate_tracks_device) against the host walk: the same code in
+IEEE double arithmetic without contracted multiply-adds on both sides, so every track, segment,
+link and area must be bit-identical. The host walk itself is pinned against the oracle's
+clip-based segmentation in test_abi_host.py."""
+import numpy as np
+import pytest
+
+from paper_2607_01591_gb300 import moc
+from paper_2607_01591_gb300 import workloads as W
+from paper_2607_01591_gb300.build import build
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build()
+
+
+def _core1(n_azim, spacing):
+    xs = W.synthetic_xs(["fuel", "fuel", "fuel", "fuel", "clad", "moderator", "reflector"], 7, 4,
+                        fuel_scales=[1.0, 0.95, 1.05, 0.9])
+    return W.Problem(W.core_mesh(1), xs, n_azim, spacing, tol=1e-6, name="core1", seed=4)
+
+
+CASES = {
+    "pin": lambda: W.pin_cell_problem(),
+    "pin_vacuum": lambda: W.Problem(W.with_bc(W.pin_cell_mesh(), (0, 0, 0, 0)), W.synthetic_xs(["fuel", "moderator"], 7, 1), 16, 0.05),
+    "lattice3_mixed_bc": lambda: W.small_lattice_problem(3, bc=(1, 0, 1, 0), n_azim=24, ray_spacing=0.03),
+    "grid": lambda: W.Problem(W.grid_mesh(5, 3, 2.0, 1.0), W.synthetic_xs(["fuel"], 2, 1), 8, 0.07),
+    "hex7_concave": lambda: W.Problem(W.hex_core_mesh(n_sub=4, n_rings=1), W.synthetic_xs(["fuel", "fuel", "coolant"], 3, 1), 12, 0.3),
+    "assembly": lambda: W.assembly_problem(),
+    "core1": lambda: _core1(16, 0.05),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_device_tracks_are_bit_identical(case):
+    prob = CASES[case]()
+    h = moc.Moc.from_problem(prob, with_xs=False)
+    d = moc.Moc.from_problem(prob, with_xs=False, device_tracking=True)
+    assert h.track_counts() == d.track_counts()
+    a, b = h.tracks(), d.tracks()
+    for key in ("seg_off", "seg_region", "seg_len", "track_dir", "track_xy", "link"):
+        assert np.array_equal(a[key], b[key]), key
+    assert np.array_equal(h.areas(), d.areas())
+
+
+def test_device_tracking_runs_the_solver():
+    """A context tracked on the device iterates like one tracked on the host (equal up to the
+    order of the sweep's atomic additions, which differs from run to run anyway)."""
+    prob = W.small_lattice_problem(3, bc=(1, 0, 1, 0), n_azim=24, ray_spacing=0.03)
+    h = moc.Moc.from_problem(prob, precision="fp64")
+    d = moc.Moc.from_problem(prob, precision="fp64", device_tracking=True)
+    kh, _ = h.outer(5)
+    kd, _ = d.outer(5)
+    assert abs(kh - kd) <= 1e-13 * kh
+    np.testing.assert_allclose(d.get_state()[0], h.get_state()[0], rtol=1e-12)
