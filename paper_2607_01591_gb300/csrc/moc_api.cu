@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -231,30 +232,40 @@ template <typename Real> int upload_tracks(moc_ctx *c) {
   });
   c->inv.resize(T);
   for (int64_t i = 0; i < T; ++i) c->inv[c->perm[i]] = i;
+  if (2 * T >= (int64_t)1 << 31) return fail(c, MOC_ERR_ARG, "too many tracks for 32-bit links");
   std::vector<TrackRec> trk(T);
-  // kSegPad padding records at each end: the sweep's prefetch reads them unconditionally
-  std::vector<SegRec<Real>> seg(S + 2 * kSegPad, SegRec<Real>{});
   std::vector<int32_t> link(2 * T);
   int64_t o = kSegPad;
   for (int64_t i = 0; i < T; ++i) {
-    int64_t t = c->perm[i];
-    int64_t n = g.seg_off[t + 1] - g.seg_off[t];
+    const int64_t t = c->perm[i];
+    const int64_t n = g.seg_off[t + 1] - g.seg_off[t];
     trk[i].off = o;
     trk[i].n = (int)n;
     trk[i].dir = g.track_dir[t];
-    for (int64_t k = 0; k < n; ++k) {
-      SegRec<Real> r{};
-      r.r = g.seg_reg[g.seg_off[t] + k];
-      r.l = (Real)g.seg_len[g.seg_off[t] + k];
-      seg[o + k] = r;
-    }
     o += n;
     for (int d = 0; d < 2; ++d) {
       int64_t e = g.link[2 * t + d];
       link[2 * i + d] = (e < 0) ? -1 : (int32_t)(2 * c->inv[e >> 1] + (e & 1));
     }
   }
-  if (2 * T >= (int64_t)1 << 31) return fail(c, MOC_ERR_ARG, "too many tracks for 32-bit links");
+  // kSegPad padding records at each end: the sweep's prefetch reads them unconditionally. Every
+  // record is written below (tracks in parallel), so the array is not zero-filled first.
+  std::unique_ptr<SegRec<Real>[]> seg(new SegRec<Real>[S + 2 * kSegPad]);
+  for (int k = 0; k < kSegPad; ++k) {
+    std::memset(&seg[k], 0, sizeof(SegRec<Real>));
+    std::memset(&seg[kSegPad + S + k], 0, sizeof(SegRec<Real>));
+  }
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int64_t i = 0; i < T; ++i) {
+    const int64_t t = c->perm[i], b = g.seg_off[t];
+    for (int64_t k = 0; k < trk[i].n; ++k) {
+      SegRec<Real> r;
+      std::memset(&r, 0, sizeof r);
+      r.r = g.seg_reg[b + k];
+      r.l = (Real)g.seg_len[b + k];
+      seg[trk[i].off + k] = r;
+    }
+  }
   std::vector<Real> wgt((size_t)g.n_dir * c->P), inv_sin(c->P);
   for (int j = 0; j < g.n_dir; ++j)
     for (int p = 0; p < c->P; ++p)
@@ -262,7 +273,7 @@ template <typename Real> int upload_tracks(moc_ctx *c) {
   for (int p = 0; p < c->P; ++p) inv_sin[p] = (Real)(1.0 / g.sin_theta[p]);
   int rc;
   SegRec<Real> *ds = nullptr;
-  if ((rc = upload(c, ds, seg.data(), seg.size()))) return rc;
+  if ((rc = upload(c, ds, seg.get(), (size_t)(S + 2 * kSegPad)))) return rc;
   c->d_seg = ds;
   if ((rc = upload(c, c->d_trk, trk.data(), trk.size()))) return rc;
   if ((rc = upload(c, c->d_link, link.data(), link.size()))) return rc;

@@ -200,7 +200,8 @@ walkdef::MeshView mesh_view(const Geometry &g) {
   return walkdef::MeshView{g.xy.data(), g.tri.data(), g.twin.data(), g.vt_off.data(), g.vt_list.data(), g.n_tri};
 }
 
-// Host emitter of the walk: pieces and tracks appended to one direction's output.
+// Host emitter of the walk: pieces and tracks appended to one direction's output (a walk that
+// emits no piece is not a track and adds nothing).
 struct HostEmit {
   WalkResult *out;
   const double *p0, *u;
@@ -353,6 +354,16 @@ int generate_tracks(Geometry &g, std::string &err, const Walker *walker) {
         err = buf;
         return MOC_ERR_GEOMETRY;
       }
+    size_t nt = 0, ns = 0;
+    for (const WalkResult &o : outs) {
+      nt += o.track_dir.size();
+      ns += o.seg_reg.size();
+    }
+    wr.track_dir.reserve(nt);
+    wr.track_xy.reserve(4 * nt);
+    wr.seg_count.reserve(nt);
+    wr.seg_reg.reserve(ns);
+    wr.seg_len.reserve(ns);
     for (int j = 0; j < g.n_dir; ++j) {
       WalkResult &o = outs[j];
       wr.track_dir.insert(wr.track_dir.end(), o.track_dir.begin(), o.track_dir.end());
@@ -426,11 +437,25 @@ int generate_tracks(Geometry &g, std::string &err, const Walker *walker) {
       g.link[2 * t + d] = it->second;
     }
   }
-  // tracked areas: both senses of each track count, with weight omega_j delta_j
+  // tracked areas: both senses of each track count, with weight omega_j delta_j. One partial sum
+  // per direction (tracks are direction-major), added in direction order: the result does not
+  // depend on the thread count.
+  std::vector<int64_t> dir_trk(g.n_dir + 1, 0);
+  for (int64_t t = 0; t < T; ++t) dir_trk[g.track_dir[t] + 1]++;
+  for (int j = 0; j < g.n_dir; ++j) dir_trk[j + 1] += dir_trk[j];
+  std::vector<std::vector<double>> part(g.n_dir);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int j = 0; j < g.n_dir; ++j) {
+    std::vector<double> &a = part[j];
+    a.assign(g.n_tri, 0.0);
+    const double w = 2.0 * g.omega[j] * g.delta[j];
+    for (int64_t t = dir_trk[j]; t < dir_trk[j + 1]; ++t)
+      for (int64_t s = g.seg_off[t]; s < g.seg_off[t + 1]; ++s) a[g.seg_reg[s]] += w * g.seg_len[s];
+  }
   g.area.assign(g.n_tri, 0.0);
-  for (int64_t t = 0; t < T; ++t) {
-    double w = 2.0 * g.omega[g.track_dir[t]] * g.delta[g.track_dir[t]];
-    for (int64_t s = g.seg_off[t]; s < g.seg_off[t + 1]; ++s) g.area[g.seg_reg[s]] += w * g.seg_len[s];
+  for (int j = 0; j < g.n_dir; ++j) {
+    for (int r = 0; r < g.n_tri; ++r) g.area[r] += part[j][r];
+    std::vector<double>().swap(part[j]);
   }
   g.has_tracks = true;
   return MOC_OK;

@@ -73,6 +73,7 @@ MOC_HD double walk(const MeshView &m, int t0, double s_start, const double *p0, 
                    Emit &em, int64_t *npieces) {
   int T = t0, prev = -1;
   double s_cur = s_start;
+  int64_t np = 0;
   const int64_t limit = 4 * (int64_t)m.n_tri + 64;
   for (int64_t step = 0; step < limit; ++step) {
     double lo, hi;
@@ -81,8 +82,9 @@ MOC_HD double walk(const MeshView &m, int t0, double s_start, const double *p0, 
     const double l = hi - s_cur;
     if (l > kSliver) {
       em.piece(T, l);
-      ++*npieces;
+      ++np;
     }
+    *npieces = np;
     if (hi >= L) return L;
     // leaving edge: smallest leaving parameter
     int ex = -1;
