@@ -224,6 +224,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--workload", default="assembly", choices=sorted(WORKLOADS))
     ap.add_argument("--no-time-to-k", action="store_true")
+    ap.add_argument("--no-tracking", action="store_true", help="skip the host vs device tracking timing")
     ap.add_argument("--cmfd", default=None, metavar="SIZE,NOUT,NIN,OMEGA",
                     help="time CMFD-accelerated outers (square coarse cells of SIZE cm); also the "
                          "parameters of the accelerated time-to-k runs")
@@ -342,6 +343,26 @@ def main():
     if not args.no_time_to_k and args.workload in ("assembly", "core"):
         time_to_k = time_to_converged_k(moc, prob, local, stream, cmfd, plain=args.workload == "assembly")
 
+    # tracking of the same workload: host half-edge walk vs the device walk (bit-identical tracks)
+    tracking = None
+    if not args.no_tracking and rank == 0:
+        tr = {}
+        for name in ("host", "device"):
+            mt = moc.Moc(local, args.precision, stream.cuda_stream)
+            mt.set_mesh(prob.mesh)
+            mt.set_quadrature(prob.n_azim, prob.ray_spacing, prob.sin_theta, prob.polar_w)
+            t0 = time.perf_counter()
+            walk_ms = mt.generate_tracks_device() if name == "device" else None
+            if name == "host":
+                mt.generate_tracks()
+            tr[name + "_s"] = time.perf_counter() - t0
+            if walk_ms is not None:
+                tr["device_walk_ms"] = walk_ms
+            mt.close()
+        tr["note"] = ("wall time of moc_generate_tracks (host walk, OpenMP) and moc_generate_tracks_device "
+                      f"(walk on the GPU, two passes) including laydown, links, areas and upload; {os.cpu_count()} host cores")
+        tracking = tr
+
     if rank != 0:
         return
     cpu = None if args.no_cpu_baseline or world > 1 or args.workload != "assembly" else cpu_baseline(prob)
@@ -370,6 +391,7 @@ def main():
         "cpu_baseline": cpu,
         "fp64": fp64,
         "time_to_k": time_to_k,
+        "tracking": tracking,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

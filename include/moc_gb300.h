@@ -57,6 +57,7 @@ enum { MOC_FP64 = 0, MOC_FP32 = 1, MOC_FP32_PLAIN = 2 };
 
 /* Boundary conditions per wall of the bounding box (x-, x+, y-, y+). */
 enum { MOC_BC_VACUUM = 0, MOC_BC_REFLECTIVE = 1 };
+enum { MOC_RAYS_MODULAR = 0, MOC_RAYS_BACK_PROJECTION = 1 };
 
 /* Create a context on CUDA device `device` (>= 0) with sweep arithmetic `precision`.
  * `stream` is a cudaStream_t the context launches all work on (NULL: the context creates its
@@ -85,6 +86,16 @@ int moc_set_mesh(moc_ctx *ctx, int n_vert, const double *xy, int n_tri, const in
  * 1 <= n_polar <= 6. Errors: MOC_ERR_ARG. */
 int moc_set_quadrature(moc_ctx *ctx, int n_azim, double ray_spacing, int n_polar,
                        const double *sin_theta, const double *polar_w);
+
+/* Ray layout of the next moc_generate_tracks (Sec. 3.1 names both): MOC_RAYS_MODULAR (default),
+ * cyclic rays over the bounding box with corrected angles, the only layout that can link
+ * reflective walls; or MOC_RAYS_BACK_PROJECTION, rays cast from the domain boundary into the
+ * mesh at the nominal angles 2 pi (a + 1/2)/n_azim (weights 1/n_azim), per direction n =
+ * ceil(extent / ray_spacing) rays spread evenly (spacing extent/n, offset half a spacing) over
+ * the extent of the mesh projected on the direction's normal -- no rays are spent on the empty
+ * corners of a non-rectangular domain's bounding box. Back projection requires every boundary
+ * to be vacuum (moc_generate_tracks returns MOC_ERR_ARG otherwise). Errors: MOC_ERR_ARG. */
+int moc_set_ray_layout(moc_ctx *ctx, int layout);
 
 /* Lay down the modular (cyclic) rays over the bounding box, intersect them with the mesh by a
  * half-edge walk, build the reflective links and the tracked region areas, and upload the

@@ -46,7 +46,7 @@ def _load():
         lib = ctypes.CDLL(build())
         lib.orc_create.restype = ctypes.c_void_p
         lib.orc_create.argtypes = [ctypes.c_int, _d, ctypes.c_int, _i32, _i32, _d, _i32, ctypes.c_int,
-                                   ctypes.c_double, ctypes.c_int, _d, _d, ctypes.c_char_p]
+                                   ctypes.c_double, ctypes.c_int, _d, _d, ctypes.c_int, ctypes.c_char_p]
         lib.orc_destroy.argtypes = [ctypes.c_void_p]
         lib.orc_error.restype = ctypes.c_char_p
         lib.orc_error.argtypes = [ctypes.c_void_p]
@@ -95,7 +95,8 @@ def _i32a(a):
 class Oracle:
     """One problem: mesh + quadrature -> tracks; then cross sections, state and iterations."""
 
-    def __init__(self, mesh, n_azim: int, ray_spacing: float, sin_theta, polar_w, threads: int = 1):
+    def __init__(self, mesh, n_azim: int, ray_spacing: float, sin_theta, polar_w, threads: int = 1,
+                 ray_layout: int = 0):
         lib = _load()
         self._lib = lib
         xy = _f64(mesh.xy)
@@ -108,7 +109,7 @@ class Oracle:
         err = ctypes.create_string_buffer(256)
         h = lib.orc_create(xy.shape[0], _p(xy, _d), tri.shape[0], _p(tri, _i32), _p(mat, _i32),
                            _p(bbox, _d), _p(bc, _i32), int(n_azim), float(ray_spacing), st.shape[0],
-                           _p(st, _d), _p(pw, _d), err)
+                           _p(st, _d), _p(pw, _d), int(ray_layout), err)
         if not h:
             raise RuntimeError("oracle: " + err.value.decode())
         self._h = ctypes.c_void_p(h)
@@ -122,7 +123,8 @@ class Oracle:
 
     @classmethod
     def from_problem(cls, prob, threads: int = 1, with_xs: bool = True) -> "Oracle":
-        o = cls(prob.mesh, prob.n_azim, prob.ray_spacing, prob.sin_theta, prob.polar_w, threads)
+        o = cls(prob.mesh, prob.n_azim, prob.ray_spacing, prob.sin_theta, prob.polar_w, threads,
+                getattr(prob, "ray_layout", 0))
         if with_xs:
             o.set_xs(prob.xs)
             if prob.fixed_source is not None:

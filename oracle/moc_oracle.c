@@ -62,6 +62,7 @@ typedef struct {
   int n_dir;       /* n_azim/2 directions in [0, pi) */
   double *phi_a, *delta_a, *omega_a;  /* [n_dir] */
   int *nx_a, *ny_a;                    /* [n_dir] */
+  int layout;                          /* 0 cyclic modular rays over the box, 1 back projection */
   int n_polar;
   double *sin_theta, *polar_w;        /* [P] */
   /* tracks */
@@ -123,6 +124,16 @@ void orc_destroy(orc_t *h) {
 }
 
 /* ---------------------------------------------------------------- quadrature ---- */
+/* smallest and largest of v . x over the mesh vertices */
+static void vertex_extent(const orc_t *h, double vx, double vy, double *lo, double *hi) {
+  *lo = INFINITY; *hi = -INFINITY;
+  for (int k = 0; k < h->n_vert; ++k) {
+    double c = vx * h->xy[2 * k] + vy * h->xy[2 * k + 1];
+    if (c < *lo) *lo = c;
+    if (c > *hi) *hi = c;
+  }
+}
+
 static int build_quadrature(orc_t *h, double spacing) {
   int A = h->n_azim, nq = A / 4;
   double W = h->xmax - h->xmin, H = h->ymax - h->ymin;
@@ -132,6 +143,20 @@ static int build_quadrature(orc_t *h, double spacing) {
   h->omega_a = xcalloc(h->n_dir, sizeof(double));
   h->nx_a = xcalloc(h->n_dir, sizeof(int));
   h->ny_a = xcalloc(h->n_dir, sizeof(int));
+  if (h->layout == 1) {
+    /* back projection: nominal angles; per direction ceil(extent / spacing) rays spread evenly
+     * over the projection of the mesh on the normal (stored as nx, with ny = 0) */
+    for (int j = 0; j < h->n_dir; ++j) {
+      double phi = 2.0 * ORC_PI * (j + 0.5) / A, lo, hi;
+      vertex_extent(h, -sin(phi), cos(phi), &lo, &hi);
+      int n = (int)ceil((hi - lo) / spacing);
+      if (n < 1) n = 1;
+      h->phi_a[j] = phi;
+      h->delta_a[j] = (hi - lo > 0.0) ? (hi - lo) / n : spacing;
+      h->nx_a[j] = n; h->ny_a[j] = 0;
+    }
+    nq = 0;
+  }
   for (int a = 0; a < nq; ++a) {
     double phi = 2.0 * ORC_PI * (a + 0.5) / A;
     int nx = (int)floor(W * sin(phi) / spacing) + 1;
@@ -238,6 +263,24 @@ static int build_tracks(orc_t *h) {
   for (int j = 0; j < h->n_dir; ++j) {
     double ph = h->phi_a[j], u[2] = {cos(ph), sin(ph)};
     int nx = h->nx_a[j], ny = h->ny_a[j];
+    if (h->layout == 1) {
+      /* ray i: the line nrm . x = lo + (i + 1/2) delta, over the bounding box's extent along u */
+      double nrm[2] = {-sin(ph), cos(ph)}, lo, hi, corner[4][2] = {{h->xmin, h->ymin}, {h->xmax, h->ymin},
+                                                                     {h->xmin, h->ymax}, {h->xmax, h->ymax}};
+      vertex_extent(h, nrm[0], nrm[1], &lo, &hi);
+      double t0 = INFINITY, t1 = -INFINITY;
+      for (int k = 0; k < 4; ++k) {
+        double t = u[0] * corner[k][0] + u[1] * corner[k][1];
+        if (t < t0) t0 = t;
+        if (t > t1) t1 = t;
+      }
+      for (int i = 0; i < nx; ++i) {
+        double c = lo + (i + 0.5) * h->delta_a[j];
+        ray[5 * r] = c * nrm[0] + t0 * u[0]; ray[5 * r + 1] = c * nrm[1] + t0 * u[1];
+        ray[5 * r + 2] = u[0]; ray[5 * r + 3] = u[1]; ray[5 * r + 4] = t1 - t0; ray_dir[r] = j; ++r;
+      }
+      continue;
+    }
     for (int i = 0; i < nx; ++i) {        /* bottom edge starts */
       double p0[2] = {h->xmin + (i + 0.5) * W / nx, h->ymin};
       ray[5 * r] = p0[0]; ray[5 * r + 1] = p0[1]; ray[5 * r + 2] = u[0]; ray[5 * r + 3] = u[1];
@@ -402,7 +445,7 @@ static int build_tracks(orc_t *h) {
 
 orc_t *orc_create(int n_vert, const double *xy, int n_tri, const int32_t *tri, const int32_t *mat,
                   const double *bbox, const int32_t *bc, int n_azim, double spacing, int n_polar,
-                  const double *sin_theta, const double *polar_w, char *err_out) {
+                  const double *sin_theta, const double *polar_w, int layout, char *err_out) {
   orc_t *h = xcalloc(1, sizeof(orc_t));
   h->n_vert = n_vert; h->n_tri = n_tri;
   h->xy = xcalloc(2 * (size_t)n_vert, sizeof(double)); memcpy(h->xy, xy, 2 * (size_t)n_vert * sizeof(double));
@@ -415,8 +458,12 @@ orc_t *orc_create(int n_vert, const double *xy, int n_tri, const int32_t *tri, c
   h->polar_w = xcalloc(n_polar, sizeof(double)); memcpy(h->polar_w, polar_w, n_polar * sizeof(double));
   h->n_threads = 1;
   h->k = 1.0;
-  if (n_azim < 4 || n_azim % 4 || spacing <= 0 || n_polar < 1) {
+  h->layout = layout;
+  if (n_azim < 4 || n_azim % 4 || spacing <= 0 || n_polar < 1 || layout < 0 || layout > 1) {
     snprintf(err_out, 256, "bad quadrature arguments"); orc_destroy(h); return NULL;
+  }
+  if (layout == 1 && (bc[0] || bc[1] || bc[2] || bc[3])) {
+    snprintf(err_out, 256, "back-projected rays need vacuum on every boundary"); orc_destroy(h); return NULL;
   }
   if (build_quadrature(h, spacing) || build_tracks(h)) {
     snprintf(err_out, 256, "%s", h->err); orc_destroy(h); return NULL;

@@ -754,6 +754,16 @@ int moc_set_quadrature(moc_ctx *c, int n_azim, double spacing, int n_polar, cons
   return MOC_OK;
 }
 
+int moc_set_ray_layout(moc_ctx *c, int layout) {
+  if (!c) return MOC_ERR_ARG;
+  if (layout != MOC_RAYS_MODULAR && layout != MOC_RAYS_BACK_PROJECTION)
+    return fail(c, MOC_ERR_ARG, "set_ray_layout: layout must be MOC_RAYS_MODULAR or MOC_RAYS_BACK_PROJECTION");
+  c->geo.layout = layout;
+  c->geo.has_tracks = false;
+  if (c->device >= 0) free_tracks(c);
+  return MOC_OK;
+}
+
 int moc_generate_tracks(moc_ctx *c) {
   if (!c) return MOC_ERR_ARG;
   if (c->device >= 0) {

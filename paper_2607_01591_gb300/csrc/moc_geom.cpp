@@ -115,6 +115,7 @@ int set_mesh(Geometry &g, int n_vert, const double *xy, int n_tri, const int32_t
   ng.sin_theta = g.sin_theta;
   ng.polar_w = g.polar_w;
   ng.has_quad = g.has_quad;
+  ng.layout = g.layout;
   g = std::move(ng);
   return MOC_OK;
 }
@@ -151,7 +152,21 @@ int set_quadrature(Geometry &g, int n_azim, double spacing, int n_polar, const d
 
 namespace {
 
-// Direction set over [0, pi) with the cyclic correction, and azimuthal weights over [0, 2 pi).
+// extent [lo, hi] of the mesh vertices projected on the unit vector (vx, vy)
+void projected_extent(const Geometry &g, double vx, double vy, double &lo, double &hi) {
+  lo = INFINITY;
+  hi = -INFINITY;
+  for (int v = 0; v < g.n_vert; ++v) {
+    const double c = vx * g.xy[2 * (size_t)v] + vy * g.xy[2 * (size_t)v + 1];
+    lo = std::min(lo, c);
+    hi = std::max(hi, c);
+  }
+}
+
+// Direction set over [0, pi) and azimuthal weights over [0, 2 pi). Modular layout: the cyclic
+// correction of the angles and spacings over the bounding box. Back projection: the nominal
+// angles 2 pi (j + 1/2)/n_azim, and per direction n = ceil(extent/spacing) rays evenly spread
+// over the projection of the mesh on the direction's normal (spacing extent/n).
 int build_directions(Geometry &g, std::string &err) {
   double W = g.bbox[1] - g.bbox[0], H = g.bbox[3] - g.bbox[2];
   int nd = g.n_dir, nq = g.n_azim / 4;
@@ -160,6 +175,19 @@ int build_directions(Geometry &g, std::string &err) {
   g.omega.assign(nd, 0.0);
   g.nx.assign(nd, 0);
   g.ny.assign(nd, 0);
+  if (g.layout == MOC_RAYS_BACK_PROJECTION) {
+    for (int j = 0; j < nd; ++j) {
+      const double ph = 2.0 * kPi * (j + 0.5) / g.n_azim;
+      double lo, hi;
+      projected_extent(g, -std::sin(ph), std::cos(ph), lo, hi);
+      const double ext = hi - lo;
+      const int n = std::max(1, (int)std::ceil(ext / g.spacing));
+      g.phi[j] = ph;
+      g.delta[j] = (ext > 0.0) ? ext / n : g.spacing;
+      g.nx[j] = n;
+    }
+    nq = 0;  // no modular directions below
+  }
   for (int a = 0; a < nq; ++a) {
     double nominal = 2.0 * kPi * (a + 0.5) / g.n_azim;
     int nx = (int)std::floor(W * std::sin(nominal) / g.spacing) + 1;
@@ -227,6 +255,12 @@ int generate_tracks(Geometry &g, std::string &err, const Walker *walker) {
     err = "generate_tracks: set the mesh and the quadrature first";
     return MOC_ERR_STATE;
   }
+  if (g.layout == MOC_RAYS_BACK_PROJECTION)
+    for (int i = 0; i < 4; ++i)
+      if (g.bc[i] != MOC_BC_VACUUM) {
+        err = "generate_tracks: back-projected rays are not cyclic; every boundary must be vacuum";
+        return MOC_ERR_ARG;
+      }
   int rc = build_directions(g, err);
   if (rc) return rc;
   const double W = g.bbox[1] - g.bbox[0], H = g.bbox[3] - g.bbox[2];
@@ -258,16 +292,35 @@ int generate_tracks(Geometry &g, std::string &err, const Walker *walker) {
     const int nr = g.nx[j] + g.ny[j];
     std::vector<double> &ray = D.ray;
     ray.resize(3 * (size_t)nr);
-    for (int i = 0; i < g.nx[j]; ++i) {
-      ray[3 * i] = g.bbox[0] + (i + 0.5) * W / g.nx[j];
-      ray[3 * i + 1] = g.bbox[2];
+    if (g.layout == MOC_RAYS_BACK_PROJECTION) {
+      // ray i on the line n . x = lo + (i + 1/2) delta, from where the line enters the
+      // bounding box's extent along u to where it leaves it
+      double lo, hi, ulo = INFINITY, uhi = -INFINITY;
+      projected_extent(g, nrm[0], nrm[1], lo, hi);
+      for (int cx = 0; cx < 2; ++cx)
+        for (int cy = 0; cy < 2; ++cy) {
+          const double t = u[0] * g.bbox[cx] + u[1] * g.bbox[2 + cy];
+          ulo = std::min(ulo, t);
+          uhi = std::max(uhi, t);
+        }
+      for (int i = 0; i < nr; ++i) {
+        const double c = lo + (i + 0.5) * g.delta[j];
+        ray[3 * i] = c * nrm[0] + ulo * u[0];
+        ray[3 * i + 1] = c * nrm[1] + ulo * u[1];
+        ray[3 * i + 2] = uhi - ulo;
+      }
+    } else {
+      for (int i = 0; i < g.nx[j]; ++i) {
+        ray[3 * i] = g.bbox[0] + (i + 0.5) * W / g.nx[j];
+        ray[3 * i + 1] = g.bbox[2];
+      }
+      for (int i = 0; i < g.ny[j]; ++i) {
+        int r = g.nx[j] + i;
+        ray[3 * r] = (u[0] > 0) ? g.bbox[0] : g.bbox[1];
+        ray[3 * r + 1] = g.bbox[2] + (i + 0.5) * H / g.ny[j];
+      }
+      for (int r = 0; r < nr; ++r) ray[3 * r + 2] = box_exit(g, &ray[3 * r], u);
     }
-    for (int i = 0; i < g.ny[j]; ++i) {
-      int r = g.nx[j] + i;
-      ray[3 * r] = (u[0] > 0) ? g.bbox[0] : g.bbox[1];
-      ray[3 * r + 1] = g.bbox[2] + (i + 0.5) * H / g.ny[j];
-    }
-    for (int r = 0; r < nr; ++r) ray[3 * r + 2] = box_exit(g, &ray[3 * r], u);
     // rays sorted by their offset along the normal, to find the rays a boundary edge spans
     std::vector<std::pair<double, int>> off(nr);
     for (int r = 0; r < nr; ++r) off[r] = {nrm[0] * ray[3 * r] + nrm[1] * ray[3 * r + 1], r};

@@ -27,7 +27,8 @@ struct Geometry {
   double spacing = 0;
   std::vector<double> sin_theta, polar_w;
   std::vector<double> phi, delta, omega;   // [n_dir]
-  std::vector<int> nx, ny;                 // [n_dir]
+  std::vector<int> nx, ny;                 // [n_dir] rays from the bottom / side walls (back projection: nx rays, ny = 0)
+  int layout = 0;                          // MOC_RAYS_MODULAR or MOC_RAYS_BACK_PROJECTION
   bool has_quad = false;
   // tracks, in the external order
   std::vector<int64_t> seg_off;    // [T+1]

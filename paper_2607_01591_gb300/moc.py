@@ -64,6 +64,7 @@ def load_library(path: Optional[str] = None):
             "moc_set_mesh": (ctypes.c_int, [_vp, ctypes.c_int, _d, ctypes.c_int, _i32, _i32, _d, _i32]),
             "moc_set_quadrature": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _d, _d]),
             "moc_generate_tracks": (ctypes.c_int, [_vp]),
+            "moc_set_ray_layout": (ctypes.c_int, [_vp, ctypes.c_int]),
             "moc_generate_tracks_device": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
             "moc_get_track_counts": (ctypes.c_int, [_vp, _i64, _i64]),
             "moc_get_tracks": (ctypes.c_int, [_vp, _i64, _i32, _d, _i32, _d, _i64]),
@@ -264,6 +265,10 @@ class Moc:
     def generate_tracks(self):
         self._check(self._lib.moc_generate_tracks(self._h))
 
+    def set_ray_layout(self, layout: int):
+        """0: cyclic modular rays over the bounding box; 1: back projection (vacuum boundaries)."""
+        self._check(self._lib.moc_set_ray_layout(self._h, int(layout)))
+
     def generate_tracks_device(self) -> float:
         """Tracks with the half-edge walk on the GPU (bit-identical to generate_tracks); returns the
         device time of the walk in ms."""
@@ -393,6 +398,8 @@ class Moc:
         m = cls(device, precision, stream)
         m.set_mesh(prob.mesh)
         m.set_quadrature(prob.n_azim, prob.ray_spacing, prob.sin_theta, prob.polar_w)
+        if getattr(prob, "ray_layout", 0):
+            m.set_ray_layout(prob.ray_layout)
         if device_tracking:
             m.generate_tracks_device()
         else:

@@ -83,6 +83,7 @@ class Problem:
     name: str = ""
     seed: int = 0
     fixed_source: Optional[np.ndarray] = None   # [R, G] isotropic volumetric source, or None
+    ray_layout: int = 0     # 0 cyclic modular rays over the bounding box, 1 back projection (vacuum only)
 
 
 # ----------------------------------------------------------------------------------------------

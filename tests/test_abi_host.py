@@ -42,7 +42,8 @@ def _compare_tracks(prob):
         np.testing.assert_allclose(q1[k], q2[k], rtol=1e-14)
 
 
-@pytest.mark.parametrize("case", ["pin", "pin_vacuum", "lattice3", "lattice3_mixed_bc", "grid", "hex7", "hex1"])
+@pytest.mark.parametrize("case", ["pin", "pin_vacuum", "lattice3", "lattice3_mixed_bc", "grid", "hex7", "hex1",
+                                  "pin_back_projection", "hex7_back_projection", "grid_back_projection"])
 def test_host_segmentation_matches_oracle(lib, case):
     if case == "pin":
         prob = W.pin_cell_problem()
@@ -57,9 +58,26 @@ def test_host_segmentation_matches_oracle(lib, case):
         prob = W.Problem(W.grid_mesh(5, 3, 2.0, 1.0), W.synthetic_xs(["fuel"], 2, 1), 8, 0.07)
     elif case == "hex7":
         prob = W.Problem(W.hex_core_mesh(n_sub=4, n_rings=1), W.synthetic_xs(["fuel", "fuel", "coolant"], 3, 1), 12, 0.3)
-    else:
+    elif case == "hex1":
         prob = W.Problem(W.hex_core_mesh(n_sub=6, n_rings=0), W.synthetic_xs(["fuel", "fuel", "coolant"], 3, 1), 8, 0.2)
+    elif case == "pin_back_projection":
+        prob = W.pin_cell_problem()
+        prob.mesh = W.with_bc(prob.mesh, (0, 0, 0, 0))
+        prob.ray_layout = 1
+    elif case == "hex7_back_projection":
+        prob = W.Problem(W.hex_core_mesh(n_sub=4, n_rings=1), W.synthetic_xs(["fuel", "fuel", "coolant"], 3, 1), 12, 0.3,
+                         ray_layout=1)
+    else:
+        prob = W.Problem(W.grid_mesh(5, 3, 2.0, 1.0, bc=(0, 0, 0, 0)), W.synthetic_xs(["fuel"], 2, 1), 12, 0.07,
+                         ray_layout=1)
     _compare_tracks(prob)
+
+
+def test_back_projection_rejects_reflective_walls(lib):
+    prob = W.pin_cell_problem()
+    prob.ray_layout = 1
+    with pytest.raises(moc.MocError):
+        moc.Moc.from_problem(prob, device=-1)
 
 
 def test_bad_inputs_are_rejected(lib):

@@ -336,3 +336,25 @@ def test_cmfd_reflector_core_converges_to_the_oracle(precision):
     assert co and c, (n, r)
     assert abs(k - ko) <= (1e-9 if precision == "fp64" else 2e-6) * ko, (k, ko)
     assert _rel(m.get_state()[0], o.get_state()[0]) <= (1e-7 if precision == "fp64" else 1e-4)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", 2e-5)])
+def test_back_projection_outers_match_oracle(precision, tol):
+    """Back-projected rays on the concave 7-hexagon cluster (vacuum): outers from the same random
+    state, GPU vs oracle, compared after each."""
+    mesh = W.hex_core_mesh(n_sub=4, n_rings=1)
+    xs = W.synthetic_xs(["fuel", "fuel", "coolant"], 7, 9, sigt_range=(0.05, 0.6))
+    prob = W.Problem(mesh, xs, 12, 0.3, ray_layout=1)
+    o = _oracle(prob)
+    m = moc.Moc.from_problem(prob, precision=precision)
+    rng = np.random.default_rng(21)
+    phi0 = rng.uniform(0.5, 1.5, (mesh.n_tri, 7))
+    o.set_state(phi0, 1.05, None)
+    o.normalise()
+    m.set_state(phi0, 1.05, None)
+    for it in range(4):
+        o.outer(True)
+        kg, _ = m.outer(1)
+        phio, ko = o.get_state()
+        assert abs(kg - ko) <= tol * ko, (it, kg, ko)
+        assert _rel(m.get_state()[0], phio) <= 10 * tol, (it, _rel(m.get_state()[0], phio))

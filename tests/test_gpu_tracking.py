@@ -29,6 +29,7 @@ CASES = {
     "lattice3_mixed_bc": lambda: W.small_lattice_problem(3, bc=(1, 0, 1, 0), n_azim=24, ray_spacing=0.03),
     "grid": lambda: W.Problem(W.grid_mesh(5, 3, 2.0, 1.0), W.synthetic_xs(["fuel"], 2, 1), 8, 0.07),
     "hex7_concave": lambda: W.Problem(W.hex_core_mesh(n_sub=4, n_rings=1), W.synthetic_xs(["fuel", "fuel", "coolant"], 3, 1), 12, 0.3),
+    "hex7_back_projection": lambda: W.Problem(W.hex_core_mesh(n_sub=4, n_rings=1), W.synthetic_xs(["fuel", "fuel", "coolant"], 3, 1), 12, 0.3, ray_layout=1),
     "assembly": lambda: W.assembly_problem(),
     "core1": lambda: _core1(16, 0.05),
 }

@@ -127,7 +127,7 @@ def _brute_force_pieces(mesh, p0, u, L):
     return merged
 
 
-@pytest.mark.parametrize("which", ["grid", "pin", "hex7"])
+@pytest.mark.parametrize("which", ["grid", "pin", "hex7", "hex7_back_projection", "pin_back_projection"])
 def test_segmentation_matches_brute_force(which):
     if which == "grid":
         mesh = W.grid_mesh(2, 2, 1.0, 1.0)
@@ -135,9 +135,13 @@ def test_segmentation_matches_brute_force(which):
     elif which == "pin":
         mesh = W.pin_cell_mesh()
         o = oracle.Oracle(mesh, 8, 0.1, W.TY3_SIN_THETA, W.TY3_WEIGHT)
+    elif which == "pin_back_projection":
+        mesh = W.with_bc(W.pin_cell_mesh(), (0, 0, 0, 0))
+        o = oracle.Oracle(mesh, 12, 0.1, W.TY3_SIN_THETA, W.TY3_WEIGHT, ray_layout=1)
     else:
         mesh = W.hex_core_mesh(n_sub=2, n_rings=1)     # 7 hexagons: concave outline, gaps in rays
-        o = oracle.Oracle(mesh, 8, 1.0, W.TY3_SIN_THETA, W.TY3_WEIGHT)
+        o = oracle.Oracle(mesh, 8 if which == "hex7" else 12, 1.0, W.TY3_SIN_THETA, W.TY3_WEIGHT,
+                          ray_layout=0 if which == "hex7" else 1)
     q, tr = _track_lines(o)
     xmin, xmax, ymin, ymax = mesh.bbox
     n_checked = 0
@@ -219,6 +223,46 @@ def test_links_reflect_at_walls(bc):
     assert seen.max() <= 1
     if all(b == 1 for b in bc):
         assert (seen == 1).all()          # a bijection of track ends
+
+
+def test_back_projection_quadrature_and_ray_offsets():
+    """Back projection: nominal angles, equal weights, and per direction n = ceil(extent/delta)
+    parallel rays at offsets (i + 1/2) * extent/n across the mesh's projection on the normal."""
+    mesh = W.grid_mesh(3, 2, 1.5, 1.0, bc=(0, 0, 0, 0))      # convex: every ray crosses the mesh
+    A, sp = 12, 0.07
+    o = oracle.Oracle(mesh, A, sp, W.TY3_SIN_THETA, W.TY3_WEIGHT, ray_layout=1)
+    q, tr = _track_lines(o)
+    np.testing.assert_allclose(q["phi"], 2 * math.pi * (np.arange(A // 2) + 0.5) / A, rtol=1e-15)
+    np.testing.assert_allclose(q["omega"], 1.0 / A, rtol=1e-13)
+    for j in range(o.n_dir):
+        ph = q["phi"][j]
+        nrm = np.array([-math.sin(ph), math.cos(ph)])
+        ext = mesh.xy @ nrm
+        n = math.ceil((ext.max() - ext.min()) / sp)
+        assert abs(q["delta"][j] - (ext.max() - ext.min()) / n) < 1e-13 and q["delta"][j] <= sp
+        sel = tr["track_dir"] == j
+        assert sel.sum() == n
+        c = np.sort(tr["track_xy"][sel, :2] @ nrm)
+        np.testing.assert_allclose(c, ext.min() + (np.arange(n) + 0.5) * q["delta"][j], rtol=0, atol=1e-12)
+        # every track spans the mesh: it starts and ends on the mesh outline
+        for st in tr["track_xy"][sel]:
+            for x, y in (st[:2], st[2:]):
+                assert min(abs(x - 0.0), abs(x - 1.5), abs(y - 0.0), abs(y - 1.0)) < 1e-12
+
+
+def test_back_projection_areas_converge():
+    mesh = W.with_bc(W.pin_cell_mesh(), (0, 0, 0, 0))
+    exact = mesh.areas()
+    errs = []
+    for sp in (0.05, 0.01, 0.002):
+        o = oracle.Oracle(mesh, 16, sp, W.TY3_SIN_THETA, W.TY3_WEIGHT, ray_layout=1)
+        errs.append(np.abs(o.areas() / exact - 1).max())
+    assert errs[1] < errs[0] / 3 and errs[2] < errs[1] / 3, errs
+
+
+def test_back_projection_needs_vacuum_walls():
+    with pytest.raises(RuntimeError):
+        oracle.Oracle(W.pin_cell_mesh(), 16, 0.05, W.TY3_SIN_THETA, W.TY3_WEIGHT, ray_layout=1)
 
 
 def test_tracked_area_total_and_convergence():
@@ -343,15 +387,16 @@ def test_infinite_medium_fixed_source():
 
 # ------------------------------------------------------------------------------ balance, symmetry
 
-@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (1, 0, 1, 0), (1, 1, 1, 1)])
-def test_global_neutron_balance(bc):
-    """At convergence: absorption + leakage = production / k, with production normalised to 1."""
+@pytest.mark.parametrize("bc,layout", [((0, 0, 0, 0), 0), ((1, 0, 1, 0), 0), ((1, 1, 1, 1), 0), ((0, 0, 0, 0), 1)])
+def test_global_neutron_balance(bc, layout):
+    """At convergence: absorption + leakage = production / k, with production normalised to 1
+    (modular and back-projected rays)."""
     prob = W.pin_cell_problem()
     mesh = W.with_bc(prob.mesh, bc)
     xs = prob.xs
     if bc == (0, 0, 0, 0):
         xs = W.CrossSections(xs.sigma_t, xs.nu_sigma_f * 4.0, xs.chi, xs.sigma_s)
-    o = oracle.Oracle(mesh, 16, 0.05, W.TY3_SIN_THETA, W.TY3_WEIGHT)
+    o = oracle.Oracle(mesh, 16, 0.05, W.TY3_SIN_THETA, W.TY3_WEIGHT, ray_layout=layout)
     o.set_xs(xs)
     k, n, r, conv = o.iterate(True, 1e-13, 1e-12, 50000)
     assert conv
