@@ -198,17 +198,21 @@ static int cmp_offs(const void *a, const void *b) {
   return (x->c < y->c) ? -1 : (x->c > y->c);
 }
 
-/* Clip the line p0 + s u, s in [0, L], against CCW triangle (a, b, c). Returns 1 and the
- * interval if the intersection has positive length. */
-static int clip_triangle(const double *p0, const double *u, double L, const double *v0,
-                         const double *v1, const double *v2, double *s_in, double *s_out) {
-  const double *V[3] = {v0, v1, v2};
+/* Clip the line p0 + s u, s in [0, L], against CCW triangle t. Returns 1 and the interval if
+ * the intersection has positive length. Each edge's side test is evaluated from its lower-id
+ * vertex (and negated for the other orientation), so the two triangles of an edge see exactly
+ * opposite values and a line along a shared edge belongs to exactly one of them. */
+static int clip_triangle(const double *xy, const int32_t *tri, int t, const double *p0, const double *u, double L,
+                         double *s_in, double *s_out) {
   double lo = 0.0, hi = L;
   for (int e = 0; e < 3; ++e) {
-    const double *a = V[e], *b = V[(e + 1) % 3];
-    double nx = -(b[1] - a[1]), ny = b[0] - a[0];           /* inward normal for CCW */
-    double f0 = nx * (p0[0] - a[0]) + ny * (p0[1] - a[1]);  /* n.(p0 - a) */
+    int ia = tri[3 * t + e], ib = tri[3 * t + (e + 1) % 3], fwd = ia < ib;
+    const double *a = xy + 2 * (int64_t)(fwd ? ia : ib), *b = xy + 2 * (int64_t)(fwd ? ib : ia);
+    double sg = fwd ? 1.0 : -1.0;
+    double nx = -(b[1] - a[1]), ny = b[0] - a[0];           /* inward normal of the CCW edge, */
+    double f0 = nx * (p0[0] - a[0]) + ny * (p0[1] - a[1]);  /* up to the orientation sign sg */
     double fu = nx * u[0] + ny * u[1];
+    nx *= sg; ny *= sg; f0 *= sg; fu *= sg;
     if (fu == 0.0) {
       /* ray parallel to this edge: outside if on the outer side; a ray running exactly along
        * the edge belongs to the triangle on its left only */
@@ -315,13 +319,17 @@ static int build_tracks(orc_t *h) {
         if (c < cmin) cmin = c;
         if (c > cmax) cmax = c;
       }
+      /* widened by a rounding margin: a ray along an edge of the triangle is a candidate even
+       * when the projections round to just outside it; the clip decides */
+      cmin -= 1e-9 * fmax(W, H);
+      cmax += 1e-9 * fmax(W, H);
       /* first ray with offset >= cmin */
       int lo = 0, hi = nr;
       while (lo < hi) { int m = (lo + hi) / 2; if (off[m].c < cmin) lo = m + 1; else hi = m; }
       for (int q = lo; q < nr && off[q].c <= cmax; ++q) {
         int64_t rr = r0 + off[q].idx;
         double s0, s1;
-        if (!clip_triangle(ray + 5 * rr, ray + 5 * rr + 2, ray[5 * rr + 4], v[0], v[1], v[2], &s0, &s1)) continue;
+        if (!clip_triangle(h->xy, h->tri, t, ray + 5 * rr, ray + 5 * rr + 2, ray[5 * rr + 4], &s0, &s1)) continue;
         if (s1 - s0 < sliver) continue;
         if (cnt[rr] == cap[rr]) {
           cap[rr] = cap[rr] ? 2 * cap[rr] : 16;
@@ -1024,7 +1032,10 @@ int orc_sample_fixed_source(int n_vert, const double *xy, int n_tri, const int32
         if (cc < cmin) cmin = cc;
         if (cc > cmax) cmax = cc;
       }
-      pj[t].cmin = cmin; pj[t].cmax = cmax; pj[t].t = t;
+      /* rounding margin, as in build_tracks */
+      pj[t].cmin = cmin - 1e-9 * fmax(h->xmax - h->xmin, h->ymax - h->ymin);
+      pj[t].cmax = cmax + 1e-9 * fmax(h->xmax - h->xmin, h->ymax - h->ymin);
+      pj[t].t = t;
       if (cmax - cmin > wmax) wmax = cmax - cmin;
     }
     qsort(pj, n_tri, sizeof(proj_t), cmp_proj);
@@ -1039,10 +1050,8 @@ int orc_sample_fixed_source(int n_vert, const double *xy, int n_tri, const int32
       for (int q2 = lo; q2 < n_tri && pj[q2].cmin <= c; ++q2) {
         if (pj[q2].cmax < c) continue;
         int t = pj[q2].t;
-        const double *v[3];
-        for (int k = 0; k < 3; ++k) v[k] = xy + 2 * (int64_t)tri[3 * t + k];
         double s0, s1;
-        if (!clip_triangle(p0 + 2 * r, u, L, v[0], v[1], v[2], &s0, &s1)) continue;
+        if (!clip_triangle(xy, tri, t, p0 + 2 * r, u, L, &s0, &s1)) continue;
         if (s1 - s0 < 1e-12) continue;
         if (cnt == cap) { cap *= 2; pc = realloc(pc, cap * sizeof(piece_t)); if (!pc) abort(); }
         pc[cnt].s0 = s0; pc[cnt].s1 = s1; pc[cnt].tri = t; cnt++;

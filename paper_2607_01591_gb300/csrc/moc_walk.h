@@ -42,17 +42,34 @@ struct Event {
 MOC_HD double dmin(double a, double b) { return (b < a) ? b : a; }
 MOC_HD double dmax(double a, double b) { return (a < b) ? b : a; }
 
+// Side test of the line p0 + s u against edge k of triangle t: f0 = n . (p0 - a) and fu = n . u
+// with n the inward normal of the counter-clockwise edge a -> b. Both are evaluated from the
+// edge's lower-id endpoint and negated for the other orientation, so the two triangles sharing
+// an edge get exactly opposite values: a line along the edge is claimed by exactly one of them
+// and an exit parameter equals the neighbour's entry parameter bit for bit.
+MOC_HD void edge_side(const MeshView &m, int t, int k, const double *p0, const double *u, double &f0, double &fu,
+                      double &nx, double &ny) {
+  const int ia = m.tri[3 * (size_t)t + k], ib = m.tri[3 * (size_t)t + (k + 1) % 3];
+  const bool fwd = ia < ib;
+  const double *p = &m.xy[2 * (size_t)(fwd ? ia : ib)];
+  const double *q = &m.xy[2 * (size_t)(fwd ? ib : ia)];
+  const double cx = -(q[1] - p[1]), cy = q[0] - p[0];  // inward normal of p -> q
+  const double g0 = cx * (p0[0] - p[0]) + cy * (p0[1] - p[1]);
+  const double gu = cx * u[0] + cy * u[1];
+  f0 = fwd ? g0 : -g0;
+  fu = fwd ? gu : -gu;
+  nx = fwd ? cx : -cx;
+  ny = fwd ? cy : -cy;
+}
+
 // Interval of the line p0 + s u inside triangle t (Cyrus-Beck half-planes). A line running
 // exactly along an edge belongs to the triangle on its left. Returns false if empty.
 MOC_HD bool clip(const MeshView &m, int t, const double *p0, const double *u, double &lo, double &hi) {
   lo = -INFINITY;
   hi = INFINITY;
   for (int k = 0; k < 3; ++k) {
-    const double *a = &m.xy[2 * (size_t)m.tri[3 * (size_t)t + k]];
-    const double *b = &m.xy[2 * (size_t)m.tri[3 * (size_t)t + (k + 1) % 3]];
-    const double nx = -(b[1] - a[1]), ny = b[0] - a[0];  // inward normal of a CCW edge
-    const double f0 = nx * (p0[0] - a[0]) + ny * (p0[1] - a[1]);
-    const double fu = nx * u[0] + ny * u[1];
+    double f0, fu, nx, ny;
+    edge_side(m, t, k, p0, u, f0, fu, nx, ny);
     if (fu == 0.0) {
       if (f0 < 0.0) return false;
       if (f0 == 0.0 && (nx * (-u[1]) + ny * u[0]) <= 0.0) return false;
@@ -90,12 +107,10 @@ MOC_HD double walk(const MeshView &m, int t0, double s_start, const double *p0, 
     int ex = -1;
     double best = INFINITY;
     for (int k = 0; k < 3; ++k) {
-      const double *a = &m.xy[2 * (size_t)m.tri[3 * (size_t)T + k]];
-      const double *b = &m.xy[2 * (size_t)m.tri[3 * (size_t)T + (k + 1) % 3]];
-      const double nx = -(b[1] - a[1]), ny = b[0] - a[0];
-      const double fu = nx * u[0] + ny * u[1];
+      double f0, fu, nx, ny;
+      edge_side(m, T, k, p0, u, f0, fu, nx, ny);
       if (fu >= 0.0) continue;
-      const double s = -(nx * (p0[0] - a[0]) + ny * (p0[1] - a[1])) / fu;
+      const double s = -f0 / fu;
       if (s < best) {
         best = s;
         ex = k;

@@ -73,6 +73,15 @@ def test_host_segmentation_matches_oracle(lib, case):
     _compare_tracks(prob)
 
 
+def test_rays_along_mesh_edges_are_traced_without_gaps(lib):
+    """12 azimuths put one direction at exactly 45 degrees, along the diagonals of the reflector's
+    square cells: rays run along edges and through vertices. Host walk and oracle must agree
+    (before edge tests were evaluated from a canonical endpoint, such rays lost pieces)."""
+    xs = W.synthetic_xs(["fuel", "fuel", "fuel", "fuel", "clad", "moderator", "reflector"], 7, 4,
+                        fuel_scales=[1.0, 0.95, 1.05, 0.9])
+    _compare_tracks(W.Problem(W.core_mesh(1), xs, 12, 0.2, tol=1e-6, name="core1", seed=4))
+
+
 def test_back_projection_rejects_reflective_walls(lib):
     prob = W.pin_cell_problem()
     prob.ray_layout = 1

@@ -32,6 +32,7 @@ CASES = {
     "hex7_back_projection": lambda: W.Problem(W.hex_core_mesh(n_sub=4, n_rings=1), W.synthetic_xs(["fuel", "fuel", "coolant"], 3, 1), 12, 0.3, ray_layout=1),
     "assembly": lambda: W.assembly_problem(),
     "core1": lambda: _core1(16, 0.05),
+    "core1_45deg": lambda: _core1(12, 0.2),        # rays along cell diagonals and through vertices
 }
 
 
