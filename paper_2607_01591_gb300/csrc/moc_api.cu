@@ -37,6 +37,9 @@ struct moc_ctx {
   TrackRec *d_trk = nullptr;
   int32_t *d_link = nullptr;
   uint8_t *d_fed = nullptr;  // per internal track end: 1 if some outgoing end feeds it
+  long long *d_perm = nullptr, *d_inv = nullptr;  // internal <-> external track order
+  double *h_scal = nullptr;   // pinned, device-mapped copy of the scalars written by state_out_kernel
+  bool pageable_ok = false;   // the GPU reads and writes pageable host memory coherently
   void *d_wgt = nullptr, *d_inv_sin = nullptr;
   int32_t *d_mat = nullptr;
   double *d_area = nullptr;
@@ -170,6 +173,8 @@ void free_tracks(moc_ctx *c) {
   dfree(c->d_trk);
   dfree(c->d_link);
   dfree(c->d_fed);
+  dfree(c->d_perm);
+  dfree(c->d_inv);
   dfree(c->d_wgt);
   dfree(c->d_inv_sin);
   dfree(c->d_mat);
@@ -281,6 +286,11 @@ template <typename Real> int upload_tracks(moc_ctx *c) {
   for (int32_t e : link)
     if (e >= 0) fed[e] = 1;
   if ((rc = upload(c, c->d_fed, fed.data(), fed.size()))) return rc;
+  {
+    std::vector<long long> pl(c->perm.begin(), c->perm.end()), il(c->inv.begin(), c->inv.end());
+    if ((rc = upload(c, c->d_perm, pl.data(), pl.size()))) return rc;
+    if ((rc = upload(c, c->d_inv, il.data(), il.size()))) return rc;
+  }
   Real *dw = nullptr, *di = nullptr;
   if ((rc = upload(c, dw, wgt.data(), wgt.size()))) return rc;
   c->d_wgt = dw;
@@ -670,16 +680,66 @@ int reset_scalars(moc_ctx *c, double k, double scale) {
   return MOC_OK;
 }
 
-// F = sum_i A_i sum_g nuSigma_f phi on the host (used to normalise a state set by the caller)
+// F = sum_i A_i sum_g nuSigma_f phi on the host (used to normalise a state set by the caller):
+// 64 fixed chunks of regions summed in parallel, then in chunk order, so F does not depend on the
+// thread count.
 double host_fission(const moc_ctx *c, const double *phi, const std::vector<double> &nsf) {
   const Geometry &g = c->geo;
-  double F = 0.0;
-  for (int r = 0; r < g.n_tri; ++r) {
-    double f = 0.0;
-    for (int k = 0; k < c->G; ++k) f += nsf[(size_t)g.mat[r] * c->G + k] * (phi ? phi[(size_t)r * c->G + k] : 1.0);
-    F += g.area[r] * f;
+  const int R = g.n_tri, G = c->G, NC = 64;
+  double part[NC];
+#pragma omp parallel for schedule(static)
+  for (int q = 0; q < NC; ++q) {
+    const int r0 = (int)((int64_t)R * q / NC), r1 = (int)((int64_t)R * (q + 1) / NC);
+    double F = 0.0;
+    for (int r = r0; r < r1; ++r) {
+      double f = 0.0;
+      for (int k = 0; k < G; ++k) f += nsf[(size_t)g.mat[r] * G + k] * (phi ? phi[(size_t)r * G + k] : 1.0);
+      F += g.area[r] * f;
+    }
+    part[q] = F;
   }
+  double F = 0.0;
+  for (int q = 0; q < NC; ++q) F += part[q];
   return F;
+}
+
+// Device-addressable view of a caller's host array (pinned or registered memory; pageable memory
+// where this GPU accesses it coherently), or nullptr: the state then goes through the staged copy.
+const void *host_view(const moc_ctx *c, const void *p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type == cudaMemoryTypeHost) return a.devicePointer;
+  if (a.type == cudaMemoryTypeUnregistered && c->pageable_ok) return p;
+  return nullptr;
+}
+
+template <typename Real> int state_in(moc_ctx *c, const double *dphi, const double *dpsi, double k, double scale) {
+  const int R = c->geo.n_tri;
+  const long long n = (long long)R * c->Gp + c->T * 2 * c->P * c->G;
+  state_in_kernel<Real><<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
+      R, c->G, c->Gp, (long long)c->T, c->P, dphi, dpsi, c->d_perm, c->d_fed, (Real *)c->d_phi,
+      (Real *)c->d_psi[c->cur], c->d_scal, k, scale);
+  CUDA_TRY(c, cudaGetLastError());
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return MOC_OK;
+}
+
+template <typename Real> int state_out(moc_ctx *c, double *dphi, double *dpsi, double *s) {
+  const int R = c->geo.n_tri;
+  const long long n = std::max<long long>(1, (dphi ? (long long)R * c->G : 0) + (dpsi ? c->T * 2 * c->P * c->G : 0));
+  double *hs = nullptr;
+  CUDA_TRY(c, cudaHostGetDevicePointer((void **)&hs, c->h_scal, 0));
+  state_out_kernel<Real><<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
+      R, c->G, c->Gp, (long long)c->T, c->P, (const Real *)c->d_phi, (const Real *)c->d_psi[c->cur], c->d_inv,
+      c->d_scal, c->eigen ? 1 : 0, dphi, dpsi, hs);
+  CUDA_TRY(c, cudaGetLastError());
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < S_COUNT; ++i) s[i] = c->h_scal[i];
+  return MOC_OK;
 }
 
 }  // namespace
@@ -707,6 +767,11 @@ int moc_create(moc_ctx **out, int device, int precision, void *stream) {
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_scal, S_COUNT * sizeof(double));
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&c->h_scal, S_COUNT * sizeof(double), cudaHostAllocMapped);
+    if (e == cudaSuccess) {
+      int pm = 0;
+      if (cudaDeviceGetAttribute(&pm, cudaDevAttrPageableMemoryAccess, device) == cudaSuccess) c->pageable_ok = pm != 0;
+    }
     if (e != cudaSuccess) {
       moc_destroy(c);
       return MOC_ERR_CUDA;
@@ -728,6 +793,7 @@ void moc_destroy(moc_ctx *c) {
     free_tracks(c);
     dfree(c->d_scal);
     if (c->h_stage) cudaFreeHost(c->h_stage);
+    if (c->h_scal) cudaFreeHost(c->h_scal);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   }
@@ -1060,14 +1126,19 @@ int moc_set_state(moc_ctx *c, const double *phi, double k, const double *psi) {
   if (rc) return rc;
   if (!(k > 0.0) || !std::isfinite(k)) return fail(c, MOC_ERR_ARG, "set_state: k must be finite and > 0");
   cudaSetDevice(c->device);
-  rc = c->precision == MOC_FP64 ? upload_state<double>(c, phi, psi) : upload_state<float>(c, phi, psi);
-  if (rc) return rc;
   double scale = 1.0;
   if (c->eigen) {
     double F = host_fission(c, phi, c->h_nsf);
     if (!std::isfinite(F)) return fail(c, MOC_ERR_ARG, "set_state: the fission source of the state is not finite");
     if (F > 0.0) scale = 1.0 / F;   // no fission at all: power iteration will report MOC_ERR_NONFINITE
   }
+  // arrays the device can address are read in place by one kernel; others are staged
+  const void *vphi = host_view(c, phi), *vpsi = host_view(c, psi);
+  if ((!phi || vphi) && (!psi || vpsi))
+    return c->precision == MOC_FP64 ? state_in<double>(c, (const double *)vphi, (const double *)vpsi, k, scale)
+                                    : state_in<float>(c, (const double *)vphi, (const double *)vpsi, k, scale);
+  rc = c->precision == MOC_FP64 ? upload_state<double>(c, phi, psi) : upload_state<float>(c, phi, psi);
+  if (rc) return rc;
   return reset_scalars(c, k, scale);
 }
 
@@ -1076,6 +1147,15 @@ int moc_get_state(moc_ctx *c, double *phi, double *k, double *psi) {
   if (rc) return rc;
   cudaSetDevice(c->device);
   double s[S_COUNT];
+  void *vphi = (void *)host_view(c, phi), *vpsi = (void *)host_view(c, psi);
+  if ((phi || psi) && (!phi || vphi) && (!psi || vpsi)) {
+    // written in place by one kernel, which also copies the scalars
+    rc = c->precision == MOC_FP64 ? state_out<double>(c, (double *)vphi, (double *)vpsi, s)
+                                  : state_out<float>(c, (double *)vphi, (double *)vpsi, s);
+    if (rc) return rc;
+    if (k) *k = s[S_K];
+    return MOC_OK;
+  }
   if ((rc = read_scalars(c, s))) return rc;
   const double scale = c->eigen ? s[S_SCALE] : 1.0;
   if (k) *k = s[S_K];

@@ -111,6 +111,69 @@ __global__ void source_kernel(int R, int G, int Gp, int M, const int32_t *__rest
   }
 }
 
+// ----------------------------------------------------------------------------- state transfer
+// A caller's state read or written in place when its host arrays are addressable from the device
+// (pinned or registered memory, or pageable memory on a system whose GPU reads it coherently):
+// one kernel converts, pads and reorders instead of a host loop, a staging copy and a second
+// pass. Thread x < R*Gp: region flux; x >= R*Gp: one boundary-flux value of an internal track end.
+
+// phi [R][G] FP64 (NULL: 1) -> d_phi [R][Gp]; psi [T][2][P][G] FP64 in external track order
+// (NULL: 0) -> d_psi in internal order, ends that no link feeds set to zero; scalars reset with
+// k and the normalisation `scale`.
+template <typename Real>
+__global__ void state_in_kernel(int R, int G, int Gp, long long T, int P, const double *__restrict__ phi,
+                                const double *__restrict__ psi, const long long *__restrict__ perm,
+                                const uint8_t *__restrict__ fed, Real *__restrict__ d_phi, Real *__restrict__ d_psi,
+                                double *__restrict__ scal, double k, double scale) {
+  const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nphi = (long long)R * Gp, half = (long long)P * G;
+  if (x == 0) {
+    for (int i = 0; i < S_COUNT; ++i) scal[i] = 0.0;
+    scal[S_K] = k;
+    scal[S_KPREV] = k;
+    scal[S_SCALE] = scale;
+    scal[S_RESID] = INFINITY;
+    scal[S_FISS] = 1.0 / scale;
+  }
+  if (x < nphi) {
+    const long long r = x / Gp;
+    const int g = (int)(x - r * Gp);
+    d_phi[x] = (g < G) ? (Real)(phi ? phi[r * G + g] : 1.0) : (Real)0;
+    return;
+  }
+  const long long y = x - nphi;  // internal end e = y / half, value q
+  if (y >= T * 2 * half) return;
+  const long long e = y / half, q = y - e * half;
+  const long long t = perm[e >> 1];
+  d_psi[y] = (psi && fed[e]) ? (Real)psi[(t * 2 + (e & 1)) * half + q] : (Real)0;
+}
+
+// d_phi * scal[S_SCALE] -> phi [R][G] FP64; d_psi (internal order) * scale -> psi [T][2][P][G]
+// (external order); the scalars copied to `scal_out`.
+template <typename Real>
+__global__ void state_out_kernel(int R, int G, int Gp, long long T, int P, const Real *__restrict__ d_phi,
+                                 const Real *__restrict__ d_psi, const long long *__restrict__ inv,
+                                 const double *__restrict__ scal, int eigen, double *__restrict__ phi,
+                                 double *__restrict__ psi, double *__restrict__ scal_out) {
+  const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nphi = phi ? (long long)R * G : 0, half = (long long)P * G;
+  const double scale = eigen ? scal[S_SCALE] : 1.0;
+  if (x == 0)
+    for (int i = 0; i < S_COUNT; ++i) scal_out[i] = scal[i];
+  if (x < nphi) {
+    const long long r = x / G;
+    const int g = (int)(x - r * G);
+    phi[x] = (double)d_phi[r * Gp + g] * scale;
+    return;
+  }
+  if (!psi) return;
+  const long long y = x - nphi;  // external end (t, d), value q
+  if (y >= T * 2 * half) return;
+  const long long ext = y / half, q = y - ext * half;
+  const long long e = 2 * inv[ext >> 1] + (ext & 1);
+  psi[y] = (double)d_psi[e * half + q] * scale;
+}
+
 // ----------------------------------------------------------------------------- sweep
 // Tally modes: 0 plain atomic add, 1 compensated (TwoSum error of each FP32 atomic add is
 // accumulated in a second array).

@@ -332,13 +332,20 @@ class Moc:
             assert psi.size == T * 2 * self.n_polar * self.G
         self._check(self._lib.moc_set_state(self._h, _p(phi, _d), float(k), _p(psi, _d)))
 
-    def get_state(self, with_psi: bool = False):
-        phi = np.zeros((self.n_regions, self.G))
+    def get_state(self, with_psi: bool = False, out=None):
+        """(phi, k) or (phi, k, psi); `out` = (phi, psi or None) writes into caller arrays
+        (float64, C-contiguous; pinned ones are written in place by the device)."""
         k = ctypes.c_double()
-        psi = None
-        if with_psi:
-            T, _ = self.track_counts()
-            psi = np.zeros((T, 2, self.n_polar, self.G))
+        if out is not None:
+            phi, psi = out
+            assert phi.dtype == np.float64 and phi.flags.c_contiguous and phi.size == self.n_regions * self.G
+            with_psi = psi is not None
+        else:
+            phi = np.zeros((self.n_regions, self.G))
+            psi = None
+            if with_psi:
+                T, _ = self.track_counts()
+                psi = np.zeros((T, 2, self.n_polar, self.G))
         self._check(self._lib.moc_get_state(self._h, _p(phi, _d), ctypes.byref(k), _p(psi, _d)))
         return (phi, k.value, psi) if with_psi else (phi, k.value)
 
