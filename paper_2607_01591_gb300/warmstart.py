@@ -6,7 +6,7 @@ cross-section perturbation -- to the region's log scalar flux per group and an e
 trained on converged solutions the library itself produces for perturbed instances of one geometry
 (converged in FP32, then finished with FP64 outers). At solve time the prediction seeds phi, k and
 the boundary flux (moc_ws_apply) and the plain power iteration converges from there; the cold start
-stays the fallback and the converged plain solve judges the result.
+stays the fallback and the converged plain solve is the reference result.
 
 Everything numeric runs in the library's kernels; this module orchestrates (datasets live in
 PyTorch-owned device memory) and measures.
