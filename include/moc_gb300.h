@@ -12,7 +12,7 @@
  *   - half-edge mesh traversal, modular rays over the domain bounding box and ray-mesh
  *     intersection precomputed once (Sec. 3.1);
  *   - ray-centric GPU sweep over all rays and angles at once for isotropic scattering (Sec. 3.1);
- *   - power iteration, the "Perform MOC" step of Alg. 1 without the HFEM/CMFD steps.
+ *   - power iteration: the fine-mesh MOC solve of Alg. 1, with the CMFD step optional and no HFEM.
  *
  * Conventions for every entry point:
  *   - Return value: MOC_OK (0) or a negative moc_status. A message for the last failure is kept

@@ -5,7 +5,7 @@
  * perturbation) to the region's log scalar flux per group and an estimate of k.
  *
  * The paper has no counterpart: it is an added pattern on top of the paper's power iteration
- * (the "Perform MOC" step of Alg. 1), whose converged plain solve remains the reference for the
+ * (the fine-mesh MOC solve of Alg. 1), whose converged plain solve remains the reference for the
  * result; the cold start (flat flux, k = 1) stays the fallback.
  *
  * Network: n_layers = 4 linear layers, n_in -> width -> width -> width -> n_out, SiLU after the

@@ -19,8 +19,8 @@
  *    psi_out = psi_in e^{-tau} + (q/Sigma_t)(1 - e^{-tau}), tau = Sigma_t * l / sin(theta_p);
  *  - the scalar flux by angular integration over all discrete directions (Sec. 2.1, text after
  *    Eq. MOC_sol): phi = 4 pi q/Sigma_t + sum_k W_k (psi_in - psi_out)_k / (Sigma_t A_i);
- *  - k-eigenvalue power iteration (Alg. 1, "Perform MOC on the fine mesh", without the HFEM and
- *    CMFD steps), one transport sweep per outer, Jacobi in energy and in boundary flux.
+ *  - k-eigenvalue power iteration (the fine-mesh MOC solve of Alg. 1, without its HFEM step; the
+ *    CMFD step optional), one transport sweep per outer, Jacobi in energy and in boundary flux.
  *
  * Readings where the paper is silent (all also listed in the design notes):
  *  - A azimuths cover [0, 2 pi); for the first quadrant phi_a = 2 pi (a + 1/2)/A,
