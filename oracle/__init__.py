@@ -58,6 +58,10 @@ def _load():
         lib.orc_set_xs.restype = ctypes.c_int
         lib.orc_set_xs.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _d, _d, _d, _d]
         lib.orc_set_fixed_source.argtypes = [ctypes.c_void_p, _d]
+        lib.orc_set_scattering.restype = ctypes.c_int
+        lib.orc_set_scattering.argtypes = [ctypes.c_void_p, ctypes.c_int, _d]
+        lib.orc_legendre.restype = ctypes.c_double
+        lib.orc_legendre.argtypes = [ctypes.c_int, ctypes.c_double]
         lib.orc_set_cmfd.restype = ctypes.c_int
         lib.orc_set_cmfd.argtypes = [ctypes.c_void_p, _i32, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double]
         lib.orc_set_state.argtypes = [ctypes.c_void_p, _d, ctypes.c_double, _d]
@@ -190,6 +194,18 @@ class Oracle:
         self._lib.orc_set_cmfd(self._h, _p(c, _i32), int(n_cells), int(n_outer), int(n_inner), float(omega))
         self._cell = c
 
+    def set_scattering(self, sigma_sl=None):
+        """Anisotropic scattering: sigma_sl [L][M][G][G] holds Sigma_s,l (g' -> g) for l = 1..L;
+        None restores isotropic scattering. Call after set_xs."""
+        if sigma_sl is None:
+            self._lib.orc_set_scattering(self._h, 0, None)
+            return
+        a = _f64(sigma_sl)
+        rc = self._lib.orc_set_scattering(self._h, int(a.shape[0]), _p(a, _d))
+        if rc:
+            raise RuntimeError("oracle: " + self._lib.orc_error(self._h).decode())
+        self._ssl = a
+
     def set_state(self, phi=None, k: float = 1.0, psi=None):
         pp = None if phi is None else _f64(phi)
         ps = None if psi is None else _f64(psi)
@@ -233,6 +249,11 @@ class Oracle:
         rc = self._lib.orc_iterate(self._h, 1 if eigen else 0, float(tol_k), float(tol_f), int(max_outer),
                                    ctypes.byref(k), ctypes.byref(n), ctypes.byref(r))
         return k.value, n.value, r.value, rc == 0
+
+
+def legendre(l: int, x: float) -> float:
+    """The oracle's Legendre polynomial P_l(x)."""
+    return float(_load().orc_legendre(int(l), float(x)))
 
 
 def track_sweep(sig, qr, length, sin_theta: float, psi_in: float) -> np.ndarray:

@@ -87,6 +87,15 @@ typedef struct {
   double *leak;     /* [G] outgoing W*psi at vacuum ends during the last sweep */
   double k;
   int n_threads;
+  /* anisotropic scattering of order L (Legendre expansion of the scattering kernel, Sec. 2):
+   * per-direction sources from the region-average angular flux of the previous outer */
+  int L;              /* 0: isotropic */
+  int ND;             /* directions m = (j * 2 + sense) * P + p, j over [0, pi) */
+  double *ssl;        /* [L][M][G][G] Sigma_s,l g' -> g for l = 1..L */
+  double *kern;       /* [L][ND][ND] 4 pi omega' w' (P_l(Om . Om'+) + P_l(Om . Om'-)) / 2 */
+  double *qdir;       /* [R][ND][G] source per steradian per direction */
+  double *tdir;       /* [R][ND][G] per-direction tally: sum of delta sin(theta) (psi_in - psi_out) */
+  double *pbar;       /* [R][ND][G] region-average angular flux (state of the anisotropic source) */
   /* coarse-mesh finite difference acceleration (Alg. 1), partial-current form */
   int cmfd, n_cells, n_if, cm_outer, cm_inner, n_colors;
   double cm_omega;    /* over-relaxation factor of the coarse sweeps */
@@ -120,6 +129,7 @@ void orc_destroy(orc_t *h) {
   free(h->phi); free(h->q); free(h->tally); free(h->psi_in); free(h->psi_next); free(h->leak);
   free(h->cell); free(h->pairs); free(h->cur); free(h->cleak); free(h->color);
   free(h->nb_off); free(h->nb_cell); free(h->nb_in);
+  free(h->ssl); free(h->kern); free(h->qdir); free(h->tdir); free(h->pbar);
   free(h);
 }
 
@@ -524,6 +534,8 @@ int orc_set_xs(orc_t *h, int n_mat, int G, const double *st, const double *nsf, 
   free(h->st); free(h->nsf); free(h->chi); free(h->ss);
   free(h->phi); free(h->q); free(h->tally); free(h->psi_in); free(h->psi_next); free(h->leak);
   free(h->ext); h->ext = NULL;
+  free(h->ssl); free(h->kern); free(h->qdir); free(h->tdir); free(h->pbar);
+  h->ssl = h->kern = h->qdir = h->tdir = h->pbar = NULL; h->L = 0;
   free(h->cell); free(h->pairs); free(h->cur); free(h->cleak); free(h->color);
   free(h->nb_off); free(h->nb_cell); free(h->nb_in);
   h->cell = NULL; h->pairs = NULL; h->cur = NULL; h->cleak = NULL; h->color = NULL; h->cmfd = 0;
@@ -558,6 +570,7 @@ int orc_set_cmfd(orc_t *h, const int32_t *cell, int n_cells, int n_outer, int n_
   h->cell = NULL; h->pairs = NULL; h->cur = NULL; h->cleak = NULL; h->color = NULL; h->cmfd = 0;
   h->nb_off = h->nb_cell = h->nb_in = NULL;
   if (!cell) return 0;
+  if (h->L) { snprintf(h->err, sizeof h->err, "CMFD with anisotropic scattering is not supported"); return -1; }
   h->cell = xcalloc(h->n_tri, sizeof(int32_t));
   memcpy(h->cell, cell, h->n_tri * sizeof(int32_t));
   int64_t np = 0;
@@ -618,6 +631,70 @@ int orc_set_cmfd(orc_t *h, const int32_t *cell, int n_cells, int n_outer, int n_
   return 0;
 }
 
+/* Legendre polynomial P_l(x) by the three-term recurrence */
+double orc_legendre(int l, double x) {
+  double p0 = 1.0, p1 = x;
+  if (l == 0) return p0;
+  for (int n = 1; n < l; ++n) {
+    double p2 = ((2.0 * n + 1.0) * x * p1 - n * p0) / (n + 1.0);
+    p0 = p1; p1 = p2;
+  }
+  return p1;
+}
+
+/* the direction of index m: azimuth phi_j (+ pi for the reverse sense), polar sin/cos (upper
+ * hemisphere) */
+static void direction_of(const orc_t *h, int m, double *om) {
+  int P = h->n_polar, p = m % P, jd = m / P, j = jd / 2, d = jd % 2;
+  double ph = h->phi_a[j] + d * ORC_PI, st = h->sin_theta[p], ct = sqrt(1.0 - st * st);
+  om[0] = st * cos(ph); om[1] = st * sin(ph); om[2] = ct;
+}
+
+static void init_pbar(orc_t *h) {
+  for (int i = 0; i < h->n_tri; ++i)
+    for (int m = 0; m < h->ND; ++m)
+      for (int g = 0; g < h->G; ++g)
+        h->pbar[((size_t)i * h->ND + m) * h->G + g] = h->phi[(size_t)i * h->G + g] / (4.0 * ORC_PI);
+}
+
+/* Anisotropic scattering of order L (0 restores isotropic scattering): ssl [L][M][G][G] holds
+ * Sigma_s,l for l = 1..L. The scattering source of direction Om is
+ *   sum_l (2l+1)/(4 pi) sum_g' Sigma_s,l g'->g  int P_l(Om . Om') psi_g'(Om') dOm',
+ * the integral taken with the discrete quadrature (both hemispheres of each polar angle) over the
+ * region-average angular flux of the previous outer. Call after orc_set_xs. */
+int orc_set_scattering(orc_t *h, int L, const double *ssl) {
+  free(h->ssl); free(h->kern); free(h->qdir); free(h->tdir); free(h->pbar);
+  h->ssl = h->kern = h->qdir = h->tdir = h->pbar = NULL; h->L = 0;
+  if (L <= 0 || !ssl) return 0;
+  if (h->cmfd) { snprintf(h->err, sizeof h->err, "anisotropic scattering with CMFD is not supported"); return -1; }
+  int G = h->G, M = h->n_mat, P = h->n_polar;
+  h->L = L;
+  h->ND = 2 * h->n_dir * P;
+  int ND = h->ND;
+  h->ssl = xcalloc((size_t)L * M * G * G, sizeof(double));
+  memcpy(h->ssl, ssl, (size_t)L * M * G * G * sizeof(double));
+  h->kern = xcalloc((size_t)L * ND * ND, sizeof(double));
+  for (int m = 0; m < ND; ++m) {
+    double om[3];
+    direction_of(h, m, om);
+    for (int m2 = 0; m2 < ND; ++m2) {
+      double o2[3];
+      direction_of(h, m2, o2);
+      int j2 = (m2 / P) / 2, p2 = m2 % P;
+      double w = 4.0 * ORC_PI * h->omega_a[j2] * h->polar_w[p2];
+      double cp = om[0] * o2[0] + om[1] * o2[1] + om[2] * o2[2];
+      double cm = om[0] * o2[0] + om[1] * o2[1] - om[2] * o2[2];
+      for (int l = 1; l <= L; ++l)
+        h->kern[((size_t)(l - 1) * ND + m) * ND + m2] = w * 0.5 * (orc_legendre(l, cp) + orc_legendre(l, cm));
+    }
+  }
+  h->qdir = xcalloc((size_t)h->n_tri * ND * G, sizeof(double));
+  h->tdir = xcalloc((size_t)h->n_tri * ND * G, sizeof(double));
+  h->pbar = xcalloc((size_t)h->n_tri * ND * G, sizeof(double));
+  init_pbar(h);
+  return 0;
+}
+
 void orc_set_fixed_source(orc_t *h, const double *S) {
   free(h->ext); h->ext = NULL;
   if (S) {
@@ -649,6 +726,7 @@ void orc_set_state(orc_t *h, const double *phi, double k, const double *psi) {
   for (int64_t e = 0; e < 2 * h->n_tracks; ++e) if (!fed[e]) memset(h->psi_in + e * per, 0, per * sizeof(double));
   free(fed);
   h->k = k;
+  if (h->L) init_pbar(h);   /* the anisotropic state restarts from an isotropic angular flux */
 }
 
 void orc_get_state(const orc_t *h, double *phi, double *k, double *psi) {
@@ -678,6 +756,30 @@ static void update_source(orc_t *h, int eigen) {
       if (h->ext) src += h->ext[(size_t)i * G + g];
       h->q[(size_t)i * G + g] = src / (4.0 * ORC_PI);
     }
+    if (h->L) {
+      int ND = h->ND;
+      double *v = xcalloc(ND, sizeof(double));
+      for (int mdir = 0; mdir < ND; ++mdir)
+        for (int g = 0; g < G; ++g) h->qdir[((size_t)i * ND + mdir) * G + g] = h->q[(size_t)i * G + g];
+      for (int l = 1; l <= h->L; ++l) {
+        const double *K = h->kern + (size_t)(l - 1) * ND * ND;
+        for (int gp = 0; gp < G; ++gp) {
+          /* v_m = int P_l(Om_m . Om') psi_g'(Om') dOm' */
+          for (int mdir = 0; mdir < ND; ++mdir) {
+            double a = 0.0;
+            for (int m2 = 0; m2 < ND; ++m2) a += K[(size_t)mdir * ND + m2] * h->pbar[((size_t)i * ND + m2) * G + gp];
+            v[mdir] = a;
+          }
+          for (int g = 0; g < G; ++g) {
+            double sl = h->ssl[(((size_t)(l - 1) * h->n_mat + m) * G + gp) * G + g];
+            if (sl == 0.0) continue;
+            double c = (2.0 * l + 1.0) / (4.0 * ORC_PI) * sl;
+            for (int mdir = 0; mdir < ND; ++mdir) h->qdir[((size_t)i * ND + mdir) * G + g] += c * v[mdir];
+          }
+        }
+      }
+      free(v);
+    }
   }
 }
 
@@ -693,6 +795,7 @@ static void transport_sweep(orc_t *h) {
     memset(h->cur, 0, 2 * (size_t)h->n_if * G * sizeof(double));
     memset(h->cleak, 0, (size_t)h->n_cells * G * sizeof(double));
   }
+  if (h->L) memset(h->tdir, 0, (size_t)h->n_tri * h->ND * G * sizeof(double));
   double *leak_g = xcalloc(G, sizeof(double));
 #pragma omp parallel for schedule(static) num_threads(h->n_threads)
   for (int g = 0; g < G; ++g) {
@@ -709,14 +812,16 @@ static void transport_sweep(orc_t *h) {
             int64_t s_first = d ? (s1 - 1) : s0;
             h->cleak[(size_t)h->cell[h->seg_reg[s_first]] * G + g] -= Wt * psi;
           }
+          int mdir = (j * 2 + d) * P + p;
           for (int64_t n = 0; n < s1 - s0; ++n) {
             int64_t s = d ? (s1 - 1 - n) : (s0 + n);
             int i = h->seg_reg[s];
             double sig = h->st[(size_t)h->mat[i] * G + g];
-            double qi = h->q[(size_t)i * G + g];
+            double qi = h->L ? h->qdir[((size_t)i * h->ND + mdir) * G + g] : h->q[(size_t)i * G + g];
             double tau = sig * h->seg_len[s] / h->sin_theta[p];
             double delta = (psi - qi / sig) * (-expm1(-tau));
             h->tally[(size_t)i * G + g] += Wt * delta;
+            if (h->L) h->tdir[((size_t)i * h->ND + mdir) * G + g] += h->delta_a[j] * h->sin_theta[p] * delta;
             psi -= delta;
             if (h->cmfd && n + 1 < s1 - s0) {
               /* partial current W psi into the next cell along the track, if the cell changes */
@@ -743,13 +848,28 @@ static void transport_sweep(orc_t *h) {
 }
 
 /* scalar flux from source and tallies */
-static void finalize_flux(const orc_t *h, double *phi_new) {
-  int G = h->G;
+static void finalize_flux(const orc_t *h, double *phi_new, double *pbar_new) {
+  int G = h->G, P = h->n_polar, ND = h->ND;
   for (int i = 0; i < h->n_tri; ++i) {
     for (int g = 0; g < G; ++g) {
       double sig = h->st[(size_t)h->mat[i] * G + g];
       size_t ig = (size_t)i * G + g;
-      double v = 4.0 * ORC_PI * h->q[ig] / sig;
+      double v;
+      if (h->L) {
+        /* angular integration of the flat-source part over the discrete directions, and the
+         * region-average angular flux of every direction for the next source */
+        v = 0.0;
+        for (int m = 0; m < ND; ++m) {
+          int j = (m / P) / 2, p = m % P;
+          double qm = h->qdir[((size_t)i * ND + m) * G + g];
+          v += 4.0 * ORC_PI * h->omega_a[j] * h->polar_w[p] * qm / sig;
+          double pb = qm / sig;
+          if (h->area[i] > 0.0) pb += h->tdir[((size_t)i * ND + m) * G + g] / (sig * h->area[i]);
+          pbar_new[((size_t)i * ND + m) * G + g] = pb;
+        }
+      } else {
+        v = 4.0 * ORC_PI * h->q[ig] / sig;
+      }
       if (h->area[i] > 0.0) v += h->tally[ig] / (sig * h->area[i]);
       phi_new[ig] = v;
     }
@@ -882,15 +1002,18 @@ double orc_outer(orc_t *h, int eigen) {
   int G = h->G;
   size_t RG = (size_t)h->n_tri * G, PB = (size_t)h->n_tracks * 2 * h->n_polar * G;
   double *phi_new = xcalloc(RG, sizeof(double));
+  size_t RD = h->L ? (size_t)h->n_tri * h->ND * G : 0;
+  double *pbar_new = h->L ? xcalloc(RD, sizeof(double)) : NULL;
   update_source(h, eigen);
   transport_sweep(h);
-  finalize_flux(h, phi_new);
+  finalize_flux(h, phi_new, pbar_new);
   double resid = 0.0;
   if (eigen) {
     double F_old = fission_total(h, h->phi);
     double F_new = fission_total(h, phi_new);
     h->k = h->k * F_new / F_old;
     for (size_t i = 0; i < RG; ++i) phi_new[i] /= F_new;
+    for (size_t i = 0; i < RD; ++i) pbar_new[i] /= F_new;
     for (size_t i = 0; i < PB; ++i) h->psi_next[i] /= F_new;
     for (int g = 0; g < G; ++g) h->leak[g] /= F_new;
     for (int i = 0; i < h->n_tri; ++i) {
@@ -913,6 +1036,7 @@ double orc_outer(orc_t *h, int eigen) {
       if (phi_new[i] > 0.0) { double r = fabs(phi_new[i] - h->phi[i]) / phi_new[i]; if (r > resid) resid = r; }
   }
   memcpy(h->phi, phi_new, RG * sizeof(double));
+  if (h->L) { memcpy(h->pbar, pbar_new, RD * sizeof(double)); free(pbar_new); }
   double *tmp = h->psi_in; h->psi_in = h->psi_next; h->psi_next = tmp;
   free(phi_new);
   return resid;
@@ -925,6 +1049,8 @@ void orc_normalise(orc_t *h) {
   if (F > 0.0) {
     for (size_t i = 0; i < RG; ++i) h->phi[i] /= F;
     for (size_t i = 0; i < PB; ++i) h->psi_in[i] /= F;
+    if (h->L)
+      for (size_t i = 0; i < (size_t)h->n_tri * h->ND * h->G; ++i) h->pbar[i] /= F;
   }
 }
 

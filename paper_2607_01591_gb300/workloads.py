@@ -464,6 +464,15 @@ def synthetic_xs(kinds: Sequence[str], G: int, seed: int, sigt_range=(0.2, 2.0),
     return CrossSections(st, nsf, chi, ss)
 
 
+def anisotropic_moments(xs: CrossSections, L: int, mean_cosine) -> np.ndarray:
+    """Synthetic higher Legendre moments of the scattering matrices: Sigma_s,l = g^l Sigma_s,0
+    with g the mean scattering cosine of each material (`mean_cosine`: one value per material,
+    0 <= g < 1, forward-peaked for g > 0). Returns [L][M][G][G] for l = 1..L."""
+    g = np.asarray(mean_cosine, dtype=np.float64)
+    assert g.shape == (xs.n_mat,) and (g >= 0).all() and (g < 1).all()
+    return np.stack([(g ** l)[:, None, None] * xs.sigma_s for l in range(1, L + 1)])
+
+
 def perturbed_xs(base: CrossSections, seed: int, sigma: float = 0.1) -> CrossSections:
     """Per-material, per-group lognormal scaling (sigma) of absorption, each scattering row and
     nu*Sigma_f; Sigma_t is rebuilt as absorption + scattering so the data stay valid."""

@@ -549,3 +549,85 @@ def test_cmfd_settles_on_the_transport_solution_with_reflective_walls():
     phi1, k1 = o.get_state()
     assert r1 < 1e-8, r1
     assert abs(k1 - k) < 1e-10
+
+
+# ------------------------------------------------------------------------------ anisotropic scattering
+
+def test_legendre_polynomials():
+    from scipy.special import eval_legendre
+    rng = np.random.default_rng(3)
+    for l in range(0, 7):
+        for x in rng.uniform(-1, 1, 5):
+            assert abs(oracle.legendre(l, x) - eval_legendre(l, x)) < 1e-14
+
+
+def _bare_square_1g(size=4.0, n=8, st=1.0, c=0.9):
+    mesh = W.grid_mesh(n, n, size, size, bc=(0, 0, 0, 0))
+    xs = W.CrossSections(np.array([[st]]), np.array([[0.25]]), np.array([[1.0]]), np.array([[[c * st]]]))
+    return mesh, xs
+
+
+def _k_of(mesh, xs, ssl=None, tol=1e-10):
+    o = oracle.Oracle(mesh, 16, 0.05, W.TY3_SIN_THETA, W.TY3_WEIGHT)
+    o.set_xs(xs)
+    if ssl is not None:
+        o.set_scattering(ssl)
+    k, n, r, conv = o.iterate(True, tol, 10 * tol, 5000)
+    assert conv
+    return k, o
+
+
+def test_p1_scattering_agrees_with_the_transport_correction():
+    """Forward-peaked P1 scattering (mean cosine g) in a bare homogeneous square lowers k (more
+    leakage) and lands close to the transport-corrected isotropic problem (Sigma_t - g Sigma_s,
+    Sigma_s - g Sigma_s): a wrong sign or a missing (2l+1) fails one of the two."""
+    mesh, xs = _bare_square_1g()
+    g = 0.4
+    k0, _ = _k_of(mesh, xs)
+    k1, _ = _k_of(mesh, xs, W.anisotropic_moments(xs, 1, [g]))
+    s = xs.sigma_s[0, 0, 0]
+    xtc = W.CrossSections(xs.sigma_t - g * s, xs.nu_sigma_f, xs.chi, xs.sigma_s - g * s)
+    ktc, _ = _k_of(mesh, xtc)
+    assert k1 < ktc < k0, (k0, k1, ktc)
+    assert abs(k1 - ktc) < 0.2 * abs(k0 - k1), (k0, k1, ktc)
+
+
+def test_p1_infinite_medium_keeps_kinf_and_zero_moments_change_nothing():
+    """All reflective, one material: the flat isotropic flux stays an exact fixed point with P1
+    scattering, so k = k_inf; and Sigma_s,1 = 0 reproduces the isotropic iteration."""
+    mesh = W.one_material(W.pin_cell_mesh())
+    xs = _xs_one(7, 12)
+    kinf, spec = _closed_form_kinf(xs)
+    k, o = _k_of(mesh, xs, W.anisotropic_moments(xs, 1, [0.3]), tol=1e-12)
+    assert abs(k - kinf) < 1e-9
+    phi, _ = o.get_state()
+    np.testing.assert_allclose(phi / phi[0], np.ones_like(phi), atol=1e-9)
+    prob = W.small_lattice_problem(3, bc=(1, 0, 1, 0), n_azim=16, ray_spacing=0.05)
+    a = oracle.Oracle.from_problem(prob)
+    b = oracle.Oracle.from_problem(prob)
+    b.set_scattering(np.zeros((1,) + prob.xs.sigma_s.shape))
+    for _ in range(4):
+        a.outer(True)
+        b.outer(True)
+    assert abs(a.get_state()[1] - b.get_state()[1]) < 1e-13
+    np.testing.assert_allclose(b.get_state()[0], a.get_state()[0], rtol=1e-12)
+
+
+def test_p1_global_balance_with_vacuum():
+    """Odd Legendre terms integrate to zero over the (symmetric) quadrature, so absorption
+    (Sigma_t - Sigma_s,0 out-scatter) + leakage = production / k still holds."""
+    prob = W.pin_cell_problem()
+    mesh = W.with_bc(prob.mesh, (0, 0, 0, 0))
+    xs = W.CrossSections(prob.xs.sigma_t, prob.xs.nu_sigma_f * 4.0, prob.xs.chi, prob.xs.sigma_s)
+    o = oracle.Oracle(mesh, 16, 0.05, W.TY3_SIN_THETA, W.TY3_WEIGHT)
+    o.set_xs(xs)
+    o.set_scattering(W.anisotropic_moments(xs, 1, [0.05, 0.3]))
+    k, n, r, conv = o.iterate(True, 1e-13, 1e-12, 50000)
+    assert conv
+    phi, _ = o.get_state()
+    A = o.areas()
+    sa = xs.sigma_t - xs.sigma_s.sum(2)
+    absorption = float((A[:, None] * sa[mesh.mat] * phi).sum())
+    production = float((A[:, None] * xs.nu_sigma_f[mesh.mat] * phi).sum())
+    leak = float(o.leakage().sum())
+    assert abs((absorption + leak) * k - production) < 1e-9
