@@ -162,6 +162,20 @@ int moc_set_xs(moc_ctx *ctx, int n_mat, int G, const double *sigma_t, const doub
  * MOC_ERR_STATE. */
 int moc_set_cmfd(moc_ctx *ctx, const int32_t *cell, int n_cells, int n_outer, int n_inner, double omega);
 
+/* Anisotropic scattering of Legendre order L (Sec. 2: the scattering kernel expanded as
+ * sum_l (2l+1)/(4 pi) P_l(Om . Om') Sigma_s,l). sigma_sl: [L][n_mat][G][G] holds Sigma_s,l g -> g'
+ * (from-group major, like sigma_s) for l = 1..L, 1 <= L <= 3; L = 0 or NULL restores isotropic
+ * scattering (Sigma_s,0 is moc_set_xs's sigma_s). The library carries the angular moments of the
+ * flux against the real harmonics with l + m even (the ones a plane problem keeps, L(L+3)/2 of
+ * them): each source update builds per region and group the moments (2l+1) Sigma_s,l phi_lm;
+ * the sweep uses the source of every discrete direction and tallies every moment; after the sweep
+ * the moments are the discrete angular integrals of the region-average angular flux (the discrete
+ * quadrature's Gram matrix, not an assumed orthogonality). set_state restarts the moments from an
+ * isotropic angular flux. Up to 3 polar angles; not combined with CMFD (MOC_ERR_STATE); FP32 moment
+ * tallies are plain atomic sums. Call after moc_set_xs (which switches it off). Errors:
+ * MOC_ERR_ARG, MOC_ERR_STATE. */
+int moc_set_scattering(moc_ctx *ctx, int L, const double *sigma_sl);
+
 /* Fixed isotropic volumetric source S: [n_tri][G] (n/cm^3/s), switching the context to
  * fixed-source mode (fission ignored, no normalisation); NULL returns to eigenvalue mode. */
 int moc_set_fixed_source(moc_ctx *ctx, const double *S);

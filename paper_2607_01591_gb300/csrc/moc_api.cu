@@ -13,6 +13,7 @@
 
 #include "moc_gb300.h"
 #include "moc_geom.h"
+#include "moc_aniso.cuh"
 #include "moc_cmfd.cuh"
 #include "moc_track.h"
 #include "moc_kernels.cuh"
@@ -53,6 +54,9 @@ struct moc_ctx {
   bool eigen = true;
   bool tracks_on_device = false, xs_set = false;
   std::vector<double> h_nsf;  // host copy of nu*Sigma_f [M][G] (normalising a caller's state)
+  // anisotropic scattering (off unless moc_set_scattering was called)
+  int aniso_L = 0, aniso_NK = 0;
+  void *d_ssl = nullptr, *d_harm = nullptr, *d_gm = nullptr, *d_mom = nullptr, *d_srck = nullptr, *d_tmom = nullptr;
   // CMFD acceleration (off unless moc_set_cmfd was called)
   bool cmfd = false;
   int n_cells = 0, n_if = 0, cm_outer = 0, cm_inner = 0, cm_colors = 0;
@@ -146,8 +150,20 @@ void free_cmfd(moc_ctx *c) {
   c->cmfd = false;
 }
 
+void free_aniso(moc_ctx *c) {
+  drop_graphs(c);
+  dfree(c->d_ssl);
+  dfree(c->d_harm);
+  dfree(c->d_gm);
+  dfree(c->d_mom);
+  dfree(c->d_srck);
+  dfree(c->d_tmom);
+  c->aniso_L = c->aniso_NK = 0;
+}
+
 void free_problem(moc_ctx *c) {
   free_cmfd(c);
+  free_aniso(c);
   drop_graphs(c);
   dfree(c->d_xsq);
   dfree(c->d_phi);
@@ -498,7 +514,40 @@ template <int TM> int launch_chunk(moc_ctx *c, cudaStream_t st) {
   return MOC_OK;
 }
 
+template <typename Real, int P, int TM, int NK> void aniso_sweep_launch(moc_ctx *c, cudaStream_t st) {
+  const long long n = (long long)c->T * 2 * c->G;
+  sweep_aniso_kernel<Real, P, TM, NK><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(
+      c->d_trk, (const SegRec<Real> *)c->d_seg, c->d_link, (const Real *)c->d_wgt, (const Real *)c->d_inv_sin,
+      (const Real *)c->d_harm, (const typename Pair<Real>::T *)c->d_xsq, (const Real *)c->d_srck, (Real *)c->d_tsum,
+      (Real *)c->d_tcomp, (Real *)c->d_tmom, (const Real *)c->d_psi[c->cur], (Real *)c->d_psi[c->cur ^ 1], c->d_scal,
+      n, c->G, c->Gp);
+}
+
+template <typename Real, int TM, int NK> int launch_aniso_p(moc_ctx *c, cudaStream_t st) {
+  switch (c->P) {
+    case 1: aniso_sweep_launch<Real, 1, TM, NK>(c, st); break;
+    case 2: aniso_sweep_launch<Real, 2, TM, NK>(c, st); break;
+    case 3: aniso_sweep_launch<Real, 3, TM, NK>(c, st); break;
+    default: return fail(c, MOC_ERR_ARG, "anisotropic scattering supports up to 3 polar angles");
+  }
+  CUDA_TRY(c, cudaGetLastError());
+  return MOC_OK;
+}
+
+template <typename Real, int TM> int launch_aniso(moc_ctx *c, cudaStream_t st) {
+  switch (c->aniso_NK) {
+    case 2: return launch_aniso_p<Real, TM, 2>(c, st);
+    case 5: return launch_aniso_p<Real, TM, 5>(c, st);
+    default: return launch_aniso_p<Real, TM, 9>(c, st);
+  }
+}
+
 int launch_sweep(moc_ctx *c, cudaStream_t st) {
+  if (c->aniso_L) {
+    if (c->precision == MOC_FP64) return launch_aniso<double, 0>(c, st);
+    if (c->precision == MOC_FP32) return launch_aniso<float, 1>(c, st);
+    return launch_aniso<float, 0>(c, st);
+  }
   if (c->cmfd) {
     if (c->precision == MOC_FP64) return launch_sweep_p<double, 0, true>(c, st);
     if (c->precision == MOC_FP32) return launch_sweep_p<float, 1, true>(c, st);
@@ -549,8 +598,37 @@ template <typename Real> int launch_finalize_reduce(moc_ctx *c, cudaStream_t st)
   return MOC_OK;
 }
 
+template <typename Real> int launch_aniso_source(moc_ctx *c, cudaStream_t st) {
+  const int R = c->geo.n_tri;
+  const size_t sm = (size_t)c->aniso_L * c->M * c->G * c->G * sizeof(Real);
+  aniso_source_kernel<Real><<<(R + 127) / 128, 128, sm, st>>>(
+      R, c->G, c->Gp, c->M, c->aniso_NK, c->d_mat, (const Real *)c->d_ssl, (const typename Pair<Real>::T *)c->d_xsq,
+      (Real *)c->d_mom, (Real *)c->d_srck, c->d_scal, c->eigen ? 1 : 0);
+  CUDA_TRY(c, cudaGetLastError());
+  return MOC_OK;
+}
+
+template <typename Real> int launch_aniso_moments(moc_ctx *c, cudaStream_t st) {
+  const long long n = (long long)c->geo.n_tri * c->G;
+  aniso_moments_kernel<Real><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+      c->geo.n_tri, c->G, c->Gp, c->aniso_NK, (const Real *)c->d_gm, (const Real *)c->d_inv_ta,
+      (typename Pair<Real>::T *)c->d_xsq, (const Real *)c->d_srck, (Real *)c->d_tmom, (Real *)c->d_mom);
+  CUDA_TRY(c, cudaGetLastError());
+  return MOC_OK;
+}
+
+template <typename Real> int launch_aniso_init(moc_ctx *c, cudaStream_t st) {
+  const long long n = (long long)c->geo.n_tri * c->aniso_NK * c->Gp;
+  aniso_init_kernel<Real><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+      c->geo.n_tri, c->G, c->Gp, c->aniso_NK, (const Real *)c->d_gm, (const Real *)c->d_phi, (Real *)c->d_mom);
+  CUDA_TRY(c, cudaGetLastError());
+  return MOC_OK;
+}
+
 int enqueue_source(moc_ctx *c, cudaStream_t st) {
-  return c->precision == MOC_FP64 ? launch_source<double>(c, st) : launch_source<float>(c, st);
+  int rc = c->precision == MOC_FP64 ? launch_source<double>(c, st) : launch_source<float>(c, st);
+  if (rc || !c->aniso_L) return rc;
+  return c->precision == MOC_FP64 ? launch_aniso_source<double>(c, st) : launch_aniso_source<float>(c, st);
 }
 
 // CMFD after finalize: homogenise, coarse solve, prolong phi and the incoming boundary flux
@@ -601,6 +679,10 @@ int enqueue_sweep(moc_ctx *c, cudaStream_t st, bool timed) {
   if (timed) {
     CUDA_TRY(c, cudaEventRecord(e1, st));
     c->ev.push_back({e0, e1});
+  }
+  if (c->aniso_L) {
+    rc = c->precision == MOC_FP64 ? launch_aniso_moments<double>(c, st) : launch_aniso_moments<float>(c, st);
+    if (rc) return rc;
   }
   rc = c->precision == MOC_FP64 ? launch_finalize_reduce<double>(c, st) : launch_finalize_reduce<float>(c, st);
   if (rc) return rc;
@@ -919,12 +1001,96 @@ int moc_set_xs(moc_ctx *c, int n_mat, int G, const double *st, const double *nsf
   return moc_set_state(c, nullptr, 1.0, nullptr);
 }
 
+int moc_set_scattering(moc_ctx *c, int L, const double *sigma_sl) {
+  int rc = need_ready(c);
+  if (rc) return rc;
+  cudaSetDevice(c->device);
+  free_aniso(c);
+  if (L == 0 || !sigma_sl) return MOC_OK;
+  if (L < 0 || L > kMaxAnisoL) return fail(c, MOC_ERR_ARG, "set_scattering: 0 <= L <= 3");
+  if (c->cmfd) return fail(c, MOC_ERR_STATE, "set_scattering: not combined with CMFD acceleration");
+  if (c->P > 3) return fail(c, MOC_ERR_ARG, "set_scattering: up to 3 polar angles");
+  const int M = c->M, G = c->G, P = c->P, nd = c->geo.n_dir, NK = L * (L + 3) / 2;
+  if ((size_t)L * M * G * G * rsize(c) > 48 * 1024) return fail(c, MOC_ERR_ARG, "set_scattering: tables too large");
+  for (size_t i = 0; i < (size_t)L * M * G * G; ++i)
+    if (!std::isfinite(sigma_sl[i])) return fail(c, MOC_ERR_ARG, "set_scattering: sigma_sl must be finite");
+  // real harmonics with l + m even, l = 1..L (Schmidt semi-normalised, no Condon-Shortley phase),
+  // for every stored direction j in [0, pi) and polar angle p
+  auto harm = [](int l, int m, double ph, double st) {
+    const double ct2 = 1.0 - st * st;
+    switch (l) {
+      case 1: return m < 0 ? st * std::sin(ph) : st * std::cos(ph);
+      case 2:
+        if (m == 0) return 0.5 * (3.0 * ct2 - 1.0);
+        return 0.5 * std::sqrt(3.0) * st * st * (m < 0 ? std::sin(2 * ph) : std::cos(2 * ph));
+      default:
+        if (m == -1 || m == 1) return 0.25 * std::sqrt(6.0) * (5.0 * ct2 - 1.0) * st * (m < 0 ? std::sin(ph) : std::cos(ph));
+        return 0.25 * std::sqrt(10.0) * st * st * st * (m < 0 ? std::sin(3 * ph) : std::cos(3 * ph));
+    }
+  };
+  std::vector<int> kl, km;
+  for (int l = 1; l <= L; ++l)
+    for (int m = -l; m <= l; m += 2) {
+      kl.push_back(l);
+      km.push_back(m);
+    }
+  std::vector<double> H((size_t)nd * P * NK);
+  for (int j = 0; j < nd; ++j)
+    for (int p = 0; p < P; ++p)
+      for (int k = 0; k < NK; ++k) H[((size_t)j * P + p) * NK + k] = harm(kl[k], km[k], c->geo.phi[j], c->geo.sin_theta[p]);
+  // Gram matrix over the discrete directions (both senses; R_0 = 1): 4 pi sum omega w R_k R_k'
+  const int n = NK + 1;
+  std::vector<double> Gm((size_t)n * n, 0.0);
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) {
+      const int la = a ? kl[a - 1] : 0, lb = b ? kl[b - 1] : 0;
+      if ((la + lb) & 1) continue;  // the two senses cancel exactly
+      double sum = 0.0;
+      for (int j = 0; j < nd; ++j)
+        for (int p = 0; p < P; ++p) {
+          const double ra = a ? H[((size_t)j * P + p) * NK + a - 1] : 1.0;
+          const double rb = b ? H[((size_t)j * P + p) * NK + b - 1] : 1.0;
+          sum += 2.0 * c->geo.omega[j] * c->geo.polar_w[p] * ra * rb;
+        }
+      Gm[(size_t)a * n + b] = kFourPi * sum;
+    }
+  const size_t rs = rsize(c);
+  auto put = [&](void *&dst, const std::vector<double> &v) -> int {
+    CUDA_TRY(c, cudaMalloc(&dst, std::max<size_t>(v.size(), 1) * rs));
+    if (c->precision == MOC_FP64) {
+      CUDA_TRY(c, cudaMemcpy(dst, v.data(), v.size() * rs, cudaMemcpyHostToDevice));
+    } else {
+      std::vector<float> f(v.begin(), v.end());
+      CUDA_TRY(c, cudaMemcpy(dst, f.data(), f.size() * rs, cudaMemcpyHostToDevice));
+    }
+    return MOC_OK;
+  };
+  std::vector<double> ssl(sigma_sl, sigma_sl + (size_t)L * M * G * G);
+  if ((rc = put(c->d_ssl, ssl))) return rc;
+  if ((rc = put(c->d_harm, H))) return rc;
+  if ((rc = put(c->d_gm, Gm))) return rc;
+  const size_t nm = (size_t)c->geo.n_tri * NK * c->Gp * rs;
+  for (void **pp : {&c->d_mom, &c->d_srck, &c->d_tmom}) {
+    CUDA_TRY(c, cudaMalloc(pp, nm));
+    CUDA_TRY(c, cudaMemsetAsync(*pp, 0, nm, c->stream));
+  }
+  c->aniso_L = L;
+  c->aniso_NK = NK;
+  drop_graphs(c);
+  // moments of the current state's isotropic angular flux
+  rc = c->precision == MOC_FP64 ? launch_aniso_init<double>(c, c->stream) : launch_aniso_init<float>(c, c->stream);
+  if (rc) return rc;
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return MOC_OK;
+}
+
 int moc_set_cmfd(moc_ctx *c, const int32_t *cell_in, int n_cells, int n_outer, int n_inner, double omega) {
   int rc = need_ready(c);
   if (rc) return rc;
   cudaSetDevice(c->device);
   free_cmfd(c);
   if (!cell_in) return MOC_OK;
+  if (c->aniso_L) return fail(c, MOC_ERR_STATE, "set_cmfd: not combined with anisotropic scattering");
   const Geometry &g = c->geo;
   const int R = g.n_tri, G = c->G;
   if (n_cells < 1 || n_outer < 1 || n_inner < 1) return fail(c, MOC_ERR_ARG, "set_cmfd: bad sizes or iteration counts");
@@ -1134,12 +1300,19 @@ int moc_set_state(moc_ctx *c, const double *phi, double k, const double *psi) {
   }
   // arrays the device can address are read in place by one kernel; others are staged
   const void *vphi = host_view(c, phi), *vpsi = host_view(c, psi);
-  if ((!phi || vphi) && (!psi || vpsi))
-    return c->precision == MOC_FP64 ? state_in<double>(c, (const double *)vphi, (const double *)vpsi, k, scale)
-                                    : state_in<float>(c, (const double *)vphi, (const double *)vpsi, k, scale);
-  rc = c->precision == MOC_FP64 ? upload_state<double>(c, phi, psi) : upload_state<float>(c, phi, psi);
+  if ((!phi || vphi) && (!psi || vpsi)) {
+    rc = c->precision == MOC_FP64 ? state_in<double>(c, (const double *)vphi, (const double *)vpsi, k, scale)
+                                  : state_in<float>(c, (const double *)vphi, (const double *)vpsi, k, scale);
+  } else {
+    rc = c->precision == MOC_FP64 ? upload_state<double>(c, phi, psi) : upload_state<float>(c, phi, psi);
+    if (!rc) rc = reset_scalars(c, k, scale);
+  }
+  if (rc || !c->aniso_L) return rc;
+  // anisotropic moments restart from an isotropic angular flux
+  rc = c->precision == MOC_FP64 ? launch_aniso_init<double>(c, c->stream) : launch_aniso_init<float>(c, c->stream);
   if (rc) return rc;
-  return reset_scalars(c, k, scale);
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return MOC_OK;
 }
 
 int moc_get_state(moc_ctx *c, double *phi, double *k, double *psi) {
@@ -1265,7 +1438,7 @@ int moc_get_work(const moc_ctx *c, int64_t *n_segments, int64_t *updates, int *k
   if (!c || !c->geo.has_tracks) return c ? MOC_ERR_STATE : MOC_ERR_ARG;
   if (n_segments) *n_segments = c->geo.n_segments();
   if (updates) *updates = 2 * c->geo.n_segments() * (int64_t)c->geo.n_polar * (int64_t)std::max(c->G, 0);
-  if (kernels) *kernels = ((c->Gp == 8) ? 3 : 4) + (c->cmfd ? 5 : 0);
+  if (kernels) *kernels = ((c->Gp == 8) ? 3 : 4) + (c->cmfd ? 5 : 0) + (c->aniso_L ? 2 : 0);
   return MOC_OK;
 }
 

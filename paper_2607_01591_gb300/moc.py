@@ -64,6 +64,7 @@ def load_library(path: Optional[str] = None):
             "moc_set_mesh": (ctypes.c_int, [_vp, ctypes.c_int, _d, ctypes.c_int, _i32, _i32, _d, _i32]),
             "moc_set_quadrature": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _d, _d]),
             "moc_generate_tracks": (ctypes.c_int, [_vp]),
+            "moc_set_scattering": (ctypes.c_int, [_vp, ctypes.c_int, _d]),
             "moc_set_ray_layout": (ctypes.c_int, [_vp, ctypes.c_int]),
             "moc_generate_tracks_device": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
             "moc_get_track_counts": (ctypes.c_int, [_vp, _i64, _i64]),
@@ -311,6 +312,14 @@ class Moc:
         if S is not None:
             assert S.shape == (self.n_regions, self.G)
         self._check(self._lib.moc_set_fixed_source(self._h, _p(S, _d)))
+
+    def set_scattering(self, sigma_sl=None):
+        """Anisotropic scattering: sigma_sl [L][M][G][G] = Sigma_s,l for l = 1..L (None: isotropic)."""
+        if sigma_sl is None:
+            self._check(self._lib.moc_set_scattering(self._h, 0, None))
+            return
+        a = _f64(sigma_sl)
+        self._check(self._lib.moc_set_scattering(self._h, int(a.shape[0]), _p(a, _d)))
 
     def set_cmfd(self, cell=None, n_cells: int = 0, n_outer: int = 6, n_inner: int = 6, omega: float = 1.0):
         """CMFD acceleration on the coarse cells `cell` [n_tri] (None switches it off): per outer,
