@@ -225,6 +225,8 @@ def main():
     ap.add_argument("--workload", default="assembly", choices=sorted(WORKLOADS))
     ap.add_argument("--no-time-to-k", action="store_true")
     ap.add_argument("--no-tracking", action="store_true", help="skip the host vs device tracking timing")
+    ap.add_argument("--aniso", type=int, default=0, metavar="L",
+                    help="time outers with P_L anisotropic scattering (synthetic moments g^l Sigma_s)")
     ap.add_argument("--cmfd", default=None, metavar="SIZE,NOUT,NIN,OMEGA",
                     help="time CMFD-accelerated outers (square coarse cells of SIZE cm); also the "
                          "parameters of the accelerated time-to-k runs")
@@ -262,6 +264,11 @@ def main():
     if args.cmfd:
         cm_cell, cm_n = W.grid_cells(prob.mesh, cmfd[0])
         m.set_cmfd(cm_cell, cm_n, cmfd[1], cmfd[2], cmfd[3])
+    aniso_g = None
+    if args.aniso:
+        # mean scattering cosines by material kind: light moderator strongly forward, heavy fuel weakly
+        aniso_g = [0.4 if i == prob.xs.n_mat - 1 else 0.05 for i in range(prob.xs.n_mat)]
+        m.set_scattering(W.anisotropic_moments(prob.xs, args.aniso, aniso_g))
     n_seg, ups, kpo = m.work()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{local}")
 
@@ -383,10 +390,12 @@ def main():
                    "updates_per_step": ups, "l2": "flushed between steps (512 MiB write, untimed)",
                    "parallelism": f"replicas x{world}",
                    "cmfd": (f"each step one CMFD-accelerated outer: {cmfd[0]} cm cells, {cmfd[1]} coarse power "
-                            f"iterations x {cmfd[2]} sweeps per group, omega {cmfd[3]}") if args.cmfd else None},
+                            f"iterations x {cmfd[2]} sweeps per group, omega {cmfd[3]}") if args.cmfd else None,
+                   "scattering": (f"P{args.aniso} anisotropic, Sigma_s,l = g^l Sigma_s,0, g per material {aniso_g}"
+                                  if args.aniso else "isotropic")},
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": alu_peak / 1e9, "unit": "Gop/s",
                      "frac": achieved / alu_peak,
-                     "traffic": SWEEP_DRAM_BYTES.get(args.workload) if args.precision == "fp32" and not args.cmfd else None,
+                     "traffic": SWEEP_DRAM_BYTES.get(args.workload) if args.precision == "fp32" and not args.cmfd and not args.aniso else None,
                      "kernel": "sweep_kernel", "avg_launch_ms": sweep_avg_s * 1e3,
                      "ops_per_update": ops_per_update,
                      "peak_note": "152 SMs x 128 FP32 lanes x max SM clock (derived; FMA counted as 1 op)",
