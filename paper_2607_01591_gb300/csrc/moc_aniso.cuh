@@ -18,6 +18,34 @@ constexpr int kMaxAnisoL = 3;
 // Legendre order of harmonic k (k = 0 .. NK-1 for l = 1..L, l + 1 harmonics each)
 __host__ __device__ __forceinline__ int harmonic_l(int k) { return k < 2 ? 1 : (k < 5 ? 2 : 3); }
 
+// Moment arrays are [R][NK][Gp] for NK > 2: for one moment, the groups of a region are
+// contiguous, so the group lanes of one track end read one row and their tally atomics hit one L2
+// sector. For P1 (NK = 2) they are [R][Gp][2]: a lane's two moments are one 8-byte pair, read with
+// one load and, in FP32, added with one float2 atomic (the warp's pairs still fill whole sectors);
+// wider vector atomics over more moments were measured slower.
+__host__ __device__ __forceinline__ size_t mom_at(int r, int k, int g, int NK, int Gp) {
+  return NK == 2 ? ((size_t)r * Gp + g) * 2 + k : ((size_t)r * NK + k) * Gp + g;
+}
+
+template <typename Real, int NK> __device__ __forceinline__ void mom_load(const Real *a, int r, int g, int Gp, Real *v) {
+  if (NK == 2 && sizeof(Real) == 4) {
+    const float2 x = *reinterpret_cast<const float2 *>(a + mom_at(r, 0, g, NK, Gp));
+    v[0] = x.x;
+    v[NK - 1] = x.y;
+  } else {
+#pragma unroll
+    for (int k = 0; k < NK; ++k) v[k] = a[mom_at(r, k, g, NK, Gp)];
+  }
+}
+
+template <typename Real, int NK> __device__ __forceinline__ void mom_add(Real *a, int r, int g, int Gp, const Real *v) {
+  if (NK == 2 && sizeof(Real) == 4) {
+    atomicAdd(reinterpret_cast<float2 *>(a + mom_at(r, 0, g, NK, Gp)), make_float2(v[0], v[NK - 1]));
+  } else {
+#pragma unroll
+    for (int k = 0; k < NK; ++k) atomicAdd(a + mom_at(r, k, g, NK, Gp), v[k]);
+  }
+}
 // source moments, one thread per region: the pending normalisation is applied to the moments
 // first (as source_kernel does to phi), then src_k = (2l+1) sum_g' Sigma_s,l phi_k / (4 pi Sigma_t)
 template <typename Real>
@@ -37,13 +65,12 @@ __global__ void aniso_source_kernel(int R, int G, int Gp, int M, int NK, const i
   const Real inv4pi = (Real)(1.0 / kFourPi);
   for (int k = 0; k < NK; ++k) {
     const int l = harmonic_l(k);
-    Real *pk = mom + ((size_t)r * NK + k) * Gp;
-    for (int g = 0; g < G; ++g) pk[g] *= scale;
+    for (int g = 0; g < G; ++g) mom[mom_at(r, k, g, NK, Gp)] *= scale;
     const Real *ss = s_ssl + ((size_t)(l - 1) * M + m) * G * G;
     for (int g = 0; g < G; ++g) {
       Real a = 0;
-      for (int gp = 0; gp < G; ++gp) a += ss[gp * G + g] * pk[gp];
-      srck[((size_t)r * NK + k) * Gp + g] = (Real)(2 * l + 1) * a * inv4pi / xsq[(size_t)r * Gp + g].x;
+      for (int gp = 0; gp < G; ++gp) a += ss[gp * G + g] * mom[mom_at(r, k, gp, NK, Gp)];
+      srck[mom_at(r, k, g, NK, Gp)] = (Real)(2 * l + 1) * a * inv4pi / xsq[(size_t)r * Gp + g].x;
     }
   }
 }
@@ -65,7 +92,7 @@ __global__ void __launch_bounds__(128) sweep_aniso_kernel(
   const TrackRec tr = trk[td >> 1];
   const int d = (int)(td & 1);
   const Real scale = (Real)scal[S_SCALE];
-  Real psi[P], w[P], is[P], hr[P][NK], wh[P][NK];
+  Real psi[P], w[P], is[P], hr[P][NK];
 #pragma unroll
   for (int p = 0; p < P; ++p) {
     psi[p] = psi_in[(td * P + p) * G + g] * scale;
@@ -76,19 +103,41 @@ __global__ void __launch_bounds__(128) sweep_aniso_kernel(
       // the reverse sense turns Om_xy around: R_lm -> (-1)^l R_lm for the harmonics kept
       const Real h = harm[((size_t)tr.dir * P + p) * NK + k];
       hr[p][k] = (d && (harmonic_l(k) & 1)) ? -h : h;
-      wh[p][k] = w[p] * hr[p][k];
     }
   }
+  // P1: segments two ahead, region rows and moments one ahead (the segment array's padding
+  // records make the look-ahead safe without a bounds test). More moments: the rows are read at
+  // use, since the look-ahead registers cost more occupancy than they save.
+  constexpr bool PF = NK <= 2;
   const int step = d ? -1 : 1;
   const SegRec<Real> *sp = seg + (d ? tr.off + tr.n - 1 : tr.off);
   Tally<TM, Real> tally;
-  tally.init((unsigned)(sp->r * Gp + g));
+  SegRec<Real> s0 = sp[0], s1 = s0;
+  typename Pair<Real>::T xq0 = xsq[(size_t)s0.r * Gp + g];
+  Real sk0[NK];
+  if (PF) {
+    s1 = sp[step];
+    mom_load<Real, NK>(srck, s0.r, g, Gp, sk0);
+  }
+  tally.init((unsigned)(s0.r * Gp + g));
   for (int n = 0; n < tr.n; ++n) {
-    const SegRec<Real> s0 = *sp;
-    const typename Pair<Real>::T xq = xsq[(size_t)s0.r * Gp + g];
+    typename Pair<Real>::T xq;
     Real sk[NK];
+    SegRec<Real> s2;
+    typename Pair<Real>::T xq1;
+    Real sk1[NK];
+    if (PF) {
+      s2 = sp[2 * step];
+      xq1 = xsq[(size_t)s1.r * Gp + g];
+      mom_load<Real, NK>(srck, s1.r, g, Gp, sk1);
+      xq = xq0;
 #pragma unroll
-    for (int k = 0; k < NK; ++k) sk[k] = srck[((size_t)s0.r * NK + k) * Gp + g];
+      for (int k = 0; k < NK; ++k) sk[k] = sk0[k];
+    } else {
+      s0 = *sp;
+      xq = xsq[(size_t)s0.r * Gp + g];
+      mom_load<Real, NK>(srck, s0.r, g, Gp, sk);
+    }
     const Real tau0 = xq.x * s0.l;
     Real acc = 0, ak[NK];
 #pragma unroll
@@ -102,12 +151,19 @@ __global__ void __launch_bounds__(128) sweep_aniso_kernel(
       const Real dl = (psi[p] - qr) * F;
       psi[p] -= dl;
       acc = fma(w[p], dl, acc);
+      const Real wd = w[p] * dl;
 #pragma unroll
-      for (int k = 0; k < NK; ++k) ak[k] = fma(wh[p][k], dl, ak[k]);
+      for (int k = 0; k < NK; ++k) ak[k] = fma(hr[p][k], wd, ak[k]);
     }
     tally.add(tsum, tcomp, (unsigned)(s0.r * Gp + g), acc);
+    mom_add<Real, NK>(tmom, s0.r, g, Gp, ak);
+    if (PF) {
+      s0 = s1;
+      s1 = s2;
+      xq0 = xq1;
 #pragma unroll
-    for (int k = 0; k < NK; ++k) atomicAdd(tmom + ((size_t)s0.r * NK + k) * Gp + g, ak[k]);
+      for (int k = 0; k < NK; ++k) sk0[k] = sk1[k];
+    }
     sp += step;
   }
   tally.flush(tcomp);
@@ -133,12 +189,12 @@ __global__ void aniso_moments_kernel(int R, int G, int Gp, int NK, const Real *_
   typename Pair<Real>::T v = xsq[a];
   Real s[1 + 9];
   s[0] = v.y;
-  for (int k = 0; k < NK; ++k) s[1 + k] = srck[((size_t)r * NK + k) * Gp + g];
+  for (int k = 0; k < NK; ++k) s[1 + k] = srck[mom_at(r, k, g, NK, Gp)];
   const Real ita = inv_ta[a];
   for (int k = 1; k < n; ++k) {
     Real ph = 0;
     for (int k2 = 0; k2 < n; ++k2) ph = fma(gm[k * n + k2], s[k2], ph);
-    const size_t b = ((size_t)r * NK + (k - 1)) * Gp + g;
+    const size_t b = mom_at(r, k - 1, g, NK, Gp);
     ph = fma(tmom[b], ita, ph);
     tmom[b] = (Real)0;
     mom[b] = ph;
@@ -156,9 +212,9 @@ __global__ void aniso_init_kernel(int R, int G, int Gp, int NK, const Real *__re
                                   const Real *__restrict__ phi, Real *__restrict__ mom) {
   const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= (long long)R * NK * Gp) return;
-  const long long r = x / ((long long)NK * Gp);
-  const int k = (int)((x / Gp) % NK), g = (int)(x % Gp);
-  mom[x] = (g < G) ? gm[(k + 1) * (NK + 1)] * phi[r * Gp + g] * (Real)(1.0 / kFourPi) : (Real)0;
+  const int r = (int)(x / ((long long)NK * Gp));
+  const int rest = (int)(x - (long long)r * NK * Gp), k = rest / Gp, g = rest - k * Gp;
+  mom[mom_at(r, k, g, NK, Gp)] = (g < G) ? gm[(k + 1) * (NK + 1)] * phi[(size_t)r * Gp + g] * (Real)(1.0 / kFourPi) : (Real)0;
 }
 
 }  // namespace moc
