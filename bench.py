@@ -43,7 +43,7 @@ def make_problem(name: str):
 L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) per launch of the sweep kernel from one ncu capture of the current kernel
 # version on the assembly workload (profiles/sweep_kernel_assembly17.md); None for other workloads.
-SWEEP_DRAM_BYTES = {"assembly": 82.330112e6 + 2.306048e6}
+SWEEP_DRAM_BYTES = {"assembly": 82.312960e6 + 2.801920e6}
 
 
 def _peaks():

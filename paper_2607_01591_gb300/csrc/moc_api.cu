@@ -38,7 +38,7 @@ struct moc_ctx {
   TrackRec *d_trk = nullptr;
   int32_t *d_link = nullptr;
   uint8_t *d_fed = nullptr;  // per internal track end: 1 if some outgoing end feeds it
-  long long *d_perm = nullptr, *d_inv = nullptr;  // internal <-> external track order
+  long long *d_inv = nullptr;  // external track -> internal track
   double *h_scal = nullptr;   // pinned, device-mapped copy of the scalars written by state_out_kernel
   bool pageable_ok = false;   // the GPU reads and writes pageable host memory coherently
   void *d_wgt = nullptr, *d_inv_sin = nullptr;
@@ -189,7 +189,6 @@ void free_tracks(moc_ctx *c) {
   dfree(c->d_trk);
   dfree(c->d_link);
   dfree(c->d_fed);
-  dfree(c->d_perm);
   dfree(c->d_inv);
   dfree(c->d_wgt);
   dfree(c->d_inv_sin);
@@ -303,8 +302,7 @@ template <typename Real> int upload_tracks(moc_ctx *c) {
     if (e >= 0) fed[e] = 1;
   if ((rc = upload(c, c->d_fed, fed.data(), fed.size()))) return rc;
   {
-    std::vector<long long> pl(c->perm.begin(), c->perm.end()), il(c->inv.begin(), c->inv.end());
-    if ((rc = upload(c, c->d_perm, pl.data(), pl.size()))) return rc;
+    std::vector<long long> il(c->inv.begin(), c->inv.end());
     if ((rc = upload(c, c->d_inv, il.data(), il.size()))) return rc;
   }
   Real *dw = nullptr, *di = nullptr;
@@ -803,7 +801,7 @@ template <typename Real> int state_in(moc_ctx *c, const double *dphi, const doub
   const int R = c->geo.n_tri;
   const long long n = (long long)R * c->Gp + c->T * 2 * c->P * c->G;
   state_in_kernel<Real><<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
-      R, c->G, c->Gp, (long long)c->T, c->P, dphi, dpsi, c->d_perm, c->d_fed, (Real *)c->d_phi,
+      R, c->G, c->Gp, (long long)c->T, c->P, dphi, dpsi, c->d_inv, c->d_fed, (Real *)c->d_phi,
       (Real *)c->d_psi[c->cur], c->d_scal, k, scale);
   CUDA_TRY(c, cudaGetLastError());
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));

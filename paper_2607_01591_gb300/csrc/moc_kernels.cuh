@@ -122,7 +122,7 @@ __global__ void source_kernel(int R, int G, int Gp, int M, const int32_t *__rest
 // k and the normalisation `scale`.
 template <typename Real>
 __global__ void state_in_kernel(int R, int G, int Gp, long long T, int P, const double *__restrict__ phi,
-                                const double *__restrict__ psi, const long long *__restrict__ perm,
+                                const double *__restrict__ psi, const long long *__restrict__ inv,
                                 const uint8_t *__restrict__ fed, Real *__restrict__ d_phi, Real *__restrict__ d_psi,
                                 double *__restrict__ scal, double k, double scale) {
   const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -141,11 +141,11 @@ __global__ void state_in_kernel(int R, int G, int Gp, long long T, int P, const 
     d_phi[x] = (g < G) ? (Real)(phi ? phi[r * G + g] : 1.0) : (Real)0;
     return;
   }
-  const long long y = x - nphi;  // internal end e = y / half, value q
-  if (y >= T * 2 * half) return;
-  const long long e = y / half, q = y - e * half;
-  const long long t = perm[e >> 1];
-  d_psi[y] = (psi && fed[e]) ? (Real)psi[(t * 2 + (e & 1)) * half + q] : (Real)0;
+  const long long y = x - nphi;  // external end (t, d) = y / half, value q: the host array is read
+  if (y >= T * 2 * half) return; // in order, the device array written at the internal position
+  const long long ext = y / half, q = y - ext * half;
+  const long long e = 2 * inv[ext >> 1] + (ext & 1);
+  d_psi[e * half + q] = (psi && fed[e]) ? (Real)psi[y] : (Real)0;
 }
 
 // d_phi * scal[S_SCALE] -> phi [R][G] FP64; d_psi (internal order) * scale -> psi [T][2][P][G]
