@@ -354,7 +354,7 @@ def main():
     # time to converged k: outers from the cold start until |k - k_ref| <= 5 pcm, k_ref from FP32
     # convergence continued in FP64 to |dk| <= 1e-10 (same workload, same stream)
     time_to_k = None
-    if not args.no_time_to_k and args.workload in ("assembly", "core"):
+    if not args.no_time_to_k and args.workload in ("assembly", "core", "hexcore"):
         time_to_k = time_to_converged_k(moc, prob, local, stream, cmfd, plain=args.workload == "assembly")
 
     # tracking of the same workload: host half-edge walk vs the device walk (bit-identical tracks)
