@@ -70,3 +70,21 @@ def test_aniso_and_cmfd_are_exclusive():
     cell, nc = W.grid_cells(prob.mesh, 1.26)
     with pytest.raises(moc.MocError):
         m.set_cmfd(cell, nc, 4, 4)
+
+
+def test_p1_full_assembly_outers_match_oracle():
+    """The bench's full-size assembly (9.1M segments) with P1 scattering: 3 outers from the same
+    state, GPU FP64 vs oracle after each."""
+    prob = W.assembly_problem()
+    ssl = W.anisotropic_moments(prob.xs, 1, [0.05, 0.05, 0.4])
+    o = oracle.Oracle.from_problem(prob, threads=8)
+    o.set_scattering(ssl)
+    o.normalise()
+    m = moc.Moc.from_problem(prob, precision="fp64")
+    m.set_scattering(ssl)
+    for it in range(3):
+        o.outer(True)
+        kg, _ = m.outer(1)
+        phio, ko = o.get_state()
+        assert abs(kg - ko) <= 1e-10 * ko, (it, kg, ko)
+        assert _rel(m.get_state()[0], phio) <= 1e-9, (it, _rel(m.get_state()[0], phio))
