@@ -66,6 +66,10 @@ struct moc_ctx {
   int32_t *d_cif_off = nullptr, *d_cif = nullptr, *d_if_cells = nullptr, *d_nbr = nullptr, *d_coff = nullptr;
   size_t cm_smem = 0;  // dynamic shared memory of the coarse solve (0: its working set stays in global memory)
   bool cm_idx16 = false;  // neighbour ids staged as 16-bit
+  int cm_cluster = 0;     // CTAs of the cluster coarse solve (0: one-block solve)
+  size_t cm_cl_smem = 0;  // its dynamic shared memory per CTA
+  int32_t *d_cl = nullptr;  // the cluster solve's ownership arrays (one allocation)
+  CmfdCluster cl{};
   void *d_cur = nullptr, *d_leak = nullptr, *d_cphi = nullptr, *d_TV = nullptr, *d_SV = nullptr, *d_FV = nullptr;
   void *d_CHI = nullptr, *d_din = nullptr, *d_diag = nullptr, *d_phic = nullptr, *d_phin = nullptr, *d_fis = nullptr;
   void *d_ratio = nullptr, *d_phio = nullptr, *d_src = nullptr;
@@ -128,6 +132,8 @@ void free_cmfd(moc_ctx *c) {
   dfree(c->d_if_cells);
   dfree(c->d_nbr);
   dfree(c->d_coff);
+  dfree(c->d_cl);
+  c->cm_cluster = 0;
   dfree(c->d_cur);
   dfree(c->d_leak);
   dfree(c->d_cphi);
@@ -643,6 +649,25 @@ template <typename Real> int launch_cmfd(moc_ctx *c, cudaStream_t st) {
       (Real *)c->d_CHI);
   CUDA_TRY(c, cudaGetLastError());
   CmfdTopo t{N, G, c->Gp, 2 * c->n_if, c->cm_colors, c->d_nbr, c->d_cif_off, c->d_cif, c->d_if_cells, c->d_coff};
+  if (c->cm_cluster) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c->cm_cluster);
+    cfg.blockDim = dim3(1024);
+    cfg.dynamicSmemBytes = c->cm_cl_smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = c->cm_cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    CUDA_TRY(c, cudaLaunchKernelEx(&cfg, cmfd_solve_cluster_kernel<Real>, t, c->cl, (double *)c->d_cur,
+                                   (double *)c->d_leak, (const Real *)c->d_cphi, (const Real *)c->d_TV,
+                                   (const Real *)c->d_SV, (const Real *)c->d_FV, (const Real *)c->d_CHI,
+                                   (Real *)c->d_din, (Real *)c->d_diag, (Real *)c->d_phic, (Real *)c->d_fis,
+                                   (Real *)c->d_ratio, c->d_scal, c->cm_outer, c->cm_inner, (Real)c->cm_omega));
+  } else {
   auto solve = !c->cm_smem ? cmfd_solve_kernel<Real, false, int32_t>
                : c->cm_idx16 ? cmfd_solve_kernel<Real, true, uint16_t> : cmfd_solve_kernel<Real, true, int32_t>;
   solve<<<1, 1024, c->cm_smem, st>>>(t, (double *)c->d_cur, (double *)c->d_leak, (const Real *)c->d_cphi,
@@ -651,6 +676,7 @@ template <typename Real> int launch_cmfd(moc_ctx *c, cudaStream_t st) {
                                      (Real *)c->d_phic, (Real *)c->d_phin, (Real *)c->d_phio,
                                      (Real *)c->d_src, (Real *)c->d_fis, (Real *)c->d_ratio, c->d_scal,
                                      c->cm_outer, c->cm_inner, (Real)c->cm_omega);
+  }
   CUDA_TRY(c, cudaGetLastError());
   cmfd_prolong_kernel<Real><<<(R + 255) / 256, 256, 0, st>>>(R, G, c->Gp, N, c->d_cell, c->d_mat, (const Real *)c->d_nsf,
                                                              c->d_area, (const Real *)c->d_ratio, (Real *)c->d_phi,
@@ -1253,6 +1279,92 @@ int moc_set_cmfd(moc_ctx *c, const int32_t *cell_in, int n_cells, int n_outer, i
         fn = idx16 ? (const void *)cmfd_solve_kernel<float, true, uint16_t> : (const void *)cmfd_solve_kernel<float, true, int32_t>;
       CUDA_TRY(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
       c->cm_smem = need;
+    }
+  }
+  // coarse problems of 1,024 cells and more: the cluster solve (8 CTAs, each owning a slice of
+  // every colour), if such a cluster fits on the device
+  c->cm_cluster = 0;
+  if (n_cells >= 1024) {
+    const int C = 8, ncol = n_colors;
+    std::vector<std::vector<int32_t>> own(C);
+    std::vector<int32_t> owner(n_cells), local(n_cells), ccoff((size_t)C * (ncol + 1), 0);
+    for (int col = 0; col < ncol; ++col) {
+      const int lo = coff[col], len = coff[col + 1] - coff[col];
+      for (int b = 0; b < C; ++b) {
+        const int a0 = lo + (int)((int64_t)len * b / C), a1 = lo + (int)((int64_t)len * (b + 1) / C);
+        ccoff[(size_t)b * (ncol + 1) + col] = (int32_t)own[b].size();
+        for (int i = a0; i < a1; ++i) {
+          owner[i] = b;
+          local[i] = (int32_t)own[b].size();
+          own[b].push_back(i);
+        }
+      }
+    }
+    for (int b = 0; b < C; ++b) ccoff[(size_t)b * (ncol + 1) + ncol] = (int32_t)own[b].size();
+    std::vector<int32_t> cbase(C + 1, 0), ebase(C + 1, 0), own_cell, eoff, ent, loc;
+    size_t need_max = 0;
+    bool fits = true;
+    for (int b = 0; b < C; ++b) {
+      cbase[b + 1] = cbase[b] + (int32_t)own[b].size();
+      int32_t ne = 0;
+      eoff.push_back(0);
+      for (int i : own[b]) {
+        own_cell.push_back(i);
+        for (int q = cif_off[i]; q < cif_off[i + 1]; ++q) {
+          const int j = nbr[q];
+          ent.push_back(q);
+          loc.push_back((owner[j] << 16) | local[j]);
+          ++ne;
+        }
+        eoff.push_back(ne);
+      }
+      ebase[b + 1] = ebase[b] + ne;
+      if (own[b].size() >= 65536) fits = false;
+    }
+    {
+      size_t ncmax = 0;
+      for (int b = 0; b < C; ++b) ncmax = std::max(ncmax, own[b].size());
+      for (int b = 0; b < C; ++b) {
+        const size_t ne = (size_t)(ebase[b + 1] - ebase[b]);
+        need_max = std::max(need_max, (3 * ncmax + ne) * rs + ne * 4 + (ncmax + 1) * 4);
+      }
+    }
+    int dev_max = 0;
+    CUDA_TRY(c, cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    if (fits && need_max + 1024 <= (size_t)dev_max) {
+      const void *fn = c->precision == MOC_FP64 ? (const void *)cmfd_solve_cluster_kernel<double>
+                                                : (const void *)cmfd_solve_cluster_kernel<float>;
+      CUDA_TRY(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need_max));
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(C);
+      cfg.blockDim = dim3(1024);
+      cfg.dynamicSmemBytes = need_max;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = C;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int n_cl = 0;
+      if (cudaOccupancyMaxActiveClusters(&n_cl, fn, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        n_cl = 0;
+      }
+      if (n_cl >= 1) {
+        // one allocation: cbase | own_cell | ccoff | ebase | eoff | ent | loc
+        std::vector<int32_t> all;
+        std::vector<size_t> at_off;
+        for (const std::vector<int32_t> *v : {&cbase, &own_cell, &ccoff, &ebase, &eoff, &ent, &loc}) {
+          at_off.push_back(all.size());
+          all.insert(all.end(), v->begin(), v->end());
+        }
+        if ((rc = upload(c, c->d_cl, all.data(), all.size()))) return rc;
+        c->cl = CmfdCluster{c->d_cl + at_off[0], c->d_cl + at_off[1], c->d_cl + at_off[2], c->d_cl + at_off[3],
+                            c->d_cl + at_off[4], c->d_cl + at_off[5], c->d_cl + at_off[6]};
+        c->cm_cluster = C;
+        c->cm_cl_smem = need_max;
+      }
     }
   }
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));

@@ -16,6 +16,8 @@
 //     in energy, over-relaxed Gauss-Seidel sweeps in space over a colouring of the cells), and the
 //     fine flux and boundary flux are scaled by the coarse flux ratio of their cell.
 #pragma once
+#include <cooperative_groups.h>
+
 #include "moc_kernels.cuh"
 
 namespace moc {
@@ -222,6 +224,152 @@ __global__ void __launch_bounds__(1024, 1) cmfd_solve_kernel(CmfdTopo t, double 
     if (isfinite(kc) && kc > 0.0) scal[S_K] = kc;
     else scal[S_STATUS] = 1.0;
   }
+}
+
+// The same coarse solve on a thread-block cluster: CTA b of the cluster owns, in every colour, a
+// contiguous slice of that colour's cells, and keeps the per-group working set of its cells
+// (source, 1/diagonal, iterate, coefficients, neighbour locators) in its own shared memory.
+// A neighbour owned by another CTA is read from that CTA's shared memory (distributed shared
+// memory); one cluster barrier ends each colour sweep. Fission sums are reduced per CTA, then
+// summed over the CTAs in rank order by every CTA, so all of them take identical k updates.
+struct CmfdCluster {
+  const int32_t *cbase;    // [C+1] owned cells of CTA b: own_cell[cbase[b] .. cbase[b+1])
+  const int32_t *own_cell; // global cell id of each owned cell, colour by colour
+  const int32_t *ccoff;    // [C][n_colors+1] local offsets of each colour within a CTA's cells
+  const int32_t *ebase;    // [C+1] owned entries of CTA b
+  const int32_t *eoff;     // [sum of cells + C] local entry offsets per owned cell (per CTA)
+  const int32_t *ent;      // [entries] global entry index (for din)
+  const int32_t *loc;      // [entries] neighbour's owner CTA << 16 | its local index there
+};
+
+template <typename Real>
+__global__ void __launch_bounds__(1024, 1) cmfd_solve_cluster_kernel(CmfdTopo t, CmfdCluster cl, double *__restrict__ cur,
+                                                                      double *__restrict__ leak, const Real *__restrict__ cphi,
+                                                                      const Real *__restrict__ TV, const Real *__restrict__ SV,
+                                                                      const Real *__restrict__ FV, const Real *__restrict__ CHI,
+                                                                      Real *__restrict__ din, Real *__restrict__ diag,
+                                                                      Real *__restrict__ phic, Real *__restrict__ fis,
+                                                                      Real *__restrict__ ratio, double *__restrict__ scal,
+                                                                      int n_outer, int n_inner, Real omega) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = (int)cluster.num_blocks(), b = (int)cluster.block_rank();
+  __shared__ double red32[32];
+  __shared__ double s_part;
+  const int N = t.N, G = t.G, Gp = t.Gp, NE = t.n_entries;
+  const int c0 = cl.cbase[b], nc = cl.cbase[b + 1] - c0;
+  const int e0 = cl.ebase[b], ne = cl.ebase[b + 1] - e0;
+  const int32_t *own = cl.own_cell + c0;
+  const int32_t *eoff = cl.eoff + c0 + b;  // nc + 1 local offsets
+  const int32_t *coff = cl.ccoff + (size_t)b * (t.n_colors + 1);
+  // the iterate sits at the same shared-memory offset in every CTA (sized by the largest slice),
+  // so a neighbour's value is read at its owner's copy of that offset
+  int ncmax = 0;
+  for (int r = 0; r < C; ++r) ncmax = max(ncmax, cl.cbase[r + 1] - cl.cbase[r]);
+  extern __shared__ unsigned char dyn[];
+  Real *s_x = reinterpret_cast<Real *>(dyn);
+  Real *s_src = s_x + ncmax;
+  Real *s_rd = s_src + ncmax;
+  Real *s_din = s_rd + ncmax;
+  int32_t *s_loc = reinterpret_cast<int32_t *>(s_din + ne);
+  int32_t *s_eoff = s_loc + ne;
+  for (int q = threadIdx.x; q < ne; q += blockDim.x) s_loc[q] = cl.loc[e0 + q];
+  for (int i = threadIdx.x; i <= nc; i += blockDim.x) s_eoff[i] = eoff[i];
+  // 1. coefficients of the owned cells from the tallied currents (FP64 leakage terms)
+  for (int x = threadIdx.x; x < nc * G; x += blockDim.x) {
+    const int li = x / G, g = x - li * G, i = own[li];
+    const size_t xi = (size_t)g * N + i;
+    const Real pi = cphi[xi];
+    const double inv_pi = (pi > (Real)0) ? 1.0 / (double)pi : 0.0;
+    double out = leak[(size_t)i * Gp + g];
+    for (int q = t.cif_off[i]; q < t.cif_off[i + 1]; ++q) {
+      const int e = t.cif[q] >> 1, side = t.cif[q] & 1;
+      const int j = t.if_cells[2 * e + (side ^ 1)];
+      const Real pj = cphi[(size_t)g * N + j];
+      out += cur[(size_t)(2 * e + side) * Gp + g];
+      din[(size_t)g * NE + q] = (pj > (Real)0) ? (Real)(cur[(size_t)(2 * e + (side ^ 1)) * Gp + g] / (double)pj) : (Real)0;
+    }
+    diag[xi] = TV[xi] - SV[((size_t)g * G + g) * N + i] + (Real)(out * inv_pi);
+    phic[xi] = pi;
+  }
+  cluster.sync();  // every CTA's currents read before any are cleared
+  for (int x = b * blockDim.x + threadIdx.x; x < NE * Gp; x += C * blockDim.x) cur[x] = 0.0;
+  for (int x = b * blockDim.x + threadIdx.x; x < N * Gp; x += C * blockDim.x) leak[x] = 0.0;
+  auto cluster_sum = [&](double v) {
+    const double p = block_sum_1024(v, red32);
+    if (threadIdx.x == 0) s_part = p;
+    cluster.sync();
+    double tot = 0.0;
+    for (int r = 0; r < C; ++r) tot += *cluster.map_shared_rank(&s_part, r);
+    cluster.sync();  // s_part is not overwritten before every CTA has read it
+    return tot;
+  };
+  double kc = scal[S_K];
+  // 2. coarse power iteration
+  for (int it = 0; it < n_outer; ++it) {
+    double fsum = 0.0;
+    for (int li = threadIdx.x; li < nc; li += blockDim.x) {
+      const int i = own[li];
+      Real f = 0;
+      for (int g = 0; g < G; ++g) f += FV[(size_t)g * N + i] * phic[(size_t)g * N + i];
+      fis[i] = f;
+      fsum += (double)f;
+    }
+    const double F_old = cluster_sum(fsum);
+    const Real inv_k = (Real)(1.0 / kc);
+    for (int g = 0; g < G; ++g) {
+      for (int li = threadIdx.x; li < nc; li += blockDim.x) {
+        const int i = own[li];
+        Real rhs = CHI[(size_t)g * N + i] * fis[i] * inv_k;
+        for (int h = 0; h < G; ++h)
+          if (h != g) rhs += SV[((size_t)g * G + h) * N + i] * phic[(size_t)h * N + i];
+        s_src[li] = rhs;
+        const Real dg = diag[(size_t)g * N + i];
+        s_rd[li] = (dg > (Real)0) ? (Real)1 / dg : (Real)0;
+        s_x[li] = phic[(size_t)g * N + i];
+      }
+      for (int q = threadIdx.x; q < ne; q += blockDim.x) s_din[q] = din[(size_t)g * NE + cl.ent[e0 + q]];
+      cluster.sync();  // every CTA's iterate staged before any is read remotely
+      for (int j = 0; j < n_inner; ++j) {
+        for (int c = 0; c < t.n_colors; ++c) {
+          for (int li = coff[c] + threadIdx.x; li < coff[c + 1]; li += blockDim.x) {
+            Real rhs = s_src[li];
+            for (int q = s_eoff[li]; q < s_eoff[li + 1]; ++q) {
+              const int l = s_loc[q], r = l >> 16, k = l & 0xffff;
+              const Real xn = (r == b) ? s_x[k] : *cluster.map_shared_rank(s_x + k, r);
+              rhs += s_din[q] * xn;
+            }
+            const Real rd = s_rd[li];
+            if (rd > (Real)0) s_x[li] = fma(omega, rhs * rd - s_x[li], s_x[li]);
+          }
+          cluster.sync();
+        }
+      }
+      for (int li = threadIdx.x; li < nc; li += blockDim.x) phic[(size_t)g * N + own[li]] = s_x[li];
+      cluster.sync();  // remote readers are done with this group's iterate; phic written
+    }
+    fsum = 0.0;
+    for (int li = threadIdx.x; li < nc; li += blockDim.x) {
+      const int i = own[li];
+      Real f = 0;
+      for (int g = 0; g < G; ++g) f += FV[(size_t)g * N + i] * phic[(size_t)g * N + i];
+      fsum += (double)f;
+    }
+    const double F_new = cluster_sum(fsum);
+    if (F_new > 0.0 && F_old > 0.0) kc = kc * F_new / F_old;
+  }
+  // 3. prolongation ratios of the owned cells and the accelerated k
+  for (int x = threadIdx.x; x < nc * G; x += blockDim.x) {
+    const int li = x / G, g = x - li * G;
+    const size_t xi = (size_t)g * N + own[li];
+    const Real a = cphi[xi], bb = phic[xi];
+    ratio[xi] = (a > (Real)0 && bb > (Real)0) ? bb / a : (Real)1;
+  }
+  if (b == 0 && threadIdx.x == 0) {
+    if (isfinite(kc) && kc > 0.0) scal[S_K] = kc;
+    else scal[S_STATUS] = 1.0;
+  }
+  cluster.sync();  // no CTA leaves while another may still read its shared memory
 }
 
 // phi *= ratio(cell); block partials of sum A f(phi); the last block sets the normalisation.

@@ -376,3 +376,28 @@ def test_cmfd_full_assembly_outers_match_oracle():
         phio, ko = o.get_state()
         assert abs(kg - ko) <= 1e-10 * ko, (it, kg, ko)
         assert _rel(m.get_state()[0], phio) <= 1e-9, (it, _rel(m.get_state()[0], phio))
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 2e-5)])
+def test_cmfd_cluster_solve_matches_oracle(precision, tol):
+    """4,624 half-pin coarse cells (one assembly + reflector band): the coarse solve runs on a
+    thread-block cluster; 3 accelerated outers from the cold start vs the oracle."""
+    xs = W.synthetic_xs(["fuel", "fuel", "fuel", "fuel", "clad", "moderator", "reflector"], 7, 4,
+                        fuel_scales=[1.0, 0.95, 1.05, 0.9])
+    prob = W.Problem(W.core_mesh(1), xs, 16, 0.2, tol=1e-6, name="core1", seed=4)
+    cell, nc = W.grid_cells(prob.mesh, 0.63)
+    assert nc >= 1024
+    o = _oracle(prob)
+    o.set_cmfd(cell, nc, 5, 3, 1.4)
+    o.normalise()
+    m = moc.Moc.from_problem(prob, precision=precision)
+    m.set_cmfd(cell, nc, 5, 3, 1.4)
+    for it in range(3):
+        o.outer(True)
+        kg, _ = m.outer(1)
+        phio, ko = o.get_state()
+        phig = m.get_state()[0]
+        assert abs(kg - ko) <= tol * ko, (it, kg, ko)
+        # the reflector's far corner holds fluxes 1e-9 of the peak: relative to max(|phi|, 1e-6 peak)
+        err = float(np.max(np.abs(phig - phio) / np.maximum(np.abs(phio), 1e-6 * np.abs(phio).max())))
+        assert err <= 10 * tol, (it, err)
