@@ -116,6 +116,24 @@ int moc_generate_tracks(moc_ctx *ctx);
  * two passes. Errors: as moc_generate_tracks; MOC_ERR_STATE on a host-only context. */
 int moc_generate_tracks_device(moc_ctx *ctx, double *walk_ms);
 
+/* Tracks from the caller instead of moc_generate_tracks (segments computed elsewhere; the paper
+ * precomputes the segment data before the sweep, Sec. 3.1). Needs moc_set_mesh (regions) and
+ * moc_set_quadrature (polar set; n_azim fixes n_dir = n_azim/2 directions over [0, pi)).
+ *   seg_off     [n_tracks+1] first segment of each track, seg_off[0] = 0, every track non-empty
+ *   seg_region  [S] region of each segment; seg_len [S] its 2D length (finite, > 0)
+ *   track_azim  [n_tracks] direction index 0..n_dir-1 of each track (swept in both senses)
+ *   azim_weight [n_dir] azimuthal weight omega_j (the 2 pi set: each stands for j and j + pi)
+ *   azim_spacing[n_dir] ray spacing delta_j
+ *   link        [n_tracks][2] incoming end (2 t' + d') fed by the outgoing end of (t, d), or -1
+ *               (vacuum); each incoming end fed at most once
+ * Areas are the tracked areas sum 2 omega_j delta_j l. The directions' angles are unknown, so
+ * moc_set_scattering is refused on such tracks. Arrays are copied; replaces tracks, cross
+ * sections and state like moc_generate_tracks. Errors: MOC_ERR_ARG (validation), MOC_ERR_STATE,
+ * MOC_ERR_OOM, MOC_ERR_CUDA. */
+int moc_set_tracks(moc_ctx *ctx, int64_t n_tracks, const int64_t *seg_off, const int32_t *seg_region,
+                   const double *seg_len, const int32_t *track_azim, const double *azim_weight,
+                   const double *azim_spacing, const int32_t *link);
+
 /* Number of tracks and segments after moc_generate_tracks(). */
 int moc_get_track_counts(const moc_ctx *ctx, int64_t *n_tracks, int64_t *n_segments);
 
@@ -199,6 +217,21 @@ int moc_sweep(moc_ctx *ctx);
 /* Enqueue n outer iterations (source update + sweep each). Asynchronous; k_out and resid_out
  * (may be NULL) are read back with a synchronisation after the last outer. */
 int moc_outer(moc_ctx *ctx, int n, double *k_out, double *resid_out);
+
+/* One outer (source, sweep, finalize, k and normalisation) with the scalar flux in device arrays
+ * owned by the caller (e.g. PyTorch tensors), enqueued on `stream` (a cudaStream_t; NULL = the
+ * context's stream; ordered after the context's pending work and before its later work).
+ *   phi_in_dev  [n_tri][G] flux the source is built from, in the context's type (float for the
+ *               FP32 modes, double for FP64), taken as normalised (e.g. the phi_out of the
+ *               previous call), or NULL to continue from the context's flux
+ *   phi_out_dev [n_tri][G] the new flux, normalised to F = 1 in eigenvalue mode, or NULL
+ * The caller keeps both alive until the stream's work completes. Asynchronous; k and the residual
+ * as after moc_outer (read with moc_outer(ctx, 0, &k, &r)). Errors: MOC_ERR_STATE, MOC_ERR_CUDA. */
+int moc_sweep_dev(moc_ctx *ctx, void *stream, const void *phi_in_dev, void *phi_out_dev);
+
+/* Average sweep time (ms) and segment-polar-group updates per second over the sweeps timed since
+ * moc_enable_timing(ctx, 1) (synchronises; 0 if none). */
+int moc_get_stats(moc_ctx *ctx, double *sweep_ms, double *updates_per_s);
 
 /* Iterate until |k' - k| <= tol_k and the L-inf relative fission-source change <= tol_flux
  * (fixed-source mode: the relative flux change <= tol_flux), or max_outer outers. Convergence

@@ -961,6 +961,64 @@ int moc_generate_tracks_device(moc_ctx *c, double *walk_ms) {
   return c->precision == MOC_FP64 ? upload_tracks<double>(c) : upload_tracks<float>(c);
 }
 
+int moc_set_tracks(moc_ctx *c, int64_t n_tracks, const int64_t *seg_off, const int32_t *seg_region,
+                   const double *seg_len, const int32_t *track_azim, const double *azim_weight,
+                   const double *azim_spacing, const int32_t *link) {
+  if (!c) return MOC_ERR_ARG;
+  Geometry &g = c->geo;
+  if (!g.has_mesh || !g.has_quad) return fail(c, MOC_ERR_STATE, "set_tracks: set the mesh and the quadrature first");
+  if (n_tracks < 1 || !seg_off || !seg_region || !seg_len || !track_azim || !azim_weight || !azim_spacing || !link)
+    return fail(c, MOC_ERR_ARG, "set_tracks: bad sizes or NULL arrays");
+  const int nd = g.n_dir;
+  if (seg_off[0] != 0) return fail(c, MOC_ERR_ARG, "set_tracks: seg_off[0] must be 0");
+  for (int64_t t = 0; t < n_tracks; ++t)
+    if (!(seg_off[t + 1] > seg_off[t])) return fail(c, MOC_ERR_ARG, "set_tracks: every track needs at least one segment");
+  const int64_t S = seg_off[n_tracks];
+  if (S >= ((int64_t)1 << 31) * 16) return fail(c, MOC_ERR_ARG, "set_tracks: too many segments");
+  for (int64_t s = 0; s < S; ++s) {
+    if (seg_region[s] < 0 || seg_region[s] >= g.n_tri) return fail(c, MOC_ERR_ARG, "set_tracks: region id out of range");
+    if (!(seg_len[s] > 0.0) || !std::isfinite(seg_len[s])) return fail(c, MOC_ERR_ARG, "set_tracks: lengths must be finite and > 0");
+  }
+  for (int j = 0; j < nd; ++j)
+    if (!(azim_weight[j] > 0.0) || !std::isfinite(azim_weight[j]) || !(azim_spacing[j] > 0.0) || !std::isfinite(azim_spacing[j]))
+      return fail(c, MOC_ERR_ARG, "set_tracks: azimuthal weights and spacings must be finite and > 0");
+  std::vector<char> fed(2 * n_tracks, 0);
+  for (int64_t t = 0; t < n_tracks; ++t) {
+    if (track_azim[t] < 0 || track_azim[t] >= nd) return fail(c, MOC_ERR_ARG, "set_tracks: track direction out of range");
+    for (int d = 0; d < 2; ++d) {
+      const int64_t e = link[2 * t + d];
+      if (e < 0) continue;
+      if (e >= 2 * n_tracks) return fail(c, MOC_ERR_ARG, "set_tracks: link target out of range");
+      if (fed[e]) return fail(c, MOC_ERR_ARG, "set_tracks: an incoming end is linked twice (links must be a bijection)");
+      fed[e] = 1;
+    }
+  }
+  if (c->device >= 0) {
+    cudaSetDevice(c->device);
+    free_tracks(c);
+  }
+  // the caller's tracks replace any laid down here: directions are known only by their weights
+  g.phi.assign(nd, NAN);
+  g.omega.assign(azim_weight, azim_weight + nd);
+  g.delta.assign(azim_spacing, azim_spacing + nd);
+  g.nx.assign(nd, 0);
+  g.ny.assign(nd, 0);
+  g.seg_off.assign(seg_off, seg_off + n_tracks + 1);
+  g.seg_reg.assign(seg_region, seg_region + S);
+  g.seg_len.assign(seg_len, seg_len + S);
+  g.track_dir.assign(track_azim, track_azim + n_tracks);
+  g.track_xy.assign(4 * (size_t)n_tracks, NAN);
+  g.link.assign(link, link + 2 * n_tracks);
+  g.area.assign(g.n_tri, 0.0);
+  for (int64_t t = 0; t < n_tracks; ++t) {
+    const double w = 2.0 * g.omega[g.track_dir[t]] * g.delta[g.track_dir[t]];
+    for (int64_t s = g.seg_off[t]; s < g.seg_off[t + 1]; ++s) g.area[g.seg_reg[s]] += w * g.seg_len[s];
+  }
+  g.has_tracks = true;
+  if (c->device < 0) return MOC_OK;
+  return c->precision == MOC_FP64 ? upload_tracks<double>(c) : upload_tracks<float>(c);
+}
+
 int moc_get_track_counts(const moc_ctx *c, int64_t *n_tracks, int64_t *n_segments) {
   if (!c || !c->geo.has_tracks) return c ? MOC_ERR_STATE : MOC_ERR_ARG;
   if (n_tracks) *n_tracks = c->geo.n_tracks();
@@ -1034,6 +1092,8 @@ int moc_set_scattering(moc_ctx *c, int L, const double *sigma_sl) {
   if (L < 0 || L > kMaxAnisoL) return fail(c, MOC_ERR_ARG, "set_scattering: 0 <= L <= 3");
   if (c->cmfd) return fail(c, MOC_ERR_STATE, "set_scattering: not combined with CMFD acceleration");
   if (c->P > 3) return fail(c, MOC_ERR_ARG, "set_scattering: up to 3 polar angles");
+  for (double ph : c->geo.phi)
+    if (!std::isfinite(ph)) return fail(c, MOC_ERR_STATE, "set_scattering: the track directions' angles are unknown (tracks set by the caller)");
   const int M = c->M, G = c->G, P = c->P, nd = c->geo.n_dir, NK = L * (L + 3) / 2;
   if ((size_t)L * M * G * G * rsize(c) > 48 * 1024) return fail(c, MOC_ERR_ARG, "set_scattering: tables too large");
   for (size_t i = 0; i < (size_t)L * M * G * G; ++i)
@@ -1476,6 +1536,75 @@ int moc_outer(moc_ctx *c, int n, double *k_out, double *resid_out) {
     if (k_out) *k_out = s[S_K];
     if (resid_out) *resid_out = s[S_RESID];
     if (s[S_STATUS] != 0.0) return fail(c, MOC_ERR_NONFINITE, "outer: k or the residual is not finite");
+  }
+  return MOC_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+template <typename Real> int sweep_dev(moc_ctx *c, cudaStream_t st, const void *in, void *out) {
+  const int R = c->geo.n_tri;
+  const long long n_in = (long long)R * c->Gp, n_out = (long long)R * c->G;
+  if (in) {
+    // the caller's flux is taken as normalised: the boundary flux settles the pending factor
+    if (c->eigen) {
+      const long long np = c->T * 2 * c->P * c->G;
+      settle_scale_kernel<Real><<<(unsigned)((np + 255) / 256), 256, 0, st>>>(np, (Real *)c->d_psi[c->cur], c->d_scal);
+      reset_scale_kernel<<<1, 32, 0, st>>>(c->d_scal);
+    }
+    flux_in_kernel<Real><<<(unsigned)((n_in + 255) / 256), 256, 0, st>>>(R, c->G, c->Gp, (const Real *)in, (Real *)c->d_phi);
+    CUDA_TRY(c, cudaGetLastError());
+  }
+  int rc = enqueue_outer(c, st, false);
+  if (rc) return rc;
+  if (out) {
+    flux_out_kernel<Real><<<(unsigned)((n_out + 255) / 256), 256, 0, st>>>(R, c->G, c->Gp, (const Real *)c->d_phi,
+                                                                          c->d_scal, c->eigen ? 1 : 0, (Real *)out);
+    CUDA_TRY(c, cudaGetLastError());
+  }
+  return MOC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int moc_sweep_dev(moc_ctx *c, void *stream, const void *phi_in_dev, void *phi_out_dev) {
+  int rc = need_ready(c);
+  if (rc) return rc;
+  cudaSetDevice(c->device);
+  cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
+  if (st != c->stream) {
+    // order the caller's stream after the context's pending work and the context's after this
+    cudaEvent_t ev;
+    CUDA_TRY(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CUDA_TRY(c, cudaEventRecord(ev, c->stream));
+    CUDA_TRY(c, cudaStreamWaitEvent(st, ev, 0));
+    rc = c->precision == MOC_FP64 ? sweep_dev<double>(c, st, phi_in_dev, phi_out_dev)
+                                  : sweep_dev<float>(c, st, phi_in_dev, phi_out_dev);
+    if (!rc) {
+      CUDA_TRY(c, cudaEventRecord(ev, st));
+      CUDA_TRY(c, cudaStreamWaitEvent(c->stream, ev, 0));
+    }
+    cudaEventDestroy(ev);
+    return rc;
+  }
+  return c->precision == MOC_FP64 ? sweep_dev<double>(c, st, phi_in_dev, phi_out_dev)
+                                  : sweep_dev<float>(c, st, phi_in_dev, phi_out_dev);
+}
+
+int moc_get_stats(moc_ctx *c, double *sweep_ms, double *updates_per_s) {
+  double ms = 0.0;
+  int64_t n = 0;
+  int rc = moc_get_timing(c, &ms, &n);
+  if (rc) return rc;
+  const double avg = n ? ms / (double)n : 0.0;
+  if (sweep_ms) *sweep_ms = avg;
+  if (updates_per_s) {
+    const double ups = 2.0 * (double)c->geo.n_segments() * c->geo.n_polar * c->G;
+    *updates_per_s = avg > 0.0 ? ups / (avg * 1e-3) : 0.0;
   }
   return MOC_OK;
 }

@@ -174,6 +174,39 @@ __global__ void state_out_kernel(int R, int G, int Gp, long long T, int P, const
   psi[y] = (double)d_psi[e * half + q] * scale;
 }
 
+// caller-owned device flux [R][G] (the context's type) <-> the context's padded [R][Gp]
+template <typename Real>
+__global__ void flux_in_kernel(int R, int G, int Gp, const Real *__restrict__ src, Real *__restrict__ phi) {
+  const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= (long long)R * Gp) return;
+  const long long r = x / Gp;
+  const int g = (int)(x - r * Gp);
+  phi[x] = (g < G) ? src[r * G + g] : (Real)0;
+}
+
+// a caller's flux replaces the context's: the boundary flux takes the pending normalisation now
+// and the pending factor becomes 1 (thread 0 of the last launch resets it)
+template <typename Real>
+__global__ void settle_scale_kernel(long long n, Real *__restrict__ psi, const double *__restrict__ scal) {
+  const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x < n) psi[x] *= (Real)scal[S_SCALE];
+}
+
+__global__ void reset_scale_kernel(double *__restrict__ scal) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) scal[S_SCALE] = 1.0;
+}
+
+// writes the flux after an outer, with the pending normalisation applied (eigen mode)
+template <typename Real>
+__global__ void flux_out_kernel(int R, int G, int Gp, const Real *__restrict__ phi, const double *__restrict__ scal,
+                                int eigen, Real *__restrict__ dst) {
+  const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= (long long)R * G) return;
+  const long long r = x / G;
+  const int g = (int)(x - r * G);
+  dst[x] = phi[r * Gp + g] * (eigen ? (Real)scal[S_SCALE] : (Real)1);
+}
+
 // ----------------------------------------------------------------------------- sweep
 // Tally modes: 0 plain atomic add, 1 compensated (TwoSum error of each FP32 atomic add is
 // accumulated in a second array).

@@ -64,6 +64,9 @@ def load_library(path: Optional[str] = None):
             "moc_set_mesh": (ctypes.c_int, [_vp, ctypes.c_int, _d, ctypes.c_int, _i32, _i32, _d, _i32]),
             "moc_set_quadrature": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _d, _d]),
             "moc_generate_tracks": (ctypes.c_int, [_vp]),
+            "moc_set_tracks": (ctypes.c_int, [_vp, ctypes.c_int64, _i64, _i32, _d, _i32, _d, _d, _i32]),
+            "moc_sweep_dev": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+            "moc_get_stats": (ctypes.c_int, [_vp, _d, _d]),
             "moc_set_scattering": (ctypes.c_int, [_vp, ctypes.c_int, _d]),
             "moc_set_ray_layout": (ctypes.c_int, [_vp, ctypes.c_int]),
             "moc_generate_tracks_device": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
@@ -265,6 +268,33 @@ class Moc:
 
     def generate_tracks(self):
         self._check(self._lib.moc_generate_tracks(self._h))
+
+    def set_tracks(self, seg_off, seg_region, seg_len, track_azim, azim_weight, azim_spacing, link):
+        """Tracks from the caller (see moc_set_tracks): segment CSR, direction per track, weights
+        and spacings per direction, links [T][2] as 2 t' + d' or -1."""
+        so = np.ascontiguousarray(seg_off, dtype=np.int64)
+        sr, sl = _i32a(seg_region), _f64(seg_len)
+        ta, aw, asp = _i32a(track_azim), _f64(azim_weight), _f64(azim_spacing)
+        lk = _i32a(np.asarray(link).reshape(-1))
+        self._check(self._lib.moc_set_tracks(self._h, int(so.size - 1), _p(so, _i64), _p(sr, _i32), _p(sl, _d),
+                                             _p(ta, _i32), _p(aw, _d), _p(asp, _d), _p(lk, _i32)))
+
+    def sweep_dev(self, phi_in=None, phi_out=None, stream=None):
+        """One outer with caller-owned device flux tensors [n_tri][G] (torch CUDA tensors of the
+        context's type, or None) on `stream` (a torch stream or None: the context's stream)."""
+        def ptr(t):
+            if t is None:
+                return None
+            assert t.is_cuda and t.is_contiguous() and t.numel() == self.n_regions * self.G
+            return ctypes.c_void_p(t.data_ptr())
+        st = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+        self._check(self._lib.moc_sweep_dev(self._h, st, ptr(phi_in), ptr(phi_out)))
+
+    def stats(self):
+        """(average sweep ms, updates/s) over the sweeps timed since enable_timing(True)."""
+        ms, ups = ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.moc_get_stats(self._h, ctypes.byref(ms), ctypes.byref(ups)))
+        return ms.value, ups.value
 
     def set_ray_layout(self, layout: int):
         """0: cyclic modular rays over the bounding box; 1: back projection (vacuum boundaries)."""

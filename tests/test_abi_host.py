@@ -120,3 +120,47 @@ def test_bad_inputs_are_rejected(lib):
         m.set_xs(W.synthetic_xs(["fuel"], 2, 1))
     assert e.value.code == -4
     assert "host-only" in str(e.value)
+
+
+def _caller_tracks(prob):
+    a = moc.Moc.from_problem(prob, device=-1)
+    tr = a.tracks()
+    q = a.quadrature(prob.n_azim // 2)
+    return a, tr, q
+
+
+def test_set_tracks_reproduces_generated_tracks(lib):
+    """Tracks generated by one context and handed to another through moc_set_tracks give the same
+    segments, links and (to rounding) tracked areas."""
+    prob = W.small_lattice_problem(3, bc=(1, 0, 1, 0), n_azim=24, ray_spacing=0.03)
+    a, tr, q = _caller_tracks(prob)
+    b = moc.Moc(-1, "fp32")
+    b.set_mesh(prob.mesh)
+    b.set_quadrature(prob.n_azim, prob.ray_spacing, prob.sin_theta, prob.polar_w)
+    b.set_tracks(tr["seg_off"], tr["seg_region"], tr["seg_len"], tr["track_dir"], q["omega"], q["delta"], tr["link"])
+    tb = b.tracks()
+    for key in ("seg_off", "seg_region", "seg_len", "track_dir", "link"):
+        assert np.array_equal(tb[key], tr[key]), key
+    np.testing.assert_allclose(b.areas(), a.areas(), rtol=1e-13)
+
+
+def test_set_tracks_validates(lib):
+    prob = W.small_lattice_problem(3, bc=(1, 0, 1, 0), n_azim=24, ray_spacing=0.03)
+    a, tr, q = _caller_tracks(prob)
+    b = moc.Moc(-1, "fp32")
+    b.set_mesh(prob.mesh)
+    b.set_quadrature(prob.n_azim, prob.ray_spacing, prob.sin_theta, prob.polar_w)
+    args = [tr["seg_off"], tr["seg_region"], tr["seg_len"], tr["track_dir"], q["omega"], q["delta"], tr["link"]]
+    bad_link = tr["link"].copy()
+    e = bad_link[bad_link >= 0][0]
+    bad_link[bad_link == -1] = e          # an incoming end fed twice
+    bad_len = tr["seg_len"].copy()
+    bad_len[3] = -1.0
+    bad_reg = tr["seg_region"].copy()
+    bad_reg[5] = prob.mesh.n_tri
+    for i, v in ((6, bad_link), (2, bad_len), (1, bad_reg)):
+        a2 = list(args)
+        a2[i] = v
+        with pytest.raises(moc.MocError) as err:
+            b.set_tracks(*a2)
+        assert err.value.code == -1

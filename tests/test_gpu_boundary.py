@@ -1,0 +1,77 @@
+"""The remaining boundary calls on the GPU: tracks supplied by the caller (moc_set_tracks), one
+outer with caller-owned device flux arrays (moc_sweep_dev), and the timing statistics
+(moc_get_stats)."""
+import numpy as np
+import pytest
+
+from paper_2607_01591_gb300 import moc
+from paper_2607_01591_gb300 import workloads as W
+from paper_2607_01591_gb300.build import build
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build()
+
+
+def _prob():
+    return W.small_lattice_problem(3, bc=(1, 0, 1, 0), n_azim=24, ray_spacing=0.03)
+
+
+def test_caller_tracks_iterate_like_generated_ones():
+    prob = _prob()
+    a = moc.Moc.from_problem(prob, precision="fp64")
+    tr, q = a.tracks(), a.quadrature(prob.n_azim // 2)
+    b = moc.Moc(0, "fp64")
+    b.set_mesh(prob.mesh)
+    b.set_quadrature(prob.n_azim, prob.ray_spacing, prob.sin_theta, prob.polar_w)
+    b.set_tracks(tr["seg_off"], tr["seg_region"], tr["seg_len"], tr["track_dir"], q["omega"], q["delta"], tr["link"])
+    b.set_xs(prob.xs)
+    ka, _ = a.outer(6)
+    kb, _ = b.outer(6)
+    assert abs(ka - kb) <= 1e-12 * ka
+    np.testing.assert_allclose(b.get_state()[0], a.get_state()[0], rtol=1e-11)
+    with pytest.raises(moc.MocError):      # the directions' angles are unknown
+        b.set_scattering(W.anisotropic_moments(prob.xs, 1, [0.1, 0.1, 0.1]))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_sweep_dev_matches_outer(precision):
+    import torch
+    prob = _prob()
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    tol = 1e-12 if precision == "fp64" else 2e-6
+    a = moc.Moc.from_problem(prob, precision=precision)
+    b = moc.Moc.from_problem(prob, precision=precision)
+    R, G = prob.mesh.n_tri, prob.xs.n_groups
+    # continuing from the context's own flux
+    out = torch.empty((R, G), dtype=dt, device="cuda")
+    stream = torch.cuda.Stream()
+    a.outer(2)
+    b.outer(1)
+    b.sweep_dev(None, out, stream)
+    stream.synchronize()
+    phi_a, ka = a.get_state()
+    kb, _ = b.outer(0)
+    assert abs(ka - kb) <= tol * ka
+    np.testing.assert_allclose(out.cpu().double().numpy(), phi_a, rtol=10 * tol)
+    # feeding the returned (normalised) flux back in continues the same iteration
+    out2 = torch.empty_like(out)
+    b.sweep_dev(out, out2, None)
+    a.outer(1)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(out2.cpu().double().numpy(), a.get_state()[0], rtol=10 * tol)
+
+
+def test_stats_report_the_timed_sweeps():
+    prob = W.assembly_problem()
+    m = moc.Moc.from_problem(prob)
+    m.outer(2)
+    m.enable_timing(True)
+    m.outer(5, read=False)
+    ms, ups = m.stats()
+    assert 0.0 < ms < 100.0
+    _, per_sweep, _ = m.work()
+    assert abs(ups - per_sweep / (ms * 1e-3)) <= 1e-9 * ups
