@@ -156,7 +156,8 @@ int moc_get_region_areas(const moc_ctx *ctx, double *area);
 
 /* Multigroup cross sections per material (Eq. MGNTE): sigma_t, nu_sigma_f, chi: [n_mat][G];
  * sigma_s: [n_mat][G_from][G_to] isotropic (P0) scattering. Requires sigma_t > 0, all data
- * finite and >= 0, and every mesh material id < n_mat. Resets the state to phi = 1, k = 1,
+ * finite and >= 0, sigma_t >= the total scattering out of each group (absorption >= 0), and
+ * every mesh material id < n_mat. Resets the state to phi = 1, k = 1,
  * zero boundary flux, eigenvalue mode. Errors: MOC_ERR_ARG, MOC_ERR_STATE, MOC_ERR_OOM. */
 int moc_set_xs(moc_ctx *ctx, int n_mat, int G, const double *sigma_t, const double *nu_sigma_f,
                const double *chi, const double *sigma_s);

@@ -1069,6 +1069,14 @@ int moc_set_xs(moc_ctx *c, int n_mat, int G, const double *st, const double *nsf
   }
   for (size_t i = 0; i < (size_t)n_mat * G * G; ++i)
     if (!(ss[i] >= 0.0) || !std::isfinite(ss[i])) return fail(c, MOC_ERR_ARG, "set_xs: sigma_s must be finite and >= 0");
+  // no material may scatter out of a group more than it removes from it (absorption >= 0)
+  for (int m = 0; m < n_mat; ++m)
+    for (int g = 0; g < G; ++g) {
+      double out = 0.0;
+      for (int h = 0; h < G; ++h) out += ss[((size_t)m * G + g) * G + h];
+      if (out > st[(size_t)m * G + g] * (1.0 + 1e-12))
+        return fail(c, MOC_ERR_ARG, "set_xs: sigma_t must be >= the total scattering out of each group");
+    }
   cudaSetDevice(c->device);
   free_problem(c);
   c->eigen = true;

@@ -75,3 +75,14 @@ def test_stats_report_the_timed_sweeps():
     assert 0.0 < ms < 100.0
     _, per_sweep, _ = m.work()
     assert abs(ups - per_sweep / (ms * 1e-3)) <= 1e-9 * ups
+
+
+def test_set_xs_rejects_negative_absorption():
+    prob = _prob()
+    m = moc.Moc.from_problem(prob, precision="fp32", with_xs=False)
+    xs = prob.xs
+    bad = W.CrossSections(xs.sigma_t, xs.nu_sigma_f, xs.chi, xs.sigma_s * 1.2)
+    with pytest.raises(moc.MocError) as e:
+        m.set_xs(bad)
+    assert e.value.code == -1 and "scattering" in str(e.value)
+    m.set_xs(xs)
