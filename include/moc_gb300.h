@@ -230,6 +230,13 @@ int moc_outer(moc_ctx *ctx, int n, double *k_out, double *resid_out);
  * as after moc_outer (read with moc_outer(ctx, 0, &k, &r)). Errors: MOC_ERR_STATE, MOC_ERR_CUDA. */
 int moc_sweep_dev(moc_ctx *ctx, void *stream, const void *phi_in_dev, void *phi_out_dev);
 
+/* Iteration history: every time the host reads k and the residual after outers (each check of
+ * moc_power_iterate, moc_outer with k_out or resid_out), one entry {outers so far (since the last
+ * moc_set_state), k, k before the last outer, residual} is recorded; the last 4,096 are kept.
+ * Copies the most recent min(max_entries, recorded) entries, oldest first, into entries
+ * [n][4] and their count into *n_out. Errors: MOC_ERR_ARG. */
+int moc_get_history(const moc_ctx *ctx, double *entries, int max_entries, int *n_out);
+
 /* Average sweep time (ms) and segment-polar-group updates per second over the sweeps timed since
  * moc_enable_timing(ctx, 1) (synchronises; 0 if none). */
 int moc_get_stats(moc_ctx *ctx, double *sweep_ms, double *updates_per_s);

@@ -80,6 +80,10 @@ struct moc_ctx {
   size_t h_stage_bytes = 0;
   // graphs: [parity of cur at launch]
   cudaGraphExec_t graph2[2] = {nullptr, nullptr};
+  // iteration history: (outer count, k, k before, residual) at every host read of the scalars,
+  // the last kHistory reads kept (a ring)
+  std::vector<double> hist;
+  int64_t hist_n = 0;
   // timing
   bool timing = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
@@ -766,6 +770,18 @@ int run_outers(moc_ctx *c, int n) {
   if (n % 2)
     if ((rc = enqueue_outer(c, c->stream, false))) return rc;
   return MOC_OK;
+}
+
+constexpr int kHistory = 4096;
+
+void record_history(moc_ctx *c, const double *s) {
+  if (c->hist.size() != 4 * (size_t)kHistory) c->hist.assign(4 * (size_t)kHistory, 0.0);
+  double *h = &c->hist[4 * (size_t)(c->hist_n % kHistory)];
+  h[0] = s[S_NOUTER];
+  h[1] = s[S_K];
+  h[2] = s[S_KPREV];
+  h[3] = s[S_RESID];
+  ++c->hist_n;
 }
 
 int read_scalars(moc_ctx *c, double *s) {
@@ -1469,6 +1485,7 @@ int moc_set_state(moc_ctx *c, const double *phi, double k, const double *psi) {
   int rc = need_ready(c);
   if (rc) return rc;
   if (!(k > 0.0) || !std::isfinite(k)) return fail(c, MOC_ERR_ARG, "set_state: k must be finite and > 0");
+  c->hist_n = 0;
   cudaSetDevice(c->device);
   double scale = 1.0;
   if (c->eigen) {
@@ -1541,6 +1558,7 @@ int moc_outer(moc_ctx *c, int n, double *k_out, double *resid_out) {
   if (k_out || resid_out) {
     double s[S_COUNT];
     if ((rc = read_scalars(c, s))) return rc;
+    if (n > 0) record_history(c, s);
     if (k_out) *k_out = s[S_K];
     if (resid_out) *resid_out = s[S_RESID];
     if (s[S_STATUS] != 0.0) return fail(c, MOC_ERR_NONFINITE, "outer: k or the residual is not finite");
@@ -1603,6 +1621,19 @@ int moc_sweep_dev(moc_ctx *c, void *stream, const void *phi_in_dev, void *phi_ou
                                   : sweep_dev<float>(c, st, phi_in_dev, phi_out_dev);
 }
 
+int moc_get_history(const moc_ctx *c, double *entries, int max_entries, int *n_out) {
+  if (!c || max_entries < 0 || (max_entries > 0 && !entries)) return MOC_ERR_ARG;
+  const int64_t avail = std::min<int64_t>(c->hist_n, kHistory);
+  const int n = (int)std::min<int64_t>(avail, max_entries);
+  for (int i = 0; i < n; ++i) {
+    const int64_t idx = c->hist_n - n + i;  // oldest of the returned first
+    const double *h = &c->hist[4 * (size_t)(idx % kHistory)];
+    for (int q = 0; q < 4; ++q) entries[4 * i + q] = h[q];
+  }
+  if (n_out) *n_out = n;
+  return MOC_OK;
+}
+
 int moc_get_stats(moc_ctx *c, double *sweep_ms, double *updates_per_s) {
   double ms = 0.0;
   int64_t n = 0;
@@ -1633,6 +1664,7 @@ int moc_power_iterate(moc_ctx *c, double tol_k, double tol_flux, int max_outer, 
     if ((rc = run_outers(c, m))) return rc;
     n += m;
     if ((rc = read_scalars(c, s))) return rc;
+    record_history(c, s);
     if (s[S_STATUS] != 0.0) return fail(c, MOC_ERR_NONFINITE, "power_iterate: k or the residual is not finite");
     bool ok_k = !c->eigen || std::fabs(s[S_K] - s[S_KPREV]) <= tol_k;
     if (ok_k && s[S_RESID] <= tol_flux) {

@@ -67,6 +67,7 @@ def load_library(path: Optional[str] = None):
             "moc_set_tracks": (ctypes.c_int, [_vp, ctypes.c_int64, _i64, _i32, _d, _i32, _d, _d, _i32]),
             "moc_sweep_dev": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
             "moc_get_stats": (ctypes.c_int, [_vp, _d, _d]),
+            "moc_get_history": (ctypes.c_int, [_vp, _d, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
             "moc_set_scattering": (ctypes.c_int, [_vp, ctypes.c_int, _d]),
             "moc_set_ray_layout": (ctypes.c_int, [_vp, ctypes.c_int]),
             "moc_generate_tracks_device": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
@@ -289,6 +290,13 @@ class Moc:
             return ctypes.c_void_p(t.data_ptr())
         st = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
         self._check(self._lib.moc_sweep_dev(self._h, st, ptr(phi_in), ptr(phi_out)))
+
+    def history(self, max_entries: int = 4096) -> np.ndarray:
+        """[n][4] rows (outers, k, k before the last outer, residual) of the recorded checks."""
+        buf = np.zeros((max_entries, 4))
+        n = ctypes.c_int()
+        self._check(self._lib.moc_get_history(self._h, _p(buf, _d), int(max_entries), ctypes.byref(n)))
+        return buf[: n.value].copy()
 
     def stats(self):
         """(average sweep ms, updates/s) over the sweeps timed since enable_timing(True)."""

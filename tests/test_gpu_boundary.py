@@ -86,3 +86,23 @@ def test_set_xs_rejects_negative_absorption():
         m.set_xs(bad)
     assert e.value.code == -1 and "scattering" in str(e.value)
     m.set_xs(xs)
+
+
+def test_history_records_every_check():
+    prob = _prob()
+    a = moc.Moc.from_problem(prob, precision="fp64")
+    k, n, r, ok = a.power_iterate(tol_k=1e-7, tol_flux=1e-6, max_outer=400, check_every=5)
+    h = a.history()
+    assert ok and h.shape == (n // 5, 4)
+    np.testing.assert_array_equal(h[:, 0], 5.0 * np.arange(1, n // 5 + 1))
+    assert h[-1, 1] == k and h[-1, 3] == r
+    assert abs(h[-1, 1] - h[-1, 2]) <= 1e-7 and h[-2, 3] > 1e-6
+    # the same iteration driven five outers at a time gives the same records
+    b = moc.Moc.from_problem(prob, precision="fp64")
+    for _ in range(3):
+        b.outer(5)
+    b.outer(0)                                  # a read without outers records nothing
+    np.testing.assert_allclose(b.history(), h[:3], rtol=1e-12)
+    assert a.history(2).shape == (2, 4) and np.array_equal(a.history(2), h[-2:])
+    a.set_state(None, 1.0)                      # a new start clears the record
+    assert a.history().shape == (0, 4)
