@@ -75,6 +75,13 @@ def _load():
         lib.orc_iterate.restype = ctypes.c_int
         lib.orc_iterate.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_int, _d, ctypes.POINTER(ctypes.c_int), _d]
+        lib.orc_set_axial.restype = ctypes.c_int
+        lib.orc_set_axial.argtypes = [ctypes.c_void_p, ctypes.c_int, _d, _i32, ctypes.c_int, ctypes.c_int]
+        lib.orc_get_flux3.argtypes = [ctypes.c_void_p, _d, _d]
+        lib.orc_get_leakage3.argtypes = [ctypes.c_void_p, _d]
+        lib.orc_expm2.argtypes = [_d, _d]
+        lib.orc_dg_segment.argtypes = [_d, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _d, _d]
         lib.orc_track_sweep.argtypes = [ctypes.c_int, _d, _d, _d, ctypes.c_double, ctypes.c_double, _d]
         lib.orc_sample_fixed_source.restype = ctypes.c_int
         lib.orc_sample_fixed_source.argtypes = [ctypes.c_int, _d, ctypes.c_int, _i32, _i32, _d, _i32, ctypes.c_int,
@@ -206,10 +213,40 @@ class Oracle:
             raise RuntimeError("oracle: " + self._lib.orc_error(self._h).decode())
         self._ssl = a
 
+    def set_axial(self, dz, mat3=None, bc=(0, 0)):
+        """DGMOC on len(dz) axial planes: mat3 [nz][R] materials (None: the planar ones in every
+        plane), bc = (bottom, top), 0 vacuum 1 reflective. Call after set_xs; the state restarts
+        flat. An empty dz returns to the planar method."""
+        dz = _f64(dz)
+        m3 = None if mat3 is None else _i32a(mat3)
+        if m3 is not None:
+            assert m3.shape == (dz.size, self.n_regions)
+        rc = self._lib.orc_set_axial(self._h, int(dz.size), _p(dz, _d), None if m3 is None else _p(m3, _i32),
+                                     int(bc[0]), int(bc[1]))
+        if rc:
+            raise RuntimeError("oracle: " + self._lib.orc_error(self._h).decode())
+        self.nz = int(dz.size)
+        self._dz, self._m3 = dz, m3
+
+    def flux3(self):
+        """(phi [nz][R][2][G]: plane-average and linear moments, k)."""
+        phi = np.zeros((self.nz, self.n_regions, 2, self.G))
+        k = ctypes.c_double()
+        self._lib.orc_get_flux3(self._h, _p(phi, _d), ctypes.byref(k))
+        return phi, k.value
+
+    def leakage3(self) -> np.ndarray:
+        """[3][G] leakage of the last DGMOC sweep: radial, bottom, top."""
+        a = np.zeros((3, self.G))
+        self._lib.orc_get_leakage3(self._h, _p(a, _d))
+        return a
+
     def set_state(self, phi=None, k: float = 1.0, psi=None):
         pp = None if phi is None else _f64(phi)
         ps = None if psi is None else _f64(psi)
-        if pp is not None:
+        if pp is not None and getattr(self, "nz", 0):
+            assert pp.size == self.nz * self.n_regions * 2 * self.G and ps is None
+        elif pp is not None:
             assert pp.size == self.n_regions * self.G
         if ps is not None:
             assert ps.size == self.n_tracks * 2 * self.n_polar * self.G
@@ -254,6 +291,23 @@ class Oracle:
 def legendre(l: int, x: float) -> float:
     """The oracle's Legendre polynomial P_l(x)."""
     return float(_load().orc_legendre(int(l), float(x)))
+
+
+def expm2(M) -> np.ndarray:
+    """The oracle's exponential of a 2 x 2 matrix."""
+    M = _f64(M).reshape(2, 2)
+    E = np.zeros((2, 2))
+    _load().orc_expm2(_p(M, _d), _p(E, _d))
+    return E
+
+
+def dg_segment(y0, psi_in, length, sin_theta, mu, h, sig, q0, q1s):
+    """One DGMOC segment: (y at the end, segment integral of y) for y = (a, b)."""
+    y0 = _f64(y0)
+    y1, yi = np.zeros(2), np.zeros(2)
+    _load().orc_dg_segment(_p(y0, _d), float(psi_in), float(length), float(sin_theta), float(mu), float(h),
+                           float(sig), float(q0), float(q1s), _p(y1, _d), _p(yi, _d))
+    return y1, yi
 
 
 def track_sweep(sig, qr, length, sin_theta: float, psi_in: float) -> np.ndarray:

@@ -21,6 +21,8 @@
  *    Eq. MOC_sol): phi = 4 pi q/Sigma_t + sum_k W_k (psi_in - psi_out)_k / (Sigma_t A_i);
  *  - k-eigenvalue power iteration (the fine-mesh MOC solve of Alg. 1, without its HFEM step; the
  *    CMFD step optional), one transport sweep per outer, Jacobi in energy and in boundary flux.
+ *  - DGMOC (Sec. 2.2, Alg. 2): the planar tracks extruded through axial planes, a linear
+ *    discontinuous-Galerkin expansion in z on every characteristic (see the DGMOC block below).
  *
  * Readings where the paper is silent (all also listed in the design notes):
  *  - A azimuths cover [0, 2 pi); for the first quadrant phi_a = 2 pi (a + 1/2)/A,
@@ -107,6 +109,17 @@ typedef struct {
   double *cur;        /* [2 n_if][G]: slot 2e a->b (a the lower id), 2e+1 b->a */
   double *cleak;      /* [n_cells][G] net current out of the domain boundary: out at every track end
                          (vacuum or reflective) minus in at every track start */
+  /* DGMOC: the planar tracks extruded through nz axial planes (0: the planar 2D method) */
+  int nz;
+  int bcz[2];         /* bottom, top: 0 vacuum 1 reflective */
+  double *dz;         /* [nz] plane heights */
+  int32_t *mat3;      /* [nz][R] material of each region in each plane */
+  double *phi3;       /* [nz][R][2][G] scalar flux moments: plane average, linear (xi) coefficient */
+  double *q3;         /* [nz][R][2][G] source moments per steradian */
+  double *tal3;       /* [nz][R][2][G] sum over segments of W * (segment integral of the moments) */
+  double *psi3_in, *psi3_next;  /* [T][2 sense][2 down/up][nz][P][2][G] radial boundary flux moments */
+  double *ztop;       /* [S][2 sense][P][G] upward top-face trace of the last sweep (reflective top) */
+  double *leak3;      /* [3][G] leakage of the last sweep: radial, bottom, top */
   char err[256];
 } orc_t;
 
@@ -130,6 +143,8 @@ void orc_destroy(orc_t *h) {
   free(h->cell); free(h->pairs); free(h->cur); free(h->cleak); free(h->color);
   free(h->nb_off); free(h->nb_cell); free(h->nb_in);
   free(h->ssl); free(h->kern); free(h->qdir); free(h->tdir); free(h->pbar);
+  free(h->dz); free(h->mat3); free(h->phi3); free(h->q3); free(h->tal3); free(h->psi3_in); free(h->psi3_next);
+  free(h->ztop); free(h->leak3);
   free(h);
 }
 
@@ -540,6 +555,10 @@ int orc_set_xs(orc_t *h, int n_mat, int G, const double *st, const double *nsf, 
   free(h->nb_off); free(h->nb_cell); free(h->nb_in);
   h->cell = NULL; h->pairs = NULL; h->cur = NULL; h->cleak = NULL; h->color = NULL; h->cmfd = 0;
   h->nb_off = h->nb_cell = h->nb_in = NULL;
+  free(h->dz); free(h->mat3); free(h->phi3); free(h->q3); free(h->tal3); free(h->psi3_in); free(h->psi3_next);
+  free(h->ztop); free(h->leak3);
+  h->dz = h->phi3 = h->q3 = h->tal3 = h->psi3_in = h->psi3_next = h->ztop = h->leak3 = NULL;
+  h->mat3 = NULL; h->nz = 0;
   h->n_mat = n_mat; h->G = G;
   h->st = xcalloc((size_t)n_mat * G, sizeof(double)); memcpy(h->st, st, (size_t)n_mat * G * sizeof(double));
   h->nsf = xcalloc((size_t)n_mat * G, sizeof(double)); memcpy(h->nsf, nsf, (size_t)n_mat * G * sizeof(double));
@@ -571,6 +590,7 @@ int orc_set_cmfd(orc_t *h, const int32_t *cell, int n_cells, int n_outer, int n_
   h->nb_off = h->nb_cell = h->nb_in = NULL;
   if (!cell) return 0;
   if (h->L) { snprintf(h->err, sizeof h->err, "CMFD with anisotropic scattering is not supported"); return -1; }
+  if (h->nz) { snprintf(h->err, sizeof h->err, "CMFD with DGMOC is not supported"); return -1; }
   h->cell = xcalloc(h->n_tri, sizeof(int32_t));
   memcpy(h->cell, cell, h->n_tri * sizeof(int32_t));
   int64_t np = 0;
@@ -667,6 +687,7 @@ int orc_set_scattering(orc_t *h, int L, const double *ssl) {
   h->ssl = h->kern = h->qdir = h->tdir = h->pbar = NULL; h->L = 0;
   if (L <= 0 || !ssl) return 0;
   if (h->cmfd) { snprintf(h->err, sizeof h->err, "anisotropic scattering with CMFD is not supported"); return -1; }
+  if (h->nz) { snprintf(h->err, sizeof h->err, "anisotropic scattering with DGMOC is not supported"); return -1; }
   int G = h->G, M = h->n_mat, P = h->n_polar;
   h->L = L;
   h->ND = 2 * h->n_dir * P;
@@ -703,6 +724,10 @@ void orc_set_fixed_source(orc_t *h, const double *S) {
   }
 }
 
+static void dg_set_state(orc_t *h, const double *phi3, double k);
+static double dg_outer(orc_t *h, int eigen);
+static double dg_fission_total(const orc_t *h, const double *phi3);
+
 /* F = sum_i A_i sum_g nuSigma_f phi */
 static double fission_total(const orc_t *h, const double *phi) {
   double F = 0.0;
@@ -716,6 +741,7 @@ static double fission_total(const orc_t *h, const double *phi) {
 }
 
 void orc_set_state(orc_t *h, const double *phi, double k, const double *psi) {
+  if (h->nz) { dg_set_state(h, phi, k); return; }   /* phi: [nz][R][2][G]; psi not used */
   size_t RG = (size_t)h->n_tri * h->G, PB = (size_t)h->n_tracks * 2 * h->n_polar * h->G;
   if (phi) memcpy(h->phi, phi, RG * sizeof(double)); else for (size_t i = 0; i < RG; ++i) h->phi[i] = 1.0;
   if (psi) memcpy(h->psi_in, psi, PB * sizeof(double)); else memset(h->psi_in, 0, PB * sizeof(double));
@@ -999,6 +1025,7 @@ static void cmfd_step(orc_t *h, double *phi_new) {
 /* One outer iteration: source, sweep, flux, and (eigen mode) k update + normalisation.
  * Returns the residual. */
 double orc_outer(orc_t *h, int eigen) {
+  if (h->nz) return dg_outer(h, eigen);
   int G = h->G;
   size_t RG = (size_t)h->n_tri * G, PB = (size_t)h->n_tracks * 2 * h->n_polar * G;
   double *phi_new = xcalloc(RG, sizeof(double));
@@ -1044,6 +1071,18 @@ double orc_outer(orc_t *h, int eigen) {
 
 /* Normalise the current state so that F = 1 (eigen mode). */
 void orc_normalise(orc_t *h) {
+  if (h->nz) {
+    double F3 = dg_fission_total(h, h->phi3);
+    size_t n3 = (size_t)h->nz * h->n_tri * 2 * h->G;
+    size_t nb = (size_t)h->n_tracks * 2 * 2 * h->nz * h->n_polar * 2 * h->G;
+    size_t nt = (size_t)h->n_seg * 2 * h->n_polar * h->G;
+    if (F3 > 0.0) {
+      for (size_t i = 0; i < n3; ++i) h->phi3[i] /= F3;
+      for (size_t i = 0; i < nb; ++i) h->psi3_in[i] /= F3;
+      for (size_t i = 0; i < nt; ++i) h->ztop[i] /= F3;
+    }
+    return;
+  }
   double F = fission_total(h, h->phi);
   size_t RG = (size_t)h->n_tri * h->G, PB = (size_t)h->n_tracks * 2 * h->n_polar * h->G;
   if (F > 0.0) {
@@ -1069,6 +1108,312 @@ int orc_iterate(orc_t *h, int eigen, double tol_k, double tol_f, int max_outer, 
   }
   *k_out = h->k; *n_out = n; *resid_out = resid;
   return conv ? 0 : 1;
+}
+
+/* ============================================================================================
+ * DGMOC (Sec. 2.2 "DGMOC formulation", Eq. DGMOC_expansion, DGMOC_weak, DGMOC_weak_up; the plane
+ * by plane upward/downward march of Alg. 2).
+ *
+ * The planar tracks are extruded through nz axial planes of heights dz. In plane i the angular
+ * flux along a track and the source are expanded in the Legendre basis u_1 = 1, u_2 = xi, with xi
+ * running from -1 at the plane's bottom to +1 at its top (n = 2 basis functions, first order, as
+ * in the paper). For an upward direction (polar cosine mu > 0, in-plane component sin(theta)),
+ * testing the transport equation with 1 and with xi over the plane, integrating the axial
+ * derivative by parts and taking the bottom-face value from the plane below (upwinding) gives,
+ * along the planar track coordinate s, with psi = a + b xi, q = q0 + q1 xi and c = mu / dz:
+ *     sin(theta) a' = q0 - Sigma_t a -   c (a + b - psi_in)
+ *     sin(theta) b' = q1 - Sigma_t b - 3 c (b - a + psi_in)
+ * i.e. y' = r - K y with y = (a, b), K = (Sigma_t I + c [[1, 1], [-3, 3]]) / sin(theta) and
+ * r = (q0 + c psi_in, q1 - 3 c psi_in) / sin(theta): a 2 x 2 matrix-exponential system on every
+ * segment. A downward direction is the mirror image xi -> -xi: the same system for (a, -b) with
+ * q1 negated, its inflow on the top face.
+ *
+ * Readings (where the paper is silent; also listed in the design notes):
+ *  - the inflow psi_in of a segment in plane i is the segment average of the outflow face trace
+ *    (a + b for upward travel) of the same segment in the plane upwind of it, computed earlier in
+ *    the same march (Alg. 2: the axial interface source of the next plane is formed after each
+ *    plane's ray tracing); flat along the segment, like the flat source;
+ *  - axial boundaries: vacuum (no inflow) or reflective. Each (track, sense, polar angle, group)
+ *    marches downward first (top plane to bottom), then upward. A reflective bottom feeds the
+ *    upward march with the downward march's bottom traces of the same sweep; a reflective top
+ *    feeds the downward march with the upward top traces of the previous sweep (lagged like the
+ *    radial boundary flux);
+ *  - radial boundary flux: both moments of every plane and both marches, routed through the
+ *    planar links (a reflection in x-y keeps mu), Jacobi-lagged as in the planar method;
+ *  - direction weight 2 pi omega_a w_p delta_a for each of the up and down copies of a polar
+ *    angle; the scalar flux moments are phi_m = sum over segments of W * integral of the
+ *    m-th coefficient / A_i (A_i the tracked area); the source moments are
+ *    q_m = [Sigma_s phi_m + chi/k nuSigma_f phi_m (+ S for m = 0)] / (4 pi);
+ *  - fission total F = sum over planes and regions of dz A_i sum_g nuSigma_f phi_0; the residual
+ *    is the planar one over (plane, region) elements.
+ * The per-segment system is solved from its definition: E = exp(-K l) by scaling and squaring a
+ * Taylor series, y_inf = K^{-1} r, y(l) = y_inf + E (y0 - y_inf) and the segment integral
+ * l y_inf + K^{-1} (y0 - y(l)).
+ * ============================================================================================ */
+
+/* exp(M) of a 2 x 2 matrix (row-major) by scaling and squaring a truncated Taylor series */
+void orc_expm2(const double *M, double *E) {
+  double nrm = fmax(fabs(M[0]) + fabs(M[1]), fabs(M[2]) + fabs(M[3]));
+  int sq = 0;
+  while (nrm > 0.25 && sq < 1100) { nrm *= 0.5; ++sq; }
+  double A[4];
+  double f = ldexp(1.0, -sq);
+  for (int i = 0; i < 4; ++i) A[i] = M[i] * f;
+  double S[4] = {1.0, 0.0, 0.0, 1.0}, T[4] = {1.0, 0.0, 0.0, 1.0};
+  for (int n = 1; n <= 24; ++n) {
+    double U[4] = {T[0] * A[0] + T[1] * A[2], T[0] * A[1] + T[1] * A[3],
+                   T[2] * A[0] + T[3] * A[2], T[2] * A[1] + T[3] * A[3]};
+    for (int i = 0; i < 4; ++i) { T[i] = U[i] / n; S[i] += T[i]; }
+  }
+  for (int k = 0; k < sq; ++k) {
+    double U[4] = {S[0] * S[0] + S[1] * S[2], S[0] * S[1] + S[1] * S[3],
+                   S[2] * S[0] + S[3] * S[2], S[2] * S[1] + S[3] * S[3]};
+    memcpy(S, U, sizeof U);
+  }
+  memcpy(E, S, sizeof S);
+}
+
+static void solve2(const double *K, const double *v, double *x) {
+  double det = K[0] * K[3] - K[1] * K[2];
+  x[0] = (K[3] * v[0] - K[1] * v[1]) / det;
+  x[1] = (K[0] * v[1] - K[2] * v[0]) / det;
+}
+
+/* One segment of one plane: y0 = (a, b) entering (b signed along the march, i.e. -b for a
+ * downward march), psi_in the axial inflow, q1s the linear source coefficient with the same
+ * sign convention. Returns y at the segment's end and the segment integral of y. */
+void orc_dg_segment(const double *y0, double psi_in, double len, double sin_theta, double mu, double h,
+                    double sig, double q0, double q1s, double *y1, double *yint) {
+  double c = mu / h;
+  double K[4] = {(sig + c) / sin_theta, c / sin_theta, -3.0 * c / sin_theta, (sig + 3.0 * c) / sin_theta};
+  double r[2] = {(q0 + c * psi_in) / sin_theta, (q1s - 3.0 * c * psi_in) / sin_theta};
+  double mK[4] = {-K[0] * len, -K[1] * len, -K[2] * len, -K[3] * len};
+  double E[4], yinf[2], d[2], w[2];
+  orc_expm2(mK, E);
+  solve2(K, r, yinf);
+  d[0] = y0[0] - yinf[0];
+  d[1] = y0[1] - yinf[1];
+  y1[0] = yinf[0] + E[0] * d[0] + E[1] * d[1];
+  y1[1] = yinf[1] + E[2] * d[0] + E[3] * d[1];
+  double dy[2] = {y0[0] - y1[0], y0[1] - y1[1]};
+  solve2(K, dy, w);
+  yint[0] = len * yinf[0] + w[0];
+  yint[1] = len * yinf[1] + w[1];
+}
+
+/* Switch to DGMOC on nz planes (call after orc_set_xs; mat3 [nz][R] or NULL for the planar
+ * materials in every plane). The state restarts flat: phi_0 = 1, phi_1 = 0, zero boundary flux. */
+int orc_set_axial(orc_t *h, int nz, const double *dz, const int32_t *mat3, int bc_bottom, int bc_top) {
+  free(h->dz); free(h->mat3); free(h->phi3); free(h->q3); free(h->tal3); free(h->psi3_in); free(h->psi3_next);
+  free(h->ztop); free(h->leak3);
+  h->dz = h->phi3 = h->q3 = h->tal3 = h->psi3_in = h->psi3_next = h->ztop = h->leak3 = NULL;
+  h->mat3 = NULL; h->nz = 0;
+  if (nz <= 0) return 0;
+  if (h->cmfd || h->L) { snprintf(h->err, sizeof h->err, "DGMOC with CMFD or anisotropic scattering is not supported"); return -1; }
+  if (!h->st) { snprintf(h->err, sizeof h->err, "set_axial before set_xs"); return -1; }
+  for (int z = 0; z < nz; ++z)
+    if (!(dz[z] > 0.0)) { snprintf(h->err, sizeof h->err, "plane heights must be > 0"); return -1; }
+  size_t R = h->n_tri, G = h->G, P = h->n_polar;
+  h->mat3 = xcalloc((size_t)nz * R, sizeof(int32_t));
+  for (int z = 0; z < nz; ++z)
+    for (size_t i = 0; i < R; ++i) {
+      int32_t m = mat3 ? mat3[(size_t)z * R + i] : h->mat[i];
+      if (m < 0 || m >= h->n_mat) { snprintf(h->err, sizeof h->err, "material id out of range"); free(h->mat3); h->mat3 = NULL; return -1; }
+      h->mat3[(size_t)z * R + i] = m;
+    }
+  h->nz = nz;
+  h->bcz[0] = bc_bottom ? 1 : 0;
+  h->bcz[1] = bc_top ? 1 : 0;
+  h->dz = xcalloc(nz, sizeof(double));
+  memcpy(h->dz, dz, nz * sizeof(double));
+  size_t n3 = (size_t)nz * R * 2 * G;
+  h->phi3 = xcalloc(n3, sizeof(double));
+  h->q3 = xcalloc(n3, sizeof(double));
+  h->tal3 = xcalloc(n3, sizeof(double));
+  size_t nb = (size_t)h->n_tracks * 2 * 2 * nz * P * 2 * G;
+  h->psi3_in = xcalloc(nb, sizeof(double));
+  h->psi3_next = xcalloc(nb, sizeof(double));
+  h->ztop = xcalloc((size_t)h->n_seg * 2 * P * G, sizeof(double));
+  h->leak3 = xcalloc(3 * G, sizeof(double));
+  dg_set_state(h, NULL, 1.0);
+  return 0;
+}
+
+static void dg_set_state(orc_t *h, const double *phi3, double k) {
+  size_t n3 = (size_t)h->nz * h->n_tri * 2 * h->G;
+  if (phi3) memcpy(h->phi3, phi3, n3 * sizeof(double));
+  else
+    for (size_t x = 0; x < n3; ++x) h->phi3[x] = (x / h->G) % 2 == 0 ? 1.0 : 0.0;
+  memset(h->psi3_in, 0, (size_t)h->n_tracks * 2 * 2 * h->nz * h->n_polar * 2 * h->G * sizeof(double));
+  memset(h->ztop, 0, (size_t)h->n_seg * 2 * h->n_polar * h->G * sizeof(double));
+  h->k = k;
+}
+
+void orc_get_flux3(const orc_t *h, double *phi3, double *k) {
+  if (phi3) memcpy(phi3, h->phi3, (size_t)h->nz * h->n_tri * 2 * h->G * sizeof(double));
+  if (k) *k = h->k;
+}
+
+void orc_get_leakage3(const orc_t *h, double *l) { memcpy(l, h->leak3, 3 * (size_t)h->G * sizeof(double)); }
+
+static double dg_fission_total(const orc_t *h, const double *phi3) {
+  int G = h->G;
+  double F = 0.0;
+  for (int z = 0; z < h->nz; ++z)
+    for (int i = 0; i < h->n_tri; ++i) {
+      const double *nf = h->nsf + (size_t)h->mat3[(size_t)z * h->n_tri + i] * G;
+      const double *ph = phi3 + ((size_t)z * h->n_tri + i) * 2 * G;
+      double f = 0.0;
+      for (int g = 0; g < G; ++g) f += nf[g] * ph[g];
+      F += h->dz[z] * h->area[i] * f;
+    }
+  return F;
+}
+
+/* source moments of every element */
+static void dg_source(orc_t *h, int eigen) {
+  int G = h->G;
+  for (int z = 0; z < h->nz; ++z)
+    for (int i = 0; i < h->n_tri; ++i) {
+      int m = h->mat3[(size_t)z * h->n_tri + i];
+      size_t e = ((size_t)z * h->n_tri + i) * 2 * G;
+      for (int mo = 0; mo < 2; ++mo) {
+        const double *ph = h->phi3 + e + (size_t)mo * G;
+        double fis = 0.0;
+        for (int gp = 0; gp < G; ++gp) fis += h->nsf[(size_t)m * G + gp] * ph[gp];
+        for (int g = 0; g < G; ++g) {
+          double src = 0.0;
+          for (int gp = 0; gp < G; ++gp) src += h->ss[((size_t)m * G + gp) * G + g] * ph[gp];
+          if (eigen) src += h->chi[(size_t)m * G + g] / h->k * fis;
+          if (mo == 0 && h->ext) src += h->ext[(size_t)i * G + g];
+          h->q3[e + (size_t)mo * G + g] = src / (4.0 * ORC_PI);
+        }
+      }
+    }
+}
+
+/* One DGMOC sweep: every track, sense, polar angle and group marches down through the planes,
+ * then up (Alg. 2), each plane a planar sweep of its segments with the axial inflow of the
+ * plane upwind. */
+static void dg_sweep(orc_t *h) {
+  int G = h->G, P = h->n_polar, nz = h->nz;
+  size_t R = h->n_tri;
+  memset(h->tal3, 0, (size_t)nz * R * 2 * G * sizeof(double));
+  memset(h->psi3_next, 0, (size_t)h->n_tracks * 2 * 2 * nz * P * 2 * G * sizeof(double));
+  int64_t maxn = 0;
+  for (int64_t t = 0; t < h->n_tracks; ++t)
+    if (h->seg_off[t + 1] - h->seg_off[t] > maxn) maxn = h->seg_off[t + 1] - h->seg_off[t];
+  double *lk = xcalloc(3 * (size_t)G, sizeof(double));
+#pragma omp parallel for schedule(static) num_threads(h->n_threads)
+  for (int g = 0; g < G; ++g) {
+    double *face = xcalloc(maxn ? maxn : 1, sizeof(double));
+    for (int64_t t = 0; t < h->n_tracks; ++t) {
+      int j = h->track_dir[t];
+      int64_t s0 = h->seg_off[t], ns = h->seg_off[t + 1] - s0;
+      for (int d = 0; d < 2; ++d)
+        for (int p = 0; p < P; ++p) {
+          double st = h->sin_theta[p], mu = sqrt(1.0 - st * st);
+          double W = 2.0 * ORC_PI * h->omega_a[j] * h->polar_w[p] * h->delta_a[j];
+          for (int ud = 0; ud < 2; ++ud) {      /* 0: downward march, 1: upward */
+            double sg = ud ? 1.0 : -1.0;        /* sign of xi along the march */
+            /* axial inflow of the first plane of the march */
+            for (int64_t n = 0; n < ns; ++n) {
+              int64_t s = d ? (s0 + ns - 1 - n) : (s0 + n);
+              if (ud == 0) face[n] = h->bcz[1] ? h->ztop[((size_t)s * 2 + d) * P * G + (size_t)p * G + g] : 0.0;
+              else if (!h->bcz[0]) face[n] = 0.0;   /* reflective bottom: keep the downward traces */
+            }
+            for (int zi = 0; zi < nz; ++zi) {
+              int z = ud ? zi : nz - 1 - zi;
+              size_t bidx = ((((size_t)(2 * t + d) * 2 + ud) * nz + z) * P + p) * 2 * G;
+              double y[2] = {h->psi3_in[bidx + g], h->psi3_in[bidx + G + g]};
+              for (int64_t n = 0; n < ns; ++n) {
+                int64_t s = d ? (s0 + ns - 1 - n) : (s0 + n);
+                int i = h->seg_reg[s];
+                int m = h->mat3[(size_t)z * R + i];
+                size_t e = ((size_t)z * R + i) * 2 * G;
+                double y1[2], yi[2];
+                orc_dg_segment(y, face[n], h->seg_len[s], st, mu, h->dz[z], h->st[(size_t)m * G + g],
+                               h->q3[e + g], sg * h->q3[e + G + g], y1, yi);
+                h->tal3[e + g] += W * yi[0];
+                h->tal3[e + G + g] += W * sg * yi[1];
+                face[n] = (yi[0] + yi[1]) / h->seg_len[s];   /* outflow face trace, segment average */
+                y[0] = y1[0];
+                y[1] = y1[1];
+              }
+              int64_t el = h->link[2 * t + d];
+              if (el >= 0) {
+                size_t o = ((((size_t)el * 2 + ud) * nz + z) * P + p) * 2 * G;
+                h->psi3_next[o + g] = y[0];
+                h->psi3_next[o + G + g] = y[1];
+              } else {
+                lk[g] += W * st * h->dz[z] * y[0];
+              }
+            }
+            /* the march's last face: bottom (downward) or top (upward) */
+            for (int64_t n = 0; n < ns; ++n) {
+              int64_t s = d ? (s0 + ns - 1 - n) : (s0 + n);
+              double J = W * mu * h->seg_len[s] * face[n];
+              if (ud == 0) { if (!h->bcz[0]) lk[(size_t)G + g] += J; }
+              else {
+                h->ztop[((size_t)s * 2 + d) * P * G + (size_t)p * G + g] = face[n];
+                if (!h->bcz[1]) lk[2 * (size_t)G + g] += J;
+              }
+            }
+          }
+        }
+    }
+    free(face);
+  }
+  memcpy(h->leak3, lk, 3 * (size_t)G * sizeof(double));
+  free(lk);
+}
+
+static double dg_outer(orc_t *h, int eigen) {
+  int G = h->G, nz = h->nz;
+  size_t R = h->n_tri, n3 = (size_t)nz * R * 2 * G;
+  size_t nb = (size_t)h->n_tracks * 2 * 2 * nz * h->n_polar * 2 * G;
+  size_t nt = (size_t)h->n_seg * 2 * h->n_polar * G;
+  dg_source(h, eigen);
+  dg_sweep(h);
+  double *pn = xcalloc(n3, sizeof(double));
+  for (int z = 0; z < nz; ++z)
+    for (size_t i = 0; i < R; ++i) {
+      int m = h->mat3[(size_t)z * R + i];
+      size_t e = ((size_t)z * R + i) * 2 * G;
+      for (int mo = 0; mo < 2; ++mo)
+        for (int g = 0; g < G; ++g) {
+          size_t x = e + (size_t)mo * G + g;
+          pn[x] = h->area[i] > 0.0 ? h->tal3[x] / h->area[i] : 4.0 * ORC_PI * h->q3[x] / h->st[(size_t)m * G + g];
+        }
+    }
+  double resid = 0.0;
+  if (eigen) {
+    double F_old = dg_fission_total(h, h->phi3), F_new = dg_fission_total(h, pn);
+    h->k = h->k * F_new / F_old;
+    for (size_t x = 0; x < n3; ++x) pn[x] /= F_new;
+    for (size_t x = 0; x < nb; ++x) h->psi3_next[x] /= F_new;
+    for (size_t x = 0; x < nt; ++x) h->ztop[x] /= F_new;
+    for (int x = 0; x < 3 * G; ++x) h->leak3[x] /= F_new;
+    for (int z = 0; z < nz; ++z)
+      for (size_t i = 0; i < R; ++i) {
+        const double *nf = h->nsf + (size_t)h->mat3[(size_t)z * R + i] * G;
+        size_t e = ((size_t)z * R + i) * 2 * G;
+        double fo = 0.0, fn = 0.0;
+        for (int g = 0; g < G; ++g) { fo += nf[g] * h->phi3[e + g] / F_old; fn += nf[g] * pn[e + g]; }
+        if (fn > 0.0) { double r = fabs(fn - fo) / fn; if (r > resid) resid = r; }
+      }
+  } else {
+    for (int z = 0; z < nz; ++z)
+      for (size_t i = 0; i < R; ++i)
+        for (int g = 0; g < G; ++g) {
+          size_t x = ((size_t)z * R + i) * 2 * G + g;
+          if (pn[x] > 0.0) { double r = fabs(pn[x] - h->phi3[x]) / pn[x]; if (r > resid) resid = r; }
+        }
+  }
+  memcpy(h->phi3, pn, n3 * sizeof(double));
+  free(pn);
+  double *tmp = h->psi3_in; h->psi3_in = h->psi3_next; h->psi3_next = tmp;
+  return resid;
 }
 
 /* One flat-source characteristic along a sequence of segments, one group and polar angle:
