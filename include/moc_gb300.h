@@ -230,6 +230,27 @@ int moc_outer(moc_ctx *ctx, int n, double *k_out, double *resid_out);
  * as after moc_outer (read with moc_outer(ctx, 0, &k, &r)). Errors: MOC_ERR_STATE, MOC_ERR_CUDA. */
 int moc_sweep_dev(moc_ctx *ctx, void *stream, const void *phi_in_dev, void *phi_out_dev);
 
+/* DGMOC (Sec. 2.2 "DGMOC formulation", Eq. DGMOC_expansion to DGMOC_weak_up; Alg. 2): extrude the
+ * planar tracks through nz axial planes of heights dz[nz] (cm, > 0) and solve the 3D problem with
+ * a linear discontinuous-Galerkin expansion in z on every characteristic (the angular flux in
+ * each plane is a + b xi, xi from -1 at the plane's bottom to +1 at its top; axial faces are
+ * upwinded; the inflow of a segment is the segment average of the upwind plane's outflow trace).
+ * mat3 [nz][n_regions] gives each region's material in each plane (NULL: the mesh's materials in
+ * every plane). bc_bottom, bc_top: 0 vacuum, 1 reflective (a reflective bottom feeds the upward
+ * march with the same sweep's bottom traces, a reflective top feeds the downward march with the
+ * previous sweep's top traces). Up to 4 polar angles; each polar angle serves an upward and a
+ * downward direction of weight 2 pi omega w_p delta. Call after moc_set_xs (moc_set_xs and new
+ * tracks switch DGMOC off); nz = 0 switches it off. Not combined with CMFD, anisotropic
+ * scattering, moc_sweep_dev or the warm start (MOC_ERR_STATE). The state restarts flat.
+ * While DGMOC is on: moc_set_state / moc_get_state take phi as [nz][n_regions][2][G] (plane
+ * average, then the xi coefficient of the scalar flux) and psi must be NULL (the boundary flux
+ * restarts at zero); moc_set_fixed_source's [n_regions][G] source applies in every plane; every
+ * other call (moc_outer, moc_power_iterate, timing, history) works as in the planar method, with
+ * the fission source summed as dz A nuSigma_f phi_0 and the residual over (plane, region) elements.
+ * FP32 modes tally in plain FP32 (no compensation). Errors: MOC_ERR_ARG (sizes, heights,
+ * material ids, more than 4 polar angles), MOC_ERR_STATE, MOC_ERR_OOM, MOC_ERR_CUDA. */
+int moc_set_axial(moc_ctx *ctx, int nz, const double *dz, const int32_t *mat3, int bc_bottom, int bc_top);
+
 /* Iteration history: every time the host reads k and the residual after outers (each check of
  * moc_power_iterate, moc_outer with k_out or resid_out), one entry {outers so far (since the last
  * moc_set_state), k, k before the last outer, residual} is recorded; the last 4,096 are kept.

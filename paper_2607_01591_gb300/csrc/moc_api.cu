@@ -15,6 +15,7 @@
 #include "moc_geom.h"
 #include "moc_aniso.cuh"
 #include "moc_cmfd.cuh"
+#include "moc_dg.cuh"
 #include "moc_track.h"
 #include "moc_kernels.cuh"
 
@@ -78,6 +79,16 @@ struct moc_ctx {
   unsigned *d_cticket = nullptr;
   void *h_stage = nullptr;    // pinned staging buffer for state transfers (grown on demand)
   size_t h_stage_bytes = 0;
+  // DGMOC (off unless moc_set_axial was called): nz planes, bottom/top condition
+  int dg_nz = 0;
+  int dg_bc[2] = {0, 0};
+  std::vector<double> h_dz;
+  std::vector<int32_t> h_mat3;
+  int32_t *d_mat3 = nullptr;
+  double *d_dz = nullptr, *d_fold3 = nullptr, *d_part3 = nullptr;
+  void *d_cz = nullptr, *d_wdg = nullptr, *d_sin = nullptr, *d_xs3 = nullptr, *d_phi3 = nullptr, *d_tal3 = nullptr;
+  void *d_psi3[2] = {nullptr, nullptr};
+  void *d_face = nullptr;
   // graphs: [parity of cur at launch]
   cudaGraphExec_t graph2[2] = {nullptr, nullptr};
   // iteration history: (outer count, k, k before, residual) at every host read of the scalars,
@@ -171,9 +182,30 @@ void free_aniso(moc_ctx *c) {
   c->aniso_L = c->aniso_NK = 0;
 }
 
+void free_dg(moc_ctx *c) {
+  drop_graphs(c);
+  dfree(c->d_mat3);
+  dfree(c->d_dz);
+  dfree(c->d_fold3);
+  dfree(c->d_part3);
+  dfree(c->d_cz);
+  dfree(c->d_wdg);
+  dfree(c->d_sin);
+  dfree(c->d_xs3);
+  dfree(c->d_phi3);
+  dfree(c->d_tal3);
+  dfree(c->d_psi3[0]);
+  dfree(c->d_psi3[1]);
+  dfree(c->d_face);
+  c->dg_nz = 0;
+  c->h_dz.clear();
+  c->h_mat3.clear();
+}
+
 void free_problem(moc_ctx *c) {
   free_cmfd(c);
   free_aniso(c);
+  free_dg(c);
   drop_graphs(c);
   dfree(c->d_xsq);
   dfree(c->d_phi);
@@ -633,7 +665,55 @@ template <typename Real> int launch_aniso_init(moc_ctx *c, cudaStream_t st) {
   return MOC_OK;
 }
 
+// ----------------------------------------------------------------------------- DGMOC launches
+template <typename Real> int launch_dg_source(moc_ctx *c, cudaStream_t st) {
+  const int R = c->geo.n_tri, E = c->dg_nz * R;
+  const size_t sm = (size_t)c->M * c->G * c->G * sizeof(Real);
+  dg_source_kernel<Real><<<(E + 127) / 128, 128, sm, st>>>(
+      E, R, c->G, c->Gp, c->M, c->d_mat3, (const Real *)c->d_sig_t, (const Real *)c->d_nsf, (const Real *)c->d_chi,
+      (const Real *)c->d_sig_s, c->d_ext, (Real *)c->d_phi3, (DgXs<Real> *)c->d_xs3, c->d_fold3, c->d_scal,
+      c->eigen ? 1 : 0);
+  CUDA_TRY(c, cudaGetLastError());
+  return MOC_OK;
+}
+
+template <typename Real, int P> void dg_sweep_launch(moc_ctx *c, cudaStream_t st) {
+  const long long n = (long long)c->T * 2 * c->G;
+  dg_sweep_kernel<Real, P><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(
+      c->d_trk, (const SegRec<Real> *)c->d_seg, c->d_link, (const Real *)c->d_wdg, (const Real *)c->d_sin,
+      (const Real *)c->d_inv_sin, (const Real *)c->d_cz, (const DgXs<Real> *)c->d_xs3, (Real *)c->d_tal3,
+      (const Real *)c->d_psi3[c->cur], (Real *)c->d_psi3[c->cur ^ 1], (Real *)c->d_face, c->d_scal, n, c->G, c->Gp,
+      c->geo.n_tri, c->dg_nz, c->dg_bc[0], c->dg_bc[1]);
+}
+
+template <typename Real> int launch_dg_sweep(moc_ctx *c, cudaStream_t st) {
+  if (c->T > 0) {
+    switch (c->P) {
+      case 1: dg_sweep_launch<Real, 1>(c, st); break;
+      case 2: dg_sweep_launch<Real, 2>(c, st); break;
+      case 3: dg_sweep_launch<Real, 3>(c, st); break;
+      case 4: dg_sweep_launch<Real, 4>(c, st); break;
+      default: return fail(c, MOC_ERR_ARG, "DGMOC: up to 4 polar angles");
+    }
+  }
+  CUDA_TRY(c, cudaGetLastError());
+  return MOC_OK;
+}
+
+template <typename Real> int launch_dg_finalize(moc_ctx *c, cudaStream_t st) {
+  const int R = c->geo.n_tri, E = c->dg_nz * R;
+  const int nb = (E + 255) / 256;
+  dg_finalize_kernel<Real><<<nb, 256, 0, st>>>(E, R, c->G, c->Gp, c->d_mat3, (const Real *)c->d_nsf, c->d_area,
+                                               c->d_dz, (const DgXs<Real> *)c->d_xs3, (Real *)c->d_tal3,
+                                               (Real *)c->d_phi3, c->d_fold3, c->d_part3, c->eigen ? 1 : 0);
+  CUDA_TRY(c, cudaGetLastError());
+  reduce_kernel<<<1, 256, 0, st>>>(nb, c->d_part3, c->d_scal, c->eigen ? 1 : 0);
+  CUDA_TRY(c, cudaGetLastError());
+  return MOC_OK;
+}
+
 int enqueue_source(moc_ctx *c, cudaStream_t st) {
+  if (c->dg_nz) return c->precision == MOC_FP64 ? launch_dg_source<double>(c, st) : launch_dg_source<float>(c, st);
   int rc = c->precision == MOC_FP64 ? launch_source<double>(c, st) : launch_source<float>(c, st);
   if (rc || !c->aniso_L) return rc;
   return c->precision == MOC_FP64 ? launch_aniso_source<double>(c, st) : launch_aniso_source<float>(c, st);
@@ -703,10 +783,17 @@ int enqueue_sweep(moc_ctx *c, cudaStream_t st, bool timed) {
     CUDA_TRY(c, cudaEventCreate(&e1));
     CUDA_TRY(c, cudaEventRecord(e0, st));
   }
-  if ((rc = launch_sweep(c, st))) return rc;
+  if (c->dg_nz) rc = c->precision == MOC_FP64 ? launch_dg_sweep<double>(c, st) : launch_dg_sweep<float>(c, st);
+  else rc = launch_sweep(c, st);
+  if (rc) return rc;
   if (timed) {
     CUDA_TRY(c, cudaEventRecord(e1, st));
     c->ev.push_back({e0, e1});
+  }
+  if (c->dg_nz) {
+    rc = c->precision == MOC_FP64 ? launch_dg_finalize<double>(c, st) : launch_dg_finalize<float>(c, st);
+    c->cur ^= 1;
+    return rc;
   }
   if (c->aniso_L) {
     rc = c->precision == MOC_FP64 ? launch_aniso_moments<double>(c, st) : launch_aniso_moments<float>(c, st);
@@ -866,8 +953,143 @@ template <typename Real> int state_out(moc_ctx *c, double *dphi, double *dpsi, d
 
 }  // namespace
 
+namespace {
+
+// DGMOC state: flux moments phi [nz][R][2][G] (NULL: phi_0 = 1, phi_1 = 0), zero radial and axial
+// boundary flux, scalars reset with k and the normalisation 1/F
+template <typename Real> int dg_set_state(moc_ctx *c, const double *phi, double k, const double *psi) {
+  if (psi) return fail(c, MOC_ERR_ARG, "set_state: with DGMOC the boundary flux restarts at zero (psi must be NULL)");
+  const int R = c->geo.n_tri, G = c->G, nz = c->dg_nz;
+  const long long E = (long long)nz * R;
+  double scale = 1.0;
+  if (c->eigen) {
+    double F = 0.0;
+    for (long long e = 0; e < E; ++e) {
+      const int m = c->h_mat3[e];
+      double f = 0.0;
+      for (int g = 0; g < G; ++g) f += c->h_nsf[(size_t)m * G + g] * (phi ? phi[(size_t)e * 2 * G + g] : 1.0);
+      F += c->h_dz[e / R] * c->geo.area[e % R] * f;
+    }
+    if (!std::isfinite(F)) return fail(c, MOC_ERR_ARG, "set_state: the fission source of the state is not finite");
+    if (F > 0.0) scale = 1.0 / F;
+  }
+  double *dphi = nullptr;
+  if (phi) {
+    CUDA_TRY(c, cudaMalloc(&dphi, (size_t)E * 2 * G * sizeof(double)));
+    cudaError_t e = cudaMemcpyAsync(dphi, phi, (size_t)E * 2 * G * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) {
+      cudaFree(dphi);
+      return fail(c, MOC_ERR_CUDA, std::string("set_state: ") + cudaGetErrorString(e));
+    }
+  }
+  const long long n = E * c->Gp * 2;
+  dg_phi_in_kernel<Real><<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(n, G, c->Gp, dphi, (Real *)c->d_phi3);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (dphi) cudaFree(dphi);
+  if (e != cudaSuccess) return fail(c, MOC_ERR_CUDA, std::string("set_state: ") + cudaGetErrorString(e));
+  const size_t nb = (size_t)c->T * 2 * 2 * nz * c->P * 2 * G * sizeof(Real);
+  CUDA_TRY(c, cudaMemsetAsync(c->d_psi3[0], 0, nb, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_psi3[1], 0, nb, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_face, 0, (size_t)(c->S + 2 * kSegPad) * 2 * c->P * G * sizeof(Real), c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_tal3, 0, (size_t)E * c->Gp * 2 * sizeof(Real), c->stream));
+  return reset_scalars(c, k, scale);
+}
+
+template <typename Real> int dg_get_state(moc_ctx *c, double *phi, double *k, double *psi) {
+  if (psi) return fail(c, MOC_ERR_ARG, "get_state: with DGMOC only the flux moments are returned (psi must be NULL)");
+  double s[S_COUNT];
+  int rc = read_scalars(c, s);
+  if (rc) return rc;
+  if (k) *k = s[S_K];
+  if (!phi) return MOC_OK;
+  const long long E = (long long)c->dg_nz * c->geo.n_tri, n = E * 2 * c->G;
+  double *dphi = nullptr;
+  CUDA_TRY(c, cudaMalloc(&dphi, (size_t)n * sizeof(double)));
+  dg_phi_out_kernel<Real><<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
+      n, c->G, c->Gp, (const Real *)c->d_phi3, c->eigen ? s[S_SCALE] : 1.0, dphi);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(phi, dphi, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(dphi);
+  if (e != cudaSuccess) return fail(c, MOC_ERR_CUDA, std::string("get_state: ") + cudaGetErrorString(e));
+  return MOC_OK;
+}
+
+template <typename Real> int dg_alloc(moc_ctx *c) {
+  const int R = c->geo.n_tri, G = c->G, Gp = c->Gp, P = c->P, nz = c->dg_nz, nd = c->geo.n_dir;
+  const size_t E = (size_t)nz * R;
+  std::vector<Real> cz((size_t)nz * P), wdg((size_t)nd * P), sn(P);
+  for (int p = 0; p < P; ++p) {
+    const double st = c->geo.sin_theta[p];
+    sn[p] = (Real)st;
+    for (int z = 0; z < nz; ++z) cz[(size_t)z * P + p] = (Real)(std::sqrt(std::max(0.0, 1.0 - st * st)) / c->h_dz[z]);
+    for (int j = 0; j < nd; ++j)
+      wdg[(size_t)j * P + p] = (Real)(0.5 * kFourPi * c->geo.omega[j] * c->geo.polar_w[p] * c->geo.delta[j]);
+  }
+  int rc;
+  Real *p_cz = nullptr, *p_w = nullptr, *p_s = nullptr;
+  if ((rc = upload(c, p_cz, cz.data(), cz.size()))) return rc;
+  c->d_cz = p_cz;
+  if ((rc = upload(c, p_w, wdg.data(), wdg.size()))) return rc;
+  c->d_wdg = p_w;
+  if ((rc = upload(c, p_s, sn.data(), sn.size()))) return rc;
+  c->d_sin = p_s;
+  if ((rc = upload(c, c->d_mat3, c->h_mat3.data(), c->h_mat3.size()))) return rc;
+  if ((rc = upload(c, c->d_dz, c->h_dz.data(), c->h_dz.size()))) return rc;
+  CUDA_TRY(c, cudaMalloc(&c->d_xs3, E * Gp * sizeof(DgXs<Real>)));
+  CUDA_TRY(c, cudaMemset(c->d_xs3, 0, E * Gp * sizeof(DgXs<Real>)));
+  CUDA_TRY(c, cudaMalloc(&c->d_phi3, E * Gp * 2 * sizeof(Real)));
+  CUDA_TRY(c, cudaMalloc(&c->d_tal3, E * Gp * 2 * sizeof(Real)));
+  const size_t nb = (size_t)c->T * 2 * 2 * nz * P * 2 * G;
+  CUDA_TRY(c, cudaMalloc(&c->d_psi3[0], std::max<size_t>(nb, 1) * sizeof(Real)));
+  CUDA_TRY(c, cudaMalloc(&c->d_psi3[1], std::max<size_t>(nb, 1) * sizeof(Real)));
+  CUDA_TRY(c, cudaMalloc(&c->d_face, (size_t)(c->S + 2 * kSegPad) * 2 * P * G * sizeof(Real)));
+  CUDA_TRY(c, cudaMalloc((void **)&c->d_fold3, E * sizeof(double)));
+  CUDA_TRY(c, cudaMemset(c->d_fold3, 0, E * sizeof(double)));
+  CUDA_TRY(c, cudaMalloc((void **)&c->d_part3, ((E + 255) / 256) * 4 * sizeof(double)));
+  return MOC_OK;
+}
+
+}  // namespace
+
 // ====================================================================================== C ABI
 extern "C" {
+
+int moc_set_axial(moc_ctx *c, int nz, const double *dz, const int32_t *mat3, int bc_bottom, int bc_top) {
+  int rc = need_ready(c);
+  if (rc) return rc;
+  cudaSetDevice(c->device);
+  free_dg(c);
+  if (nz == 0) return moc_set_state(c, nullptr, 1.0, nullptr);
+  if (nz < 0 || !dz) return fail(c, MOC_ERR_ARG, "set_axial: nz > 0 plane heights required");
+  if (c->cmfd || c->aniso_L) return fail(c, MOC_ERR_STATE, "set_axial: not combined with CMFD or anisotropic scattering");
+  if (c->P > 4) return fail(c, MOC_ERR_ARG, "set_axial: up to 4 polar angles");
+  const int R = c->geo.n_tri;
+  if ((long long)nz * R >= (1LL << 31)) return fail(c, MOC_ERR_ARG, "set_axial: nz * n_regions too large");
+  for (int z = 0; z < nz; ++z)
+    if (!(dz[z] > 0.0) || !std::isfinite(dz[z])) return fail(c, MOC_ERR_ARG, "set_axial: plane heights must be finite and > 0");
+  std::vector<int32_t> m3((size_t)nz * R);
+  for (int z = 0; z < nz; ++z)
+    for (int r = 0; r < R; ++r) {
+      const int32_t m = mat3 ? mat3[(size_t)z * R + r] : c->geo.mat[r];
+      if (m < 0 || m >= c->M) return fail(c, MOC_ERR_ARG, "set_axial: a material id is out of range");
+      m3[(size_t)z * R + r] = m;
+    }
+  for (double ph : c->geo.omega)
+    if (!std::isfinite(ph)) return fail(c, MOC_ERR_STATE, "set_axial: direction weights unknown");
+  c->h_mat3 = std::move(m3);
+  c->h_dz.assign(dz, dz + nz);
+  c->dg_nz = nz;
+  c->dg_bc[0] = bc_bottom ? 1 : 0;
+  c->dg_bc[1] = bc_top ? 1 : 0;
+  rc = c->precision == MOC_FP64 ? dg_alloc<double>(c) : dg_alloc<float>(c);
+  if (rc) {
+    free_dg(c);
+    return rc;
+  }
+  return moc_set_state(c, nullptr, 1.0, nullptr);
+}
 
 int moc_create(moc_ctx **out, int device, int precision, void *stream) {
   if (!out) return MOC_ERR_ARG;
@@ -1115,6 +1337,7 @@ int moc_set_scattering(moc_ctx *c, int L, const double *sigma_sl) {
   if (L == 0 || !sigma_sl) return MOC_OK;
   if (L < 0 || L > kMaxAnisoL) return fail(c, MOC_ERR_ARG, "set_scattering: 0 <= L <= 3");
   if (c->cmfd) return fail(c, MOC_ERR_STATE, "set_scattering: not combined with CMFD acceleration");
+  if (c->dg_nz) return fail(c, MOC_ERR_STATE, "set_scattering: not combined with DGMOC");
   if (c->P > 3) return fail(c, MOC_ERR_ARG, "set_scattering: up to 3 polar angles");
   for (double ph : c->geo.phi)
     if (!std::isfinite(ph)) return fail(c, MOC_ERR_STATE, "set_scattering: the track directions' angles are unknown (tracks set by the caller)");
@@ -1199,6 +1422,7 @@ int moc_set_cmfd(moc_ctx *c, const int32_t *cell_in, int n_cells, int n_outer, i
   free_cmfd(c);
   if (!cell_in) return MOC_OK;
   if (c->aniso_L) return fail(c, MOC_ERR_STATE, "set_cmfd: not combined with anisotropic scattering");
+  if (c->dg_nz) return fail(c, MOC_ERR_STATE, "set_cmfd: not combined with DGMOC");
   const Geometry &g = c->geo;
   const int R = g.n_tri, G = c->G;
   if (n_cells < 1 || n_outer < 1 || n_inner < 1) return fail(c, MOC_ERR_ARG, "set_cmfd: bad sizes or iteration counts");
@@ -1487,6 +1711,7 @@ int moc_set_state(moc_ctx *c, const double *phi, double k, const double *psi) {
   if (!(k > 0.0) || !std::isfinite(k)) return fail(c, MOC_ERR_ARG, "set_state: k must be finite and > 0");
   c->hist_n = 0;
   cudaSetDevice(c->device);
+  if (c->dg_nz) return c->precision == MOC_FP64 ? dg_set_state<double>(c, phi, k, psi) : dg_set_state<float>(c, phi, k, psi);
   double scale = 1.0;
   if (c->eigen) {
     double F = host_fission(c, phi, c->h_nsf);
@@ -1514,6 +1739,7 @@ int moc_get_state(moc_ctx *c, double *phi, double *k, double *psi) {
   int rc = need_ready(c);
   if (rc) return rc;
   cudaSetDevice(c->device);
+  if (c->dg_nz) return c->precision == MOC_FP64 ? dg_get_state<double>(c, phi, k, psi) : dg_get_state<float>(c, phi, k, psi);
   double s[S_COUNT];
   void *vphi = (void *)host_view(c, phi), *vpsi = (void *)host_view(c, psi);
   if ((phi || psi) && (!phi || vphi) && (!psi || vpsi)) {
@@ -1600,6 +1826,7 @@ extern "C" {
 int moc_sweep_dev(moc_ctx *c, void *stream, const void *phi_in_dev, void *phi_out_dev) {
   int rc = need_ready(c);
   if (rc) return rc;
+  if (c->dg_nz) return fail(c, MOC_ERR_STATE, "sweep_dev: planar method only (DGMOC is on)");
   cudaSetDevice(c->device);
   cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
   if (st != c->stream) {
@@ -1716,8 +1943,11 @@ int moc_get_timing(moc_ctx *c, double *ms, int64_t *n) {
 int moc_get_work(const moc_ctx *c, int64_t *n_segments, int64_t *updates, int *kernels) {
   if (!c || !c->geo.has_tracks) return c ? MOC_ERR_STATE : MOC_ERR_ARG;
   if (n_segments) *n_segments = c->geo.n_segments();
-  if (updates) *updates = 2 * c->geo.n_segments() * (int64_t)c->geo.n_polar * (int64_t)std::max(c->G, 0);
-  if (kernels) *kernels = ((c->Gp == 8) ? 3 : 4) + (c->cmfd ? 5 : 0) + (c->aniso_L ? 2 : 0);
+  // DGMOC: every segment in every plane, both marches
+  const int64_t planes = c->dg_nz ? 2 * (int64_t)c->dg_nz : 1;
+  if (updates) *updates = 2 * c->geo.n_segments() * (int64_t)c->geo.n_polar * (int64_t)std::max(c->G, 0) * planes;
+  if (kernels)
+    *kernels = c->dg_nz ? 4 : ((c->Gp == 8) ? 3 : 4) + (c->cmfd ? 5 : 0) + (c->aniso_L ? 2 : 0);
   return MOC_OK;
 }
 
@@ -1741,6 +1971,7 @@ extern "C" {
 int moc_ws_features(moc_ctx *c, const float *geo, int n_geo, const float *glob, int n_glob, float *feat) {
   int rc = need_ready(c);
   if (rc) return rc;
+  if (c->dg_nz) return fail(c, MOC_ERR_STATE, "ws_features: planar method only (DGMOC is on)");
   if (n_geo < 0 || n_glob < 0 || (n_geo > 0 && !geo) || (n_glob > 0 && !glob) || !feat)
     return fail(c, MOC_ERR_ARG, "ws_features: bad arguments");
   cudaSetDevice(c->device);
@@ -1780,6 +2011,7 @@ extern "C" {
 int moc_ws_apply(moc_ctx *c, const float *pred, double *k_out) {
   int rc = need_ready(c);
   if (rc) return rc;
+  if (c->dg_nz) return fail(c, MOC_ERR_STATE, "ws_apply: planar method only (DGMOC is on)");
   if (!pred) return fail(c, MOC_ERR_ARG, "ws_apply: NULL prediction");
   if (!c->eigen) return fail(c, MOC_ERR_STATE, "ws_apply: eigenvalue mode only");
   cudaSetDevice(c->device);

@@ -1,0 +1,314 @@
+// DGMOC kernels (Sec. 2.2 "DGMOC formulation", Eq. DGMOC_expansion to DGMOC_weak_up; the
+// plane-by-plane upward/downward march of Alg. 2): the planar tracks extruded through nz axial
+// planes, the angular flux on each characteristic expanded in every plane as a + b xi (xi from -1
+// at the plane's bottom to +1 at its top), axial faces upwinded.
+//
+// Along a track, for a march in the direction of increasing xi (upward; a downward march is the
+// same system for (a, -b) with the linear source negated), c = mu / dz:
+//     y' = r - K y,   y = (a, b),   K = [(Sigma_t + 2c) I + c N] / sin(theta),   N = [[-1, 1], [-3, 1]],
+//     r = (q0 + c psi_in, q1 - 3 c psi_in) / sin(theta),
+// with psi_in the axial inflow (segment average of the upwind plane's outflow trace a + b).
+// N^2 = -2 I, so every function of K is a combination of I and N: with
+//     gamma = (Sigma_t + 2c) l / sin(theta),  beta = sqrt(2) c l / sin(theta),
+//     exp(-K l) = e^-gamma [cos(beta) I - sin(beta)/sqrt(2) N],
+//     K^-1 = sin(theta) [(Sigma_t + 2c) I - c N] / D,   D = (Sigma_t + 2c)^2 + 2 c^2,
+// and one segment is
+//     y_inf = [(Sigma_t + 2c) rr - c N rr] / D          (rr = sin(theta) r: sin(theta) cancels),
+//     (I - E)(y0 - y_inf) = A0 d + A1 N d,  d = y0 - y_inf,
+//         A0 = (1 - e^-gamma) + e^-gamma 2 sin^2(beta/2),  A1 = e^-gamma sin(beta)/sqrt(2),
+//     y(l) = y0 - (I - E) d,
+//     integral of y over the segment = l y_inf + K^-1 (y0 - y(l)).
+// The closed forms avoid a general matrix exponential and any cancellation in 1 - e^-gamma.
+//
+// Per outer: dg_source_kernel (source moments), dg_sweep_kernel (both marches of every track,
+// sense, polar angle and group), dg_finalize_kernel (flux moments, FP64 block partials), and the
+// planar reduce_kernel (k, normalisation, residual).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "moc_kernels.cuh"
+
+namespace moc {
+
+template <typename Real> struct alignas(4 * sizeof(Real)) DgXs {
+  Real t;    // Sigma_t
+  Real q0;   // plane-average source per steradian
+  Real q1;   // linear (xi) source coefficient per steradian
+  Real pad;
+};
+
+template <typename Real> struct DgMath;
+template <> struct DgMath<double> {
+  __device__ static double one_minus_exp(double x) { return -expm1(-x); }
+  __device__ static void sincos_(double x, double *s, double *c) { sincos(x, s, c); }
+};
+template <> struct DgMath<float> {
+  __device__ static float one_minus_exp(float x) { return moc::one_minus_exp(x); }
+  __device__ static void sincos_(float x, float *s, float *c) { sincosf(x, s, c); }
+};
+
+// Source moments of every element (plane z, region r): one thread per element.
+// phi3 [E][Gp][2] (m fastest), E = nz * R, is scaled by the pending normalisation first; fold[e]
+// receives the element's normalised fission rate.
+template <typename Real>
+__global__ void dg_source_kernel(int E, int R, int G, int Gp, int M, const int32_t *__restrict__ mat3,
+                                 const Real *__restrict__ sig_t, const Real *__restrict__ nsf,
+                                 const Real *__restrict__ chi, const Real *__restrict__ sig_s,
+                                 const double *__restrict__ ext, Real *__restrict__ phi3, DgXs<Real> *__restrict__ xs3,
+                                 double *__restrict__ fold, const double *__restrict__ scal, int eigen) {
+  extern __shared__ unsigned char smem_raw[];
+  Real *s_ss = reinterpret_cast<Real *>(smem_raw);  // [M][G][G]
+  for (int i = threadIdx.x; i < M * G * G; i += blockDim.x) s_ss[i] = sig_s[i];
+  __syncthreads();
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const int r = e % R;
+  const int m = mat3[e];
+  const Real scale = eigen ? (Real)scal[S_SCALE] : (Real)1;
+  const Real inv_k = eigen ? (Real)(1.0 / scal[S_K]) : (Real)0;
+  Real *ph = phi3 + (size_t)e * Gp * 2;
+  Real fis0 = 0, fis1 = 0;
+  for (int g = 0; g < G; ++g) {
+    const Real v0 = ph[2 * g] * scale, v1 = ph[2 * g + 1] * scale;
+    ph[2 * g] = v0;
+    ph[2 * g + 1] = v1;
+    fis0 += nsf[m * G + g] * v0;
+    fis1 += nsf[m * G + g] * v1;
+  }
+  if (eigen) fold[e] = (double)fis0;
+  const Real *ss = s_ss + (size_t)m * G * G;
+  const Real inv4pi = (Real)(1.0 / kFourPi);
+  for (int g = 0; g < G; ++g) {
+    Real s0 = 0, s1 = 0;
+    for (int gp = 0; gp < G; ++gp) {
+      s0 += ss[gp * G + g] * ph[2 * gp];
+      s1 += ss[gp * G + g] * ph[2 * gp + 1];
+    }
+    s0 += chi[m * G + g] * inv_k * fis0;
+    s1 += chi[m * G + g] * inv_k * fis1;
+    if (ext) s0 += (Real)ext[(size_t)r * G + g];
+    DgXs<Real> x;
+    x.t = sig_t[m * G + g];
+    x.q0 = s0 * inv4pi;
+    x.q1 = s1 * inv4pi;
+    x.pad = 0;
+    xs3[(size_t)e * Gp + g] = x;
+  }
+}
+
+template <typename Real> __device__ __forceinline__ void dg_tally(Real *t, Real a0, Real a1) {
+  atomicAdd(t, a0);
+  atomicAdd(t + 1, a1);
+}
+template <> __device__ __forceinline__ void dg_tally<float>(float *t, float a0, float a1) {
+  atomicAdd(reinterpret_cast<float2 *>(t), make_float2(a0, a1));
+}
+
+// One thread per (track, sense, group); polar angles in registers. The thread marches its track
+// down through the planes (top first), then up, each plane a pass over the track's segments. The
+// axial inflow of a segment comes from `face`, where the same thread stored the segment's outflow
+// trace in the previous plane of the march, so no other thread is involved:
+//   face [S + pad][2 sense][P][G]: before the downward march it holds the previous sweep's upward
+//   top traces (used if the top is reflective), after it the bottom traces (used by the upward
+//   march if the bottom is reflective), after the upward march the top traces again.
+// Radial boundary moments psi3 [2T][2 march][nz][P][2][G] are routed through the planar links
+// (Jacobi, double-buffered). Tally [E][Gp][2]: sum of W * segment integral of (a, b) per element.
+template <typename Real, int P>
+__global__ void __launch_bounds__(128) dg_sweep_kernel(
+    const TrackRec *__restrict__ trk, const SegRec<Real> *__restrict__ seg, const int32_t *__restrict__ link,
+    const Real *__restrict__ wdg, const Real *__restrict__ sin_t, const Real *__restrict__ inv_sin,
+    const Real *__restrict__ cz, const DgXs<Real> *__restrict__ xs3, Real *__restrict__ tally,
+    const Real *__restrict__ psi_in, Real *__restrict__ psi_out, Real *__restrict__ face,
+    const double *__restrict__ scal, long long n_threads, int G, int Gp, int R, int nz, int bc_bottom, int bc_top) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n_threads) return;
+  const long long td = idx / G;
+  const int g = (int)(idx - td * G);
+  const TrackRec tr = trk[td >> 1];
+  const int d = (int)(td & 1);
+  const Real scale = (Real)scal[S_SCALE];
+  Real w[P], st[P], is[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    w[p] = wdg[tr.dir * P + p];
+    st[p] = sin_t[p];
+    is[p] = inv_sin[p];
+  }
+  const int step = d ? -1 : 1;
+  const long long s_first = d ? tr.off + tr.n - 1 : tr.off;
+  const Real rs2 = (Real)0.70710678118654752440;  // 1/sqrt(2)
+  const int e_out = link[td];
+  for (int ud = 0; ud < 2; ++ud) {
+    const Real sg = ud ? (Real)1 : (Real)-1;
+    // inflow of the march's first plane: reflective top (downward) reads the previous sweep's
+    // top traces in the previous normalisation; reflective bottom (upward) this sweep's bottom
+    // traces; vacuum: none
+    const bool refl = ud ? (bc_bottom != 0) : (bc_top != 0);
+    const Real f0scale = ud ? (Real)1 : scale;
+    for (int zi = 0; zi < nz; ++zi) {
+      const int z = ud ? zi : nz - 1 - zi;
+      const bool first = (zi == 0);
+      const Real fmul = first ? (refl ? f0scale : (Real)0) : (Real)1;
+      Real y0[P], y1[P], c[P];
+      const long long bb = (((td * 2 + ud) * nz + z) * P) * 2;
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        y0[p] = psi_in[(bb + 2 * p) * G + g] * scale;
+        y1[p] = psi_in[(bb + 2 * p + 1) * G + g] * scale;
+        c[p] = cz[z * P + p];
+      }
+      const DgXs<Real> *xz = xs3 + (size_t)z * R * Gp + g;
+      Real *tz = tally + ((size_t)z * R * Gp + g) * 2;
+      const SegRec<Real> *sp = seg + s_first;
+      Real *fp = face + ((s_first * 2 + d) * P) * G + g;
+      const long long fstep = (long long)step * 2 * P * G;
+      for (int n = 0; n < tr.n; ++n) {
+        const SegRec<Real> s = *sp;
+        const DgXs<Real> x = xz[(size_t)s.r * Gp];
+        const Real q1s = sg * x.q1;
+        Real a0 = 0, a1 = 0;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          // a vacuum or reflective first inflow is zero or the stored trace, without branching
+          const Real fin = fp[p * G];
+          const Real pin = fmul == (Real)0 ? (Real)0 : fin * fmul;
+          const Real cc = c[p];
+          const Real al = x.t + 2 * cc;
+          const Real iD = (Real)1 / (al * al + 2 * cc * cc);
+          // y_inf = (al rr - c N rr) / D
+          const Real r0 = x.q0 + cc * pin, r1 = q1s - 3 * cc * pin;
+          const Real n0 = r1 - r0, n1 = r1 - 3 * r0;  // N rr
+          const Real yi0 = (al * r0 - cc * n0) * iD, yi1 = (al * r1 - cc * n1) * iD;
+          const Real lis = s.l * is[p];
+          const Real ga = al * lis;
+          const Real omg = DgMath<Real>::one_minus_exp(ga);
+          const Real eg = (Real)1 - omg;
+          Real sh, ch;
+          DgMath<Real>::sincos_(cc * lis * rs2, &sh, &ch);  // beta / 2
+          const Real A0 = omg + eg * 2 * sh * sh;
+          const Real A1 = eg * (2 * sh * ch) * rs2;
+          const Real d0 = y0[p] - yi0, d1 = y1[p] - yi1;
+          const Real dy0 = A0 * d0 + A1 * (d1 - d0);        // (I - E) d
+          const Real dy1 = A0 * d1 + A1 * (d1 - 3 * d0);
+          y0[p] -= dy0;
+          y1[p] -= dy1;
+          // segment integral: l y_inf + sin(theta) (al dy - c N dy) / D
+          const Real sD = st[p] * iD;
+          const Real i0 = s.l * yi0 + sD * (al * dy0 - cc * (dy1 - dy0));
+          const Real i1 = s.l * yi1 + sD * (al * dy1 - cc * (dy1 - 3 * dy0));
+          a0 = fma(w[p], i0, a0);
+          a1 = fma(w[p], i1, a1);
+          fp[p * G] = (i0 + i1) / s.l;  // outflow trace, segment average
+        }
+        dg_tally<Real>(tz + (size_t)s.r * Gp * 2, a0, sg * a1);
+        sp += step;
+        fp += fstep;
+      }
+      if (e_out >= 0) {
+        const long long ob = ((((long long)e_out * 2 + ud) * nz + z) * P) * 2;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          psi_out[(ob + 2 * p) * G + g] = y0[p];
+          psi_out[(ob + 2 * p + 1) * G + g] = y1[p];
+        }
+      }
+    }
+  }
+}
+
+// Flux moments of every element from the tallies (phi_m = tally_m / A; the source's
+// infinite-medium value 4 pi q_m / Sigma_t where the tracked area is 0), tallies cleared, FP64
+// block partials for the planar reduce: sum of dz A f, min and max of fold / f, and the
+// fixed-source residual over the plane-average moments.
+template <typename Real>
+__global__ void __launch_bounds__(256) dg_finalize_kernel(
+    int E, int R, int G, int Gp, const int32_t *__restrict__ mat3, const Real *__restrict__ nsf,
+    const double *__restrict__ area, const double *__restrict__ dz, const DgXs<Real> *__restrict__ xs3,
+    Real *__restrict__ tally, Real *__restrict__ phi3, const double *__restrict__ fold, double *__restrict__ part,
+    int eigen) {
+  __shared__ double s_sum[256], s_min[256], s_max[256], s_res[256];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  double fsum = 0.0, rmin = INFINITY, rmax = -INFINITY, res = 0.0;
+  if (e < E) {
+    const int r = e % R, z = e / R;
+    const int m = mat3[e];
+    const double A = area[r];
+    double f = 0.0;
+    for (int g = 0; g < G; ++g) {
+      const size_t a = ((size_t)e * Gp + g) * 2;
+      double v0, v1;
+      if (A > 0.0) {
+        v0 = (double)tally[a] / A;
+        v1 = (double)tally[a + 1] / A;
+      } else {
+        const DgXs<Real> x = xs3[(size_t)e * Gp + g];
+        v0 = kFourPi * (double)x.q0 / (double)x.t;
+        v1 = kFourPi * (double)x.q1 / (double)x.t;
+      }
+      tally[a] = (Real)0;
+      tally[a + 1] = (Real)0;
+      if (!eigen) {
+        const double old = (double)phi3[a];
+        if (v0 > 0.0) res = fmax(res, fabs(v0 - old) / v0);
+      }
+      phi3[a] = (Real)v0;
+      phi3[a + 1] = (Real)v1;
+      f += (double)nsf[m * G + g] * (double)(Real)v0;
+    }
+    fsum = dz[z] * A * f;
+    if (eigen && f > 0.0) {
+      const double rho = fold[e] / f;
+      rmin = rho;
+      rmax = rho;
+    }
+  }
+  s_sum[threadIdx.x] = fsum;
+  s_min[threadIdx.x] = rmin;
+  s_max[threadIdx.x] = rmax;
+  s_res[threadIdx.x] = res;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) {
+      s_sum[threadIdx.x] += s_sum[threadIdx.x + k];
+      s_min[threadIdx.x] = fmin(s_min[threadIdx.x], s_min[threadIdx.x + k]);
+      s_max[threadIdx.x] = fmax(s_max[threadIdx.x], s_max[threadIdx.x + k]);
+      s_res[threadIdx.x] = fmax(s_res[threadIdx.x], s_res[threadIdx.x + k]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[4 * blockIdx.x + 0] = s_sum[0];
+    part[4 * blockIdx.x + 1] = s_min[0];
+    part[4 * blockIdx.x + 2] = s_max[0];
+    part[4 * blockIdx.x + 3] = s_res[0];
+  }
+}
+
+// state in/out of the flux moments: phi [E][2][G] FP64 (NULL: phi_0 = 1, phi_1 = 0) <-> phi3
+// [E][Gp][2] in the sweep's type, scaled by `scale` on the way out
+template <typename Real>
+__global__ void dg_phi_in_kernel(long long n, int G, int Gp, const double *__restrict__ phi, Real *__restrict__ phi3) {
+  const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= n) return;  // n = E * Gp * 2
+  const int m = (int)(x & 1);
+  const long long eg = x >> 1;
+  const long long e = eg / Gp;
+  const int g = (int)(eg - e * Gp);
+  Real v = 0;
+  if (g < G) v = phi ? (Real)phi[(e * 2 + m) * G + g] : (Real)(m == 0 ? 1 : 0);
+  phi3[x] = v;
+}
+
+template <typename Real>
+__global__ void dg_phi_out_kernel(long long n, int G, int Gp, const Real *__restrict__ phi3, double scale,
+                                  double *__restrict__ phi) {
+  const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= n) return;  // n = E * 2 * G
+  const long long e = x / (2 * G);
+  const int rem = (int)(x - e * 2 * G);
+  const int m = rem / G, g = rem - m * G;
+  phi[x] = (double)phi3[(e * Gp + g) * 2 + m] * scale;
+}
+
+}  // namespace moc

@@ -68,6 +68,7 @@ def load_library(path: Optional[str] = None):
             "moc_sweep_dev": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
             "moc_get_stats": (ctypes.c_int, [_vp, _d, _d]),
             "moc_get_history": (ctypes.c_int, [_vp, _d, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+            "moc_set_axial": (ctypes.c_int, [_vp, ctypes.c_int, _d, _i32, ctypes.c_int, ctypes.c_int]),
             "moc_set_scattering": (ctypes.c_int, [_vp, ctypes.c_int, _d]),
             "moc_set_ray_layout": (ctypes.c_int, [_vp, ctypes.c_int]),
             "moc_generate_tracks_device": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
@@ -344,6 +345,7 @@ class Moc:
         M, G = st.shape
         self._check(self._lib.moc_set_xs(self._h, M, G, _p(st, _d), _p(nsf, _d), _p(chi, _d), _p(ss, _d)))
         self.G = G
+        self.nz = 0
 
     def set_fixed_source(self, S):
         S = _f64(S)
@@ -370,10 +372,26 @@ class Moc:
         self._check(self._lib.moc_set_cmfd(self._h, _p(cell, _i32), int(n_cells), int(n_outer), int(n_inner),
                                            float(omega)))
 
+    def set_axial(self, dz, mat3=None, bc=(0, 0)):
+        """DGMOC on len(dz) axial planes (empty: back to the planar method): mat3 [nz][R] materials
+        (None: the mesh's in every plane), bc = (bottom, top), 0 vacuum 1 reflective. The flux of
+        get_state/set_state is then [nz][R][2][G] (plane average, linear coefficient)."""
+        dz = np.ascontiguousarray(dz, dtype=np.float64)
+        m3 = None if mat3 is None else np.ascontiguousarray(mat3, dtype=np.int32)
+        if m3 is not None:
+            assert m3.shape == (dz.size, self.n_regions)
+        self._check(self._lib.moc_set_axial(self._h, int(dz.size), _p(dz, _d) if dz.size else None,
+                                            None if m3 is None else _p(m3, _i32), int(bc[0]), int(bc[1])))
+        self.nz = int(dz.size)
+
+    def _phi_shape(self):
+        nz = getattr(self, "nz", 0)
+        return (nz, self.n_regions, 2, self.G) if nz else (self.n_regions, self.G)
+
     def set_state(self, phi=None, k: float = 1.0, psi=None):
         phi, psi = _f64(phi), _f64(psi)
         if phi is not None:
-            assert phi.size == self.n_regions * self.G
+            assert phi.size == int(np.prod(self._phi_shape()))
         if psi is not None:
             T, _ = self.track_counts()
             assert psi.size == T * 2 * self.n_polar * self.G
@@ -385,10 +403,10 @@ class Moc:
         k = ctypes.c_double()
         if out is not None:
             phi, psi = out
-            assert phi.dtype == np.float64 and phi.flags.c_contiguous and phi.size == self.n_regions * self.G
+            assert phi.dtype == np.float64 and phi.flags.c_contiguous and phi.size == int(np.prod(self._phi_shape()))
             with_psi = psi is not None
         else:
-            phi = np.zeros((self.n_regions, self.G))
+            phi = np.zeros(self._phi_shape())
             psi = None
             if with_psi:
                 T, _ = self.track_counts()

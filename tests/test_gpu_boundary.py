@@ -96,7 +96,8 @@ def test_history_records_every_check():
     assert ok and h.shape == (n // 5, 4)
     np.testing.assert_array_equal(h[:, 0], 5.0 * np.arange(1, n // 5 + 1))
     assert h[-1, 1] == k and h[-1, 3] == r
-    assert abs(h[-1, 1] - h[-1, 2]) <= 1e-7 and h[-2, 3] > 1e-6
+    assert abs(h[-1, 1] - h[-1, 2]) <= 1e-7 and h[-1, 3] <= 1e-6
+    assert not (abs(h[-2, 1] - h[-2, 2]) <= 1e-7 and h[-2, 3] <= 1e-6)   # the previous check had not converged
     # the same iteration driven five outers at a time gives the same records
     b = moc.Moc.from_problem(prob, precision="fp64")
     for _ in range(3):
