@@ -139,6 +139,59 @@ def cpu_baseline(prob, outers: int = 2):
                       f"{dt:.2f} s"}
 
 
+# thread instructions per DGMOC update (segment x polar x group x plane x march) of dg_sweep_kernel,
+# FP32, from ncu's executed-instruction count on the extruded assembly (profiles/dg_sweep_assembly17x8.md)
+DG_INST_PER_UPDATE = None
+
+
+def dgmoc_block(moc, W, prob, device, stream, precision, nz, steps):
+    """DGMOC (Sec. 2.2, Alg. 2) on the assembly extruded like the paper's 3D lattice benchmark:
+    nz axial planes of 10.71 cm, the top quarter reflector (the moderator material in every
+    region), reflective bottom (mid-plane symmetry) and vacuum top. Times whole outers and the
+    sweep kernel alone (CUDA events on the launching stream)."""
+    import torch
+
+    n_refl = max(1, nz // 4)
+    mat3 = np.tile(prob.mesh.mat, (nz, 1))
+    mat3[nz - n_refl:] = prob.mesh.mat.max()
+    dz = np.full(nz, 10.71)
+    m = moc.Moc.from_problem(prob, device=device, precision=precision, stream=stream.cuda_stream)
+    m.set_axial(dz, mat3, bc=(1, 0))
+    _, ups, kpo = m.work()
+
+    def run(k):
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            m.outer(k, read=False)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    run(3)
+    ms = run(steps)
+    m.enable_timing(True)
+    m.outer(steps, read=False)
+    sweep_ms, n_sw = m.timing()
+    m.enable_timing(False)
+    k, _ = m.outer(0)
+    m.close()
+    sweep_s = sweep_ms / n_sw / 1e3
+    out = {"workload": f"{WORKLOADS['assembly']} extruded to {nz} planes x 10.71 cm ({n_refl} reflector "
+                       "planes on top), reflective bottom, vacuum top, linear axial DG",
+           "precision": precision, "planes": nz, "updates_per_outer": ups,
+           "ms_per_outer": ms / steps, "value": ups * steps / (ms / 1e3), "unit": "updates/s",
+           "sweep_ms": sweep_s * 1e3, "kernel": "dg_sweep_res_kernel (plane-inner; dg_sweep_kernel when its shared memory would exceed 100 KB per block)", "k_after": k + 0.0,
+           "outers_timed": steps, "gpu_launches_per_outer": kpo}
+    if DG_INST_PER_UPDATE and precision != "fp64":
+        peak = 152 * 128 * float(_peaks().get("sm_max_mhz", 2070.0)) * 1e6
+        out["roofline"] = {"bound": "alu", "achieved": DG_INST_PER_UPDATE * ups / sweep_s / 1e9,
+                           "peak": peak / 1e9, "unit": "Ginst/s", "frac": DG_INST_PER_UPDATE * ups / sweep_s / peak,
+                           "inst_per_update": DG_INST_PER_UPDATE}
+    return out
+
+
 def time_to_converged_k(moc, prob, device, stream, cmfd, plain: bool = True, pcm: float = 5.0):
     """Wall time and outers of the cold-start power iteration until |k - k_ref| <= pcm * 1e-5, in
     FP32 and FP64, plain (when `plain`) and CMFD-accelerated with cmfd = (cell size, coarse power
@@ -227,6 +280,10 @@ def main():
     ap.add_argument("--no-tracking", action="store_true", help="skip the host vs device tracking timing")
     ap.add_argument("--aniso", type=int, default=0, metavar="L",
                     help="time outers with P_L anisotropic scattering (synthetic moments g^l Sigma_s)")
+    ap.add_argument("--axial", type=int, default=8, metavar="NZ",
+                    help="planes of the DGMOC measurement on the extruded assembly (0 skips it)")
+    ap.add_argument("--dgmoc-only", action="store_true",
+                    help="run only the DGMOC measurement (FP32 and FP64) and print it")
     ap.add_argument("--cmfd", default=None, metavar="SIZE,NOUT,NIN,OMEGA",
                     help="time CMFD-accelerated outers (square coarse cells of SIZE cm); also the "
                          "parameters of the accelerated time-to-k runs")
@@ -260,6 +317,12 @@ def main():
     moc.load_library()
     prob = make_problem(args.workload)
     stream = torch.cuda.Stream(device=local)
+    if args.dgmoc_only:
+        blk = dgmoc_block(moc, W, make_problem("assembly"), local, stream, args.precision, args.axial, args.steps)
+        blk64 = dgmoc_block(moc, W, make_problem("assembly"), local, stream, "fp64", args.axial, 1)
+        if rank == 0:
+            print(json.dumps({"dgmoc": blk, "dgmoc_fp64": blk64}), flush=True)
+        return
     m = moc.Moc.from_problem(prob, device=local, precision=args.precision, stream=stream.cuda_stream)
     if args.cmfd:
         cm_cell, cm_n = W.grid_cells(prob.mesh, cmfd[0])
@@ -357,6 +420,14 @@ def main():
     if not args.no_time_to_k and args.workload in ("assembly", "core", "hexcore"):
         time_to_k = time_to_converged_k(moc, prob, local, stream, cmfd, plain=args.workload == "assembly")
 
+    # DGMOC on the extruded assembly (FP32 timed; one FP64 outer for context)
+    dgmoc = None
+    if args.axial > 0 and args.workload == "assembly":
+        dgmoc = dgmoc_block(moc, W, prob, local, stream, args.precision, args.axial, 5)
+        if args.fp64_steps > 0 and args.precision != "fp64":
+            d64 = dgmoc_block(moc, W, prob, local, stream, "fp64", args.axial, 1)
+            dgmoc["fp64"] = {"ms_per_outer": d64["ms_per_outer"], "value": d64["value"], "k_after": d64["k_after"]}
+
     # tracking of the same workload: host half-edge walk vs the device walk (bit-identical tracks)
     tracking = None
     if not args.no_tracking and rank == 0:
@@ -408,6 +479,7 @@ def main():
         "fp64": fp64,
         "time_to_k": time_to_k,
         "tracking": tracking,
+        "dgmoc": dgmoc,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

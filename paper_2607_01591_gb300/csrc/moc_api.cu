@@ -82,6 +82,7 @@ struct moc_ctx {
   // DGMOC (off unless moc_set_axial was called): nz planes, bottom/top condition
   int dg_nz = 0;
   int dg_bc[2] = {0, 0};
+  size_t dg_res_smem = 0;  // shared memory of the plane-inner sweep per block (0: plane-by-plane sweep)
   std::vector<double> h_dz;
   std::vector<int32_t> h_mat3;
   int32_t *d_mat3 = nullptr;
@@ -198,6 +199,7 @@ void free_dg(moc_ctx *c) {
   dfree(c->d_psi3[1]);
   dfree(c->d_face);
   c->dg_nz = 0;
+  c->dg_res_smem = 0;
   c->h_dz.clear();
   c->h_mat3.clear();
 }
@@ -677,8 +679,23 @@ template <typename Real> int launch_dg_source(moc_ctx *c, cudaStream_t st) {
   return MOC_OK;
 }
 
+constexpr int kDgResBlock = 64;
+constexpr size_t kDgResSmemMax = 100 * 1024;
+
+template <typename Real, int P> size_t dg_res_smem(int nz) {
+  return (size_t)kDgResBlock * nz * (4 * P * sizeof(Real) + sizeof(DgXs<Real>));
+}
+
 template <typename Real, int P> void dg_sweep_launch(moc_ctx *c, cudaStream_t st) {
   const long long n = (long long)c->T * 2 * c->G;
+  if (c->dg_res_smem) {
+    dg_sweep_res_kernel<Real, P><<<(unsigned)((n + kDgResBlock - 1) / kDgResBlock), kDgResBlock, c->dg_res_smem, st>>>(
+        c->d_trk, (const SegRec<Real> *)c->d_seg, c->d_link, (const Real *)c->d_wdg, (const Real *)c->d_sin,
+        (const Real *)c->d_inv_sin, (const Real *)c->d_cz, (const DgXs<Real> *)c->d_xs3, (Real *)c->d_tal3,
+        (const Real *)c->d_psi3[c->cur], (Real *)c->d_psi3[c->cur ^ 1], (Real *)c->d_face, c->d_scal, n, c->G,
+        c->Gp, c->geo.n_tri, c->dg_nz, c->dg_bc[0], c->dg_bc[1]);
+    return;
+  }
   dg_sweep_kernel<Real, P><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(
       c->d_trk, (const SegRec<Real> *)c->d_seg, c->d_link, (const Real *)c->d_wdg, (const Real *)c->d_sin,
       (const Real *)c->d_inv_sin, (const Real *)c->d_cz, (const DgXs<Real> *)c->d_xs3, (Real *)c->d_tal3,
@@ -1048,6 +1065,17 @@ template <typename Real> int dg_alloc(moc_ctx *c) {
   CUDA_TRY(c, cudaMalloc((void **)&c->d_fold3, E * sizeof(double)));
   CUDA_TRY(c, cudaMemset(c->d_fold3, 0, E * sizeof(double)));
   CUDA_TRY(c, cudaMalloc((void **)&c->d_part3, ((E + 255) / 256) * 4 * sizeof(double)));
+  // the plane-inner sweep when its per-block shared memory stays moderate, else plane by plane
+  size_t sm = 0;
+  cudaError_t e = cudaSuccess;
+  switch (P) {
+    case 1: sm = dg_res_smem<Real, 1>(nz); if (sm <= kDgResSmemMax) e = cudaFuncSetAttribute(dg_sweep_res_kernel<Real, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); break;
+    case 2: sm = dg_res_smem<Real, 2>(nz); if (sm <= kDgResSmemMax) e = cudaFuncSetAttribute(dg_sweep_res_kernel<Real, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); break;
+    case 3: sm = dg_res_smem<Real, 3>(nz); if (sm <= kDgResSmemMax) e = cudaFuncSetAttribute(dg_sweep_res_kernel<Real, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); break;
+    default: sm = dg_res_smem<Real, 4>(nz); if (sm <= kDgResSmemMax) e = cudaFuncSetAttribute(dg_sweep_res_kernel<Real, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); break;
+  }
+  if (e != cudaSuccess) return fail(c, MOC_ERR_CUDA, std::string("set_axial: ") + cudaGetErrorString(e));
+  c->dg_res_smem = sm <= kDgResSmemMax ? sm : 0;
   return MOC_OK;
 }
 

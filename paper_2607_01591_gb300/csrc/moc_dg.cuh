@@ -97,6 +97,36 @@ __global__ void dg_source_kernel(int E, int R, int G, int Gp, int M, const int32
   }
 }
 
+// One segment of one plane for one polar angle: (y0, y1) = (a, +-b) entering, pin the axial
+// inflow, cc = mu/dz, lis = l/sin(theta), st = sin(theta). Updates (y0, y1) to the segment's end
+// and returns the segment integrals (i0, i1) of the two moments.
+template <typename Real>
+__device__ __forceinline__ void dg_update(Real t, Real q0, Real q1s, Real cc, Real l, Real lis, Real st, Real pin,
+                                          Real &y0, Real &y1, Real &i0, Real &i1) {
+  const Real rs2 = (Real)0.70710678118654752440;  // 1/sqrt(2)
+  const Real al = t + 2 * cc;
+  const Real iD = (Real)1 / (al * al + 2 * cc * cc);
+  // y_inf = (al rr - c N rr) / D
+  const Real r0 = q0 + cc * pin, r1 = q1s - 3 * cc * pin;
+  const Real n0 = r1 - r0, n1 = r1 - 3 * r0;  // N rr
+  const Real yi0 = (al * r0 - cc * n0) * iD, yi1 = (al * r1 - cc * n1) * iD;
+  const Real omg = DgMath<Real>::one_minus_exp(al * lis);
+  const Real eg = (Real)1 - omg;
+  Real sh, ch;
+  DgMath<Real>::sincos_(cc * lis * rs2, &sh, &ch);  // beta / 2
+  const Real A0 = omg + eg * 2 * sh * sh;
+  const Real A1 = eg * (2 * sh * ch) * rs2;
+  const Real d0 = y0 - yi0, d1 = y1 - yi1;
+  const Real dy0 = A0 * d0 + A1 * (d1 - d0);  // (I - E) d
+  const Real dy1 = A0 * d1 + A1 * (d1 - 3 * d0);
+  y0 -= dy0;
+  y1 -= dy1;
+  // segment integral: l y_inf + sin(theta) (al dy - c N dy) / D
+  const Real sD = st * iD;
+  i0 = l * yi0 + sD * (al * dy0 - cc * (dy1 - dy0));
+  i1 = l * yi1 + sD * (al * dy1 - cc * (dy1 - 3 * dy0));
+}
+
 template <typename Real> __device__ __forceinline__ void dg_tally(Real *t, Real a0, Real a1) {
   atomicAdd(t, a0);
   atomicAdd(t + 1, a1);
@@ -137,7 +167,6 @@ __global__ void __launch_bounds__(128) dg_sweep_kernel(
   }
   const int step = d ? -1 : 1;
   const long long s_first = d ? tr.off + tr.n - 1 : tr.off;
-  const Real rs2 = (Real)0.70710678118654752440;  // 1/sqrt(2)
   const int e_out = link[td];
   for (int ud = 0; ud < 2; ++ud) {
     const Real sg = ud ? (Real)1 : (Real)-1;
@@ -167,39 +196,18 @@ __global__ void __launch_bounds__(128) dg_sweep_kernel(
         const SegRec<Real> s = *sp;
         const DgXs<Real> x = xz[(size_t)s.r * Gp];
         const Real q1s = sg * x.q1;
+        const Real il = (Real)1 / s.l;
         Real a0 = 0, a1 = 0;
 #pragma unroll
         for (int p = 0; p < P; ++p) {
           // a vacuum or reflective first inflow is zero or the stored trace, without branching
           const Real fin = fp[p * G];
           const Real pin = fmul == (Real)0 ? (Real)0 : fin * fmul;
-          const Real cc = c[p];
-          const Real al = x.t + 2 * cc;
-          const Real iD = (Real)1 / (al * al + 2 * cc * cc);
-          // y_inf = (al rr - c N rr) / D
-          const Real r0 = x.q0 + cc * pin, r1 = q1s - 3 * cc * pin;
-          const Real n0 = r1 - r0, n1 = r1 - 3 * r0;  // N rr
-          const Real yi0 = (al * r0 - cc * n0) * iD, yi1 = (al * r1 - cc * n1) * iD;
-          const Real lis = s.l * is[p];
-          const Real ga = al * lis;
-          const Real omg = DgMath<Real>::one_minus_exp(ga);
-          const Real eg = (Real)1 - omg;
-          Real sh, ch;
-          DgMath<Real>::sincos_(cc * lis * rs2, &sh, &ch);  // beta / 2
-          const Real A0 = omg + eg * 2 * sh * sh;
-          const Real A1 = eg * (2 * sh * ch) * rs2;
-          const Real d0 = y0[p] - yi0, d1 = y1[p] - yi1;
-          const Real dy0 = A0 * d0 + A1 * (d1 - d0);        // (I - E) d
-          const Real dy1 = A0 * d1 + A1 * (d1 - 3 * d0);
-          y0[p] -= dy0;
-          y1[p] -= dy1;
-          // segment integral: l y_inf + sin(theta) (al dy - c N dy) / D
-          const Real sD = st[p] * iD;
-          const Real i0 = s.l * yi0 + sD * (al * dy0 - cc * (dy1 - dy0));
-          const Real i1 = s.l * yi1 + sD * (al * dy1 - cc * (dy1 - 3 * dy0));
+          Real i0, i1;
+          dg_update<Real>(x.t, x.q0, q1s, c[p], s.l, s.l * is[p], st[p], pin, y0[p], y1[p], i0, i1);
           a0 = fma(w[p], i0, a0);
           a1 = fma(w[p], i1, a1);
-          fp[p * G] = (i0 + i1) / s.l;  // outflow trace, segment average
+          fp[p * G] = (i0 + i1) * il;  // outflow trace, segment average
         }
         dg_tally<Real>(tz + (size_t)s.r * Gp * 2, a0, sg * a1);
         sp += step;
@@ -214,6 +222,98 @@ __global__ void __launch_bounds__(128) dg_sweep_kernel(
         }
       }
     }
+  }
+}
+
+// The same sweep with the loops interchanged: for each segment of the track, the downward march
+// through all planes and then the upward march, so the axial inflow of a plane is the outflow the
+// thread computed for the same segment one plane upwind, kept in a register (no interface buffer
+// in memory; only a reflective top stores its top traces for the next sweep). The radial state of
+// every (march, plane, polar angle) lives in shared memory, one column per thread
+// ([slot][blockDim], conflict-free), and the nz cross-section rows of the segment's region are
+// loaded once per segment into a shared-memory row cache. Every value computed equals the
+// plane-by-plane order's (the same inflows, the same radial states); only the order of the tally
+// atomics differs.
+template <typename Real, int P>
+__global__ void __launch_bounds__(64) dg_sweep_res_kernel(
+    const TrackRec *__restrict__ trk, const SegRec<Real> *__restrict__ seg, const int32_t *__restrict__ link,
+    const Real *__restrict__ wdg, const Real *__restrict__ sin_t, const Real *__restrict__ inv_sin,
+    const Real *__restrict__ cz, const DgXs<Real> *__restrict__ xs3, Real *__restrict__ tally,
+    const Real *__restrict__ psi_in, Real *__restrict__ psi_out, Real *__restrict__ face,
+    const double *__restrict__ scal, long long n_threads, int G, int Gp, int R, int nz, int bc_bottom, int bc_top) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int B = blockDim.x, tid = threadIdx.x;
+  Real *ys = reinterpret_cast<Real *>(smem_raw);                          // [2][nz][P][2][B]
+  DgXs<Real> *rc = reinterpret_cast<DgXs<Real> *>(ys + (size_t)4 * nz * P * B);  // [nz][B]
+  const long long idx = (long long)blockIdx.x * B + tid;
+  if (idx >= n_threads) return;
+  const long long td = idx / G;
+  const int g = (int)(idx - td * G);
+  const TrackRec tr = trk[td >> 1];
+  const int d = (int)(td & 1);
+  const Real scale = (Real)scal[S_SCALE];
+  Real w[P], st[P], is[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    w[p] = wdg[tr.dir * P + p];
+    st[p] = sin_t[p];
+    is[p] = inv_sin[p];
+  }
+  const int nslot = 4 * nz * P;
+  {
+    const Real *pi = psi_in + td * nslot * G + g;  // [2T][2][nz][P][2][G]: slots of one end in order
+    for (int k = 0; k < nslot; ++k) ys[(size_t)k * B + tid] = pi[(size_t)k * G] * scale;
+  }
+  const int step = d ? -1 : 1;
+  const SegRec<Real> *sp = seg + (d ? tr.off + tr.n - 1 : tr.off);
+  Real *fp = face + (((d ? tr.off + tr.n - 1 : tr.off) * 2 + d) * P) * G + g;
+  const long long fstep = (long long)step * 2 * P * G;
+  SegRec<Real> s = sp[0];
+  for (int n = 0; n < tr.n; ++n) {
+    const SegRec<Real> s_next = sp[step];  // padding records at both ends of the array
+    for (int z = 0; z < nz; ++z) rc[(size_t)z * B + tid] = xs3[((size_t)z * R + s.r) * Gp + g];
+    const Real il = (Real)1 / s.l;
+    Real fin[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) fin[p] = bc_top ? fp[p * G] * scale : (Real)0;
+    for (int ud = 0; ud < 2; ++ud) {
+      const Real sg = ud ? (Real)1 : (Real)-1;
+      if (ud == 1 && !bc_bottom) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) fin[p] = 0;
+      }
+      for (int zi = 0; zi < nz; ++zi) {
+        const int z = ud ? zi : nz - 1 - zi;
+        const DgXs<Real> x = rc[(size_t)z * B + tid];
+        const Real q1s = sg * x.q1;
+        Real *yz = ys + ((size_t)((ud * nz + z) * P) * 2) * B + tid;
+        Real a0 = 0, a1 = 0;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          Real y0 = yz[(2 * p) * B], y1 = yz[(2 * p + 1) * B];
+          Real i0, i1;
+          dg_update<Real>(x.t, x.q0, q1s, cz[z * P + p], s.l, s.l * is[p], st[p], fin[p], y0, y1, i0, i1);
+          yz[(2 * p) * B] = y0;
+          yz[(2 * p + 1) * B] = y1;
+          a0 = fma(w[p], i0, a0);
+          a1 = fma(w[p], i1, a1);
+          fin[p] = (i0 + i1) * il;
+        }
+        dg_tally<Real>(tally + (((size_t)z * R + s.r) * Gp + g) * 2, a0, sg * a1);
+      }
+    }
+    if (bc_top) {
+#pragma unroll
+      for (int p = 0; p < P; ++p) fp[p * G] = fin[p];
+    }
+    s = s_next;
+    sp += step;
+    fp += fstep;
+  }
+  const int e_out = link[td];
+  if (e_out >= 0) {
+    Real *po = psi_out + (long long)e_out * nslot * G + g;
+    for (int k = 0; k < nslot; ++k) po[(size_t)k * G] = ys[(size_t)k * B + tid];
   }
 }
 
