@@ -683,7 +683,7 @@ constexpr int kDgResBlock = 64;
 constexpr size_t kDgResSmemMax = 100 * 1024;
 
 template <typename Real, int P> size_t dg_res_smem(int nz) {
-  return (size_t)kDgResBlock * nz * (4 * P * sizeof(Real) + sizeof(DgXs<Real>));
+  return (size_t)kDgResBlock * nz * (4 * P + 3) * sizeof(Real);
 }
 
 template <typename Real, int P> void dg_sweep_launch(moc_ctx *c, cudaStream_t st) {

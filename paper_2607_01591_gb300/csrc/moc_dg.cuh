@@ -231,9 +231,10 @@ __global__ void __launch_bounds__(128) dg_sweep_kernel(
 // in memory; only a reflective top stores its top traces for the next sweep). The radial state of
 // every (march, plane, polar angle) lives in shared memory, one column per thread
 // ([slot][blockDim], conflict-free), and the nz cross-section rows of the segment's region are
-// loaded once per segment into a shared-memory row cache. Every value computed equals the
-// plane-by-plane order's (the same inflows, the same radial states); only the order of the tally
-// atomics differs.
+// loaded once per segment into a shared-memory row cache (3 values per plane, no padding: 7
+// blocks of 64 threads fit an SM at 8 planes and 3 polar angles in FP32). Every value computed
+// equals the plane-by-plane order's (the same inflows, the same radial states); only the order of
+// the tally atomics differs.
 template <typename Real, int P>
 __global__ void __launch_bounds__(64) dg_sweep_res_kernel(
     const TrackRec *__restrict__ trk, const SegRec<Real> *__restrict__ seg, const int32_t *__restrict__ link,
@@ -243,8 +244,8 @@ __global__ void __launch_bounds__(64) dg_sweep_res_kernel(
     const double *__restrict__ scal, long long n_threads, int G, int Gp, int R, int nz, int bc_bottom, int bc_top) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int B = blockDim.x, tid = threadIdx.x;
-  Real *ys = reinterpret_cast<Real *>(smem_raw);                          // [2][nz][P][2][B]
-  DgXs<Real> *rc = reinterpret_cast<DgXs<Real> *>(ys + (size_t)4 * nz * P * B);  // [nz][B]
+  Real *ys = reinterpret_cast<Real *>(smem_raw);  // [2][nz][P][2][B]
+  Real *rc = ys + (size_t)4 * nz * P * B;         // [3][nz][B]: Sigma_t, q0, q1 of the segment's region
   const long long idx = (long long)blockIdx.x * B + tid;
   if (idx >= n_threads) return;
   const long long td = idx / G;
@@ -271,7 +272,12 @@ __global__ void __launch_bounds__(64) dg_sweep_res_kernel(
   SegRec<Real> s = sp[0];
   for (int n = 0; n < tr.n; ++n) {
     const SegRec<Real> s_next = sp[step];  // padding records at both ends of the array
-    for (int z = 0; z < nz; ++z) rc[(size_t)z * B + tid] = xs3[((size_t)z * R + s.r) * Gp + g];
+    for (int z = 0; z < nz; ++z) {
+      const DgXs<Real> x = xs3[((size_t)z * R + s.r) * Gp + g];
+      rc[(size_t)z * B + tid] = x.t;
+      rc[(size_t)(nz + z) * B + tid] = x.q0;
+      rc[(size_t)(2 * nz + z) * B + tid] = x.q1;
+    }
     const Real il = (Real)1 / s.l;
     Real fin[P];
 #pragma unroll
@@ -284,15 +290,15 @@ __global__ void __launch_bounds__(64) dg_sweep_res_kernel(
       }
       for (int zi = 0; zi < nz; ++zi) {
         const int z = ud ? zi : nz - 1 - zi;
-        const DgXs<Real> x = rc[(size_t)z * B + tid];
-        const Real q1s = sg * x.q1;
+        const Real xt = rc[(size_t)z * B + tid], xq0 = rc[(size_t)(nz + z) * B + tid];
+        const Real q1s = sg * rc[(size_t)(2 * nz + z) * B + tid];
         Real *yz = ys + ((size_t)((ud * nz + z) * P) * 2) * B + tid;
         Real a0 = 0, a1 = 0;
 #pragma unroll
         for (int p = 0; p < P; ++p) {
           Real y0 = yz[(2 * p) * B], y1 = yz[(2 * p + 1) * B];
           Real i0, i1;
-          dg_update<Real>(x.t, x.q0, q1s, cz[z * P + p], s.l, s.l * is[p], st[p], fin[p], y0, y1, i0, i1);
+          dg_update<Real>(xt, xq0, q1s, cz[z * P + p], s.l, s.l * is[p], st[p], fin[p], y0, y1, i0, i1);
           yz[(2 * p) * B] = y0;
           yz[(2 * p + 1) * B] = y1;
           a0 = fma(w[p], i0, a0);
