@@ -141,7 +141,7 @@ def cpu_baseline(prob, outers: int = 2):
 
 # thread instructions per DGMOC update (segment x polar x group x plane x march) of dg_sweep_kernel,
 # FP32, from ncu's executed-instruction count on the extruded assembly (profiles/dg_sweep_assembly17x8.md)
-DG_INST_PER_UPDATE = 129.8
+DG_INST_PER_UPDATE = 114.4
 
 
 def dgmoc_block(moc, W, prob, device, stream, precision, nz, steps):

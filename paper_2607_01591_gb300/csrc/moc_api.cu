@@ -679,7 +679,6 @@ template <typename Real> int launch_dg_source(moc_ctx *c, cudaStream_t st) {
   return MOC_OK;
 }
 
-constexpr int kDgResBlock = 64;
 constexpr size_t kDgResSmemMax = 100 * 1024;
 
 template <typename Real, int P> size_t dg_res_smem(int nz) {

@@ -40,12 +40,25 @@ template <typename Real> struct alignas(4 * sizeof(Real)) DgXs {
 
 template <typename Real> struct DgMath;
 template <> struct DgMath<double> {
+  __device__ static double rcp(double x) { return 1.0 / x; }
   __device__ static double one_minus_exp(double x) { return -expm1(-x); }
   __device__ static void sincos_(double x, double *s, double *c) { sincos(x, s, c); }
 };
 template <> struct DgMath<float> {
+  __device__ static float rcp(float x) { return __frcp_rn(x); }  // correctly rounded 1/x
   __device__ static float one_minus_exp(float x) { return moc::one_minus_exp(x); }
-  __device__ static void sincos_(float x, float *s, float *c) { sincosf(x, s, c); }
+  // x >= 0. Below 0.5 (thick planes: the usual case) the Taylor polynomials of sin to x^7 and cos
+  // to x^8, whose remainders (x^9/9!, x^10/10!) stay below 1.1e-8 relative, i.e. within FP32
+  // rounding; above it CUDA's sincosf.
+  __device__ static void sincos_(float x, float *s, float *c) {
+    if (x <= 0.5f) {
+      const float x2 = x * x;
+      *s = x * fmaf(x2, fmaf(x2, fmaf(x2, -1.0f / 5040.0f, 1.0f / 120.0f), -1.0f / 6.0f), 1.0f);
+      *c = fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, 1.0f / 40320.0f, -1.0f / 720.0f), 1.0f / 24.0f), -0.5f), 1.0f);
+    } else {
+      sincosf(x, s, c);
+    }
+  }
 };
 
 // Source moments of every element (plane z, region r): one thread per element.
@@ -105,7 +118,7 @@ __device__ __forceinline__ void dg_update(Real t, Real q0, Real q1s, Real cc, Re
                                           Real &y0, Real &y1, Real &i0, Real &i1) {
   const Real rs2 = (Real)0.70710678118654752440;  // 1/sqrt(2)
   const Real al = t + 2 * cc;
-  const Real iD = (Real)1 / (al * al + 2 * cc * cc);
+  const Real iD = DgMath<Real>::rcp(al * al + 2 * cc * cc);
   // y_inf = (al rr - c N rr) / D
   const Real r0 = q0 + cc * pin, r1 = q1s - 3 * cc * pin;
   const Real n0 = r1 - r0, n1 = r1 - 3 * r0;  // N rr
@@ -196,7 +209,7 @@ __global__ void __launch_bounds__(128) dg_sweep_kernel(
         const SegRec<Real> s = *sp;
         const DgXs<Real> x = xz[(size_t)s.r * Gp];
         const Real q1s = sg * x.q1;
-        const Real il = (Real)1 / s.l;
+        const Real il = DgMath<Real>::rcp(s.l);
         Real a0 = 0, a1 = 0;
 #pragma unroll
         for (int p = 0; p < P; ++p) {
@@ -235,15 +248,18 @@ __global__ void __launch_bounds__(128) dg_sweep_kernel(
 // blocks of 64 threads fit an SM at 8 planes and 3 polar angles in FP32). Every value computed
 // equals the plane-by-plane order's (the same inflows, the same radial states); only the order of
 // the tally atomics differs.
+constexpr int kDgResBlock = 64;  // threads per block of the plane-inner sweep
+
 template <typename Real, int P>
-__global__ void __launch_bounds__(64) dg_sweep_res_kernel(
+__global__ void __launch_bounds__(kDgResBlock) dg_sweep_res_kernel(
     const TrackRec *__restrict__ trk, const SegRec<Real> *__restrict__ seg, const int32_t *__restrict__ link,
     const Real *__restrict__ wdg, const Real *__restrict__ sin_t, const Real *__restrict__ inv_sin,
     const Real *__restrict__ cz, const DgXs<Real> *__restrict__ xs3, Real *__restrict__ tally,
     const Real *__restrict__ psi_in, Real *__restrict__ psi_out, Real *__restrict__ face,
     const double *__restrict__ scal, long long n_threads, int G, int Gp, int R, int nz, int bc_bottom, int bc_top) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int B = blockDim.x, tid = threadIdx.x;
+  constexpr int B = kDgResBlock;  // launched with exactly this many threads
+  const int tid = threadIdx.x;
   Real *ys = reinterpret_cast<Real *>(smem_raw);  // [2][nz][P][2][B]
   Real *rc = ys + (size_t)4 * nz * P * B;         // [3][nz][B]: Sigma_t, q0, q1 of the segment's region
   const long long idx = (long long)blockIdx.x * B + tid;
@@ -278,7 +294,7 @@ __global__ void __launch_bounds__(64) dg_sweep_res_kernel(
       rc[(size_t)(nz + z) * B + tid] = x.q0;
       rc[(size_t)(2 * nz + z) * B + tid] = x.q1;
     }
-    const Real il = (Real)1 / s.l;
+    const Real il = DgMath<Real>::rcp(s.l);
     Real fin[P];
 #pragma unroll
     for (int p = 0; p < P; ++p) fin[p] = bc_top ? fp[p * G] * scale : (Real)0;
