@@ -144,7 +144,7 @@ def cpu_baseline(prob, outers: int = 2):
 DG_INST_PER_UPDATE = 114.4
 
 
-def dgmoc_block(moc, W, prob, device, stream, precision, nz, steps):
+def dgmoc_block(moc, W, prob, device, stream, precision, nz, steps, converge=False):
     """DGMOC (Sec. 2.2, Alg. 2) on the assembly extruded like the paper's 3D lattice benchmark:
     nz axial planes of 10.71 cm, the top quarter reflector (the moderator material in every
     region), reflective bottom (mid-plane symmetry) and vacuum top. Times whole outers and the
@@ -176,6 +176,16 @@ def dgmoc_block(moc, W, prob, device, stream, precision, nz, steps):
     sweep_ms, n_sw = m.timing()
     m.enable_timing(False)
     k, _ = m.outer(0)
+    ttk = None
+    if converge:
+        # power iteration from the flat start to |dk| <= 1e-6 and fission residual <= 1e-5 (host
+        # check every 10 outers), wall time through the public API
+        m.set_state(None, 1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        kc, n, r, ok = m.power_iterate(tol_k=1e-6, tol_flux=1e-5, max_outer=5000, check_every=10, raise_on_fail=False)
+        ttk = {"s": time.perf_counter() - t0, "outers": n, "k": kc, "residual": r, "converged": ok,
+               "tolerance": "|dk| <= 1e-6, max relative fission-rate change <= 1e-5, checked every 10 outers"}
     m.close()
     sweep_s = sweep_ms / n_sw / 1e3
     out = {"workload": f"{WORKLOADS['assembly']} extruded to {nz} planes x 10.71 cm ({n_refl} reflector "
@@ -183,7 +193,7 @@ def dgmoc_block(moc, W, prob, device, stream, precision, nz, steps):
            "precision": precision, "planes": nz, "updates_per_outer": ups,
            "ms_per_outer": ms / steps, "value": ups * steps / (ms / 1e3), "unit": "updates/s",
            "sweep_ms": sweep_s * 1e3, "kernel": "dg_sweep_res_kernel (plane-inner; dg_sweep_kernel when its shared memory would exceed 100 KB per block)", "k_after": k + 0.0,
-           "outers_timed": steps, "gpu_launches_per_outer": kpo}
+           "outers_timed": steps, "gpu_launches_per_outer": kpo, "time_to_k": ttk}
     if DG_INST_PER_UPDATE and precision != "fp64":
         peak = 152 * 128 * float(_peaks().get("sm_max_mhz", 2070.0)) * 1e6
         out["roofline"] = {"bound": "alu", "achieved": DG_INST_PER_UPDATE * ups / sweep_s / 1e9,
@@ -283,7 +293,8 @@ def main():
     ap.add_argument("--axial", type=int, default=8, metavar="NZ",
                     help="planes of the DGMOC measurement on the extruded assembly (0 skips it)")
     ap.add_argument("--dgmoc-only", action="store_true",
-                    help="run only the DGMOC measurement (FP32 and FP64) and print it")
+                    help="run only the DGMOC measurement (FP32 with its time to converged k, and FP64) "
+                         "and print it")
     ap.add_argument("--cmfd", default=None, metavar="SIZE,NOUT,NIN,OMEGA",
                     help="time CMFD-accelerated outers (square coarse cells of SIZE cm); also the "
                          "parameters of the accelerated time-to-k runs")
@@ -318,7 +329,8 @@ def main():
     prob = make_problem(args.workload)
     stream = torch.cuda.Stream(device=local)
     if args.dgmoc_only:
-        blk = dgmoc_block(moc, W, make_problem("assembly"), local, stream, args.precision, args.axial, args.steps)
+        blk = dgmoc_block(moc, W, make_problem("assembly"), local, stream, args.precision, args.axial, args.steps,
+                          converge=not args.no_time_to_k)
         blk64 = dgmoc_block(moc, W, make_problem("assembly"), local, stream, "fp64", args.axial, 1)
         if rank == 0:
             print(json.dumps({"dgmoc": blk, "dgmoc_fp64": blk64}), flush=True)
