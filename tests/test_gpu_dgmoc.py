@@ -167,3 +167,41 @@ def test_plane_by_plane_variant_matches_oracle():
     assert abs(k - ko) <= 1e-11 * ko
     assert _rel(pg[:, :, 0], po[:, :, 0]) <= 1e-11
     assert np.abs(pg[:, :, 1] - po[:, :, 1]).max() <= 1e-11 * np.abs(po[:, :, 0]).max()
+
+
+def _outers_vs_oracle(prob, dz, mat3, bc, n=3, threads=8):
+    o = oracle.Oracle.from_problem(prob, threads=threads)
+    o.set_axial(dz, mat3, bc=bc)
+    m = moc.Moc.from_problem(prob, precision="fp64")
+    m.set_axial(dz, mat3, bc=bc)
+    for _ in range(n):
+        o.outer(prob.fixed_source is None)
+    k, _ = m.outer(n)
+    po, ko = o.flux3()
+    pg, _ = m.get_state()
+    assert prob.fixed_source is not None or abs(k - ko) <= 1e-11 * ko
+    assert _rel(pg[:, :, 0], po[:, :, 0]) <= 1e-11
+    assert np.abs(pg[:, :, 1] - po[:, :, 1]).max() <= 1e-11 * np.abs(po[:, :, 0]).max()
+
+
+@pytest.mark.parametrize("n_polar", [1, 2, 4])
+def test_polar_counts_match_oracle(n_polar):
+    """every compiled polar count of the sweep (3 is covered above)"""
+    prob, dz, mat3 = _case()
+    st = {1: [0.8], 2: [0.35, 0.9], 4: [0.1, 0.4, 0.7, 0.95]}[n_polar]
+    w = np.full(n_polar, 1.0 / n_polar)
+    prob = W.Problem(prob.mesh, prob.xs, prob.n_azim, prob.ray_spacing, np.array(st), w)
+    _outers_vs_oracle(prob, dz, mat3, (1, 0))
+
+
+def test_one_plane_many_groups_and_back_projection():
+    """one plane (both faces reflective), 33 groups (threads per track beyond a warp's quarter);
+    then back-projected rays on the concave 7-hexagon cluster (vacuum) with 2 planes"""
+    mesh = W.grid_mesh(3, 3, 3.0, 3.0, bc=(1, 0, 1, 0), mat_fn=lambda i, j: (i + j) % 2)
+    xs = W.synthetic_xs(["fuel", "moderator"], 33, 12)
+    prob = W.Problem(mesh, xs, 8, 0.2)
+    _outers_vs_oracle(prob, np.array([3.0]), None, (1, 1), n=2)
+    mesh = W.hex_core_mesh(n_sub=4, n_rings=1)
+    xs = W.synthetic_xs(["fuel", "fuel", "coolant"], 7, 9, sigt_range=(0.05, 0.6))
+    prob = W.Problem(mesh, xs, 12, 0.3, ray_layout=1)
+    _outers_vs_oracle(prob, np.array([2.0, 1.0]), None, (0, 0), n=3)
