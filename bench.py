@@ -139,8 +139,11 @@ def cpu_baseline(prob, outers: int = 2):
                       f"{dt:.2f} s"}
 
 
-# thread instructions per DGMOC update (segment x polar x group x plane x march) of dg_sweep_kernel,
-# FP32, from ncu's executed-instruction count on the extruded assembly (profiles/dg_sweep_assembly17x8.md)
+# Per DGMOC update (segment x polar x group x plane x march), FP32: the algorithmic operations of the
+# closed-form 2x2 segment solution counted from its formulas (FMA = 1, the 1 - e^-x evaluation 13,
+# small-angle sin/cos 10, the reciprocal 1), and the thread instructions the plane-inner sweep
+# actually executes, from ncu on the extruded assembly (profiles/dg_sweep_assembly17x8.md)
+DG_OPS_PER_UPDATE = 74
 DG_INST_PER_UPDATE = 114.4
 
 
@@ -194,11 +197,15 @@ def dgmoc_block(moc, W, prob, device, stream, precision, nz, steps, converge=Fal
            "ms_per_outer": ms / steps, "value": ups * steps / (ms / 1e3), "unit": "updates/s",
            "sweep_ms": sweep_s * 1e3, "kernel": "dg_sweep_res_kernel (plane-inner; dg_sweep_kernel when its shared memory would exceed 100 KB per block)", "k_after": k + 0.0,
            "outers_timed": steps, "gpu_launches_per_outer": kpo, "time_to_k": ttk}
-    if DG_INST_PER_UPDATE and precision != "fp64":
+    if precision != "fp64":
         peak = 152 * 128 * float(_peaks().get("sm_max_mhz", 2070.0)) * 1e6
-        out["roofline"] = {"bound": "alu", "achieved": DG_INST_PER_UPDATE * ups / sweep_s / 1e9,
-                           "peak": peak / 1e9, "unit": "Ginst/s", "frac": DG_INST_PER_UPDATE * ups / sweep_s / peak,
-                           "inst_per_update": DG_INST_PER_UPDATE}
+        out["roofline"] = {"bound": "alu", "achieved": DG_OPS_PER_UPDATE * ups / sweep_s / 1e9,
+                           "peak": peak / 1e9, "unit": "Gop/s", "frac": DG_OPS_PER_UPDATE * ups / sweep_s / peak,
+                           "ops_per_update": DG_OPS_PER_UPDATE,
+                           "issue_frac": DG_INST_PER_UPDATE * ups / sweep_s / peak,
+                           "inst_per_update": DG_INST_PER_UPDATE,
+                           "peak_note": "152 SMs x 128 FP32 lanes x max SM clock; issue_frac counts executed "
+                                        "thread instructions (ncu) instead of algorithmic operations"}
     return out
 
 
