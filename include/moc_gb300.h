@@ -251,6 +251,19 @@ int moc_sweep_dev(moc_ctx *ctx, void *stream, const void *phi_in_dev, void *phi_
  * material ids, more than 4 polar angles), MOC_ERR_STATE, MOC_ERR_OOM, MOC_ERR_CUDA. */
 int moc_set_axial(moc_ctx *ctx, int nz, const double *dz, const int32_t *mat3, int bc_bottom, int bc_top);
 
+/* Axial coarse-mesh acceleration of DGMOC (the CMFD step of Alg. 1 with the planes as coarse
+ * cells), eigenvalue mode: each outer's sweep also tallies the partial currents between planes and
+ * each plane's net current through the domain boundary (radial track ends, bottom and top faces,
+ * out minus in); the planes' flux-volume homogenised balance, with D = J / phi from those currents
+ * (a fixed point at the transport solution), is iterated n_outer times (power iteration;
+ * Gauss-Seidel in energy; n_inner sweeps over the even then the odd planes, over-relaxed by omega
+ * in (0, 2)), and both flux moments, the next sweep's radial boundary flux and the stored top
+ * traces are scaled by their plane's coarse/fine ratio; k becomes the coarse k. n_outer = 0
+ * switches it off; moc_set_axial switches it off. Needs the plane-inner sweep (its shared memory
+ * with the current sums must fit 100 KB per block: nz <= 22 in FP32, 11 in FP64 with 3 polar
+ * angles). Errors: MOC_ERR_STATE (no moc_set_axial), MOC_ERR_ARG, MOC_ERR_OOM, MOC_ERR_CUDA. */
+int moc_set_dg_cmfd(moc_ctx *ctx, int n_outer, int n_inner, double omega);
+
 /* Iteration history: every time the host reads k and the residual after outers (each check of
  * moc_power_iterate, moc_outer with k_out or resid_out), one entry {outers so far (since the last
  * moc_set_state), k, k before the last outer, residual} is recorded; the last 4,096 are kept.

@@ -78,6 +78,8 @@ def _load():
         lib.orc_set_axial.restype = ctypes.c_int
         lib.orc_set_axial.argtypes = [ctypes.c_void_p, ctypes.c_int, _d, _i32, ctypes.c_int, ctypes.c_int]
         lib.orc_get_flux3.argtypes = [ctypes.c_void_p, _d, _d]
+        lib.orc_set_dg_cmfd.restype = ctypes.c_int
+        lib.orc_set_dg_cmfd.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_double]
         lib.orc_get_leakage3.argtypes = [ctypes.c_void_p, _d]
         lib.orc_expm2.argtypes = [_d, _d]
         lib.orc_dg_segment.argtypes = [_d, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -227,6 +229,11 @@ class Oracle:
             raise RuntimeError("oracle: " + self._lib.orc_error(self._h).decode())
         self.nz = int(dz.size)
         self._dz, self._m3 = dz, m3
+
+    def set_dg_cmfd(self, n_outer: int = 0, n_inner: int = 4, omega: float = 1.0):
+        """Axial coarse-mesh acceleration of DGMOC (coarse cells = planes); n_outer = 0 disables."""
+        if self._lib.orc_set_dg_cmfd(self._h, int(n_outer), int(n_inner), float(omega)):
+            raise RuntimeError("oracle: " + self._lib.orc_error(self._h).decode())
 
     def flux3(self):
         """(phi [nz][R][2][G]: plane-average and linear moments, k)."""

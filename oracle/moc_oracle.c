@@ -120,6 +120,12 @@ typedef struct {
   double *psi3_in, *psi3_next;  /* [T][2 sense][2 down/up][nz][P][2][G] radial boundary flux moments */
   double *ztop;       /* [S][2 sense][P][G] upward top-face trace of the last sweep (reflective top) */
   double *leak3;      /* [3][G] leakage of the last sweep: radial, bottom, top */
+  /* axial coarse-mesh acceleration of DGMOC: coarse cells = planes */
+  int dgcm, dgcm_outer, dgcm_inner;
+  double dgcm_omega;
+  double *jz;         /* [2][nz-1][G]: partial currents up (plane z -> z+1) and down (z+1 -> z) */
+  double *zleak;      /* [nz][G]: net current out of each plane through the domain boundary
+                         (radial track ends, bottom and top faces): out minus in */
   char err[256];
 } orc_t;
 
@@ -144,7 +150,7 @@ void orc_destroy(orc_t *h) {
   free(h->nb_off); free(h->nb_cell); free(h->nb_in);
   free(h->ssl); free(h->kern); free(h->qdir); free(h->tdir); free(h->pbar);
   free(h->dz); free(h->mat3); free(h->phi3); free(h->q3); free(h->tal3); free(h->psi3_in); free(h->psi3_next);
-  free(h->ztop); free(h->leak3);
+  free(h->ztop); free(h->leak3); free(h->jz); free(h->zleak);
   free(h);
 }
 
@@ -556,9 +562,9 @@ int orc_set_xs(orc_t *h, int n_mat, int G, const double *st, const double *nsf, 
   h->cell = NULL; h->pairs = NULL; h->cur = NULL; h->cleak = NULL; h->color = NULL; h->cmfd = 0;
   h->nb_off = h->nb_cell = h->nb_in = NULL;
   free(h->dz); free(h->mat3); free(h->phi3); free(h->q3); free(h->tal3); free(h->psi3_in); free(h->psi3_next);
-  free(h->ztop); free(h->leak3);
-  h->dz = h->phi3 = h->q3 = h->tal3 = h->psi3_in = h->psi3_next = h->ztop = h->leak3 = NULL;
-  h->mat3 = NULL; h->nz = 0;
+  free(h->ztop); free(h->leak3); free(h->jz); free(h->zleak);
+  h->dz = h->phi3 = h->q3 = h->tal3 = h->psi3_in = h->psi3_next = h->ztop = h->leak3 = h->jz = h->zleak = NULL;
+  h->mat3 = NULL; h->nz = 0; h->dgcm = 0;
   h->n_mat = n_mat; h->G = G;
   h->st = xcalloc((size_t)n_mat * G, sizeof(double)); memcpy(h->st, st, (size_t)n_mat * G * sizeof(double));
   h->nsf = xcalloc((size_t)n_mat * G, sizeof(double)); memcpy(h->nsf, nsf, (size_t)n_mat * G * sizeof(double));
@@ -1205,9 +1211,9 @@ void orc_dg_segment(const double *y0, double psi_in, double len, double sin_thet
  * materials in every plane). The state restarts flat: phi_0 = 1, phi_1 = 0, zero boundary flux. */
 int orc_set_axial(orc_t *h, int nz, const double *dz, const int32_t *mat3, int bc_bottom, int bc_top) {
   free(h->dz); free(h->mat3); free(h->phi3); free(h->q3); free(h->tal3); free(h->psi3_in); free(h->psi3_next);
-  free(h->ztop); free(h->leak3);
-  h->dz = h->phi3 = h->q3 = h->tal3 = h->psi3_in = h->psi3_next = h->ztop = h->leak3 = NULL;
-  h->mat3 = NULL; h->nz = 0;
+  free(h->ztop); free(h->leak3); free(h->jz); free(h->zleak);
+  h->dz = h->phi3 = h->q3 = h->tal3 = h->psi3_in = h->psi3_next = h->ztop = h->leak3 = h->jz = h->zleak = NULL;
+  h->mat3 = NULL; h->nz = 0; h->dgcm = 0;
   if (nz <= 0) return 0;
   if (h->cmfd || h->L) { snprintf(h->err, sizeof h->err, "DGMOC with CMFD or anisotropic scattering is not supported"); return -1; }
   if (!h->st) { snprintf(h->err, sizeof h->err, "set_axial before set_xs"); return -1; }
@@ -1235,7 +1241,21 @@ int orc_set_axial(orc_t *h, int nz, const double *dz, const int32_t *mat3, int b
   h->psi3_next = xcalloc(nb, sizeof(double));
   h->ztop = xcalloc((size_t)h->n_seg * 2 * P * G, sizeof(double));
   h->leak3 = xcalloc(3 * G, sizeof(double));
+  h->jz = xcalloc(2 * (size_t)(nz > 1 ? nz - 1 : 1) * G, sizeof(double));
+  h->zleak = xcalloc((size_t)nz * G, sizeof(double));
   dg_set_state(h, NULL, 1.0);
+  return 0;
+}
+
+/* Axial coarse-mesh acceleration of DGMOC (the CMFD step of Alg. 1 with the planes as coarse
+ * cells): n_outer coarse power iterations of n_inner over-relaxed (omega) Gauss-Seidel sweeps per
+ * group, odd and even planes as the two colours. n_outer = 0 switches it off. */
+int orc_set_dg_cmfd(orc_t *h, int n_outer, int n_inner, double omega) {
+  h->dgcm = 0;
+  if (n_outer <= 0) return 0;
+  if (!h->nz) { snprintf(h->err, sizeof h->err, "DGMOC acceleration needs set_axial first"); return -1; }
+  if (n_inner <= 0 || !(omega > 0.0 && omega < 2.0)) { snprintf(h->err, sizeof h->err, "bad acceleration parameters"); return -1; }
+  h->dgcm = 1; h->dgcm_outer = n_outer; h->dgcm_inner = n_inner; h->dgcm_omega = omega;
   return 0;
 }
 
@@ -1300,6 +1320,9 @@ static void dg_sweep(orc_t *h) {
   size_t R = h->n_tri;
   memset(h->tal3, 0, (size_t)nz * R * 2 * G * sizeof(double));
   memset(h->psi3_next, 0, (size_t)h->n_tracks * 2 * 2 * nz * P * 2 * G * sizeof(double));
+  size_t nif = nz > 1 ? nz - 1 : 1;
+  memset(h->jz, 0, 2 * nif * G * sizeof(double));
+  memset(h->zleak, 0, (size_t)nz * G * sizeof(double));
   int64_t maxn = 0;
   for (int64_t t = 0; t < h->n_tracks; ++t)
     if (h->seg_off[t + 1] - h->seg_off[t] > maxn) maxn = h->seg_off[t + 1] - h->seg_off[t];
@@ -1321,11 +1344,14 @@ static void dg_sweep(orc_t *h) {
               int64_t s = d ? (s0 + ns - 1 - n) : (s0 + n);
               if (ud == 0) face[n] = h->bcz[1] ? h->ztop[((size_t)s * 2 + d) * P * G + (size_t)p * G + g] : 0.0;
               else if (!h->bcz[0]) face[n] = 0.0;   /* reflective bottom: keep the downward traces */
+              /* current entering the first plane of the march through the top or bottom face */
+              h->zleak[(size_t)(ud ? 0 : nz - 1) * G + g] -= W * mu * h->seg_len[s] * face[n];
             }
             for (int zi = 0; zi < nz; ++zi) {
               int z = ud ? zi : nz - 1 - zi;
               size_t bidx = ((((size_t)(2 * t + d) * 2 + ud) * nz + z) * P + p) * 2 * G;
               double y[2] = {h->psi3_in[bidx + g], h->psi3_in[bidx + G + g]};
+              h->zleak[(size_t)z * G + g] -= W * st * h->dz[z] * y[0];   /* radial current in at the start */
               for (int64_t n = 0; n < ns; ++n) {
                 int64_t s = d ? (s0 + ns - 1 - n) : (s0 + n);
                 int i = h->seg_reg[s];
@@ -1348,6 +1374,17 @@ static void dg_sweep(orc_t *h) {
               } else {
                 lk[g] += W * st * h->dz[z] * y[0];
               }
+              h->zleak[(size_t)z * G + g] += W * st * h->dz[z] * y[0];   /* radial current out at the end */
+              /* the plane's outflow through its downwind face: into the next plane of the march,
+               * or out of the domain */
+              double J = 0.0;
+              for (int64_t n = 0; n < ns; ++n) {
+                int64_t s = d ? (s0 + ns - 1 - n) : (s0 + n);
+                J += W * mu * h->seg_len[s] * face[n];
+              }
+              if (ud == 1 && z < nz - 1) h->jz[(size_t)z * G + g] += J;
+              else if (ud == 0 && z > 0) h->jz[(nif + (size_t)(z - 1)) * G + g] += J;
+              else h->zleak[(size_t)z * G + g] += J;
             }
             /* the march's last face: bottom (downward) or top (upward) */
             for (int64_t n = 0; n < ns; ++n) {
@@ -1366,6 +1403,114 @@ static void dg_sweep(orc_t *h) {
   }
   memcpy(h->leak3, lk, 3 * (size_t)G * sizeof(double));
   free(lk);
+}
+
+/* The coarse step with the planes as coarse cells, on the normalised new moments pn (currents
+ * normalised alike): flux-volume homogenisation per plane, coarse balance
+ *   (Sigma_t V - Sigma_s,gg V + J_out/phi_z + L_z/phi_z) phi_z
+ *     = sum_{g' != g} Sigma_s,g'g V phi_z,g' + chi/k nuSigma_f V phi + J_in from each neighbour
+ * with D = J / phi of the current iterate (a fixed point at the transport solution), a fixed
+ * number of coarse power iterations (Gauss-Seidel in energy, over-relaxed Gauss-Seidel over the
+ * planes, even planes then odd), then both moments of every element, the radial boundary flux of
+ * every plane and the stored top traces scaled by their plane's coarse/fine ratio; k = coarse k. */
+static void dg_cmfd_step(orc_t *h, double *pn) {
+  int G = h->G, nz = h->nz;
+  size_t R = h->n_tri, nif = nz > 1 ? nz - 1 : 1;
+  double *cphi = xcalloc((size_t)nz * G, sizeof(double)), *TV = xcalloc((size_t)nz * G, sizeof(double));
+  double *FV = xcalloc((size_t)nz * G, sizeof(double)), *CH = xcalloc((size_t)nz * G, sizeof(double));
+  double *SV = xcalloc((size_t)nz * G * G, sizeof(double)), *V = xcalloc(nz, sizeof(double));
+  for (int z = 0; z < nz; ++z)
+    for (size_t r = 0; r < R; ++r) {
+      int m = h->mat3[(size_t)z * R + r];
+      double A = h->area[r] * h->dz[z], f = 0.0;
+      const double *ph = pn + ((size_t)z * R + r) * 2 * G;
+      V[z] += A;
+      for (int g = 0; g < G; ++g) f += h->nsf[(size_t)m * G + g] * ph[g];
+      for (int g = 0; g < G; ++g) {
+        double a = A * ph[g];
+        cphi[(size_t)z * G + g] += a;
+        TV[(size_t)z * G + g] += h->st[(size_t)m * G + g] * a;
+        FV[(size_t)z * G + g] += h->nsf[(size_t)m * G + g] * a;
+        CH[(size_t)z * G + g] += h->chi[(size_t)m * G + g] * A * f;
+        for (int gg = 0; gg < G; ++gg) SV[((size_t)z * G + g) * G + gg] += h->ss[((size_t)m * G + g) * G + gg] * a;
+      }
+    }
+  for (int z = 0; z < nz; ++z) {
+    double chs = 0.0;
+    for (int g = 0; g < G; ++g) chs += CH[(size_t)z * G + g];
+    for (int g = 0; g < G; ++g) {
+      size_t x = (size_t)z * G + g;
+      double raw = cphi[x];
+      if (raw > 0.0) {
+        TV[x] = TV[x] * V[z] / raw;
+        FV[x] = FV[x] * V[z] / raw;
+        for (int gg = 0; gg < G; ++gg) SV[x * G + gg] = SV[x * G + gg] * V[z] / raw;
+      } else {
+        TV[x] = FV[x] = 0.0;
+        for (int gg = 0; gg < G; ++gg) SV[x * G + gg] = 0.0;
+      }
+      cphi[x] = V[z] > 0.0 ? raw / V[z] : 0.0;
+      CH[x] = chs > 0.0 ? CH[x] / chs : 0.0;
+    }
+  }
+  const double *jup = h->jz, *jdn = h->jz + nif * G;
+  double *diag = xcalloc((size_t)nz * G, sizeof(double)), *phic = xcalloc((size_t)nz * G, sizeof(double));
+  double *fis = xcalloc(nz, sizeof(double));
+  for (int z = 0; z < nz; ++z)
+    for (int g = 0; g < G; ++g) {
+      size_t x = (size_t)z * G + g;
+      double pz = cphi[x], dg = TV[x] - SV[x * G + g];
+      if (pz > 0.0) {
+        dg += h->zleak[x] / pz;
+        if (z < nz - 1) dg += jup[(size_t)z * G + g] / pz;
+        if (z > 0) dg += jdn[(size_t)(z - 1) * G + g] / pz;
+      }
+      diag[x] = dg;
+      phic[x] = pz;
+    }
+  double kc = h->k;
+  for (int it = 0; it < h->dgcm_outer; ++it) {
+    double F_old = 0.0;
+    for (int z = 0; z < nz; ++z) {
+      double f = 0.0;
+      for (int g = 0; g < G; ++g) f += FV[(size_t)z * G + g] * phic[(size_t)z * G + g];
+      fis[z] = f;
+      F_old += f;
+    }
+    for (int g = 0; g < G; ++g)
+      for (int j = 0; j < h->dgcm_inner; ++j)
+        for (int c = 0; c < 2; ++c)
+          for (int z = c; z < nz; z += 2) {
+            size_t x = (size_t)z * G + g;
+            double rhs = CH[x] * fis[z] / kc;
+            for (int gg = 0; gg < G; ++gg)
+              if (gg != g) rhs += SV[((size_t)z * G + gg) * G + g] * phic[(size_t)z * G + gg];
+            if (z > 0 && cphi[x - G] > 0.0) rhs += jup[(size_t)(z - 1) * G + g] / cphi[x - G] * phic[x - G];
+            if (z < nz - 1 && cphi[x + G] > 0.0) rhs += jdn[(size_t)z * G + g] / cphi[x + G] * phic[x + G];
+            if (diag[x] > 0.0) phic[x] += h->dgcm_omega * (rhs / diag[x] - phic[x]);
+          }
+    double F_new = 0.0;
+    for (int z = 0; z < nz; ++z)
+      for (int g = 0; g < G; ++g) F_new += FV[(size_t)z * G + g] * phic[(size_t)z * G + g];
+    if (F_new > 0.0 && F_old > 0.0) kc = kc * F_new / F_old;
+  }
+  double *ratio = xcalloc((size_t)nz * G, sizeof(double));
+  for (size_t x = 0; x < (size_t)nz * G; ++x) ratio[x] = (cphi[x] > 0.0 && phic[x] > 0.0) ? phic[x] / cphi[x] : 1.0;
+  for (int z = 0; z < nz; ++z)
+    for (size_t r = 0; r < R; ++r)
+      for (int mo = 0; mo < 2; ++mo)
+        for (int g = 0; g < G; ++g) pn[(((size_t)z * R + r) * 2 + mo) * G + g] *= ratio[(size_t)z * G + g];
+  int P = h->n_polar;
+  for (int64_t e = 0; e < 2 * h->n_tracks; ++e)
+    for (int ud = 0; ud < 2; ++ud)
+      for (int z = 0; z < nz; ++z)
+        for (int p = 0; p < P; ++p)
+          for (int mo = 0; mo < 2; ++mo)
+            for (int g = 0; g < G; ++g)
+              h->psi3_next[(((((size_t)e * 2 + ud) * nz + z) * P + p) * 2 + mo) * G + g] *= ratio[(size_t)z * G + g];
+  for (size_t x = 0; x < (size_t)h->n_seg * 2 * P * G; ++x) h->ztop[x] *= ratio[(size_t)(nz - 1) * G + x % G];
+  h->k = kc;
+  free(cphi); free(TV); free(FV); free(CH); free(SV); free(V); free(diag); free(phic); free(fis); free(ratio);
 }
 
 static double dg_outer(orc_t *h, int eigen) {
@@ -1394,6 +1539,8 @@ static double dg_outer(orc_t *h, int eigen) {
     for (size_t x = 0; x < nb; ++x) h->psi3_next[x] /= F_new;
     for (size_t x = 0; x < nt; ++x) h->ztop[x] /= F_new;
     for (int x = 0; x < 3 * G; ++x) h->leak3[x] /= F_new;
+    for (size_t x = 0; x < 2 * (size_t)(nz > 1 ? nz - 1 : 1) * G; ++x) h->jz[x] /= F_new;
+    for (size_t x = 0; x < (size_t)nz * G; ++x) h->zleak[x] /= F_new;
     for (int z = 0; z < nz; ++z)
       for (size_t i = 0; i < R; ++i) {
         const double *nf = h->nsf + (size_t)h->mat3[(size_t)z * R + i] * G;
@@ -1402,6 +1549,13 @@ static double dg_outer(orc_t *h, int eigen) {
         for (int g = 0; g < G; ++g) { fo += nf[g] * h->phi3[e + g] / F_old; fn += nf[g] * pn[e + g]; }
         if (fn > 0.0) { double r = fabs(fn - fo) / fn; if (r > resid) resid = r; }
       }
+    if (h->dgcm) {
+      dg_cmfd_step(h, pn);
+      double F2 = dg_fission_total(h, pn);
+      for (size_t x = 0; x < n3; ++x) pn[x] /= F2;
+      for (size_t x = 0; x < nb; ++x) h->psi3_next[x] /= F2;
+      for (size_t x = 0; x < nt; ++x) h->ztop[x] /= F2;
+    }
   } else {
     for (int z = 0; z < nz; ++z)
       for (size_t i = 0; i < R; ++i)

@@ -83,6 +83,16 @@ struct moc_ctx {
   int dg_nz = 0;
   int dg_bc[2] = {0, 0};
   size_t dg_res_smem = 0;  // shared memory of the plane-inner sweep per block (0: plane-by-plane sweep)
+  // axial coarse-mesh acceleration of DGMOC (planes as coarse cells; off unless moc_set_dg_cmfd)
+  int dgcm_outer = 0, dgcm_inner = 0;
+  double dgcm_omega = 1.0;
+  size_t dgcm_smem = 0;
+  void *d_mu = nullptr, *d_dzr = nullptr;
+  double *d_dgcur = nullptr, *d_dgleak = nullptr, *d_dgvol = nullptr, *d_dgpsum = nullptr;
+  double *d_dgdiag = nullptr, *d_dgphic = nullptr, *d_dgfis = nullptr, *d_dgpart = nullptr;
+  void *d_dgcphi = nullptr, *d_dgTV = nullptr, *d_dgSV = nullptr, *d_dgFV = nullptr, *d_dgCHI = nullptr,
+       *d_dgratio = nullptr;
+  unsigned *d_dgticket = nullptr;
   std::vector<double> h_dz;
   std::vector<int32_t> h_mat3;
   int32_t *d_mat3 = nullptr;
@@ -183,8 +193,31 @@ void free_aniso(moc_ctx *c) {
   c->aniso_L = c->aniso_NK = 0;
 }
 
-void free_dg(moc_ctx *c) {
+void free_dgcm(moc_ctx *c) {
   drop_graphs(c);
+  dfree(c->d_mu);
+  dfree(c->d_dzr);
+  dfree(c->d_dgcur);
+  dfree(c->d_dgleak);
+  dfree(c->d_dgvol);
+  dfree(c->d_dgpsum);
+  dfree(c->d_dgdiag);
+  dfree(c->d_dgphic);
+  dfree(c->d_dgfis);
+  dfree(c->d_dgpart);
+  dfree(c->d_dgcphi);
+  dfree(c->d_dgTV);
+  dfree(c->d_dgSV);
+  dfree(c->d_dgFV);
+  dfree(c->d_dgCHI);
+  dfree(c->d_dgratio);
+  dfree(c->d_dgticket);
+  c->dgcm_outer = 0;
+  c->dgcm_smem = 0;
+}
+
+void free_dg(moc_ctx *c) {
+  free_dgcm(c);
   dfree(c->d_mat3);
   dfree(c->d_dz);
   dfree(c->d_fold3);
@@ -688,11 +721,20 @@ template <typename Real, int P> size_t dg_res_smem(int nz) {
 template <typename Real, int P> void dg_sweep_launch(moc_ctx *c, cudaStream_t st) {
   const long long n = (long long)c->T * 2 * c->G;
   if (c->dg_res_smem) {
-    dg_sweep_res_kernel<Real, P><<<(unsigned)((n + kDgResBlock - 1) / kDgResBlock), kDgResBlock, c->dg_res_smem, st>>>(
-        c->d_trk, (const SegRec<Real> *)c->d_seg, c->d_link, (const Real *)c->d_wdg, (const Real *)c->d_sin,
-        (const Real *)c->d_inv_sin, (const Real *)c->d_cz, (const DgXs<Real> *)c->d_xs3, (Real *)c->d_tal3,
-        (const Real *)c->d_psi3[c->cur], (Real *)c->d_psi3[c->cur ^ 1], (Real *)c->d_face, c->d_scal, n, c->G,
-        c->Gp, c->geo.n_tri, c->dg_nz, c->dg_bc[0], c->dg_bc[1]);
+    const unsigned nb = (unsigned)((n + kDgResBlock - 1) / kDgResBlock);
+    const DgCm<Real> cm{(const Real *)c->d_mu, (const Real *)c->d_dzr, c->d_dgcur, c->d_dgleak};
+    if (c->dgcm_outer && c->eigen)
+      dg_sweep_res_kernel<Real, P, true><<<nb, kDgResBlock, c->dgcm_smem, st>>>(
+          c->d_trk, (const SegRec<Real> *)c->d_seg, c->d_link, (const Real *)c->d_wdg, (const Real *)c->d_sin,
+          (const Real *)c->d_inv_sin, (const Real *)c->d_cz, (const DgXs<Real> *)c->d_xs3, (Real *)c->d_tal3,
+          (const Real *)c->d_psi3[c->cur], (Real *)c->d_psi3[c->cur ^ 1], (Real *)c->d_face, c->d_scal, n, c->G,
+          c->Gp, c->geo.n_tri, c->dg_nz, c->dg_bc[0], c->dg_bc[1], cm);
+    else
+      dg_sweep_res_kernel<Real, P, false><<<nb, kDgResBlock, c->dg_res_smem, st>>>(
+          c->d_trk, (const SegRec<Real> *)c->d_seg, c->d_link, (const Real *)c->d_wdg, (const Real *)c->d_sin,
+          (const Real *)c->d_inv_sin, (const Real *)c->d_cz, (const DgXs<Real> *)c->d_xs3, (Real *)c->d_tal3,
+          (const Real *)c->d_psi3[c->cur], (Real *)c->d_psi3[c->cur ^ 1], (Real *)c->d_face, c->d_scal, n, c->G,
+          c->Gp, c->geo.n_tri, c->dg_nz, c->dg_bc[0], c->dg_bc[1], cm);
     return;
   }
   dg_sweep_kernel<Real, P><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(
@@ -712,6 +754,36 @@ template <typename Real> int launch_dg_sweep(moc_ctx *c, cudaStream_t st) {
       default: return fail(c, MOC_ERR_ARG, "DGMOC: up to 4 polar angles");
     }
   }
+  CUDA_TRY(c, cudaGetLastError());
+  return MOC_OK;
+}
+
+// axial CMFD after finalize and the buffer flip: homogenise per plane, coarse solve, prolong the
+// moments, the next sweep's radial boundary flux and the stored top traces
+template <typename Real> int launch_dg_cmfd(moc_ctx *c, cudaStream_t st) {
+  const int R = c->geo.n_tri, G = c->G, nz = c->dg_nz, E = nz * R;
+  CUDA_TRY(c, cudaMemsetAsync(c->d_dgpsum, 0, (size_t)nz * c->M * G * sizeof(double), st));
+  const long long neg = (long long)E * G;
+  dg_cm_sums_kernel<Real><<<(unsigned)((neg + 255) / 256), 256, 0, st>>>(E, R, G, c->Gp, c->M, c->d_mat3, c->d_area,
+                                                                       (const Real *)c->d_dzr, (const Real *)c->d_phi3,
+                                                                       c->d_dgpsum);
+  cmfd_coeff_kernel<Real><<<(nz * G + 127) / 128, 128, 0, st>>>(
+      nz, G, c->M, c->d_dgpsum, c->d_dgvol, (const Real *)c->d_sig_t, (const Real *)c->d_nsf, (const Real *)c->d_chi,
+      (const Real *)c->d_sig_s, (Real *)c->d_dgcphi, (Real *)c->d_dgTV, (Real *)c->d_dgSV, (Real *)c->d_dgFV,
+      (Real *)c->d_dgCHI);
+  dg_cm_solve_kernel<Real><<<1, 256, 0, st>>>(nz, G, c->Gp, c->d_dgcur, c->d_dgleak, (const Real *)c->d_dgcphi,
+                                              (const Real *)c->d_dgTV, (const Real *)c->d_dgSV,
+                                              (const Real *)c->d_dgFV, (const Real *)c->d_dgCHI, c->d_dgdiag,
+                                              c->d_dgphic, c->d_dgfis, (Real *)c->d_dgratio, c->d_scal,
+                                              c->dgcm_outer, c->dgcm_inner, c->dgcm_omega);
+  dg_cm_prolong_kernel<Real><<<(E + 255) / 256, 256, 0, st>>>(E, R, G, c->Gp, nz, c->d_mat3, (const Real *)c->d_nsf,
+                                                              c->d_area, (const Real *)c->d_dzr,
+                                                              (const Real *)c->d_dgratio, (Real *)c->d_phi3,
+                                                              c->d_dgpart, c->d_dgticket, c->d_scal);
+  const long long n_psi = (long long)c->T * 2 * 2 * nz * c->P * 2 * G;
+  const long long n_face = c->dg_bc[1] ? (long long)(c->S + 2 * kSegPad) * 2 * c->P * G : 0;
+  dg_cm_psi_kernel<Real><<<(unsigned)((n_psi + n_face + 255) / 256), 256, 0, st>>>(
+      n_psi, n_face, c->P, G, nz, (const Real *)c->d_dgratio, (Real *)c->d_psi3[c->cur], (Real *)c->d_face);
   CUDA_TRY(c, cudaGetLastError());
   return MOC_OK;
 }
@@ -809,6 +881,8 @@ int enqueue_sweep(moc_ctx *c, cudaStream_t st, bool timed) {
   if (c->dg_nz) {
     rc = c->precision == MOC_FP64 ? launch_dg_finalize<double>(c, st) : launch_dg_finalize<float>(c, st);
     c->cur ^= 1;
+    if (!rc && c->dgcm_outer && c->eigen)
+      rc = c->precision == MOC_FP64 ? launch_dg_cmfd<double>(c, st) : launch_dg_cmfd<float>(c, st);
     return rc;
   }
   if (c->aniso_L) {
@@ -1068,10 +1142,10 @@ template <typename Real> int dg_alloc(moc_ctx *c) {
   size_t sm = 0;
   cudaError_t e = cudaSuccess;
   switch (P) {
-    case 1: sm = dg_res_smem<Real, 1>(nz); if (sm <= kDgResSmemMax) e = cudaFuncSetAttribute(dg_sweep_res_kernel<Real, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); break;
-    case 2: sm = dg_res_smem<Real, 2>(nz); if (sm <= kDgResSmemMax) e = cudaFuncSetAttribute(dg_sweep_res_kernel<Real, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); break;
-    case 3: sm = dg_res_smem<Real, 3>(nz); if (sm <= kDgResSmemMax) e = cudaFuncSetAttribute(dg_sweep_res_kernel<Real, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); break;
-    default: sm = dg_res_smem<Real, 4>(nz); if (sm <= kDgResSmemMax) e = cudaFuncSetAttribute(dg_sweep_res_kernel<Real, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); break;
+    case 1: sm = dg_res_smem<Real, 1>(nz); if (sm <= kDgResSmemMax) e = cudaFuncSetAttribute(dg_sweep_res_kernel<Real, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); break;
+    case 2: sm = dg_res_smem<Real, 2>(nz); if (sm <= kDgResSmemMax) e = cudaFuncSetAttribute(dg_sweep_res_kernel<Real, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); break;
+    case 3: sm = dg_res_smem<Real, 3>(nz); if (sm <= kDgResSmemMax) e = cudaFuncSetAttribute(dg_sweep_res_kernel<Real, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); break;
+    default: sm = dg_res_smem<Real, 4>(nz); if (sm <= kDgResSmemMax) e = cudaFuncSetAttribute(dg_sweep_res_kernel<Real, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); break;
   }
   if (e != cudaSuccess) return fail(c, MOC_ERR_CUDA, std::string("set_axial: ") + cudaGetErrorString(e));
   c->dg_res_smem = sm <= kDgResSmemMax ? sm : 0;
@@ -1116,6 +1190,81 @@ int moc_set_axial(moc_ctx *c, int nz, const double *dz, const int32_t *mat3, int
     return rc;
   }
   return moc_set_state(c, nullptr, 1.0, nullptr);
+}
+
+}  // extern "C"
+
+namespace {
+
+template <typename Real, int P> int dg_cm_attr(moc_ctx *c, size_t sm) {
+  CUDA_TRY(c, cudaFuncSetAttribute(dg_sweep_res_kernel<Real, P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)sm));
+  return MOC_OK;
+}
+
+template <typename Real> int dg_cm_alloc(moc_ctx *c) {
+  const int nz = c->dg_nz, G = c->G, Gp = c->Gp, P = c->P, R = c->geo.n_tri;
+  const size_t sm = c->dg_res_smem + (size_t)kDgResBlock * 3 * nz * sizeof(Real);
+  if (!c->dg_res_smem || sm > kDgResSmemMax)
+    return fail(c, MOC_ERR_ARG, "set_dg_cmfd: too many planes for the plane-inner sweep's shared memory");
+  int rc = P == 1 ? dg_cm_attr<Real, 1>(c, sm) : P == 2 ? dg_cm_attr<Real, 2>(c, sm)
+         : P == 3 ? dg_cm_attr<Real, 3>(c, sm) : dg_cm_attr<Real, 4>(c, sm);
+  if (rc) return rc;
+  std::vector<Real> mu(P), dzr(nz);
+  for (int p = 0; p < P; ++p) mu[p] = (Real)std::sqrt(std::max(0.0, 1.0 - c->geo.sin_theta[p] * c->geo.sin_theta[p]));
+  for (int z = 0; z < nz; ++z) dzr[z] = (Real)c->h_dz[z];
+  std::vector<double> vol(nz, 0.0);
+  for (int z = 0; z < nz; ++z)
+    for (int r = 0; r < R; ++r) vol[z] += c->geo.area[r] * (double)(Real)c->h_dz[z];
+  Real *pm = nullptr, *pz = nullptr;
+  if ((rc = upload(c, pm, mu.data(), mu.size()))) return rc;
+  c->d_mu = pm;
+  if ((rc = upload(c, pz, dzr.data(), dzr.size()))) return rc;
+  c->d_dzr = pz;
+  if ((rc = upload(c, c->d_dgvol, vol.data(), vol.size()))) return rc;
+  CUDA_TRY(c, cudaMalloc((void **)&c->d_dgcur, (size_t)2 * nz * Gp * sizeof(double)));
+  CUDA_TRY(c, cudaMemset(c->d_dgcur, 0, (size_t)2 * nz * Gp * sizeof(double)));
+  CUDA_TRY(c, cudaMalloc((void **)&c->d_dgleak, (size_t)nz * Gp * sizeof(double)));
+  CUDA_TRY(c, cudaMemset(c->d_dgleak, 0, (size_t)nz * Gp * sizeof(double)));
+  CUDA_TRY(c, cudaMalloc((void **)&c->d_dgpsum, (size_t)nz * c->M * G * sizeof(double)));
+  CUDA_TRY(c, cudaMalloc((void **)&c->d_dgdiag, (size_t)nz * G * sizeof(double)));
+  CUDA_TRY(c, cudaMalloc((void **)&c->d_dgphic, (size_t)nz * G * sizeof(double)));
+  CUDA_TRY(c, cudaMalloc((void **)&c->d_dgfis, (size_t)nz * sizeof(double)));
+  CUDA_TRY(c, cudaMalloc((void **)&c->d_dgpart, (size_t)((nz * R + 255) / 256) * sizeof(double)));
+  CUDA_TRY(c, cudaMalloc(&c->d_dgcphi, (size_t)nz * G * sizeof(Real)));
+  CUDA_TRY(c, cudaMalloc(&c->d_dgTV, (size_t)nz * G * sizeof(Real)));
+  CUDA_TRY(c, cudaMalloc(&c->d_dgSV, (size_t)nz * G * G * sizeof(Real)));
+  CUDA_TRY(c, cudaMalloc(&c->d_dgFV, (size_t)nz * G * sizeof(Real)));
+  CUDA_TRY(c, cudaMalloc(&c->d_dgCHI, (size_t)nz * G * sizeof(Real)));
+  CUDA_TRY(c, cudaMalloc(&c->d_dgratio, (size_t)nz * G * sizeof(Real)));
+  CUDA_TRY(c, cudaMalloc((void **)&c->d_dgticket, sizeof(unsigned)));
+  CUDA_TRY(c, cudaMemset(c->d_dgticket, 0, sizeof(unsigned)));
+  c->dgcm_smem = sm;
+  return MOC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int moc_set_dg_cmfd(moc_ctx *c, int n_outer, int n_inner, double omega) {
+  int rc = need_ready(c);
+  if (rc) return rc;
+  cudaSetDevice(c->device);
+  free_dgcm(c);
+  if (n_outer == 0) return MOC_OK;
+  if (!c->dg_nz) return fail(c, MOC_ERR_STATE, "set_dg_cmfd: call moc_set_axial first");
+  if (n_outer < 0 || n_inner < 1) return fail(c, MOC_ERR_ARG, "set_dg_cmfd: bad iteration counts");
+  if (!(omega > 0.0 && omega < 2.0)) return fail(c, MOC_ERR_ARG, "set_dg_cmfd: omega must lie in (0, 2)");
+  rc = c->precision == MOC_FP64 ? dg_cm_alloc<double>(c) : dg_cm_alloc<float>(c);
+  if (rc) {
+    free_dgcm(c);
+    return rc;
+  }
+  c->dgcm_outer = n_outer;
+  c->dgcm_inner = n_inner;
+  c->dgcm_omega = omega;
+  return MOC_OK;
 }
 
 int moc_create(moc_ctx **out, int device, int precision, void *stream) {
@@ -1974,7 +2123,8 @@ int moc_get_work(const moc_ctx *c, int64_t *n_segments, int64_t *updates, int *k
   const int64_t planes = c->dg_nz ? 2 * (int64_t)c->dg_nz : 1;
   if (updates) *updates = 2 * c->geo.n_segments() * (int64_t)c->geo.n_polar * (int64_t)std::max(c->G, 0) * planes;
   if (kernels)
-    *kernels = c->dg_nz ? 4 : ((c->Gp == 8) ? 3 : 4) + (c->cmfd ? 5 : 0) + (c->aniso_L ? 2 : 0);
+    *kernels = c->dg_nz ? 4 + (c->dgcm_outer && c->eigen ? 5 : 0)
+                        : ((c->Gp == 8) ? 3 : 4) + (c->cmfd ? 5 : 0) + (c->aniso_L ? 2 : 0);
   return MOC_OK;
 }
 

@@ -250,18 +250,30 @@ __global__ void __launch_bounds__(128) dg_sweep_kernel(
 // the tally atomics differs.
 constexpr int kDgResBlock = 64;  // threads per block of the plane-inner sweep
 
-template <typename Real, int P>
+// Axial coarse-mesh acceleration (coarse cells = planes), tallied by the plane-inner sweep:
+// partial currents between planes and the net current out of each plane through the domain
+// boundary (radial track ends, bottom and top faces: out minus in), FP64 as in the planar CMFD.
+template <typename Real> struct DgCm {
+  const Real *mu;   // [P] polar cosines
+  const Real *dz;   // [nz] plane heights
+  double *cur;      // [2][nz][Gp]: [0][z] plane z -> z+1, [1][z] plane z+1 -> z
+  double *leak;     // [nz][Gp]
+};
+
+template <typename Real, int P, bool CM>
 __global__ void __launch_bounds__(kDgResBlock) dg_sweep_res_kernel(
     const TrackRec *__restrict__ trk, const SegRec<Real> *__restrict__ seg, const int32_t *__restrict__ link,
     const Real *__restrict__ wdg, const Real *__restrict__ sin_t, const Real *__restrict__ inv_sin,
     const Real *__restrict__ cz, const DgXs<Real> *__restrict__ xs3, Real *__restrict__ tally,
     const Real *__restrict__ psi_in, Real *__restrict__ psi_out, Real *__restrict__ face,
-    const double *__restrict__ scal, long long n_threads, int G, int Gp, int R, int nz, int bc_bottom, int bc_top) {
+    const double *__restrict__ scal, long long n_threads, int G, int Gp, int R, int nz, int bc_bottom, int bc_top,
+    DgCm<Real> cm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int B = kDgResBlock;  // launched with exactly this many threads
   const int tid = threadIdx.x;
   Real *ys = reinterpret_cast<Real *>(smem_raw);  // [2][nz][P][2][B]
   Real *rc = ys + (size_t)4 * nz * P * B;         // [3][nz][B]: Sigma_t, q0, q1 of the segment's region
+  Real *ca = rc + (size_t)3 * nz * B;             // CM: [3][nz][B] current up, current down, boundary
   const long long idx = (long long)blockIdx.x * B + tid;
   if (idx >= n_threads) return;
   const long long td = idx / G;
@@ -280,6 +292,20 @@ __global__ void __launch_bounds__(kDgResBlock) dg_sweep_res_kernel(
   {
     const Real *pi = psi_in + td * nslot * G + g;  // [2T][2][nz][P][2][G]: slots of one end in order
     for (int k = 0; k < nslot; ++k) ys[(size_t)k * B + tid] = pi[(size_t)k * G] * scale;
+  }
+  Real mu[P];
+  if (CM) {
+#pragma unroll
+    for (int p = 0; p < P; ++p) mu[p] = cm.mu[p];
+    for (int k = 0; k < 3 * nz; ++k) ca[(size_t)k * B + tid] = 0;
+    // radial current in at the track's start, every plane and march
+    for (int ud = 0; ud < 2; ++ud)
+      for (int z = 0; z < nz; ++z) {
+        Real j = 0;
+#pragma unroll
+        for (int p = 0; p < P; ++p) j = fma(w[p] * st[p], ys[((size_t)((ud * nz + z) * P + p) * 2) * B + tid], j);
+        ca[(size_t)(2 * nz + z) * B + tid] -= j * cm.dz[z];
+      }
   }
   const int step = d ? -1 : 1;
   const SegRec<Real> *sp = seg + (d ? tr.off + tr.n - 1 : tr.off);
@@ -304,6 +330,13 @@ __global__ void __launch_bounds__(kDgResBlock) dg_sweep_res_kernel(
 #pragma unroll
         for (int p = 0; p < P; ++p) fin[p] = 0;
       }
+      if (CM) {
+        // current entering the march's first plane through the top or bottom face
+        Real j = 0;
+#pragma unroll
+        for (int p = 0; p < P; ++p) j = fma(w[p] * mu[p], fin[p], j);
+        ca[(size_t)(2 * nz + (ud ? 0 : nz - 1)) * B + tid] -= j * s.l;
+      }
       for (int zi = 0; zi < nz; ++zi) {
         const int z = ud ? zi : nz - 1 - zi;
         const Real xt = rc[(size_t)z * B + tid], xq0 = rc[(size_t)(nz + z) * B + tid];
@@ -322,6 +355,14 @@ __global__ void __launch_bounds__(kDgResBlock) dg_sweep_res_kernel(
           fin[p] = (i0 + i1) * il;
         }
         dg_tally<Real>(tally + (((size_t)z * R + s.r) * Gp + g) * 2, a0, sg * a1);
+        if (CM) {
+          // the plane's outflow through its downwind face: into the next plane or out of the domain
+          Real j = 0;
+#pragma unroll
+          for (int p = 0; p < P; ++p) j = fma(w[p] * mu[p], fin[p], j);
+          const int slot = ud ? (z < nz - 1 ? z : 2 * nz + z) : (z > 0 ? nz + z - 1 : 2 * nz);
+          ca[(size_t)slot * B + tid] += j * s.l;
+        }
       }
     }
     if (bc_top) {
@@ -336,6 +377,191 @@ __global__ void __launch_bounds__(kDgResBlock) dg_sweep_res_kernel(
   if (e_out >= 0) {
     Real *po = psi_out + (long long)e_out * nslot * G + g;
     for (int k = 0; k < nslot; ++k) po[(size_t)k * G] = ys[(size_t)k * B + tid];
+  }
+  if (CM) {
+    // radial current out at the track's end, then this thread's sums into the FP64 totals
+    for (int ud = 0; ud < 2; ++ud)
+      for (int z = 0; z < nz; ++z) {
+        Real j = 0;
+#pragma unroll
+        for (int p = 0; p < P; ++p) j = fma(w[p] * st[p], ys[((size_t)((ud * nz + z) * P + p) * 2) * B + tid], j);
+        ca[(size_t)(2 * nz + z) * B + tid] += j * cm.dz[z];
+      }
+    for (int z = 0; z < nz; ++z) {
+      if (z < nz - 1) {
+        atomicAdd(cm.cur + (size_t)z * Gp + g, (double)ca[(size_t)z * B + tid]);
+        atomicAdd(cm.cur + (size_t)(nz + z) * Gp + g, (double)ca[(size_t)(nz + z) * B + tid]);
+      }
+      atomicAdd(cm.leak + (size_t)z * Gp + g, (double)ca[(size_t)(2 * nz + z) * B + tid]);
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------- axial CMFD
+// flux sums per (plane, material, group): psum[(z M + m) G + g] += A dz phi_0 (the planar CMFD's
+// homogenisation input with the planes as cells)
+template <typename Real>
+__global__ void dg_cm_sums_kernel(int E, int R, int G, int Gp, int M, const int32_t *__restrict__ mat3,
+                                  const double *__restrict__ area, const Real *__restrict__ dz,
+                                  const Real *__restrict__ phi3, double *__restrict__ psum) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)E * G) return;
+  const int e = (int)(idx / G), g = (int)(idx - (long long)e * G);
+  const int z = e / R, r = e - z * R;
+  atomicAdd(psum + ((size_t)z * M + mat3[e]) * G + g,
+            area[r] * (double)dz[z] * (double)phi3[((size_t)e * Gp + g) * 2]);
+}
+
+// One block: the coarse eigenproblem on the planes (the arrays from cmfd_coeff_kernel, group-major
+// [g][z]; SV [g_to][h_from][z]), a fixed number of power iterations, each Gauss-Seidel in energy
+// with n_inner over-relaxed sweeps over the even planes then the odd ones; then the coarse/fine
+// ratio per (group, plane), the coarse k, and the current tallies cleared for the next sweep.
+template <typename Real>
+__global__ void __launch_bounds__(256) dg_cm_solve_kernel(int nz, int G, int Gp, double *__restrict__ cur,
+                                                          double *__restrict__ leak, const Real *__restrict__ cphi,
+                                                          const Real *__restrict__ TV, const Real *__restrict__ SV,
+                                                          const Real *__restrict__ FV, const Real *__restrict__ CHI,
+                                                          double *__restrict__ diag, double *__restrict__ phic,
+                                                          double *__restrict__ fis, Real *__restrict__ ratio,
+                                                          double *__restrict__ scal, int n_outer, int n_inner,
+                                                          double omega) {
+  __shared__ double s_k, s_fold;
+  const int N = nz;
+  for (int x = threadIdx.x; x < N * G; x += blockDim.x) {
+    const int g = x / N, z = x - g * N;
+    const double pz = (double)cphi[x];
+    double dg = (double)TV[x] - (double)SV[((size_t)g * G + g) * N + z];
+    if (pz > 0.0) {
+      dg += leak[(size_t)z * Gp + g] / pz;
+      if (z < nz - 1) dg += cur[(size_t)z * Gp + g] / pz;
+      if (z > 0) dg += cur[(size_t)(nz + z - 1) * Gp + g] / pz;
+    }
+    diag[x] = dg;
+    phic[x] = pz;
+  }
+  if (threadIdx.x == 0) s_k = scal[S_K];
+  __syncthreads();
+  for (int it = 0; it < n_outer; ++it) {
+    for (int z = threadIdx.x; z < N; z += blockDim.x) {
+      double f = 0.0;
+      for (int g = 0; g < G; ++g) f += (double)FV[(size_t)g * N + z] * phic[(size_t)g * N + z];
+      fis[z] = f;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double F = 0.0;
+      for (int z = 0; z < N; ++z) F += fis[z];
+      s_fold = F;
+    }
+    __syncthreads();
+    const double kc = s_k;
+    for (int g = 0; g < G; ++g)
+      for (int j = 0; j < n_inner; ++j)
+        for (int c = 0; c < 2; ++c) {
+          for (int z = c + 2 * threadIdx.x; z < N; z += 2 * blockDim.x) {
+            const size_t x = (size_t)g * N + z;
+            double rhs = (double)CHI[x] * fis[z] / kc;
+            for (int h = 0; h < G; ++h)
+              if (h != g) rhs += (double)SV[((size_t)g * G + h) * N + z] * phic[(size_t)h * N + z];
+            if (z > 0 && cphi[x - 1] > (Real)0) rhs += cur[(size_t)(z - 1) * Gp + g] / (double)cphi[x - 1] * phic[x - 1];
+            if (z < nz - 1 && cphi[x + 1] > (Real)0)
+              rhs += cur[(size_t)(nz + z) * Gp + g] / (double)cphi[x + 1] * phic[x + 1];
+            if (diag[x] > 0.0) phic[x] += omega * (rhs / diag[x] - phic[x]);
+          }
+          __syncthreads();
+        }
+    if (threadIdx.x == 0) {
+      double F = 0.0;
+      for (int z = 0; z < N; ++z)
+        for (int g = 0; g < G; ++g) F += (double)FV[(size_t)g * N + z] * phic[(size_t)g * N + z];
+      if (F > 0.0 && s_fold > 0.0) s_k = s_k * F / s_fold;
+    }
+    __syncthreads();
+  }
+  for (int x = threadIdx.x; x < N * G; x += blockDim.x) {
+    const double pz = (double)cphi[x];
+    ratio[x] = (Real)((pz > 0.0 && phic[x] > 0.0) ? phic[x] / pz : 1.0);
+  }
+  for (int x = threadIdx.x; x < 2 * nz * Gp; x += blockDim.x) cur[x] = 0.0;
+  for (int x = threadIdx.x; x < nz * Gp; x += blockDim.x) leak[x] = 0.0;
+  if (threadIdx.x == 0) scal[S_K] = s_k;
+}
+
+// both moments of every element *= the ratio of its plane; FP64 fission partials; the last block
+// sets the pending normalisation 1/F (as the planar prolongation does)
+template <typename Real>
+__global__ void __launch_bounds__(256) dg_cm_prolong_kernel(int E, int R, int G, int Gp, int nz,
+                                                            const int32_t *__restrict__ mat3,
+                                                            const Real *__restrict__ nsf,
+                                                            const double *__restrict__ area,
+                                                            const Real *__restrict__ dz, const Real *__restrict__ ratio,
+                                                            Real *__restrict__ phi3, double *__restrict__ part,
+                                                            unsigned *__restrict__ ticket, double *__restrict__ scal) {
+  __shared__ double red[256];
+  __shared__ bool last;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  double fa = 0.0;
+  if (e < E) {
+    const int z = e / R, r = e - z * R, m = mat3[e];
+    Real f = 0;
+    for (int g = 0; g < G; ++g) {
+      const Real q = ratio[(size_t)g * nz + z];
+      Real *ph = phi3 + ((size_t)e * Gp + g) * 2;
+      const Real v = ph[0] * q;
+      ph[0] = v;
+      ph[1] *= q;
+      f += nsf[m * G + g] * v;
+    }
+    fa = area[r] * (double)dz[z] * (double)f;
+  }
+  red[threadIdx.x] = fa;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = red[0];
+    __threadfence();
+    last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    double a = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) a += part[b];
+    red[threadIdx.x] = a;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+      if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      const double F = red[0];
+      if (F > 0.0 && isfinite(F)) {
+        scal[S_SCALE] = 1.0 / F;
+        scal[S_FISS] = F;
+      } else {
+        scal[S_STATUS] = 1.0;
+      }
+      *ticket = 0u;
+    }
+  }
+}
+
+// the radial boundary moments of the next sweep ([2T][2][nz][P][2][G]) and the stored top traces
+// ([S + pad][2][P][G], top plane) *= the ratio of their plane
+template <typename Real>
+__global__ void dg_cm_psi_kernel(long long n_psi, long long n_face, int P, int G, int nz,
+                                 const Real *__restrict__ ratio, Real *__restrict__ psi, Real *__restrict__ face) {
+  const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x < n_psi) {
+    const int g = (int)(x % G);
+    const int z = (int)((x / ((long long)G * 2 * P)) % nz);
+    psi[x] *= ratio[(size_t)g * nz + z];
+  } else if (x < n_psi + n_face) {
+    const long long y = x - n_psi;
+    face[y] *= ratio[(size_t)(y % G) * nz + nz - 1];
   }
 }
 

@@ -69,6 +69,7 @@ def load_library(path: Optional[str] = None):
             "moc_get_stats": (ctypes.c_int, [_vp, _d, _d]),
             "moc_get_history": (ctypes.c_int, [_vp, _d, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
             "moc_set_axial": (ctypes.c_int, [_vp, ctypes.c_int, _d, _i32, ctypes.c_int, ctypes.c_int]),
+            "moc_set_dg_cmfd": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double]),
             "moc_set_scattering": (ctypes.c_int, [_vp, ctypes.c_int, _d]),
             "moc_set_ray_layout": (ctypes.c_int, [_vp, ctypes.c_int]),
             "moc_generate_tracks_device": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
@@ -383,6 +384,11 @@ class Moc:
         self._check(self._lib.moc_set_axial(self._h, int(dz.size), _p(dz, _d) if dz.size else None,
                                             None if m3 is None else _p(m3, _i32), int(bc[0]), int(bc[1])))
         self.nz = int(dz.size)
+
+    def set_dg_cmfd(self, n_outer: int = 0, n_inner: int = 4, omega: float = 1.0):
+        """Axial coarse-mesh acceleration of DGMOC (planes as coarse cells); n_outer = 0 disables.
+        Call after set_axial."""
+        self._check(self._lib.moc_set_dg_cmfd(self._h, int(n_outer), int(n_inner), float(omega)))
 
     def _phi_shape(self):
         nz = getattr(self, "nz", 0)
