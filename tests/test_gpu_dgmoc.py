@@ -254,3 +254,24 @@ def test_axial_acceleration_reaches_the_plain_limit_faster(precision, tol):
     p.set_axial(dz, mat3, bc=(1, 0))
     _, n_plain, _, _ = p.power_iterate(tol_k=tk, tol_flux=tf, max_outer=3 * n_acc, raise_on_fail=False)
     assert n_plain >= 3 * n_acc - 10, (n_acc, n_plain)   # plain needs at least three times as many
+
+
+def test_full_assembly_infinite_medium():
+    """The benchmark's mesh, tracks and launch configuration (17x17 assembly, 9.1M segments,
+    8 planes, plane-inner sweep, FP32) with one material everywhere and every face reflective,
+    iterated with the axial acceleration: the closed-form k-infinity, a flat plane-average flux
+    and zero slopes, at full size."""
+    base = W.assembly_problem()
+    xs = W.synthetic_xs(["fuel"], 7, 31)
+    prob = W.Problem(W.one_material(base.mesh), xs, base.n_azim, base.ray_spacing)
+    M = np.diag(xs.sigma_t[0]) - xs.sigma_s[0].T
+    kinf = float(xs.nu_sigma_f[0] @ np.linalg.solve(M, xs.chi[0]))
+    m = moc.Moc.from_problem(prob, precision="fp32")
+    m.set_axial(np.full(8, 10.71), bc=(1, 1))
+    m.set_dg_cmfd(8, 4, 1.0)
+    k, n, r, ok = m.power_iterate(tol_k=1e-8, tol_flux=1e-6, max_outer=400)
+    assert ok and abs(k - kinf) <= 2e-6 * kinf, (k, kinf, n)
+    phi, _ = m.get_state()
+    spec = phi[:, :, 0, :].reshape(-1, 7)
+    np.testing.assert_allclose(spec, np.broadcast_to(spec.mean(axis=0), spec.shape), rtol=2e-5)
+    assert np.abs(phi[:, :, 1]).max() <= 2e-5 * np.abs(spec).max()
