@@ -139,6 +139,30 @@ def cpu_baseline(prob, outers: int = 2):
                       f"{dt:.2f} s"}
 
 
+def dg_cpu_baseline(nz: int = 8):
+    """The oracle's DGMOC as it stands on the host cores, on a bounded sample of the DGMOC workload:
+    one outer of a 3x3-pin lattice cut from the assembly's pin geometry, with the assembly's
+    quadrature (32 azimuths, 0.02 cm, TY-3), extruded like the benchmark (nz planes of 10.71 cm,
+    the top quarter moderator, reflective bottom, vacuum top); updates/s in the same units."""
+    import oracle
+    from paper_2607_01591_gb300 import workloads as W
+
+    lat = W.small_lattice_problem(3, bc=(1, 1, 1, 1), n_azim=32, ray_spacing=0.02)
+    threads = min(os.cpu_count() or 1, lat.xs.n_groups)
+    o = oracle.Oracle.from_problem(lat, threads=threads)
+    mat3 = np.tile(lat.mesh.mat, (nz, 1))
+    mat3[nz - max(1, nz // 4):] = lat.mesh.mat.max()
+    o.set_axial(np.full(nz, 10.71), mat3, bc=(1, 0))
+    o.normalise()
+    t0 = time.perf_counter()
+    o.outer(True)
+    dt = time.perf_counter() - t0
+    ups = 2 * o.n_segments * len(lat.sin_theta) * lat.xs.n_groups * 2 * nz
+    return {"value": ups / dt, "unit": "updates/s", "cores": threads, "kind": "oracle",
+            "sample": f"one oracle DGMOC outer (FP64, one thread per group) on a 3x3-pin lattice with the "
+                      f"assembly's quadrature, {nz} planes: {o.n_segments} segments, {dt:.2f} s"}
+
+
 # Per DGMOC update (segment x polar x group x plane x march), FP32: the algorithmic operations of the
 # closed-form 2x2 segment solution counted from its formulas (FMA = 1, the 1 - e^-x evaluation 13,
 # small-angle sin/cos 10, the reciprocal 1), and the thread instructions the plane-inner sweep
@@ -455,6 +479,8 @@ def main():
         if args.fp64_steps > 0 and args.precision != "fp64":
             d64 = dgmoc_block(moc, W, prob, local, stream, "fp64", args.axial, 1)
             dgmoc["fp64"] = {"ms_per_outer": d64["ms_per_outer"], "value": d64["value"], "k_after": d64["k_after"]}
+        if not args.no_cpu_baseline and world == 1:
+            dgmoc["cpu_baseline"] = dg_cpu_baseline(args.axial)
 
     # tracking of the same workload: host half-edge walk vs the device walk (bit-identical tracks)
     tracking = None
