@@ -455,8 +455,9 @@ template <typename Real> int upload_xs(moc_ctx *c, int n_mat, int G, const doubl
   }
   CUDA_TRY(c, cudaMalloc(&c->d_fold, (size_t)R * sizeof(double)));
   CUDA_TRY(c, cudaMemsetAsync(c->d_fold, 0, (size_t)R * sizeof(double), c->stream));
-  const int nb = (R + 31) / 32;  // enough block partials for either finalize variant
-  CUDA_TRY(c, cudaMalloc(&c->d_part, (size_t)nb * 4 * sizeof(double)));
+  // enough block partials for either finalize variant and for the state kernel's normalisation
+  const size_t nb = std::max<size_t>((size_t)(R + 31) / 32 * 4, (RG + 255) / 256);
+  CUDA_TRY(c, cudaMalloc(&c->d_part, nb * sizeof(double)));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   c->xs_set = true;
   return MOC_OK;
@@ -1016,14 +1017,22 @@ const void *host_view(const moc_ctx *c, const void *p) {
   return nullptr;
 }
 
-template <typename Real> int state_in(moc_ctx *c, const double *dphi, const double *dpsi, double k, double scale) {
+// The caller's state read in place by one kernel; in eigenvalue mode the kernel also sums the
+// fission source F of the state and sets the normalisation 1/F itself (no host pass over phi).
+template <typename Real> int state_in(moc_ctx *c, const double *dphi, const double *dpsi, double k) {
   const int R = c->geo.n_tri;
-  const long long n = (long long)R * c->Gp + c->T * 2 * c->P * c->G;
+  const long long n = std::max<long long>(1, (long long)R * c->Gp + c->T * 2 * c->P * c->G);
+  double *hs = nullptr;
+  CUDA_TRY(c, cudaHostGetDevicePointer((void **)&hs, c->h_scal, 0));
+  c->h_scal[S_FISS] = 0.0;
   state_in_kernel<Real><<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
       R, c->G, c->Gp, (long long)c->T, c->P, dphi, dpsi, c->d_inv, c->d_fed, (Real *)c->d_phi,
-      (Real *)c->d_psi[c->cur], c->d_scal, k, scale);
+      (Real *)c->d_psi[c->cur], c->d_scal, k, 1.0, c->eigen ? 1 : 0, c->d_mat, (const Real *)c->d_nsf, c->d_area,
+      c->d_part, c->d_ticket, hs);
   CUDA_TRY(c, cudaGetLastError());
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (c->eigen && !std::isfinite(c->h_scal[S_FISS]))
+    return fail(c, MOC_ERR_ARG, "set_state: the fission source of the state is not finite");
   return MOC_OK;
 }
 
@@ -1888,18 +1897,19 @@ int moc_set_state(moc_ctx *c, const double *phi, double k, const double *psi) {
   c->hist_n = 0;
   cudaSetDevice(c->device);
   if (c->dg_nz) return c->precision == MOC_FP64 ? dg_set_state<double>(c, phi, k, psi) : dg_set_state<float>(c, phi, k, psi);
-  double scale = 1.0;
-  if (c->eigen) {
-    double F = host_fission(c, phi, c->h_nsf);
-    if (!std::isfinite(F)) return fail(c, MOC_ERR_ARG, "set_state: the fission source of the state is not finite");
-    if (F > 0.0) scale = 1.0 / F;   // no fission at all: power iteration will report MOC_ERR_NONFINITE
-  }
-  // arrays the device can address are read in place by one kernel; others are staged
+  // arrays the device can address are read in place by one kernel, which also normalises; others
+  // are staged and normalised from a host pass
   const void *vphi = host_view(c, phi), *vpsi = host_view(c, psi);
   if ((!phi || vphi) && (!psi || vpsi)) {
-    rc = c->precision == MOC_FP64 ? state_in<double>(c, (const double *)vphi, (const double *)vpsi, k, scale)
-                                  : state_in<float>(c, (const double *)vphi, (const double *)vpsi, k, scale);
+    rc = c->precision == MOC_FP64 ? state_in<double>(c, (const double *)vphi, (const double *)vpsi, k)
+                                  : state_in<float>(c, (const double *)vphi, (const double *)vpsi, k);
   } else {
+    double scale = 1.0;
+    if (c->eigen) {
+      double F = host_fission(c, phi, c->h_nsf);
+      if (!std::isfinite(F)) return fail(c, MOC_ERR_ARG, "set_state: the fission source of the state is not finite");
+      if (F > 0.0) scale = 1.0 / F;   // no fission at all: power iteration will report MOC_ERR_NONFINITE
+    }
     rc = c->precision == MOC_FP64 ? upload_state<double>(c, phi, psi) : upload_state<float>(c, phi, psi);
     if (!rc) rc = reset_scalars(c, k, scale);
   }

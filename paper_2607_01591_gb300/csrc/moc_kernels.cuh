@@ -121,31 +121,78 @@ __global__ void source_kernel(int R, int G, int Gp, int M, const int32_t *__rest
 // (NULL: 0) -> d_psi in internal order, ends that no link feeds set to zero; scalars reset with
 // k and the normalisation `scale`.
 template <typename Real>
-__global__ void state_in_kernel(int R, int G, int Gp, long long T, int P, const double *__restrict__ phi,
-                                const double *__restrict__ psi, const long long *__restrict__ inv,
-                                const uint8_t *__restrict__ fed, Real *__restrict__ d_phi, Real *__restrict__ d_psi,
-                                double *__restrict__ scal, double k, double scale) {
+__global__ void __launch_bounds__(256) state_in_kernel(
+    int R, int G, int Gp, long long T, int P, const double *__restrict__ phi, const double *__restrict__ psi,
+    const long long *__restrict__ inv, const uint8_t *__restrict__ fed, Real *__restrict__ d_phi,
+    Real *__restrict__ d_psi, double *__restrict__ scal, double k, double scale, int dev_norm,
+    const int32_t *__restrict__ mat, const Real *__restrict__ nsf, const double *__restrict__ area,
+    double *__restrict__ part, unsigned *__restrict__ ticket, double *__restrict__ scal_host) {
+  __shared__ double red[256];
+  __shared__ bool last;
   const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nphi = (long long)R * Gp, half = (long long)P * G;
   if (x == 0) {
-    for (int i = 0; i < S_COUNT; ++i) scal[i] = 0.0;
+    for (int i = 0; i < S_COUNT; ++i)
+      if (!dev_norm || (i != S_SCALE && i != S_FISS)) scal[i] = 0.0;
     scal[S_K] = k;
     scal[S_KPREV] = k;
-    scal[S_SCALE] = scale;
     scal[S_RESID] = INFINITY;
-    scal[S_FISS] = 1.0 / scale;
+    if (!dev_norm) {
+      scal[S_SCALE] = scale;
+      scal[S_FISS] = 1.0 / scale;
+    }
   }
+  double fa = 0.0;  // this element's share of F = sum_i A_i sum_g nuSigma_f phi
   if (x < nphi) {
     const long long r = x / Gp;
     const int g = (int)(x - r * Gp);
-    d_phi[x] = (g < G) ? (Real)(phi ? phi[r * G + g] : 1.0) : (Real)0;
-    return;
+    const double v = (g < G) ? (phi ? phi[r * G + g] : 1.0) : 0.0;
+    d_phi[x] = (Real)v;
+    if (dev_norm && g < G) fa = area[r] * (double)nsf[mat[r] * G + g] * v;
+  } else {
+    const long long y = x - nphi;  // external end (t, d) = y / half, value q: the host array is read
+    if (y < T * 2 * half) {        // in order, the device array written at the internal position
+      const long long ext = y / half, q = y - ext * half;
+      const long long e = 2 * inv[ext >> 1] + (ext & 1);
+      d_psi[e * half + q] = (psi && fed[e]) ? (Real)psi[y] : (Real)0;
+    }
   }
-  const long long y = x - nphi;  // external end (t, d) = y / half, value q: the host array is read
-  if (y >= T * 2 * half) return; // in order, the device array written at the internal position
-  const long long ext = y / half, q = y - ext * half;
-  const long long e = 2 * inv[ext >> 1] + (ext & 1);
-  d_psi[e * half + q] = (psi && fed[e]) ? (Real)psi[y] : (Real)0;
+  // the normalisation from the state itself: fixed-order block partials over the blocks that hold
+  // flux entries, the last of them to finish sums the partials and sets 1/F (no host pass)
+  const unsigned nbp = (unsigned)((nphi + blockDim.x - 1) / blockDim.x);
+  if (!dev_norm || blockIdx.x >= nbp) return;
+  red[threadIdx.x] = fa;
+  __syncthreads();
+  for (int k2 = blockDim.x / 2; k2 > 0; k2 >>= 1) {
+    if (threadIdx.x < k2) red[threadIdx.x] += red[threadIdx.x + k2];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = red[0];
+    __threadfence();
+    last = (atomicAdd(ticket, 1u) == nbp - 1);
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    double a = 0.0;
+    for (unsigned b = threadIdx.x; b < nbp; b += blockDim.x) a += part[b];
+    red[threadIdx.x] = a;
+    __syncthreads();
+    for (int k2 = blockDim.x / 2; k2 > 0; k2 >>= 1) {
+      if (threadIdx.x < k2) red[threadIdx.x] += red[threadIdx.x + k2];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      const double F = red[0];
+      // no fission at all: scale 1 (power iteration then reports a non-finite k)
+      const double sc = (F > 0.0 && isfinite(F)) ? 1.0 / F : 1.0;
+      scal[S_SCALE] = sc;
+      scal[S_FISS] = F;
+      scal_host[S_FISS] = F;
+      *ticket = 0u;
+    }
+  }
 }
 
 // d_phi * scal[S_SCALE] -> phi [R][G] FP64; d_psi (internal order) * scale -> psi [T][2][P][G]
