@@ -782,7 +782,7 @@ template <typename Real> int launch_dg_cmfd(moc_ctx *c, cudaStream_t st) {
                                                               (const Real *)c->d_dgratio, (Real *)c->d_phi3,
                                                               c->d_dgpart, c->d_dgticket, c->d_scal);
   const long long n_psi = (long long)c->T * 2 * 2 * nz * c->P * 2 * G;
-  const long long n_face = c->dg_bc[1] ? (long long)(c->S + 2 * kSegPad) * 2 * c->P * G : 0;
+  const long long n_face = (c->dg_bc[1] && c->d_face) ? (long long)(c->S + 2 * kSegPad) * 2 * c->P * G : 0;
   dg_cm_psi_kernel<Real><<<(unsigned)((n_psi + n_face + 255) / 256), 256, 0, st>>>(
       n_psi, n_face, c->P, G, nz, (const Real *)c->d_dgratio, (Real *)c->d_psi3[c->cur], (Real *)c->d_face);
   CUDA_TRY(c, cudaGetLastError());
@@ -1090,7 +1090,8 @@ template <typename Real> int dg_set_state(moc_ctx *c, const double *phi, double 
   const size_t nb = (size_t)c->T * 2 * 2 * nz * c->P * 2 * G * sizeof(Real);
   CUDA_TRY(c, cudaMemsetAsync(c->d_psi3[0], 0, nb, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(c->d_psi3[1], 0, nb, c->stream));
-  CUDA_TRY(c, cudaMemsetAsync(c->d_face, 0, (size_t)(c->S + 2 * kSegPad) * 2 * c->P * G * sizeof(Real), c->stream));
+  if (c->d_face)
+    CUDA_TRY(c, cudaMemsetAsync(c->d_face, 0, (size_t)(c->S + 2 * kSegPad) * 2 * c->P * G * sizeof(Real), c->stream));
   CUDA_TRY(c, cudaMemsetAsync(c->d_tal3, 0, (size_t)E * c->Gp * 2 * sizeof(Real), c->stream));
   return reset_scalars(c, k, scale);
 }
@@ -1143,7 +1144,6 @@ template <typename Real> int dg_alloc(moc_ctx *c) {
   const size_t nb = (size_t)c->T * 2 * 2 * nz * P * 2 * G;
   CUDA_TRY(c, cudaMalloc(&c->d_psi3[0], std::max<size_t>(nb, 1) * sizeof(Real)));
   CUDA_TRY(c, cudaMalloc(&c->d_psi3[1], std::max<size_t>(nb, 1) * sizeof(Real)));
-  CUDA_TRY(c, cudaMalloc(&c->d_face, (size_t)(c->S + 2 * kSegPad) * 2 * P * G * sizeof(Real)));
   CUDA_TRY(c, cudaMalloc((void **)&c->d_fold3, E * sizeof(double)));
   CUDA_TRY(c, cudaMemset(c->d_fold3, 0, E * sizeof(double)));
   CUDA_TRY(c, cudaMalloc((void **)&c->d_part3, ((E + 255) / 256) * 4 * sizeof(double)));
@@ -1158,6 +1158,10 @@ template <typename Real> int dg_alloc(moc_ctx *c) {
   }
   if (e != cudaSuccess) return fail(c, MOC_ERR_CUDA, std::string("set_axial: ") + cudaGetErrorString(e));
   c->dg_res_smem = sm <= kDgResSmemMax ? sm : 0;
+  // the interface buffer: every plane's traces for the plane-by-plane sweep; for the plane-inner
+  // sweep only the top traces a reflective top needs (none at all with a vacuum top)
+  if (!c->dg_res_smem || c->dg_bc[1])
+    CUDA_TRY(c, cudaMalloc(&c->d_face, (size_t)(c->S + 2 * kSegPad) * 2 * P * G * sizeof(Real)));
   return MOC_OK;
 }
 

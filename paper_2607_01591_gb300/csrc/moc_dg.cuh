@@ -309,7 +309,8 @@ __global__ void __launch_bounds__(kDgResBlock) dg_sweep_res_kernel(
   }
   const int step = d ? -1 : 1;
   const SegRec<Real> *sp = seg + (d ? tr.off + tr.n - 1 : tr.off);
-  Real *fp = face + (((d ? tr.off + tr.n - 1 : tr.off) * 2 + d) * P) * G + g;
+  // the top traces (reflective top only; the buffer is not allocated otherwise)
+  Real *fp = bc_top ? face + (((d ? tr.off + tr.n - 1 : tr.off) * 2 + d) * P) * G + g : nullptr;
   const long long fstep = (long long)step * 2 * P * G;
   SegRec<Real> s = sp[0];
   for (int n = 0; n < tr.n; ++n) {
@@ -322,8 +323,13 @@ __global__ void __launch_bounds__(kDgResBlock) dg_sweep_res_kernel(
     }
     const Real il = DgMath<Real>::rcp(s.l);
     Real fin[P];
+    if (bc_top) {
 #pragma unroll
-    for (int p = 0; p < P; ++p) fin[p] = bc_top ? fp[p * G] * scale : (Real)0;
+      for (int p = 0; p < P; ++p) fin[p] = fp[p * G] * scale;
+    } else {
+#pragma unroll
+      for (int p = 0; p < P; ++p) fin[p] = 0;
+    }
     for (int ud = 0; ud < 2; ++ud) {
       const Real sg = ud ? (Real)1 : (Real)-1;
       if (ud == 1 && !bc_bottom) {
@@ -371,7 +377,7 @@ __global__ void __launch_bounds__(kDgResBlock) dg_sweep_res_kernel(
     }
     s = s_next;
     sp += step;
-    fp += fstep;
+    if (bc_top) fp += fstep;
   }
   const int e_out = link[td];
   if (e_out >= 0) {
