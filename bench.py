@@ -171,7 +171,7 @@ DG_OPS_PER_UPDATE = 74
 DG_INST_PER_UPDATE = 114.4
 
 
-def dgmoc_block(moc, W, prob, device, stream, precision, nz, steps, converge=False):
+def dgmoc_block(moc, W, prob, device, stream, precision, nz, steps, converge=False, name="assembly"):
     """DGMOC (Sec. 2.2, Alg. 2) on the assembly extruded like the paper's 3D lattice benchmark:
     nz axial planes of 10.71 cm, the top quarter reflector (the moderator material in every
     region), reflective bottom (mid-plane symmetry) and vacuum top. Times whole outers and the
@@ -224,9 +224,9 @@ def dgmoc_block(moc, W, prob, device, stream, precision, nz, steps, converge=Fal
         m.set_dg_cmfd(0)
     m.close()
     sweep_s = sweep_ms / n_sw / 1e3
-    out = {"workload": f"{WORKLOADS['assembly']} extruded to {nz} planes x 10.71 cm ({n_refl} reflector "
+    out = {"workload": f"{WORKLOADS[name]} extruded to {nz} planes x 10.71 cm ({n_refl} reflector "
                        "planes on top), reflective bottom, vacuum top, linear axial DG",
-           "precision": precision, "planes": nz, "updates_per_outer": ups,
+           "precision": precision, "planes": nz, "elements": nz * prob.mesh.n_tri, "updates_per_outer": ups,
            "ms_per_outer": ms / steps, "value": ups * steps / (ms / 1e3), "unit": "updates/s",
            "sweep_ms": sweep_s * 1e3, "kernel": "dg_sweep_res_kernel (plane-inner; dg_sweep_kernel when its shared memory would exceed 100 KB per block)", "k_after": k + 0.0,
            "outers_timed": steps, "gpu_launches_per_outer": kpo, "time_to_k": ttk}
@@ -369,9 +369,10 @@ def main():
     prob = make_problem(args.workload)
     stream = torch.cuda.Stream(device=local)
     if args.dgmoc_only:
-        blk = dgmoc_block(moc, W, make_problem("assembly"), local, stream, args.precision, args.axial, args.steps,
-                          converge=not args.no_time_to_k)
-        blk64 = dgmoc_block(moc, W, make_problem("assembly"), local, stream, "fp64", args.axial, 1)
+        blk = dgmoc_block(moc, W, prob, local, stream, args.precision, args.axial, args.steps,
+                          converge=not args.no_time_to_k, name=args.workload)
+        blk64 = (dgmoc_block(moc, W, prob, local, stream, "fp64", args.axial, 1, name=args.workload)
+                 if args.fp64_steps > 0 else None)
         if rank == 0:
             print(json.dumps({"dgmoc": blk, "dgmoc_fp64": blk64}), flush=True)
         return
