@@ -6,7 +6,11 @@ reductions, on the seeded synthetic 17x17 assembly (39,304 triangles, 7 groups, 
 TY-3 polar, 0.02 cm ray spacing). updates per step = 2 * segments * polar * groups.
 
 Prints one JSON line (rank 0). Under torchrun each rank runs an independent replica on its own
-GPU (the sweep has no data-path exchange); value = all ranks' updates / max time.
+GPU (the sweep has no data-path exchange); value = all ranks' updates / max time. The line also
+carries context measurements: the FP64 mode, the time to a converged k (plain and CMFD), host
+against device tracking, and a `dgmoc` block (the assembly extruded to `--axial` planes, DGMOC
+outers with their roofline and the oracle's DGMOC timed on a bounded sample); `--dgmoc-only`
+prints only that block, with the time to converged k of the plain and the accelerated DGMOC.
 `--impl reference` times the CPU oracle on the host cores instead (one oracle outer per step).
 """
 from __future__ import annotations
