@@ -20,9 +20,11 @@
 //     integral of y over the segment = l y_inf + K^-1 (y0 - y(l)).
 // The closed forms avoid a general matrix exponential and any cancellation in 1 - e^-gamma.
 //
-// Per outer: dg_source_kernel (source moments), dg_sweep_kernel (both marches of every track,
-// sense, polar angle and group), dg_finalize_kernel (flux moments, FP64 block partials), and the
-// planar reduce_kernel (k, normalisation, residual).
+// Per outer: dg_source_kernel (source moments), the sweep (dg_sweep_res_kernel, or
+// dg_sweep_kernel when its shared memory would not fit: both marches of every track, sense, polar
+// angle and group), dg_finalize_kernel (flux moments, FP64 block partials) and the planar
+// reduce_kernel (k, normalisation, residual); with the axial acceleration also dg_cm_sums_kernel,
+// the planar cmfd_coeff_kernel, dg_cm_solve_kernel, dg_cm_prolong_kernel and dg_cm_psi_kernel.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
