@@ -107,3 +107,13 @@ def test_history_records_every_check():
     assert a.history(2).shape == (2, 4) and np.array_equal(a.history(2), h[-2:])
     a.set_state(None, 1.0)                      # a new start clears the record
     assert a.history().shape == (0, 4)
+
+
+def test_history_ring_keeps_the_last_4096_checks_in_order():
+    m = moc.Moc.from_problem(W.pin_cell_problem(), precision="fp32")
+    _, n, _, ok = m.power_iterate(tol_k=0.0, tol_flux=0.0, max_outer=4100, check_every=1, raise_on_fail=False)
+    assert not ok and n == 4100
+    h = m.history()
+    assert h.shape == (4096, 4)
+    np.testing.assert_array_equal(h[:, 0], np.arange(5, 4101, dtype=float))   # oldest first after wrapping
+    assert np.array_equal(m.history(3), h[-3:])
