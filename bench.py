@@ -172,7 +172,7 @@ def dg_cpu_baseline(nz: int = 8):
 # small-angle sin/cos 10, the reciprocal 1), and the thread instructions the plane-inner sweep
 # actually executes, from ncu on the extruded assembly (profiles/dg_sweep_assembly17x8.md)
 DG_OPS_PER_UPDATE = 74
-DG_INST_PER_UPDATE = 114.4
+DG_INST_PER_UPDATE = 110.4
 
 
 def dgmoc_block(moc, W, prob, device, stream, precision, nz, steps, converge=False, name="assembly"):

@@ -43,11 +43,16 @@ template <typename Real> struct alignas(4 * sizeof(Real)) DgXs {
 template <typename Real> struct DgMath;
 template <> struct DgMath<double> {
   __device__ static double rcp(double x) { return 1.0 / x; }
+  __device__ static double rcp_fast(double x) { return 1.0 / x; }
   __device__ static double one_minus_exp(double x) { return -expm1(-x); }
   __device__ static void sincos_(double x, double *s, double *c) { sincos(x, s, c); }
 };
 template <> struct DgMath<float> {
   __device__ static float rcp(float x) { return __frcp_rn(x); }  // correctly rounded 1/x
+  // the per-update 1/D (D = (Sigma_t + 2c)^2 + 2c^2, always a normal positive number): CUDA's
+  // approximate division, within 2 ulp, in place of the correctly rounded reciprocal, whose
+  // longer path cost 13% of the sweep
+  __device__ static float rcp_fast(float x) { return __fdividef(1.0f, x); }
   __device__ static float one_minus_exp(float x) { return moc::one_minus_exp(x); }
   // x >= 0. Below 0.5 (thick planes: the usual case) the Taylor polynomials of sin to x^7 and cos
   // to x^8, whose remainders (x^9/9!, x^10/10!) stay below 1.1e-8 relative, i.e. within FP32
@@ -120,7 +125,7 @@ __device__ __forceinline__ void dg_update(Real t, Real q0, Real q1s, Real cc, Re
                                           Real &y0, Real &y1, Real &i0, Real &i1) {
   const Real rs2 = (Real)0.70710678118654752440;  // 1/sqrt(2)
   const Real al = t + 2 * cc;
-  const Real iD = DgMath<Real>::rcp(al * al + 2 * cc * cc);
+  const Real iD = DgMath<Real>::rcp_fast(al * al + 2 * cc * cc);
   // y_inf = (al rr - c N rr) / D
   const Real r0 = q0 + cc * pin, r1 = q1s - 3 * cc * pin;
   const Real n0 = r1 - r0, n1 = r1 - 3 * r0;  // N rr

@@ -275,3 +275,20 @@ def test_full_assembly_infinite_medium():
     spec = phi[:, :, 0, :].reshape(-1, 7)
     np.testing.assert_allclose(spec, np.broadcast_to(spec.mean(axis=0), spec.shape), rtol=2e-5)
     assert np.abs(phi[:, :, 1]).max() <= 2e-5 * np.abs(spec).max()
+
+
+def test_axial_acceleration_is_for_eigenvalue_mode_only():
+    """a fixed-source DGMOC iteration with the acceleration switched on is the plain one"""
+    mesh = W.grid_mesh(2, 2, 2.0, 2.0, bc=(1, 0, 1, 0))
+    xs = W.CrossSections(np.array([[1.0]]), np.zeros((1, 1)), np.zeros((1, 1)), np.array([[[0.5]]]))
+    prob = W.Problem(mesh, xs, 8, 0.2, fixed_source=np.ones((mesh.n_tri, 1)))
+    res = []
+    for acc in (False, True):
+        m = moc.Moc.from_problem(prob, precision="fp64")
+        m.set_axial(np.full(3, 1.0), bc=(0, 0))
+        if acc:
+            m.set_dg_cmfd(8, 4, 1.0)
+        m.outer(5)
+        res.append(m.get_state()[0])
+    # equal up to the order of the tally atomics
+    np.testing.assert_allclose(res[1], res[0], rtol=1e-12, atol=1e-14 * np.abs(res[0]).max())
