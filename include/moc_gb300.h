@@ -247,8 +247,9 @@ int moc_sweep_dev(moc_ctx *ctx, void *stream, const void *phi_in_dev, void *phi_
  * restarts at zero); moc_set_fixed_source's [n_regions][G] source applies in every plane; every
  * other call (moc_outer, moc_power_iterate, timing, history) works as in the planar method, with
  * the fission source summed as dz A nuSigma_f phi_0 and the residual over (plane, region) elements.
- * FP32 modes tally in plain FP32 (no compensation). Errors: MOC_ERR_ARG (sizes, heights,
- * material ids, more than 4 polar angles), MOC_ERR_STATE, MOC_ERR_OOM, MOC_ERR_CUDA. */
+ * FP32 modes tally in plain FP32 (no compensation). Errors: MOC_ERR_ARG (sizes, heights not
+ * finite or below 1e-9 cm, material ids, more than 4 polar angles), MOC_ERR_STATE, MOC_ERR_OOM,
+ * MOC_ERR_CUDA. */
 int moc_set_axial(moc_ctx *ctx, int nz, const double *dz, const int32_t *mat3, int bc_bottom, int bc_top);
 
 /* Axial coarse-mesh acceleration of DGMOC (the CMFD step of Alg. 1 with the planes as coarse
@@ -278,8 +279,9 @@ int moc_get_stats(moc_ctx *ctx, double *sweep_ms, double *updates_per_s);
 /* Iterate until |k' - k| <= tol_k and the L-inf relative fission-source change <= tol_flux
  * (fixed-source mode: the relative flux change <= tol_flux), or max_outer outers. Convergence
  * is checked on the host every `check_every` outers (the outers in between run as one CUDA
- * graph launch). Returns MOC_ERR_NOT_CONVERGED if max_outer is reached, MOC_ERR_NONFINITE if
- * k or the residual is not finite. */
+ * graph launch). Returns MOC_ERR_ARG unless max_outer >= 1, check_every >= 1, tol_k >= 0 and
+ * tol_flux >= 0 (NaN tolerances included), MOC_ERR_NOT_CONVERGED if max_outer is reached,
+ * MOC_ERR_NONFINITE if k or the residual is not finite. */
 int moc_power_iterate(moc_ctx *ctx, double tol_k, double tol_flux, int max_outer,
                       int check_every, double *k_out, int *n_outer_out, double *resid_out);
 

@@ -1182,7 +1182,8 @@ int moc_set_axial(moc_ctx *c, int nz, const double *dz, const int32_t *mat3, int
   const int R = c->geo.n_tri;
   if ((long long)nz * R >= (1LL << 31)) return fail(c, MOC_ERR_ARG, "set_axial: nz * n_regions too large");
   for (int z = 0; z < nz; ++z)
-    if (!(dz[z] > 0.0) || !std::isfinite(dz[z])) return fail(c, MOC_ERR_ARG, "set_axial: plane heights must be finite and > 0");
+    if (!(dz[z] >= kDgMinPlane) || !std::isfinite(dz[z]))
+      return fail(c, MOC_ERR_ARG, "set_axial: plane heights must be finite and at least 1e-9 cm");
   std::vector<int32_t> m3((size_t)nz * R);
   for (int z = 0; z < nz; ++z)
     for (int r = 0; r < R; ++r) {
@@ -2067,9 +2068,12 @@ int moc_get_stats(moc_ctx *c, double *sweep_ms, double *updates_per_s) {
 
 int moc_power_iterate(moc_ctx *c, double tol_k, double tol_flux, int max_outer, int check_every, double *k_out,
                       int *n_outer_out, double *resid_out) {
+  if (!c) return MOC_ERR_ARG;
+  // arguments first: a NaN or negative tolerance could never be met
+  if (max_outer < 1 || check_every < 1 || !(tol_flux >= 0.0) || !(tol_k >= 0.0))
+    return fail(c, MOC_ERR_ARG, "power_iterate: bad arguments");
   int rc = need_ready(c);
   if (rc) return rc;
-  if (max_outer < 1 || check_every < 1 || !(tol_flux >= 0.0)) return fail(c, MOC_ERR_ARG, "power_iterate: bad arguments");
   cudaSetDevice(c->device);
   int n = 0;
   double s[S_COUNT] = {0};

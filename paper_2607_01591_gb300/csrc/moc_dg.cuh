@@ -40,6 +40,9 @@ template <typename Real> struct alignas(4 * sizeof(Real)) DgXs {
   Real pad;
 };
 
+// thinnest plane moc_set_axial accepts (cm); it bounds c = mu/dz for the approximate reciprocal
+constexpr double kDgMinPlane = 1e-9;
+
 template <typename Real> struct DgMath;
 template <> struct DgMath<double> {
   __device__ static double rcp(double x) { return 1.0 / x; }
@@ -49,9 +52,11 @@ template <> struct DgMath<double> {
 };
 template <> struct DgMath<float> {
   __device__ static float rcp(float x) { return __frcp_rn(x); }  // correctly rounded 1/x
-  // the per-update 1/D (D = (Sigma_t + 2c)^2 + 2c^2, always a normal positive number): CUDA's
-  // approximate division, within 2 ulp, in place of the correctly rounded reciprocal, whose
-  // longer path cost 13% of the sweep
+  // the per-update 1/D (D = (Sigma_t + 2c)^2 + 2c^2, c = mu/dz): CUDA's approximate division,
+  // within 2 ulp for D up to 2^126, in place of the correctly rounded reciprocal, whose longer
+  // path cost 13% of the sweep. moc_set_axial rejects planes thinner than kDgMinPlane, so
+  // c <= 1e9/cm and D stays far below 2^126 for any Sigma_t under 1e18/cm (above 2^126 the
+  // approximate quotient would flush to 0)
   __device__ static float rcp_fast(float x) { return __fdividef(1.0f, x); }
   __device__ static float one_minus_exp(float x) { return moc::one_minus_exp(x); }
   // x >= 0. Below 0.5 (thick planes: the usual case) the Taylor polynomials of sin to x^7 and cos

@@ -164,3 +164,19 @@ def test_set_tracks_validates(lib):
         with pytest.raises(moc.MocError) as err:
             b.set_tracks(*a2)
         assert err.value.code == -1
+
+
+@pytest.mark.parametrize("tol_k,tol_flux,max_outer,check_every",
+                         [(float("nan"), 1e-6, 10, 1), (-1e-6, 1e-6, 10, 1), (1e-6, float("nan"), 10, 1),
+                          (1e-6, -1.0, 10, 1), (1e-6, 1e-6, 0, 1), (1e-6, 1e-6, 10, 0)])
+def test_power_iterate_rejects_bad_arguments(lib, tol_k, tol_flux, max_outer, check_every):
+    """Tolerances that can never be met (NaN, negative) and empty loops are argument errors, checked
+    before anything else (so also on a host-only context)."""
+    m = moc.Moc.from_problem(W.pin_cell_problem(), device=-1)
+    with pytest.raises(moc.MocError) as e:
+        m.power_iterate(tol_k, tol_flux, max_outer, check_every=check_every)
+    assert e.value.code == -1
+    # valid arguments on a host-only context: a state error, not an argument error
+    with pytest.raises(moc.MocError) as e:
+        m.power_iterate(1e-6, 1e-6, 10, check_every=1)
+    assert e.value.code == -4

@@ -110,6 +110,11 @@ def test_axial_mode_switches_and_rejections():
         m.set_cmfd(cell, nc)
     with pytest.raises(moc.MocError):
         m.set_axial(np.array([1.0, -1.0]))
+    # planes thinner than 1e-9 cm are refused (they would push the per-update 1/D of the FP32
+    # sweep outside the approximate division's range)
+    with pytest.raises(moc.MocError) as e:
+        m.set_axial(np.array([1.0, 1e-10]))
+    assert e.value.code == -1
     with pytest.raises(moc.MocError):
         m.set_axial(dz, np.full_like(mat3, 99))
     # a state set in the DG layout round-trips
