@@ -34,6 +34,7 @@ WORKLOADS = {
     "assembly": "17x17 assembly, 39,304 triangles, 7 groups, 32 azimuths, 3 polar (TY), ray spacing 0.02 cm",
     "core": "3x3-assembly core + reflector, 608,804 triangles, 7 groups, 64 azimuths, 3 polar, ray spacing 0.01 cm",
     "hexcore": "19-hexagon core, 1,507,650 triangles, 33 groups, 48 azimuths, 3 polar, ray spacing 0.02 cm",
+    "hexcore7": "central 7 hexagons of the hex core, 555,450 triangles, 33 groups, 48 azimuths, 3 polar, ray spacing 0.02 cm",
     "pin": "pin cell, 200 triangles, 7 groups, 16 azimuths, 3 polar, ray spacing 0.05 cm",
 }
 WORKLOAD = WORKLOADS["assembly"]
@@ -43,11 +44,24 @@ def make_problem(name: str):
     from paper_2607_01591_gb300 import workloads as W
 
     return {"assembly": W.assembly_problem, "core": W.core_problem, "hexcore": W.hex_core_problem,
-            "pin": W.pin_cell_problem}[name]()
+            "hexcore7": lambda: W.hex_core_problem(n_rings=1), "pin": W.pin_cell_problem}[name]()
 L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) per launch of the sweep kernel from one ncu capture of the current kernel
 # version on the assembly workload (profiles/sweep_kernel_assembly17.md); None for other workloads.
 SWEEP_DRAM_BYTES = {"assembly": 82.312960e6 + 2.801920e6}
+
+
+def measured_rates(device: int) -> dict:
+    """The library's hardware rate probes (FP32/FP64 FMA issue, L2 atomics by access shape) on this
+    device, plus its multiprocessor count."""
+    from paper_2607_01591_gb300 import moc
+
+    out = {}
+    for kind in moc.PROBES:
+        r = moc.probe_rate(kind, device)
+        out["sm_count"] = r["sm_count"]
+        out[kind] = {"lane_ops_per_s": r["lane_ops_per_s"], "sectors_per_s": r["sectors_per_s"]}
+    return out
 
 
 def _peaks():
@@ -339,11 +353,13 @@ def main():
     ap.add_argument("--dgmoc-only", action="store_true",
                     help="run only the DGMOC measurement (FP32 with its time to converged k, and FP64) "
                          "and print it")
+    ap.add_argument("--rates-only", action="store_true",
+                    help="print the hardware rate probes (FMA issue, L2 atomics) of this GPU and exit")
     ap.add_argument("--cmfd", default=None, metavar="SIZE,NOUT,NIN,OMEGA",
                     help="time CMFD-accelerated outers (square coarse cells of SIZE cm); also the "
                          "parameters of the accelerated time-to-k runs")
     args = ap.parse_args()
-    cm_default = {"assembly": "1.26,6,6,1.0", "core": "1.26,80,3,1.5", "hexcore": "2.52,10,5,1.0",
+    cm_default = {"assembly": "1.26,6,6,1.0", "core": "1.26,80,3,1.5", "hexcore": "2.52,10,5,1.0", "hexcore7": "2.52,10,5,1.0",
                   "pin": "0.63,6,6,1.0"}[args.workload]
     cmp = (args.cmfd or cm_default).split(",")
     cmfd = (float(cmp[0]), int(cmp[1]), int(cmp[2]), float(cmp[3]))
@@ -370,6 +386,12 @@ def main():
     if world > 1:
         dist.barrier()
     moc.load_library()
+    if args.rates_only:
+        with ClockSampler(local) as clk:
+            rates = measured_rates(local)
+        if rank == 0:
+            print(json.dumps({"rates": rates, "clocks": clk.summary()}), flush=True)
+        return
     prob = make_problem(args.workload)
     stream = torch.cuda.Stream(device=local)
     if args.dgmoc_only:

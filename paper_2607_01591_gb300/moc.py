@@ -109,6 +109,7 @@ def load_library(path: Optional[str] = None):
             "moc_mlp_forward_noalloc": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, _vp]),
             "moc_eval_one_minus_exp_f32": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_float),
                                                           ctypes.POINTER(ctypes.c_float), ctypes.c_int64]),
+            "moc_probe_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _d, _d, ctypes.POINTER(ctypes.c_int)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -220,6 +221,21 @@ def eval_one_minus_exp_f32(tau: np.ndarray, device: int = 0) -> np.ndarray:
     if rc != 0:
         raise MocError(rc, "moc_eval_one_minus_exp_f32 failed")
     return out
+
+
+PROBES = ("ffma", "dfma", "red_f32", "red_f32x2", "red_f32x4", "red_f32x4_pair", "red_f32_row8", "atom_f32",
+          "red_f64", "red_f32x4_hbm")
+
+
+def probe_rate(kind: str, device: int = 0) -> dict:
+    """One hardware rate probe of include/moc_probe.h: lane operations/s, 32-byte sectors/s and
+    the device's multiprocessor count."""
+    lib = load_library()
+    ops, sec, sms = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    rc = lib.moc_probe_rate(int(device), PROBES.index(kind), ctypes.byref(ops), ctypes.byref(sec), ctypes.byref(sms))
+    if rc != 0:
+        raise MocError(rc, f"moc_probe_rate({kind}) failed")
+    return {"lane_ops_per_s": ops.value, "sectors_per_s": sec.value, "sm_count": sms.value}
 
 
 class Moc:

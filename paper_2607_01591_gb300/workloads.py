@@ -522,13 +522,15 @@ def core_problem(seed: int = 4) -> Problem:
     return Problem(mesh, xs, 64, 0.01, tol=1e-6, name="core3x3", seed=seed)
 
 
-def hex_core_problem(seed: int = 5, n_sub: int = 115) -> Problem:
+def hex_core_problem(seed: int = 5, n_sub: int = 115, n_rings: int = 2) -> Problem:
     """33-group fast-spectrum-like 19-assembly hexagonal core (~1.5M triangles), vacuum,
-    48 azimuths, ray spacing 0.02 cm."""
-    mesh = hex_core_mesh(n_sub=n_sub)
+    48 azimuths, ray spacing 0.02 cm. n_rings = 1 keeps the central 7 assemblies (the same
+    assemblies, cross sections and quadrature on a smaller core)."""
+    mesh = hex_core_mesh(n_sub=n_sub, n_rings=n_rings)
     xs = synthetic_xs(["fuel", "fuel", "coolant"], 33, seed, sigt_range=(0.05, 0.6),
                       fuel_scales=[1.0, 0.9])
-    return Problem(mesh, xs, 48, 0.02, tol=1e-6, name="hexcore19", seed=seed)
+    return Problem(mesh, xs, 48, 0.02, tol=1e-6, name="hexcore19" if n_rings == 2 else f"hexcore{1 + 3 * n_rings * (n_rings + 1)}",
+                   seed=seed)
 
 
 def warm_start_instances(n: int, seed: int = 1000, base_seed: int = 2) -> List[CrossSections]:
