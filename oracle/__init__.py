@@ -329,7 +329,8 @@ def track_sweep(sig, qr, length, sin_theta: float, psi_in: float) -> np.ndarray:
 
 def sample_fixed_source(mesh, n_azim, spacing, sin_theta, polar_w, xs, S, phi0, psi0, sample):
     """Flux of the sampled regions after one fixed-source outer from (phi0, psi0), computed from
-    only the rays that cross them; also returns their tracked areas. Rectangular meshes only."""
+    only the rays that cross them; also returns their tracked areas. Rectangular meshes, or any
+    mesh whose walls are all vacuum (each in-mesh chord a track with zero inflow; psi0 unused)."""
     lib = _load()
     xy, tri, mat, bbox, bc = _f64(mesh.xy), _i32a(mesh.tri), _i32a(mesh.mat), _f64(mesh.bbox), _i32a(mesh.bc)
     st_, pw = _f64(sin_theta), _f64(polar_w)

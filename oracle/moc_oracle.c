@@ -1587,7 +1587,10 @@ void orc_track_sweep(int n, const double *sig, const double *qr, const double *l
  * regions, without segmenting the whole problem: only rays crossing a sampled region are laid down
  * and clipped (same laydown, clipping and weights as above, restated for a subset). For a
  * rectangular mesh the ray index equals the track index of the full track list, so psi0 is indexed
- * [ray][2][P][G]. Returns 0 on success. */
+ * [ray][2][P][G]. A mesh that does not fill its box (non-rectangular, or with holes) is accepted
+ * when every wall is vacuum: each maximal in-mesh chord of a ray is then a track with zero inflow
+ * (the reading of Sec. 3.1's modular rays on such meshes used throughout) and psi0 is not read.
+ * Returns 0 on success, -2 for a gap along a ray when some wall is reflective. */
 typedef struct { double cmin, cmax; int t; } proj_t;
 static int cmp_proj(const void *a, const void *b) {
   const proj_t *x = a, *y = b;
@@ -1608,6 +1611,7 @@ int orc_sample_fixed_source(int n_vert, const double *xy, int n_tri, const int32
   h->n_azim = n_azim; h->n_polar = n_polar;
   if (build_quadrature(h, spacing)) return -1;
   double W = h->xmax - h->xmin, H = h->ymax - h->ymin;
+  const int allvac = bc[0] == 0 && bc[1] == 0 && bc[2] == 0 && bc[3] == 0;
   /* sample lookup */
   int *slot = xcalloc(n_tri, sizeof(int));
   for (int i = 0; i < n_tri; ++i) slot[i] = -1;
@@ -1682,20 +1686,29 @@ int orc_sample_fixed_source(int n_vert, const double *xy, int n_tri, const int32
         pc[cnt].s0 = s0; pc[cnt].s1 = s1; pc[cnt].tri = t; cnt++;
       }
       qsort(pc, cnt, sizeof(piece_t), cmp_piece);
+      /* brk[k]: a gap precedes piece k, so piece k starts a new chord of this ray. Each maximal
+       * in-mesh chord is its own track with vacuum inflow (the exterior absorbs); that is only
+       * consistent with the caller's psi0 (one track per ray) when every wall is vacuum */
+      char *brk = xcalloc(cnt + 1, 1);
       for (int k = 1; k < cnt; ++k)
-        if (pc[k].s0 - pc[k - 1].s1 > 1e-9) fail = 1;   /* a gap: not a rectangular, box-filling mesh */
+        if (pc[k].s0 - pc[k - 1].s1 > 1e-9) {
+          brk[k] = 1;
+          if (!allvac) fail = 1;   /* a gap in a mesh with a reflective wall: not supported */
+        }
       int64_t tr = ray_base + r;
       for (int d = 0; d < 2; ++d) {
         /* entry point of this sense; inflow through a vacuum wall is zero */
         double ex = d ? p0[2 * r] + L * u[0] : p0[2 * r], ey = d ? p0[2 * r + 1] + L * u[1] : p0[2 * r + 1];
         int w = wall_of(h, ex, ey, 1e-9 * fmax(W, H));
-        int vac = (w >= 0 && bc[w] == 0);
+        int vac = allvac || (w >= 0 && bc[w] == 0);
         for (int p = 0; p < n_polar; ++p) {
           double Wt = 4.0 * ORC_PI * h->omega_a[j] * polar_w[p] * h->delta_a[j] * sin_theta[p];
           for (int g = 0; g < G; ++g) {
             double psi = vac ? 0.0 : psi0[((size_t)(2 * tr + d) * n_polar + p) * G + g];
             for (int n = 0; n < cnt; ++n) {
               int k = d ? (cnt - 1 - n) : n;
+              /* entering a new chord (backward travel crosses the gap after piece k) */
+              if (n > 0 && (d ? brk[k + 1] : brk[k])) psi = 0.0;
               int i = pc[k].tri, m = mat[i];
               double sig = st[(size_t)m * G + g];
               /* Eq. MGNTE_element source of region i from phi0 (fixed source, no fission) */
@@ -1712,6 +1725,7 @@ int orc_sample_fixed_source(int n_vert, const double *xy, int n_tri, const int32
       }
       for (int n = 0; n < cnt; ++n)
         if (slot[pc[n].tri] >= 0) area_j[slot[pc[n].tri]] += 2.0 * h->omega_a[j] * h->delta_a[j] * (pc[n].s1 - pc[n].s0);
+      free(brk);
       free(pc);
     }
     free(pj);

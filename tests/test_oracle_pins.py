@@ -631,3 +631,35 @@ def test_p1_global_balance_with_vacuum():
     production = float((A[:, None] * xs.nu_sigma_f[mesh.mat] * phi).sum())
     leak = float(o.leakage().sum())
     assert abs((absorption + leak) * k - production) < 1e-9
+
+
+# ------------------------------------------------------------------------------ sampled-region flux
+
+@pytest.mark.parametrize("case", ["lattice_mixed_bc", "hex_cluster_vacuum"])
+def test_sampled_fixed_source_flux_equals_the_full_outer(case):
+    """The sampled-region check used at full size (only the rays crossing the sampled regions are
+    laid down and swept) equals the whole oracle's fixed-source outer from the same state, on a
+    rectangular lattice with mixed walls and on a concave 7-hexagon cluster whose rays leave and
+    re-enter the mesh (every in-mesh chord a track with zero inflow)."""
+    rng = np.random.default_rng(31)
+    if case == "lattice_mixed_bc":
+        prob = W.small_lattice_problem(3, bc=(1, 0, 1, 0), n_azim=16, ray_spacing=0.05)
+    else:
+        mesh = W.hex_core_mesh(n_sub=4, n_rings=1)
+        prob = W.Problem(mesh, W.synthetic_xs(["fuel", "fuel", "coolant"], 5, 9, sigt_range=(0.05, 0.6)), 12, 0.2)
+    xs = W.CrossSections(prob.xs.sigma_t, np.zeros_like(prob.xs.nu_sigma_f), prob.xs.chi, prob.xs.sigma_s)
+    R, G = prob.mesh.n_tri, xs.n_groups
+    o = oracle.Oracle.from_problem(prob, threads=2, with_xs=False)
+    o.set_xs(xs)
+    S = rng.uniform(0.0, 1.0, (R, G))
+    phi0 = rng.uniform(0.5, 1.5, (R, G))
+    psi0 = rng.uniform(0.0, 0.2, (o.n_tracks, 2, len(prob.sin_theta), G))
+    o.set_fixed_source(S)
+    o.set_state(phi0, 1.0, psi0)
+    o.outer(False)
+    full, _ = o.get_state()
+    sample = np.unique(rng.choice(R, 25, replace=False))
+    ref, area = oracle.sample_fixed_source(prob.mesh, prob.n_azim, prob.ray_spacing, prob.sin_theta, prob.polar_w,
+                                           xs, S, phi0, psi0, sample)
+    np.testing.assert_allclose(area, o.areas()[sample], rtol=1e-12)
+    np.testing.assert_allclose(ref, full[sample], rtol=1e-12)
