@@ -817,66 +817,111 @@ static void update_source(orc_t *h, int eigen) {
 
 /* One transport sweep of every track, both directions, every polar angle and group (Eq. MOC_sol),
  * tallying W (psi_in - psi_out) per segment into its region; outgoing fluxes are routed to the
- * linked incoming ends for the next sweep (Jacobi in boundary flux). */
+ * linked incoming ends for the next sweep (Jacobi in boundary flux).
+ *
+ * Parallel in a fixed order: groups one after another; within a group the tracks are cut into
+ * n_chunks fixed ranges of track indices (a function of the problem, never of the thread count),
+ * each chunk sums its own partial tallies and currents, and the partials are added in chunk order.
+ * The result is therefore the same for any thread count. */
+static int sweep_chunks(const orc_t *h) {
+  int64_t nc = h->n_tracks / 64;
+  int cap = h->L ? 4 : 32;   /* per-direction tallies make a chunk's partials large */
+  if (nc < 1) nc = 1;
+  if (nc > cap) nc = cap;
+  return (int)nc;
+}
+
 static void transport_sweep(orc_t *h) {
-  int G = h->G, P = h->n_polar;
-  size_t RG = (size_t)h->n_tri * G, PB = (size_t)h->n_tracks * 2 * P * G;
-  memset(h->tally, 0, RG * sizeof(double));
+  const int G = h->G, P = h->n_polar, R = h->n_tri, ND = h->L ? h->ND : 0;
+  const int NC = sweep_chunks(h);
+  const size_t PB = (size_t)h->n_tracks * 2 * P * G;
+  const size_t n_cur = h->cmfd ? 2 * (size_t)h->n_if : 0, n_cl = h->cmfd ? (size_t)h->n_cells : 0;
+  /* per-chunk partials of one group: tally [R], per-direction tally [R][ND], currents, leakage */
+  const size_t per = (size_t)R + (size_t)R * ND + n_cur + n_cl + 1;
+  double *part = xcalloc((size_t)NC * per, sizeof(double));
   memset(h->psi_next, 0, PB * sizeof(double));
-  if (h->cmfd) {
-    memset(h->cur, 0, 2 * (size_t)h->n_if * G * sizeof(double));
-    memset(h->cleak, 0, (size_t)h->n_cells * G * sizeof(double));
-  }
-  if (h->L) memset(h->tdir, 0, (size_t)h->n_tri * h->ND * G * sizeof(double));
-  double *leak_g = xcalloc(G, sizeof(double));
-#pragma omp parallel for schedule(static) num_threads(h->n_threads)
   for (int g = 0; g < G; ++g) {
-    double lk = 0.0;
-    for (int64_t t = 0; t < h->n_tracks; ++t) {
-      int j = h->track_dir[t];
-      int64_t s0 = h->seg_off[t], s1 = h->seg_off[t + 1];
-      for (int d = 0; d < 2; ++d) {
-        for (int p = 0; p < P; ++p) {
-          double Wt = 4.0 * ORC_PI * h->omega_a[j] * h->polar_w[p] * h->delta_a[j] * h->sin_theta[p];
-          double psi = h->psi_in[((size_t)(2 * t + d) * P + p) * G + g];
-          if (h->cmfd) {
-            /* current entering the domain at this start (zero at vacuum starts) */
-            int64_t s_first = d ? (s1 - 1) : s0;
-            h->cleak[(size_t)h->cell[h->seg_reg[s_first]] * G + g] -= Wt * psi;
-          }
-          int mdir = (j * 2 + d) * P + p;
-          for (int64_t n = 0; n < s1 - s0; ++n) {
-            int64_t s = d ? (s1 - 1 - n) : (s0 + n);
-            int i = h->seg_reg[s];
-            double sig = h->st[(size_t)h->mat[i] * G + g];
-            double qi = h->L ? h->qdir[((size_t)i * h->ND + mdir) * G + g] : h->q[(size_t)i * G + g];
-            double tau = sig * h->seg_len[s] / h->sin_theta[p];
-            double delta = (psi - qi / sig) * (-expm1(-tau));
-            h->tally[(size_t)i * G + g] += Wt * delta;
-            if (h->L) h->tdir[((size_t)i * h->ND + mdir) * G + g] += h->delta_a[j] * h->sin_theta[p] * delta;
-            psi -= delta;
-            if (h->cmfd && n + 1 < s1 - s0) {
-              /* partial current W psi into the next cell along the track, if the cell changes */
-              int64_t sn = d ? (s - 1) : (s + 1);
-              int a = h->cell[i], b = h->cell[h->seg_reg[sn]];
-              if (a != b) h->cur[(size_t)cmfd_slot(h, a, b) * G + g] += Wt * psi;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(h->n_threads)
+    for (int c = 0; c < NC; ++c) {
+      double *tal = part + (size_t)c * per, *tdir = tal + R, *cur = tdir + (size_t)R * ND, *cleak = cur + n_cur;
+      double *lk = cleak + n_cl;
+      const int64_t t0 = h->n_tracks * c / NC, t1 = h->n_tracks * (c + 1) / NC;
+      for (int64_t t = t0; t < t1; ++t) {
+        int j = h->track_dir[t];
+        int64_t s0 = h->seg_off[t], s1 = h->seg_off[t + 1];
+        for (int d = 0; d < 2; ++d) {
+          for (int p = 0; p < P; ++p) {
+            double Wt = 4.0 * ORC_PI * h->omega_a[j] * h->polar_w[p] * h->delta_a[j] * h->sin_theta[p];
+            double psi = h->psi_in[((size_t)(2 * t + d) * P + p) * G + g];
+            if (h->cmfd) {
+              /* current entering the domain at this start (zero at vacuum starts) */
+              int64_t s_first = d ? (s1 - 1) : s0;
+              cleak[h->cell[h->seg_reg[s_first]]] -= Wt * psi;
             }
-          }
-          int64_t e = h->link[2 * t + d];
-          if (e >= 0) h->psi_next[((size_t)e * P + p) * G + g] = psi;
-          else lk += Wt * psi;
-          if (h->cmfd) {
-            /* current leaving the domain at this end, vacuum or reflective */
-            int64_t s_last = d ? s0 : (s1 - 1);
-            h->cleak[(size_t)h->cell[h->seg_reg[s_last]] * G + g] += Wt * psi;
+            int mdir = (j * 2 + d) * P + p;
+            for (int64_t n = 0; n < s1 - s0; ++n) {
+              int64_t s = d ? (s1 - 1 - n) : (s0 + n);
+              int i = h->seg_reg[s];
+              double sig = h->st[(size_t)h->mat[i] * G + g];
+              double qi = h->L ? h->qdir[((size_t)i * h->ND + mdir) * G + g] : h->q[(size_t)i * G + g];
+              double tau = sig * h->seg_len[s] / h->sin_theta[p];
+              double delta = (psi - qi / sig) * (-expm1(-tau));
+              tal[i] += Wt * delta;
+              if (h->L) tdir[(size_t)i * ND + mdir] += h->delta_a[j] * h->sin_theta[p] * delta;
+              psi -= delta;
+              if (h->cmfd && n + 1 < s1 - s0) {
+                /* partial current W psi into the next cell along the track, if the cell changes */
+                int64_t sn = d ? (s - 1) : (s + 1);
+                int a = h->cell[i], b = h->cell[h->seg_reg[sn]];
+                if (a != b) cur[cmfd_slot(h, a, b)] += Wt * psi;
+              }
+            }
+            int64_t e = h->link[2 * t + d];
+            if (e >= 0) h->psi_next[((size_t)e * P + p) * G + g] = psi;
+            else *lk += Wt * psi;
+            if (h->cmfd) {
+              /* current leaving the domain at this end, vacuum or reflective */
+              int64_t s_last = d ? s0 : (s1 - 1);
+              cleak[h->cell[h->seg_reg[s_last]]] += Wt * psi;
+            }
           }
         }
       }
     }
-    leak_g[g] = lk;
+    /* the chunks' partials in chunk order (and cleared for the next group) */
+#pragma omp parallel for schedule(static) num_threads(h->n_threads)
+    for (int i = 0; i < R; ++i) {
+      double a = 0.0;
+      for (int c = 0; c < NC; ++c) {
+        double *v = part + (size_t)c * per + i;
+        a += *v;
+        *v = 0.0;
+      }
+      h->tally[(size_t)i * G + g] = a;
+      for (int m = 0; m < ND; ++m) {
+        double b = 0.0;
+        for (int c = 0; c < NC; ++c) {
+          double *v = part + (size_t)c * per + R + (size_t)i * ND + m;
+          b += *v;
+          *v = 0.0;
+        }
+        h->tdir[((size_t)i * ND + m) * G + g] = b;
+      }
+    }
+    const size_t tail = (size_t)R + (size_t)R * ND;
+    for (size_t x = 0; x < n_cur + n_cl + 1; ++x) {
+      double a = 0.0;
+      for (int c = 0; c < NC; ++c) {
+        double *v = part + (size_t)c * per + tail + x;
+        a += *v;
+        *v = 0.0;
+      }
+      if (x < n_cur) h->cur[x * G + g] = a;
+      else if (x < n_cur + n_cl) h->cleak[(x - n_cur) * G + g] = a;
+      else h->leak[g] = a;
+    }
   }
-  memcpy(h->leak, leak_g, G * sizeof(double));
-  free(leak_g);
+  free(part);
 }
 
 /* scalar flux from source and tallies */
