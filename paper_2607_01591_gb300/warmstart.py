@@ -12,6 +12,10 @@ Everything numeric runs in the library's kernels; this module orchestrates (data
 PyTorch-owned device memory) and measures.
 
 Usage: python -m paper_2607_01591_gb300.warmstart --train 2000 --eval 200 --out result.json
+       [--save weights.npz]   (the trained network: FP32 master weights and standardisation)
+
+The network the package ships (data/warmstart_assembly17.npz) was trained this way on one GB300;
+`evaluate` measures it on held-out instances (bench.py's warm-start block does).
 """
 from __future__ import annotations
 
@@ -29,6 +33,10 @@ from . import moc
 from . import workloads as W
 
 PCM = 1e-5
+HERE = os.path.dirname(os.path.abspath(__file__))
+SHIPPED = os.path.join(HERE, "data", "warmstart_assembly17.npz")
+TRAIN_SEED = 1000            # instance i of the training set: perturbed_xs(base, TRAIN_SEED + i)
+HELD_OUT_SEED = TRAIN_SEED + 100000
 
 
 def lattice_geometry_features(mesh: W.Mesh, pitch: float = 1.26, guide_tubes=None) -> np.ndarray:
@@ -167,6 +175,65 @@ class WarmStart:
         torch.cuda.synchronize(self.device)
         return losses, time.perf_counter() - t0
 
+    # ------------------------------------------------------------------------------ persistence
+    def save(self, path: str, meta: dict = None):
+        """The network's FP32 master weights, its standardisation and its layer sizes."""
+        os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+        n = self.net.norm
+        np.savez_compressed(path, params=self.net.get_params(), in_mean=n[0], in_std=n[1], out_mean=n[2],
+                            out_std=n[3], dims=np.array(self.net.dims, dtype=np.int32),
+                            meta=np.array(json.dumps(meta or {})))
+
+    def load(self, path: str) -> dict:
+        z = np.load(path)
+        if list(z["dims"]) != list(self.net.dims):
+            raise ValueError(f"{path}: network {list(z['dims'])} does not match {self.net.dims}")
+        self.net.set_params(z["params"])
+        self.net.set_normalization(z["in_mean"], z["in_std"], z["out_mean"], z["out_std"])
+        return json.loads(str(z["meta"]))
+
+    def time_network(self, batch: int = 8192, reps: int = 20) -> dict:
+        """CUDA-event times of the network's forward pass over all regions of the geometry and of
+        one training step (forward, backward, Adam) on a batch of random rows; the parameters are
+        restored afterwards."""
+        torch = self.torch
+        p = self.net.get_params()
+        norm = [v.copy() for v in self.net.norm]
+        x = torch.randn((self.R, self.n_in), dtype=torch.float32, device=self.dev)
+        xb = torch.randn((batch, self.n_in), dtype=torch.float32, device=self.dev)
+        yb = torch.randn((batch, self.n_out), dtype=torch.float32, device=self.dev)
+        st = self.stream
+
+        def timed(fn):
+            with torch.cuda.stream(st):
+                fn()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                for _ in range(reps):
+                    fn()
+                e1.record(st)
+            torch.cuda.synchronize(self.device)
+            return e0.elapsed_time(e1) / reps
+
+        fwd = timed(lambda: self.net.forward(x, self.pred, self.R, st.cuda_stream))
+        trn = timed(lambda: self.net.train_step(xb, yb, batch, 1e-6, st.cuda_stream, False))
+        self.net.set_params(p)
+        self.net.set_normalization(*norm)
+        flops = 2 * sum(a * b for a, b in zip(self.net.dims[:-1], self.net.dims[1:]))
+        return {"forward_rows": self.R, "forward_ms": fwd, "forward_tflops": flops * self.R / fwd / 1e9,
+                "train_batch": batch, "train_step_ms": trn, "train_tflops": 3 * flops * batch / trn / 1e9}
+
+    def mean_solution(self, instances: List[W.CrossSections]):
+        """The ablation without a network: the mean over solved training instances of the log
+        flux per region and group, and of k, as a prediction in the network's output layout."""
+        torch = self.torch
+        acc = torch.zeros((self.R, self.n_out), dtype=torch.float64, device=self.dev)
+        for xs in instances:
+            phi, k = self.solve_reference(xs)
+            acc[:, :self.G] += torch.from_numpy(np.log(phi)).to(self.dev)
+            acc[:, self.G] += k
+        return (acc / len(instances)).float()
+
     # ------------------------------------------------------------------------------ solving
     def _iterate_to(self, ctx, k_ref: float, max_outer: int, tol: float = 5 * PCM):
         """Outers until |k - k_ref| <= tol; returns (outers, seconds of iteration)."""
@@ -204,42 +271,25 @@ class WarmStart:
         return n, t_inf + t_it, k, k0, t_inf
 
 
-def run(n_train: int, n_eval: int, n_eval_fp64: int, rows_per_instance: int, epochs: int, out: str,
-        lattice: int = 17, seed: int = 1000):
-    import torch
-
-    if lattice == 17:
-        prob = W.assembly_problem()
-        gts = W.guide_tube_positions()
-    else:
-        prob = W.small_lattice_problem(lattice, n_azim=16, ray_spacing=0.04)
-        gts = None
-    base = W.synthetic_xs(["fuel", "clad", "moderator"], 7, 2)
-    train = [W.perturbed_xs(base, seed + i) for i in range(n_train)]
-    held = [W.perturbed_xs(base, seed + 100000 + i) for i in range(n_eval)]
-    ws = WarmStart(prob, base, gts)
-    X, Y, ktr, t_data = ws.make_dataset(train, rows_per_instance, seed=1)
-    losses, t_fit = ws.fit(X, Y, epochs=epochs)
-    # reference k of held-out instances (same solve as the training data)
-    refs = [ws.solve_reference(xs, tight=True) for xs in held]
-    # ablation: start from the training-mean solution (mean log flux per region, mean k)
-    mean_pred = torch.empty((ws.R, ws.n_out), dtype=torch.float32, device=ws.dev)
-    acc = torch.zeros((ws.R, ws.n_out), dtype=torch.float64, device=ws.dev)
-    for xs in train[:min(50, n_train)]:
-        phi, k = ws.solve_reference(xs)
-        acc[:, :ws.G] += torch.from_numpy(np.log(phi)).to(ws.dev)
-        acc[:, ws.G] += k
-    mean_pred.copy_((acc / min(50, n_train)).float())
-    res: Dict[str, list] = {"cold_fp32": [], "warm_fp32": [], "mean_fp32": [], "cold_fp64": [], "warm_k0_err": []}
-    for i, (xs, (phi_ref, k_ref)) in enumerate(zip(held, refs)):
+def evaluate(ws: WarmStart, held: List[W.CrossSections], mean_pred, n_fp64: int) -> dict:
+    """Time to |k - k_ref| <= 5 pcm on held-out instances from four starts: cold FP32, cold FP64
+    (first n_fp64 instances), the training-mean solution without a network (ablation) and the
+    learned start (wall time including the feature and network kernels). k_ref: FP32 to |dk| <=
+    1e-7 continued in FP64 to |dk| <= 1e-10."""
+    res: Dict[str, list] = {"cold_fp32": [], "warm_fp32": [], "mean_fp32": [], "cold_fp64": [], "warm_k0_err": [],
+                            "mean_k0_err": [], "inference_s": []}
+    for i, xs in enumerate(held):
+        _, k_ref = ws.solve_reference(xs, tight=True)
         n, t, k = ws.cold(ws.ctx32, xs, k_ref)
         res["cold_fp32"].append((n, t))
         n, t, k, k0, t_inf = ws.warm(ws.ctx32, xs, k_ref)
         res["warm_fp32"].append((n, t))
         res["warm_k0_err"].append(abs(k0 - k_ref))
-        n, t, k, _, _ = ws.warm(ws.ctx32, xs, k_ref, pred_fn=mean_pred)
+        res["inference_s"].append(t_inf)
+        n, t, k, k0, _ = ws.warm(ws.ctx32, xs, k_ref, pred_fn=mean_pred)
         res["mean_fp32"].append((n, t))
-        if i < n_eval_fp64:
+        res["mean_k0_err"].append(abs(k0 - k_ref))
+        if i < n_fp64:
             n, t, k = ws.cold(ws.ctx64, xs, k_ref)
             res["cold_fp64"].append((n, t))
 
@@ -248,17 +298,50 @@ def run(n_train: int, n_eval: int, n_eval_fp64: int, rows_per_instance: int, epo
         return {"outers_mean": float(a[:, 0].mean()), "outers_median": float(np.median(a[:, 0])),
                 "seconds_mean": float(a[:, 1].mean()), "n": int(a.shape[0])}
 
+    return {"stop": "first outer with |k - k_ref| <= 5 pcm; k_ref: FP32 to 1e-7, then FP64 to |dk| <= 1e-10",
+            "cold_fp32": summ(res["cold_fp32"]), "warm_fp32": summ(res["warm_fp32"]),
+            "mean_solution_fp32": summ(res["mean_fp32"]),
+            "cold_fp64": summ(res["cold_fp64"]) if res["cold_fp64"] else None,
+            "warm_initial_k_err_pcm_mean": float(np.mean(res["warm_k0_err"]) / PCM),
+            "mean_solution_initial_k_err_pcm_mean": float(np.mean(res["mean_k0_err"]) / PCM),
+            "inference_s_mean": float(np.mean(res["inference_s"]))}
+
+
+def assembly_base():
+    """The base cross sections of the assembly instances (fuel, clad, moderator; 7 groups)."""
+    return W.synthetic_xs(["fuel", "clad", "moderator"], 7, 2)
+
+
+def run(n_train: int, n_eval: int, n_eval_fp64: int, rows_per_instance: int, epochs: int, out: str,
+        lattice: int = 17, seed: int = TRAIN_SEED, save: str = ""):
+    import torch
+
+    if lattice == 17:
+        prob = W.assembly_problem()
+        gts = W.guide_tube_positions()
+    else:
+        prob = W.small_lattice_problem(lattice, n_azim=16, ray_spacing=0.04)
+        gts = None
+    base = assembly_base()
+    train = [W.perturbed_xs(base, seed + i) for i in range(n_train)]
+    held = [W.perturbed_xs(base, seed + 100000 + i) for i in range(n_eval)]
+    ws = WarmStart(prob, base, gts)
+    X, Y, ktr, t_data = ws.make_dataset(train, rows_per_instance, seed=1)
+    losses, t_fit = ws.fit(X, Y, epochs=epochs)
+    mean_pred = ws.mean_solution(train[:min(50, n_train)])
+    ev = evaluate(ws, held, mean_pred, n_eval_fp64)
+    ev["network_times"] = ws.time_network()
     result = {
         "workload": f"{lattice}x{lattice} lattice, {prob.mesh.n_tri} triangles, 7 groups; XS x lognormal(0.1) per material/group",
         "n_train": n_train, "n_eval": n_eval, "rows_per_instance": rows_per_instance, "epochs": epochs,
         "net": {"dims": ws.net.dims, "params": ws.net.n_params, "weights": "bf16 (FP32 master, Adam)"},
         "data_seconds": t_data, "fit_seconds": t_fit, "loss_first_last": [losses[0], losses[-1]],
-        "stop": "first outer with |k - k_ref| <= 5 pcm; k_ref: FP32 to 1e-7, then FP64 to |dk| <= 1e-10",
-        "cold_fp32": summ(res["cold_fp32"]), "warm_fp32": summ(res["warm_fp32"]),
-        "mean_solution_fp32": summ(res["mean_fp32"]),
-        "cold_fp64": summ(res["cold_fp64"]) if res["cold_fp64"] else None,
-        "warm_initial_k_err_pcm_mean": float(np.mean(res["warm_k0_err"]) / PCM),
+        **ev,
     }
+    if save:
+        ws.save(save, {"n_train": n_train, "rows_per_instance": rows_per_instance, "epochs": epochs,
+                       "train_seed": seed, "lattice": lattice, "data_seconds": t_data, "fit_seconds": t_fit,
+                       "loss_first_last": [losses[0], losses[-1]]})
     if out:
         with open(out, "w") as f:
             json.dump(result, f, indent=1)
@@ -275,8 +358,17 @@ def main():
     ap.add_argument("--epochs", type=int, default=4)
     ap.add_argument("--lattice", type=int, default=17)
     ap.add_argument("--out", default="")
+    ap.add_argument("--save", default="", help="write the trained network here (.npz)")
+    ap.add_argument("--time-network", action="store_true",
+                    help="only time the shipped network's forward pass over the assembly's regions and a "
+                         "training step (CUDA events), and print them")
     a = ap.parse_args()
-    run(a.train, a.eval, a.eval_fp64, a.rows, a.epochs, a.out, a.lattice)
+    if a.time_network:
+        ws = WarmStart(W.assembly_problem(), assembly_base(), W.guide_tube_positions())
+        ws.load(SHIPPED)
+        print(json.dumps(ws.time_network()), flush=True)
+        return
+    run(a.train, a.eval, a.eval_fp64, a.rows, a.epochs, a.out, a.lattice, save=a.save)
 
 
 if __name__ == "__main__":

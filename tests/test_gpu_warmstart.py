@@ -27,12 +27,15 @@ def _net_and_data(n_in=93, width=256, n_out=8, rows=64, seed=0):
     return net, norm, x, y, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
 
 
-def test_forward_and_gradients_match_cpu_oracle():
+@pytest.mark.parametrize("rows,width,n_out", [(64, 256, 8), (300, 512, 40)])
+def test_forward_and_gradients_match_cpu_oracle(rows, width, n_out):
+    """The network's tensor-core forward and backward passes (tiles of 128 rows and 256 columns,
+    partial tiles at both edges) against the FP64 network oracle."""
     import torch
 
-    net, norm, x, y, xd, yd = _net_and_data()
+    net, norm, x, y, xd, yd = _net_and_data(width=width, n_out=n_out, rows=rows)
     p = net.get_params().astype(np.float64)
-    out = torch.empty((x.shape[0], 8), dtype=torch.float32, device="cuda")
+    out = torch.empty((x.shape[0], n_out), dtype=torch.float32, device="cuda")
     net.forward(xd, out, x.shape[0])
     torch.cuda.synchronize()
     ref, _ = MO.forward(p, net.dims, x, norm, bf16=True)
@@ -73,3 +76,22 @@ def test_learned_start_needs_fewer_outers_than_cold():
     print(r)
     # the trained network's start needs fewer outers than the cold start
     assert r["warm_fp32"]["outers_mean"] < r["cold_fp32"]["outers_mean"]
+
+
+def test_shipped_network_beats_the_ablation_and_the_cold_start():
+    """The network the package ships (trained on the GPU by the library's own kernels on 2000
+    perturbed assembly instances), on held-out instances it never saw: its start needs fewer
+    outers to |k - k_ref| <= 5 pcm than the training-mean solution without a network (the
+    ablation), which in turn needs fewer than the cold start."""
+    from paper_2607_01591_gb300 import warmstart
+    from paper_2607_01591_gb300 import workloads as W
+
+    base = warmstart.assembly_base()
+    ws = warmstart.WarmStart(W.assembly_problem(), base, W.guide_tube_positions())
+    ws.load(warmstart.SHIPPED)
+    mean_pred = ws.mean_solution([W.perturbed_xs(base, warmstart.TRAIN_SEED + i) for i in range(10)])
+    held = [W.perturbed_xs(base, warmstart.HELD_OUT_SEED + 5000 + i) for i in range(8)]
+    r = warmstart.evaluate(ws, held, mean_pred, n_fp64=0)
+    print(r)
+    assert r["warm_fp32"]["outers_mean"] < r["mean_solution_fp32"]["outers_mean"] < r["cold_fp32"]["outers_mean"]
+    assert r["warm_initial_k_err_pcm_mean"] < r["mean_solution_initial_k_err_pcm_mean"]
