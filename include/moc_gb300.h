@@ -181,6 +181,19 @@ int moc_set_xs(moc_ctx *ctx, int n_mat, int G, const double *sigma_t, const doub
  * MOC_ERR_STATE. */
 int moc_set_cmfd(moc_ctx *ctx, const int32_t *cell, int n_cells, int n_outer, int n_inner, double omega);
 
+/* Early stop of the CMFD coarse power iteration (a production mode; the paper fixes no coarse
+ * iteration count): with tol > 0, each outer's coarse iteration ends after the first coarse
+ * iteration (at most n_outer of moc_set_cmfd) whose k change is <= tol * k and whose coarse
+ * fission source, normalised to unit sum, changes by <= tol relative in every cell. tol = 0, the
+ * value a new context starts with, runs exactly n_outer iterations; moc_set_cmfd leaves the
+ * setting as it is. The converged MOC solution does not depend on it (it is a fixed point of every
+ * coarse step). Errors: MOC_ERR_ARG (tol negative or not finite). */
+int moc_set_cmfd_tolerance(moc_ctx *ctx, double tol);
+
+/* Coarse power iterations run since the last moc_set_state (or moc_set_xs), summed over outers.
+ * Synchronises. Errors: MOC_ERR_ARG, MOC_ERR_STATE (host-only context), MOC_ERR_CUDA. */
+int moc_get_cmfd_iterations(moc_ctx *ctx, int64_t *total);
+
 /* Anisotropic scattering of Legendre order L (Sec. 2: the scattering kernel expanded as
  * sum_l (2l+1)/(4 pi) P_l(Om . Om') Sigma_s,l). sigma_sl: [L][n_mat][G][G] holds Sigma_s,l g -> g'
  * (from-group major, like sigma_s) for l = 1..L, 1 <= L <= 3; L = 0 or NULL restores isotropic

@@ -20,7 +20,8 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmoc_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["moc_api.cu", "moc_mlp.cu", "moc_track.cu", "moc_probe.cu", "moc_geom.cpp"]
-HEADERS = ["moc_kernels.cuh", "moc_cmfd.cuh", "moc_dg.cuh", "moc_aniso.cuh", "moc_geom.h", "moc_walk.h", "moc_track.h", "exp_f32_coef.h"]
+HEADERS = ["moc_kernels.cuh", "moc_cmfd.cuh", "moc_dg.cuh", "moc_aniso.cuh", "moc_tc.cuh", "moc_geom.h", "moc_walk.h",
+           "moc_track.h", "exp_f32_coef.h"]
 # the device walk must round every double multiply and add separately, like the host build
 NO_FMA = {"moc_track.cu"}
 

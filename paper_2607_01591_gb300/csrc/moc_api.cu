@@ -51,6 +51,8 @@ struct moc_ctx {
   double *d_fold = nullptr, *d_ext = nullptr, *d_part = nullptr, *d_scal = nullptr;
   void *d_inv_ta = nullptr;    // [R][Gp] 1/(Sigma_t A) in the sweep's type, 0 where the tracked area is 0
   unsigned *d_ticket = nullptr;  // finalize's last-block counter (back to 0 after each launch)
+  int2 *d_srange = nullptr;      // [M][G] first and last source group of each scattering column
+  int n_sm = 0;                  // the device's multiprocessor count
   int cur = 0;          // psi buffer holding the incoming flux of the next sweep
   bool eigen = true;
   bool tracks_on_device = false, xs_set = false;
@@ -62,6 +64,7 @@ struct moc_ctx {
   bool cmfd = false;
   int n_cells = 0, n_if = 0, cm_outer = 0, cm_inner = 0, cm_colors = 0;
   double cm_omega = 1.0;
+  double cm_tol = 0.0;  // coarse power iteration stops early when k and the source settle to this (0: fixed count)
   int32_t *d_xoff = nullptr, *d_cell = nullptr;
   int2 *d_xent = nullptr;
   int32_t *d_cif_off = nullptr, *d_cif = nullptr, *d_if_cells = nullptr, *d_nbr = nullptr, *d_coff = nullptr;
@@ -257,6 +260,7 @@ void free_problem(moc_ctx *c) {
   dfree(c->d_nsf);
   dfree(c->d_chi);
   dfree(c->d_sig_s);
+  dfree(c->d_srange);
   c->xs_set = false;
 }
 
@@ -413,6 +417,21 @@ template <typename Real> int upload_xs(moc_ctx *c, int n_mat, int G, const doubl
   c->d_chi = p3;
   if ((rc = upload(c, p4, vss.data(), vss.size()))) return rc;
   c->d_sig_s = p4;
+  {
+    // nonzero band of every scattering column (g' -> g over g'), for the many-group source
+    std::vector<int2> band((size_t)n_mat * G);
+    for (int m = 0; m < n_mat; ++m)
+      for (int g = 0; g < G; ++g) {
+        int lo = G, hi = -1;
+        for (int gp = 0; gp < G; ++gp)
+          if (vss[((size_t)m * G + gp) * G + g] != (Real)0) {
+            lo = std::min(lo, gp);
+            hi = gp;
+          }
+        band[(size_t)m * G + g] = (hi < 0) ? make_int2(1, 0) : make_int2(lo, hi);
+      }
+    if ((rc = upload(c, c->d_srange, band.data(), band.size()))) return rc;
+  }
   // region pairs {Sigma_t, q/Sigma_t}; padding groups get Sigma_t = 1, q = 0
   std::vector<typename Pair<Real>::T> xsq((size_t)R * Gp);
   for (int r = 0; r < R; ++r)
@@ -455,7 +474,8 @@ template <typename Real> int upload_xs(moc_ctx *c, int n_mat, int G, const doubl
   }
   CUDA_TRY(c, cudaMalloc(&c->d_fold, (size_t)R * sizeof(double)));
   CUDA_TRY(c, cudaMemsetAsync(c->d_fold, 0, (size_t)R * sizeof(double), c->stream));
-  // enough block partials for either finalize variant and for the state kernel's normalisation
+  // enough block partials for either finalize variant (4 per block of 32 regions) and for the state
+  // kernel's normalisation
   const size_t nb = std::max<size_t>((size_t)(R + 31) / 32 * 4, (RG + 255) / 256);
   CUDA_TRY(c, cudaMalloc(&c->d_part, nb * sizeof(double)));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -526,8 +546,23 @@ template <typename Real> int download_state(moc_ctx *c, double scale, double *ph
 }
 
 // ---------------------------------------------------------------------------------- launches
+// the many-group source and finalize kernels (eight threads per region) apply for 8 < G <= 256
+bool lane_rows(const moc_ctx *c) { return c->G > 8 && c->Gp <= 256; }
+
 template <typename Real> int launch_source(moc_ctx *c, cudaStream_t st) {
   const int R = c->geo.n_tri;
+  if (lane_rows(c)) {
+    const unsigned nb = (unsigned)((R + 31) / 32);
+    const size_t sm = (size_t)32 * c->Gp * sizeof(Real);
+    auto src = c->Gp == 40 ? source_lanes_kernel<Real, 5> : c->Gp == 16 ? source_lanes_kernel<Real, 2>
+             : c->Gp == 24 ? source_lanes_kernel<Real, 3> : c->Gp == 32 ? source_lanes_kernel<Real, 4>
+                           : source_lanes_kernel<Real, 0>;
+    src<<<nb, 256, sm, st>>>(R, c->G, c->Gp, c->d_mat, (const Real *)c->d_sig_s, (const Real *)c->d_nsf,
+                            (const Real *)c->d_chi, c->d_srange, c->d_ext, (Real *)c->d_phi,
+                            (typename Pair<Real>::T *)c->d_xsq, c->d_fold, c->d_scal, c->eigen ? 1 : 0);
+    CUDA_TRY(c, cudaGetLastError());
+    return MOC_OK;
+  }
   size_t sm = (size_t)c->M * c->G * c->G * sizeof(Real);
   if (sm > 48 * 1024) return fail(c, MOC_ERR_ARG, "scattering tables too large for shared memory (n_mat*G*G)");
   source_kernel<Real><<<(R + 127) / 128, 128, sm, st>>>(
@@ -563,29 +598,16 @@ template <typename Real, int TM, bool CM> int launch_sweep_p(moc_ctx *c, cudaStr
   return MOC_OK;
 }
 
-template <int GPT, int NACT, int TM> void chunk_launch(moc_ctx *c, cudaStream_t st, int lanes) {
-  const long long n = (long long)c->T * 2 * lanes;
-  const int bs = 64;
-  sweep_chunk_kernel<3, GPT, NACT, TM><<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(
-      c->d_trk, (const SegRec<float> *)c->d_seg, c->d_link, (const float *)c->d_wgt, (const float *)c->d_inv_sin,
-      (const float2 *)c->d_xsq, (float *)c->d_tsum, (float *)c->d_tcomp, (const float *)c->d_psi[c->cur],
-      (float *)c->d_psi[c->cur ^ 1], c->d_scal, n, c->G, c->Gp, lanes);
-}
-
-// FP32 with 3 polar angles: one thread per (track end, chunk of groups); G <= 8 in one chunk
+// FP32 with 3 polar angles and G > 8: ceil(G / 4) four-group lanes per track end
 template <int TM> int launch_chunk(moc_ctx *c, cudaStream_t st) {
-  const int G = c->G;
-  switch (G) {
-    case 1: chunk_launch<4, 1, TM>(c, st, 1); break;
-    case 2: chunk_launch<4, 2, TM>(c, st, 1); break;
-    case 3: chunk_launch<4, 3, TM>(c, st, 1); break;
-    case 4: chunk_launch<4, 4, TM>(c, st, 1); break;
-    case 5: chunk_launch<8, 5, TM>(c, st, 1); break;
-    case 6: chunk_launch<8, 6, TM>(c, st, 1); break;
-    case 7: chunk_launch<8, 7, TM>(c, st, 1); break;
-    case 8: chunk_launch<8, 8, TM>(c, st, 1); break;
-    default: chunk_launch<4, 4, TM>(c, st, (G + 3) / 4); break;
-  }
+  const int lanes = (c->G + 3) / 4;
+  const long long n = (long long)c->T * 2 * lanes;
+  PolarInv<3> is;
+  for (int p = 0; p < 3; ++p) is.v[p] = (float)(1.0 / c->geo.sin_theta[p]);
+  sweep_chunk_kernel<3, TM><<<(unsigned)((n + 63) / 64), 64, 0, st>>>(
+      c->d_trk, (const SegRec<float> *)c->d_seg, c->d_link, (const float *)c->d_wgt, is, (const float2 *)c->d_xsq,
+      (float *)c->d_tsum, (float *)c->d_tcomp, (const float *)c->d_psi[c->cur], (float *)c->d_psi[c->cur ^ 1],
+      c->d_scal, n, c->G, c->Gp, lanes);
   CUDA_TRY(c, cudaGetLastError());
   return MOC_OK;
 }
@@ -652,6 +674,21 @@ template <typename Real> int launch_finalize_reduce(moc_ctx *c, cudaStream_t st)
           R, c->G, c->d_mat, (const Real *)c->d_nsf, (const Real *)c->d_inv_ta, (const typename Pair<Real>::T *)c->d_xsq,
           (Real *)c->d_tsum, (Real *)c->d_tcomp, (Real *)c->d_phi, c->d_fold, c->d_area, c->d_part, c->d_ticket,
           c->d_scal, c->eigen ? 1 : 0);
+    CUDA_TRY(c, cudaGetLastError());
+    return MOC_OK;
+  }
+  if (lane_rows(c)) {
+    const unsigned nb = (unsigned)((R + 31) / 32);
+    const bool tm = tally_mode(c) == 1;
+    auto fin = c->Gp == 40 ? (tm ? finalize_lanes_kernel<Real, 1, 5> : finalize_lanes_kernel<Real, 0, 5>)
+             : c->Gp == 16 ? (tm ? finalize_lanes_kernel<Real, 1, 2> : finalize_lanes_kernel<Real, 0, 2>)
+             : c->Gp == 24 ? (tm ? finalize_lanes_kernel<Real, 1, 3> : finalize_lanes_kernel<Real, 0, 3>)
+             : c->Gp == 32 ? (tm ? finalize_lanes_kernel<Real, 1, 4> : finalize_lanes_kernel<Real, 0, 4>)
+                           : (tm ? finalize_lanes_kernel<Real, 1, 0> : finalize_lanes_kernel<Real, 0, 0>);
+    fin<<<nb, 256, 0, st>>>(R, c->G, c->Gp, c->d_mat, (const Real *)c->d_nsf, (const Real *)c->d_inv_ta,
+                            (const typename Pair<Real>::T *)c->d_xsq, (Real *)c->d_tsum, (Real *)c->d_tcomp,
+                            (Real *)c->d_phi, c->d_fold, c->d_area, c->d_part, c->d_ticket, c->d_scal,
+                            c->eigen ? 1 : 0);
     CUDA_TRY(c, cudaGetLastError());
     return MOC_OK;
   }
@@ -839,7 +876,8 @@ template <typename Real> int launch_cmfd(moc_ctx *c, cudaStream_t st) {
                                    (double *)c->d_leak, (const Real *)c->d_cphi, (const Real *)c->d_TV,
                                    (const Real *)c->d_SV, (const Real *)c->d_FV, (const Real *)c->d_CHI,
                                    (Real *)c->d_din, (Real *)c->d_diag, (Real *)c->d_phic, (Real *)c->d_fis,
-                                   (Real *)c->d_ratio, c->d_scal, c->cm_outer, c->cm_inner, (Real)c->cm_omega));
+                                   (Real *)c->d_ratio, c->d_scal, c->cm_outer, c->cm_inner, (Real)c->cm_omega,
+                                   c->cm_tol));
   } else {
   auto solve = !c->cm_smem ? cmfd_solve_kernel<Real, false, int32_t>
                : c->cm_idx16 ? cmfd_solve_kernel<Real, true, uint16_t> : cmfd_solve_kernel<Real, true, int32_t>;
@@ -848,7 +886,7 @@ template <typename Real> int launch_cmfd(moc_ctx *c, cudaStream_t st) {
                                      (const Real *)c->d_CHI, (Real *)c->d_din, (Real *)c->d_diag,
                                      (Real *)c->d_phic, (Real *)c->d_phin, (Real *)c->d_phio,
                                      (Real *)c->d_src, (Real *)c->d_fis, (Real *)c->d_ratio, c->d_scal,
-                                     c->cm_outer, c->cm_inner, (Real)c->cm_omega);
+                                     c->cm_outer, c->cm_inner, (Real)c->cm_omega, c->cm_tol);
   }
   CUDA_TRY(c, cudaGetLastError());
   cmfd_prolong_kernel<Real><<<(R + 255) / 256, 256, 0, st>>>(R, G, c->Gp, N, c->d_cell, c->d_mat, (const Real *)c->d_nsf,
@@ -1305,6 +1343,7 @@ int moc_create(moc_ctx **out, int device, int precision, void *stream) {
     if (e == cudaSuccess) {
       int pm = 0;
       if (cudaDeviceGetAttribute(&pm, cudaDevAttrPageableMemoryAccess, device) == cudaSuccess) c->pageable_ok = pm != 0;
+      e = cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device);
     }
     if (e != cudaSuccess) {
       moc_destroy(c);
@@ -1877,6 +1916,23 @@ int moc_set_cmfd(moc_ctx *c, const int32_t *cell_in, int n_cells, int n_outer, i
   return MOC_OK;
 }
 
+int moc_set_cmfd_tolerance(moc_ctx *c, double tol) {
+  if (!c) return MOC_ERR_ARG;
+  if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(c, MOC_ERR_ARG, "set_cmfd_tolerance: tol must be finite and >= 0");
+  c->cm_tol = tol;
+  return MOC_OK;
+}
+
+int moc_get_cmfd_iterations(moc_ctx *c, int64_t *total) {
+  int rc = need_gpu(c);
+  if (rc) return rc;
+  if (!total) return fail(c, MOC_ERR_ARG, "get_cmfd_iterations: null output");
+  double s[S_COUNT];
+  if ((rc = read_scalars(c, s))) return rc;
+  *total = (int64_t)s[S_CMFD_IT];
+  return MOC_OK;
+}
+
 int moc_set_fixed_source(moc_ctx *c, const double *S) {
   int rc = need_ready(c);
   if (rc) return rc;
@@ -2142,7 +2198,7 @@ int moc_get_work(const moc_ctx *c, int64_t *n_segments, int64_t *updates, int *k
   if (updates) *updates = 2 * c->geo.n_segments() * (int64_t)c->geo.n_polar * (int64_t)std::max(c->G, 0) * planes;
   if (kernels)
     *kernels = c->dg_nz ? 4 + (c->dgcm_outer && c->eigen ? 5 : 0)
-                        : ((c->Gp == 8) ? 3 : 4) + (c->cmfd ? 5 : 0) + (c->aniso_L ? 2 : 0);
+                        : ((c->Gp == 8 || lane_rows(c)) ? 3 : 4) + (c->cmfd ? 5 : 0) + (c->aniso_L ? 2 : 0);
   return MOC_OK;
 }
 

@@ -103,6 +103,17 @@ __device__ __forceinline__ double block_sum_1024(double v, double *red32) {
   return s;
 }
 
+// Maximum of v over the block (1024 threads), the same in every thread.
+__device__ __forceinline__ double block_max_1024(double v, double *red32) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red32[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < 32; ++w) s = fmax(s, red32[w]);
+  __syncthreads();
+  return s;
+}
+
 // The whole coarse solve in one block of 1024 threads (fixed iteration counts, deterministic
 // order); writes the flux ratio per cell and group and the accelerated k. Scratch arrays are owned
 // by the context. SMEM: the per-group working set (source, 1/diagonal, iterate, coefficients,
@@ -117,7 +128,7 @@ __global__ void __launch_bounds__(1024, 1) cmfd_solve_kernel(CmfdTopo t, double 
                                                              Real *__restrict__ gx, Real *__restrict__ grd,
                                                              Real *__restrict__ gsrc, Real *__restrict__ fis,
                                                              Real *__restrict__ ratio, double *__restrict__ scal,
-                                                             int n_outer, int n_inner, Real omega) {
+                                                             int n_outer, int n_inner, Real omega, double tol) {
   __shared__ double red32[32];
   const int N = t.N, G = t.G, Gp = t.Gp, NE = t.n_entries;
   extern __shared__ unsigned char dyn[];
@@ -213,7 +224,22 @@ __global__ void __launch_bounds__(1024, 1) cmfd_solve_kernel(CmfdTopo t, double 
       fsum += (double)f;
     }
     const double F_new = block_sum_1024(fsum, red32);
+    const double k_prev = kc;
     if (F_new > 0.0 && F_old > 0.0) kc = kc * F_new / F_old;
+    if (tol > 0.0 && F_new > 0.0 && F_old > 0.0) {
+      // stop once k and the normalised coarse fission source have settled to tol
+      double dmax = 0.0;
+      for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        Real f = 0;
+        for (int g = 0; g < G; ++g) f += FV[(size_t)g * N + i] * phic[(size_t)g * N + i];
+        if (f > (Real)0) dmax = fmax(dmax, fabs(1.0 - ((double)fis[i] / F_old) * (F_new / (double)f)));
+      }
+      const double dm = block_max_1024(dmax, red32);
+      if (threadIdx.x == 0) scal[S_CMFD_IT] += 1.0;
+      if (fabs(kc - k_prev) <= tol * kc && dm <= tol) break;
+    } else if (threadIdx.x == 0) {
+      scal[S_CMFD_IT] += 1.0;
+    }
   }
   // 3. prolongation ratios and the accelerated k
   for (int x = threadIdx.x; x < N * G; x += blockDim.x) {
@@ -250,7 +276,7 @@ __global__ void __launch_bounds__(1024, 1) cmfd_solve_cluster_kernel(CmfdTopo t,
                                                                       Real *__restrict__ din, Real *__restrict__ diag,
                                                                       Real *__restrict__ phic, Real *__restrict__ fis,
                                                                       Real *__restrict__ ratio, double *__restrict__ scal,
-                                                                      int n_outer, int n_inner, Real omega) {
+                                                                      int n_outer, int n_inner, Real omega, double tol) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks(), b = (int)cluster.block_rank();
@@ -304,6 +330,15 @@ __global__ void __launch_bounds__(1024, 1) cmfd_solve_cluster_kernel(CmfdTopo t,
     cluster.sync();  // s_part is not overwritten before every CTA has read it
     return tot;
   };
+  auto cluster_max = [&](double v) {
+    const double p = block_max_1024(v, red32);
+    if (threadIdx.x == 0) s_part = p;
+    cluster.sync();
+    double m = 0.0;
+    for (int r = 0; r < C; ++r) m = fmax(m, *cluster.map_shared_rank(&s_part, r));
+    cluster.sync();
+    return m;
+  };
   double kc = scal[S_K];
   // 2. coarse power iteration
   for (int it = 0; it < n_outer; ++it) {
@@ -356,7 +391,24 @@ __global__ void __launch_bounds__(1024, 1) cmfd_solve_cluster_kernel(CmfdTopo t,
       fsum += (double)f;
     }
     const double F_new = cluster_sum(fsum);
+    const double k_prev = kc;
     if (F_new > 0.0 && F_old > 0.0) kc = kc * F_new / F_old;
+    if (tol > 0.0 && F_new > 0.0 && F_old > 0.0) {
+      // stop once k and the normalised coarse fission source have settled to tol (every CTA takes
+      // the same decision from the same cluster-wide values)
+      double dmax = 0.0;
+      for (int li = threadIdx.x; li < nc; li += blockDim.x) {
+        const int i = own[li];
+        Real f = 0;
+        for (int g = 0; g < G; ++g) f += FV[(size_t)g * N + i] * phic[(size_t)g * N + i];
+        if (f > (Real)0) dmax = fmax(dmax, fabs(1.0 - ((double)fis[i] / F_old) * (F_new / (double)f)));
+      }
+      const double dm = cluster_max(dmax);
+      if (b == 0 && threadIdx.x == 0) scal[S_CMFD_IT] += 1.0;
+      if (fabs(kc - k_prev) <= tol * kc && dm <= tol) break;
+    } else if (b == 0 && threadIdx.x == 0) {
+      scal[S_CMFD_IT] += 1.0;
+    }
   }
   // 3. prolongation ratios of the owned cells and the accelerated k
   for (int x = threadIdx.x; x < nc * G; x += blockDim.x) {

@@ -20,7 +20,8 @@ constexpr double kFourPi = 12.566370614359172953850;
 constexpr int kSegPad = 4;  // padding records at each end of the segment array
 
 // scalar slots in device memory (double)
-enum Scal { S_K = 0, S_SCALE = 1, S_RESID = 2, S_FISS = 3, S_KPREV = 4, S_STATUS = 5, S_NOUTER = 6, S_COUNT = 8 };
+enum Scal { S_K = 0, S_SCALE = 1, S_RESID = 2, S_FISS = 3, S_KPREV = 4, S_STATUS = 5, S_NOUTER = 6, S_CMFD_IT = 7,
+            S_COUNT = 8 };
 
 struct TrackRec {
   long long off;  // first segment
@@ -111,7 +112,62 @@ __global__ void source_kernel(int R, int G, int Gp, int M, const int32_t *__rest
   }
 }
 
-// ----------------------------------------------------------------------------- state transfer
+// Many groups (G > 8): eight consecutive threads per region, lane l owning the groups l, l + 8, ...
+// (GPL = Gp / 8 of them; 0: read from Gp at run time), 32 regions per block of 256. The block's
+// normalised flux rows are staged in shared memory (one barrier), the fission rate is an 8-lane
+// shuffle sum, and each group visits only the nonzero band srange[m][g] = [first, last] source
+// group of column g of the material's scattering matrix (a downscatter-only matrix has half its
+// entries zero).
+template <typename Real, int GPL>
+__global__ void __launch_bounds__(256) source_lanes_kernel(
+    int R, int G, int Gp, const int32_t *__restrict__ mat, const Real *__restrict__ sig_s,
+    const Real *__restrict__ nsf, const Real *__restrict__ chi, const int2 *__restrict__ srange,
+    const double *__restrict__ ext, Real *__restrict__ phi, typename Pair<Real>::T *__restrict__ xsq,
+    double *__restrict__ fold, const double *__restrict__ scal, int eigen) {
+  extern __shared__ unsigned char smem_raw[];
+  const int gpl = GPL > 0 ? GPL : Gp / 8;
+  const int rl = threadIdx.x >> 3, l = threadIdx.x & 7;
+  const int r = blockIdx.x * 32 + rl;
+  const bool live = r < R;
+  Real *row = reinterpret_cast<Real *>(smem_raw) + (size_t)rl * Gp;
+  const Real scale = eigen ? (Real)scal[S_SCALE] : (Real)1;
+  const Real inv_k = eigen ? (Real)(1.0 / scal[S_K]) : (Real)0;
+  const Real inv4pi = (Real)(1.0 / kFourPi);
+  const int m = live ? mat[r] : 0;
+  Real f = 0;
+#pragma unroll 5
+  for (int j = 0; j < gpl; ++j) {
+    const int g = l + 8 * j;
+    Real v = 0;
+    if (live && g < G) {
+      v = phi[(size_t)r * Gp + g] * scale;
+      phi[(size_t)r * Gp + g] = v;
+      f += nsf[m * G + g] * v;
+    }
+    row[g] = v;
+  }
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+  if (eigen && live && l == 0) fold[r] = (double)f;
+  __syncthreads();
+  if (!live) return;
+  for (int j = 0; j < gpl; ++j) {
+    const int g = l + 8 * j;
+    if (g >= G) break;
+    const int2 band = srange[m * G + g];
+    const Real *ss = sig_s + (size_t)m * G * G + g;
+    Real sc = 0;
+    for (int gp = band.x; gp <= band.y; ++gp) sc += ss[gp * G] * row[gp];
+    Real src = sc + chi[m * G + g] * inv_k * f;
+    if (ext) src += (Real)ext[(size_t)r * G + g];
+    const size_t a = (size_t)r * Gp + g;
+    typename Pair<Real>::T v = xsq[a];
+    v.y = src * inv4pi / v.x;
+    xsq[a] = v;
+  }
+}
+
+// ----------------------------------------------------------------------------- state transfer// ----------------------------------------------------------------------------- state transfer// ----------------------------------------------------------------------------- state transfer
 // A caller's state read or written in place when its host arrays are addressable from the device
 // (pinned or registered memory, or pageable memory on a system whose GPU reads it coherently):
 // one kernel converts, pads and reorders instead of a host loop, a staging copy and a second
@@ -411,119 +467,104 @@ __global__ void __launch_bounds__(128, CM ? 8 : 9) sweep_kernel(
   }
 }
 
-// FP32 sweep, one thread per (track, sense, chunk of GPT groups); the first NACT groups of the
-// chunk are computed (NACT < GPT only when G itself is smaller than the chunk, e.g. 7 of 8).
-// Region rows are read as GPT/2 128-bit loads of {Sigma_t, q/Sigma_t} pairs and the tallies are
-// added with GPT/4 float4 atomics, so the per-segment cost (segment record, addresses, loop,
-// atomics) is shared by P * NACT updates. The segment array carries kSegPad padding records at each
-// end, so the two-ahead prefetch never needs a bounds test.
+// FP32 sweep for many groups (G > 8): one thread per (track, sense, chunk of four groups), the
+// chunk fastest, so the ceil(G / 4) threads of a track end sit side by side in a warp and read one
+// region row together. All P polar angles stay in registers; region rows are read as two 128-bit
+// loads of {Sigma_t, q/Sigma_t} pairs and the tallies are added with one float4 atomic, so the
+// per-segment cost (segment record, addresses, loop, atomics) is shared by 4 P updates. The last
+// chunk of a G that is not a multiple of 4 carries padding groups (Sigma_t = 1, q = 0, no inflow),
+// whose updates are zero. The segment array carries kSegPad padding records at each end, so the
+// two-ahead prefetch never needs a bounds test. 1/sin(theta_p) arrive as kernel parameters
+// (uniform over the grid, no registers or loads).
 // TwoSum (Knuth): the exact rounding error (old + x) - fl(old + x) of each lane, where fl is the
 // round-to-nearest sum the atomic unit stored.
-__device__ __forceinline__ float4 two_sum_err(float4 o, float4 x) {
-  float4 e;
-  { const float sm = o.x + x.x, bb = sm - o.x; e.x = (o.x - (sm - bb)) + (x.x - bb); }
-  { const float sm = o.y + x.y, bb = sm - o.y; e.y = (o.y - (sm - bb)) + (x.y - bb); }
-  { const float sm = o.z + x.z, bb = sm - o.z; e.z = (o.z - (sm - bb)) + (x.z - bb); }
-  { const float sm = o.w + x.w, bb = sm - o.w; e.w = (o.w - (sm - bb)) + (x.w - bb); }
-  return e;
+__device__ __forceinline__ float two_sum_err(float o, float x) {
+  const float sm = o + x, bb = sm - o;
+  return (o - (sm - bb)) + (x - bb);
 }
 
-template <int GPT> struct Row {
-  float4 v[GPT / 2];
+__device__ __forceinline__ float4 two_sum_err(float4 o, float4 x) {
+  return make_float4(two_sum_err(o.x, x.x), two_sum_err(o.y, x.y), two_sum_err(o.z, x.z), two_sum_err(o.w, x.w));
+}
+
+template <int P> struct PolarInv {
+  float v[P];
 };
 
-template <int P, int GPT, int NACT, int TM>
-__global__ void __launch_bounds__(64) sweep_chunk_kernel(
+template <int P, int TM>
+__global__ void __launch_bounds__(64, 16) sweep_chunk_kernel(
     const TrackRec *__restrict__ trk, const SegRec<float> *__restrict__ seg, const int32_t *__restrict__ link,
-    const float *__restrict__ wgt, const float *__restrict__ inv_sin, const float2 *__restrict__ xsq,
-    float *__restrict__ tsum, float *__restrict__ tcomp, const float *__restrict__ psi_in,
-    float *__restrict__ psi_out, const double *__restrict__ scal, long long n_threads, int G, int Gp, int lanes) {
+    const float *__restrict__ wgt, const PolarInv<P> is, const float2 *__restrict__ xsq, float *__restrict__ tsum,
+    float *__restrict__ tcomp, const float *__restrict__ psi_in, float *__restrict__ psi_out,
+    const double *__restrict__ scal, long long n_threads, int G, int Gp, int lanes) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n_threads) return;
   const long long td = idx / lanes;
-  const int g0 = (int)(idx - td * lanes) * GPT;
+  const int g0 = (int)(idx - td * lanes) * 4;
   const TrackRec tr = trk[td >> 1];
   const int d = (int)(td & 1);
   const float scale = (float)scal[S_SCALE];
-  float psi[NACT][P], w[P], is[P];
+  float psi[4][P], w[P];
 #pragma unroll
   for (int p = 0; p < P; ++p) {
     w[p] = wgt[tr.dir * P + p];
-    is[p] = inv_sin[p];
 #pragma unroll
-    for (int k = 0; k < NACT; ++k)
-      psi[k][p] = (g0 + k < G) ? psi_in[(td * P + p) * G + g0 + k] * scale : 0.0f;
+    for (int k = 0; k < 4; ++k) psi[k][p] = (g0 + k < G) ? psi_in[(td * P + p) * G + g0 + k] * scale : 0.0f;
   }
   const int step = d ? -1 : 1;
   const SegRec<float> *sp = seg + (d ? tr.off + tr.n - 1 : tr.off);
   const float4 *rows = reinterpret_cast<const float4 *>(xsq + g0);
   const int rstride = Gp / 2;  // float4 per region row
   SegRec<float> s0 = sp[0], s1 = sp[step];
-  Row<GPT> r0, r1;
-#pragma unroll
-  for (int q = 0; q < GPT / 2; ++q) r0.v[q] = rows[(size_t)s0.r * rstride + q];
+  float4 r0a = rows[(size_t)s0.r * rstride], r0b = rows[(size_t)s0.r * rstride + 1];
   float4 *tsum4 = reinterpret_cast<float4 *>(tsum + g0);
   float4 *tcomp4 = reinterpret_cast<float4 *>(tcomp + g0);
   const int tstride = Gp / 4;
-  // compensated mode: the old values returned by this segment's atomics are turned into TwoSum
-  // errors one segment later, so the atomics' latency overlaps the next segment's arithmetic
-  float4 p_old[GPT / 4], p_x[GPT / 4];
+  // compensated mode: the old values returned by this segment's atomic become TwoSum errors one
+  // segment later, so the atomic's latency overlaps the next segment's arithmetic
+  float4 p_old = make_float4(0.f, 0.f, 0.f, 0.f), p_x = p_old;
   size_t p_a = (size_t)s0.r * tstride;
-#pragma unroll
-  for (int q = 0; q < GPT / 4; ++q) {
-    p_old[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-    p_x[q] = p_old[q];
-  }
   for (int n = 0; n < tr.n; ++n) {
     const SegRec<float> s2 = sp[2 * step];
+    const float4 r1a = rows[(size_t)s1.r * rstride], r1b = rows[(size_t)s1.r * rstride + 1];
+    const float sig[4] = {r0a.x, r0a.z, r0b.x, r0b.z}, qr[4] = {r0a.y, r0a.w, r0b.y, r0b.w};
+    float acc[4];
 #pragma unroll
-    for (int q = 0; q < GPT / 2; ++q) r1.v[q] = rows[(size_t)s1.r * rstride + q];
-    float acc[GPT];
-#pragma unroll
-    for (int k = 0; k < GPT; ++k) acc[k] = 0.0f;
-#pragma unroll
-    for (int k = 0; k < NACT; ++k) {
-      const float4 pr = r0.v[k / 2];
-      const float sig = (k & 1) ? pr.z : pr.x;
-      const float qr = (k & 1) ? pr.w : pr.y;
-      const float tau0 = sig * s0.l;
+    for (int k = 0; k < 4; ++k) {
+      const float tau0 = sig[k] * s0.l;
+      acc[k] = 0.0f;
 #pragma unroll
       for (int p = 0; p < P; ++p) {
-        const float F = one_minus_exp(tau0 * is[p]);
-        const float dl = (psi[k][p] - qr) * F;
+        const float F = one_minus_exp(tau0 * is.v[p]);
+        const float dl = (psi[k][p] - qr[k]) * F;
         psi[k][p] -= dl;
         acc[k] = fmaf(w[p], dl, acc[k]);
       }
     }
     const size_t a = (size_t)s0.r * tstride;
-#pragma unroll
-    for (int q = 0; q < GPT / 4; ++q) {
-      const float4 x = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
-      if (TM == 1) {
-        const float4 o = atomicAdd(tsum4 + a + q, x);
-        atomicAdd(tcomp4 + p_a + q, two_sum_err(p_old[q], p_x[q]));
-        p_old[q] = o;
-        p_x[q] = x;
-      } else {
-        atomicAdd(tsum4 + a + q, x);
-      }
+    const float4 x = make_float4(acc[0], acc[1], acc[2], acc[3]);
+    if (TM == 1) {
+      const float4 o = atomicAdd(tsum4 + a, x);
+      atomicAdd(tcomp4 + p_a, two_sum_err(p_old, p_x));
+      p_old = o;
+      p_x = x;
+    } else {
+      atomicAdd(tsum4 + a, x);
     }
     p_a = a;
     s0 = s1;
     s1 = s2;
-    r0 = r1;
+    r0a = r1a;
+    r0b = r1b;
     sp += step;
   }
-  if (TM == 1) {
-#pragma unroll
-    for (int q = 0; q < GPT / 4; ++q) atomicAdd(tcomp4 + p_a + q, two_sum_err(p_old[q], p_x[q]));
-  }
+  if (TM == 1) atomicAdd(tcomp4 + p_a, two_sum_err(p_old, p_x));
   const int e = link[td];
   if (e >= 0) {
 #pragma unroll
     for (int p = 0; p < P; ++p)
 #pragma unroll
-      for (int k = 0; k < NACT; ++k)
+      for (int k = 0; k < 4; ++k)
         if (g0 + k < G) psi_out[((long long)e * P + p) * G + g0 + k] = psi[k][p];
   }
 }
@@ -642,6 +683,88 @@ __global__ void __launch_bounds__(256) finalize8_kernel(
     for (int o = 4; o > 0; o >>= 1) res = fmax(res, __shfl_xor_sync(0xffffffffu, res, o));
   }
   if (g == 0) {
+    const int q = threadIdx.x >> 3;
+    const bool fis = live && eigen && f > (Real)0;
+    const Real rho = fis ? (Real)fold[r] / f : (Real)0;
+    l_sum[q] = live ? area[r] * (double)f : 0.0;
+    l_min[q] = fis ? rho : (Real)INFINITY;
+    l_max[q] = fis ? rho : (Real)-INFINITY;
+    l_res[q] = res;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    Real mn = (Real)INFINITY, mx = (Real)-INFINITY, rs = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 3); ++q) {
+      a += l_sum[q];
+      mn = fmin(mn, l_min[q]);
+      mx = fmax(mx, l_max[q]);
+      rs = fmax(rs, l_res[q]);
+    }
+    part[4 * blockIdx.x + 0] = a;
+    part[4 * blockIdx.x + 1] = (double)mn;
+    part[4 * blockIdx.x + 2] = (double)mx;
+    part[4 * blockIdx.x + 3] = (double)rs;
+    __threadfence();
+    last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    reduce_partials(gridDim.x, part, scal, eigen);
+    if (threadIdx.x == 0) *ticket = 0u;
+  }
+}
+
+// Many groups (G > 8): finalize8_kernel with GPL = Gp / 8 groups per lane (lane l owns l, l + 8,
+// ...; 0: read from Gp at run time): eight threads per region, 32 regions per block, the region's
+// fission rate an 8-lane shuffle sum, the last block to finish reducing all partials.
+template <typename Real, int TM, int GPL>
+__global__ void __launch_bounds__(256) finalize_lanes_kernel(
+    int R, int G, int Gp, const int32_t *__restrict__ mat, const Real *__restrict__ nsf,
+    const Real *__restrict__ inv_ta, const typename Pair<Real>::T *__restrict__ xsq, Real *__restrict__ tsum,
+    Real *__restrict__ tcomp, Real *__restrict__ phi, const double *__restrict__ fold,
+    const double *__restrict__ area, double *__restrict__ part, unsigned *__restrict__ ticket,
+    double *__restrict__ scal, int eigen) {
+  __shared__ double l_sum[32];
+  __shared__ Real l_min[32], l_max[32], l_res[32];
+  __shared__ bool last;
+  const int gpl = GPL > 0 ? GPL : Gp / 8;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = tid >> 3, l = tid & 7;
+  const bool live = r < R;
+  Real f = 0, res = 0;
+  if (live) {
+    const int m = mat[r];
+#pragma unroll 5
+    for (int j = 0; j < gpl; ++j) {
+      const int g = l + 8 * j;
+      const size_t a = (size_t)r * Gp + g;
+      const typename Pair<Real>::T v = xsq[a];
+      Real t = tsum[a];
+      tsum[a] = (Real)0;
+      if (TM == 1) {
+        t += tcomp[a];
+        tcomp[a] = (Real)0;
+      }
+      if (g < G) {
+        const Real ph = fma(t, inv_ta[a], (Real)kFourPi * v.y);
+        if (!eigen) {
+          const Real old = phi[a];
+          if (ph > (Real)0) res = fmax(res, fabs(ph - old) / ph);
+        }
+        phi[a] = ph;
+        f += nsf[m * G + g] * ph;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+  if (!eigen) {
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) res = fmax(res, __shfl_xor_sync(0xffffffffu, res, o));
+  }
+  if (l == 0) {
     const int q = threadIdx.x >> 3;
     const bool fis = live && eigen && f > (Real)0;
     const Real rho = fis ? (Real)fold[r] / f : (Real)0;

@@ -1,5 +1,7 @@
 // Learned warm start: a 4-layer MLP (bf16 weights, FP32 accumulation, FP32 master weights, Adam)
-// in hand-written CUDA kernels. See include/moc_mlp.h for the contract.
+// in hand-written CUDA kernels. The GEMMs of the forward and backward passes run on the tensor
+// cores (tcgen05, moc_tc.cuh) with bias, SiLU and its derivative fused into their epilogues. See
+// include/moc_mlp.h for the contract.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -11,77 +13,11 @@
 
 #include "moc_gb300.h"
 #include "moc_mlp.h"
+#include "moc_tc.cuh"
 
 namespace {
 
 constexpr int kLayers = 4;
-
-__device__ __forceinline__ float to_f(float v) { return v; }
-__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
-
-// C[M][N] (=, or += atomically) sum over k of A(m,k) B(k,n); A(m,k) = TA ? A[k lda + m] :
-// A[m lda + k]; B(k,n) = TB ? B[n ldb + k] : B[k ldb + n]. 64x64 tiles, 16-deep k slices, 256
-// threads each owning a 4x4 block of C; blockIdx.z splits K into chunks of k_per_block.
-template <bool TA, bool TB, typename BT>
-__global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const float *__restrict__ A, int lda,
-                                                   const BT *__restrict__ B, int ldb, float *__restrict__ C, int ldc,
-                                                   int k_per_block, int atomic_out) {
-  __shared__ float As[16][64 + 4];
-  __shared__ float Bs[16][64 + 4];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-  const int kbeg = blockIdx.z * k_per_block;
-  const int kend = min(K, kbeg + k_per_block);
-  float acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-  for (int k0 = kbeg; k0 < kend; k0 += 16) {
-    for (int e = threadIdx.x; e < 1024; e += 256) {
-      int mm, kk;
-      if (TA) { mm = e & 63; kk = e >> 6; } else { kk = e & 15; mm = e >> 4; }
-      const int gm = m0 + mm, gk = k0 + kk;
-      float v = 0.f;
-      if (gm < M && gk < kend) v = TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
-      As[kk][mm] = v;
-    }
-    for (int e = threadIdx.x; e < 1024; e += 256) {
-      int nn, kk;
-      if (TB) { kk = e & 15; nn = e >> 4; } else { nn = e & 63; kk = e >> 6; }
-      const int gn = n0 + nn, gk = k0 + kk;
-      float v = 0.f;
-      if (gn < N && gk < kend) v = to_f(TB ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn]);
-      Bs[kk][nn] = v;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < 16; ++kk) {
-      float a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int gm = m0 + ty * 4 + i, gn = n0 + tx * 4 + j;
-      if (gm < M && gn < N) {
-        if (atomic_out) atomicAdd(&C[(size_t)gm * ldc + gn], acc[i][j]);
-        else C[(size_t)gm * ldc + gn] = acc[i][j];
-      }
-    }
-}
-
-__device__ __forceinline__ float sigmoid(float x) { return 1.0f / (1.0f + expf(-x)); }
 
 __global__ void normalize_kernel(int64_t n, int d, const float *__restrict__ x, const float *__restrict__ mean,
                                  const float *__restrict__ sd, float *__restrict__ out) {
@@ -89,24 +25,6 @@ __global__ void normalize_kernel(int64_t n, int d, const float *__restrict__ x, 
   if (i >= n * d) return;
   const int j = (int)(i % d);
   out[i] = (x[i] - mean[j]) / sd[j];
-}
-
-// Z += b (per column); if act, A = SiLU(Z)
-__global__ void bias_act_kernel(int64_t n, int d, float *__restrict__ Z, const float *__restrict__ b,
-                                float *__restrict__ Aout, int act) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n * d) return;
-  const float z = Z[i] + b[i % d];
-  Z[i] = z;
-  if (act) Aout[i] = z * sigmoid(z);
-}
-
-__global__ void denorm_kernel(int64_t n, int d, const float *__restrict__ z, const float *__restrict__ mean,
-                              const float *__restrict__ sd, float *__restrict__ y) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n * d) return;
-  const int j = (int)(i % d);
-  y[i] = z[i] * sd[j] + mean[j];
 }
 
 // dZ = 2 (z - (y - mean)/sd) / (n d); loss += sum (z - y_norm)^2 / (n d)
@@ -130,15 +48,6 @@ __global__ void mse_grad_kernel(int64_t n, int d, const float *__restrict__ z, c
     __syncthreads();
   }
   if (threadIdx.x == 0) atomicAdd(loss, red[0]);
-}
-
-// dZ = dA * SiLU'(Z)
-__global__ void silu_back_kernel(int64_t n, const float *__restrict__ dA, const float *__restrict__ Z,
-                                 float *__restrict__ dZ) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const float s = sigmoid(Z[i]);
-  dZ[i] = dA[i] * s * (1.0f + Z[i] * (1.0f - s));
 }
 
 // gb[j] += sum over a chunk of rows of dZ[row][j]
@@ -186,7 +95,8 @@ struct moc_mlp {
   float *in_mean = nullptr, *in_std = nullptr, *out_mean = nullptr, *out_std = nullptr;
   int64_t cap = 0;
   float *Z[kLayers] = {}, *A[kLayers] = {};
-  float *dA = nullptr, *dZ = nullptr, *dZ2 = nullptr, *loss = nullptr;
+  float *dZ = nullptr, *dZ2 = nullptr, *loss = nullptr;
+  int *d_err = nullptr;  // set by a tensor-core GEMM whose wait ran out
   int64_t step = 0;
 };
 
@@ -207,12 +117,55 @@ int mfail(moc_mlp *n, int code, const std::string &m) {
 
 int64_t wsize(const moc_mlp *n, int l) { return (int64_t)n->dims[l + 1] * n->dims[l]; }
 
-template <bool TA, bool TB, typename BT>
-void gemm(int M, int N, int K, const float *A, int lda, const BT *B, int ldb, float *C, int ldc, cudaStream_t st,
-          int k_per_block = 0, bool atomic_out = false) {
-  if (k_per_block <= 0) k_per_block = K;
-  dim3 grid((N + 63) / 64, (M + 63) / 64, (K + k_per_block - 1) / k_per_block);
-  gemm_kernel<TA, TB, BT><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, k_per_block, atomic_out ? 1 : 0);
+// D = A B^T on the tensor cores (mlp_tc::tc_gemm_kernel): rows of D in tiles of 128, columns in
+// tiles of 256, k split over blockIdx.y in chunks of k_per_cta (the atomic epilogue only)
+template <int ASRC, int BSRC, int EPI> int tc_gemm(moc_mlp *n, mlp_tc::TcArgs g, cudaStream_t st) {
+  auto kern = mlp_tc::tc_gemm_kernel<ASRC, BSRC, EPI>;
+  // the kernel's shared-memory limit (a per-device function attribute; setting it allocates nothing)
+  MLP_TRY(n, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_tc::kSmemBytes));
+  if (g.k_per_cta <= 0) g.k_per_cta = g.K;
+  g.err = n->d_err;
+  const dim3 grid((unsigned)((g.M + mlp_tc::kTileM - 1) / mlp_tc::kTileM),
+                  (unsigned)((g.K + g.k_per_cta - 1) / g.k_per_cta),
+                  (unsigned)((g.N + mlp_tc::kMaxN - 1) / mlp_tc::kMaxN));
+  kern<<<grid, mlp_tc::kThreads, mlp_tc::kSmemBytes, st>>>(g);
+  MLP_TRY(n, cudaGetLastError());
+  return MOC_OK;
+}
+
+mlp_tc::TcArgs targs(int M, int N, int K, const void *a, int lda, const void *b, int ldb, float *out, int ldo) {
+  mlp_tc::TcArgs g{};
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.a = a;
+  g.lda = lda;
+  g.b = b;
+  g.ldb = ldb;
+  g.out = out;
+  g.ldo = ldo;
+  return g;
+}
+
+// the four layers' GEMMs with fused epilogues: A_in [rows][dims[0]] (standardised) -> Z[l], A[l+1]
+// (SiLU) -> ... -> Z[3]; y (may be null) gets the de-standardised output
+int forward_layers(moc_mlp *n, float *const *Aw, float *const *Zw, int64_t rows, float *y, cudaStream_t st) {
+  int rc = MOC_OK;
+  for (int l = 0; l < kLayers && !rc; ++l) {
+    const int din = n->dims[l], dout = n->dims[l + 1];
+    mlp_tc::TcArgs g = targs((int)rows, dout, din, Aw[l], din, n->Wh[l], din, Zw[l], dout);
+    g.bias = n->b[l];
+    if (l < kLayers - 1) {
+      g.out2 = Aw[l + 1];
+      rc = tc_gemm<mlp_tc::SRC_F32, mlp_tc::SRC_BF16, mlp_tc::EPI_ACT>(n, g, st);
+    } else {
+      g.out2 = y;
+      g.out_mean = n->out_mean;
+      g.out_sd = n->out_std;
+      rc = tc_gemm<mlp_tc::SRC_F32, mlp_tc::SRC_BF16, mlp_tc::EPI_LAST>(n, g, st);
+    }
+  }
+  return rc;
 }
 
 int ensure_workspace(moc_mlp *n, int64_t rows) {
@@ -222,37 +175,29 @@ int ensure_workspace(moc_mlp *n, int64_t rows) {
     cudaFree(n->A[l]);
     n->Z[l] = n->A[l] = nullptr;
   }
-  cudaFree(n->dA);
   cudaFree(n->dZ);
   cudaFree(n->dZ2);
-  n->dA = n->dZ = n->dZ2 = nullptr;
+  n->dZ = n->dZ2 = nullptr;
   int wmax = 0;
   for (int l = 0; l <= kLayers; ++l) wmax = std::max(wmax, n->dims[l]);
   for (int l = 0; l < kLayers; ++l) {
     MLP_TRY(n, cudaMalloc(&n->Z[l], (size_t)rows * n->dims[l + 1] * sizeof(float)));
     MLP_TRY(n, cudaMalloc(&n->A[l], (size_t)rows * n->dims[l] * sizeof(float)));
   }
-  MLP_TRY(n, cudaMalloc(&n->dA, (size_t)rows * wmax * sizeof(float)));
   MLP_TRY(n, cudaMalloc(&n->dZ, (size_t)rows * wmax * sizeof(float)));
   MLP_TRY(n, cudaMalloc(&n->dZ2, (size_t)rows * wmax * sizeof(float)));
   n->cap = rows;
   return MOC_OK;
 }
 
-// forward pass into Z[3] (standardised outputs); keeps Z/A for the backward pass
-int forward(moc_mlp *n, const float *x, int64_t rows, cudaStream_t st) {
+// forward pass into Z[3] (standardised outputs); keeps Z/A for the backward pass; y (may be null)
+// gets the de-standardised outputs
+int forward(moc_mlp *n, const float *x, int64_t rows, float *y, cudaStream_t st) {
   int rc = ensure_workspace(n, rows);
   if (rc) return rc;
   normalize_kernel<<<grid1(rows * n->dims[0]), 256, 0, st>>>(rows, n->dims[0], x, n->in_mean, n->in_std, n->A[0]);
-  for (int l = 0; l < kLayers; ++l) {
-    const int din = n->dims[l], dout = n->dims[l + 1];
-    gemm<false, true, __nv_bfloat16>((int)rows, dout, din, n->A[l], din, n->Wh[l], din, n->Z[l], dout, st);
-    const bool act = l < kLayers - 1;
-    bias_act_kernel<<<grid1(rows * dout), 256, 0, st>>>(rows, dout, n->Z[l], n->b[l], act ? n->A[l + 1] : nullptr,
-                                                        act ? 1 : 0);
-  }
   MLP_TRY(n, cudaGetLastError());
-  return MOC_OK;
+  return forward_layers(n, n->A, n->Z, rows, y, st);
 }
 
 // backward pass of the MSE loss; fills gW, gb and the loss scalar
@@ -266,18 +211,31 @@ int backward(moc_mlp *n, const float *y, int64_t rows, cudaStream_t st) {
     const int din = n->dims[l], dout = n->dims[l + 1];
     MLP_TRY(n, cudaMemsetAsync(n->gW[l], 0, wsize(n, l) * sizeof(float), st));
     MLP_TRY(n, cudaMemsetAsync(n->gb[l], 0, dout * sizeof(float), st));
-    // gW[out][in] = sum_rows dZ[row][out] A[row][in], split over chunks of 2048 rows
-    gemm<true, false, float>(dout, din, (int)rows, dZ, dout, n->A[l], din, n->gW[l], din, st, 2048, true);
+    // gW[out][in] = sum_rows dZ[row][out] A[row][in], the rows split over CTAs in chunks of 2048
+    mlp_tc::TcArgs g = targs(dout, din, (int)rows, dZ, dout, n->A[l], din, n->gW[l], din);
+    g.k_per_cta = 2048;
+    int rc = tc_gemm<mlp_tc::SRC_F32_T, mlp_tc::SRC_F32_T, mlp_tc::EPI_ATOMIC>(n, g, st);
+    if (rc) return rc;
     dim3 g2((dout + 255) / 256, (unsigned)((rows + 2047) / 2048));
     colsum_kernel<<<g2, 256, 0, st>>>(rows, dout, dZ, n->gb[l], 2048);
     if (l > 0) {
-      // dA[row][in] = sum_out dZ[row][out] W[out][in]; dZ_prev = dA * SiLU'(Z_prev)
-      gemm<false, false, __nv_bfloat16>((int)rows, din, dout, dZ, dout, n->Wh[l], din, n->dA, din, st);
-      silu_back_kernel<<<grid1(rows * din), 256, 0, st>>>(rows * din, n->dA, n->Z[l - 1], dZn);
+      // dZ_prev[row][in] = (sum_out dZ[row][out] W[out][in]) SiLU'(Z_prev[row][in])
+      mlp_tc::TcArgs h = targs((int)rows, din, dout, dZ, dout, n->Wh[l], din, dZn, din);
+      h.aux = n->Z[l - 1];
+      rc = tc_gemm<mlp_tc::SRC_F32, mlp_tc::SRC_BF16_T, mlp_tc::EPI_DACT>(n, h, st);
+      if (rc) return rc;
       std::swap(dZ, dZn);
     }
   }
   MLP_TRY(n, cudaGetLastError());
+  return MOC_OK;
+}
+
+// a tensor-core GEMM whose wait ran out (read at the calls that synchronise anyway)
+int check_err(moc_mlp *n) {
+  int e = 0;
+  MLP_TRY(n, cudaMemcpy(&e, n->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) return mfail(n, MOC_ERR_CUDA, "tensor-core GEMM: a wait for the MMA ran out");
   return MOC_OK;
 }
 
@@ -316,7 +274,8 @@ int moc_mlp_create(moc_mlp **out, int device, int n_in, int width, int n_out, ui
   }
   ok = ok && cudaMalloc(&n->in_mean, n_in * 4) == cudaSuccess && cudaMalloc(&n->in_std, n_in * 4) == cudaSuccess &&
        cudaMalloc(&n->out_mean, n_out * 4) == cudaSuccess && cudaMalloc(&n->out_std, n_out * 4) == cudaSuccess &&
-       cudaMalloc(&n->loss, 4) == cudaSuccess;
+       cudaMalloc(&n->loss, 4) == cudaSuccess && cudaMalloc(&n->d_err, sizeof(int)) == cudaSuccess &&
+       cudaMemset(n->d_err, 0, sizeof(int)) == cudaSuccess;
   if (!ok) {
     moc_mlp_destroy(n);
     return MOC_ERR_OOM;
@@ -366,10 +325,10 @@ void moc_mlp_destroy(moc_mlp *n) {
   cudaFree(n->in_std);
   cudaFree(n->out_mean);
   cudaFree(n->out_std);
-  cudaFree(n->dA);
   cudaFree(n->dZ);
   cudaFree(n->dZ2);
   cudaFree(n->loss);
+  cudaFree(n->d_err);
   delete n;
 }
 
@@ -444,12 +403,7 @@ int moc_mlp_forward(moc_mlp *n, const float *x, float *y, int64_t rows, void *st
   if (rows == 0) return MOC_OK;
   cudaSetDevice(n->device);
   cudaStream_t st = (cudaStream_t)stream;
-  int rc = forward(n, x, rows, st);
-  if (rc) return rc;
-  const int dlast = n->dims[kLayers];
-  denorm_kernel<<<grid1(rows * dlast), 256, 0, st>>>(rows, dlast, n->Z[kLayers - 1], n->out_mean, n->out_std, y);
-  MLP_TRY(n, cudaGetLastError());
-  return MOC_OK;
+  return forward(n, x, rows, y, st);
 }
 
 int moc_mlp_train_step(moc_mlp *n, const float *x, const float *y, int64_t rows, float lr, float *loss_out,
@@ -457,7 +411,7 @@ int moc_mlp_train_step(moc_mlp *n, const float *x, const float *y, int64_t rows,
   if (!n || rows < 1 || !x || !y || !(lr > 0.f)) return MOC_ERR_ARG;
   cudaSetDevice(n->device);
   cudaStream_t st = (cudaStream_t)stream;
-  int rc = forward(n, x, rows, st);
+  int rc = forward(n, x, rows, nullptr, st);
   if (!rc) rc = backward(n, y, rows, st);
   if (rc) return rc;
   n->step += 1;
@@ -473,6 +427,7 @@ int moc_mlp_train_step(moc_mlp *n, const float *x, const float *y, int64_t rows,
   if (loss_out) {
     MLP_TRY(n, cudaMemcpyAsync(loss_out, n->loss, 4, cudaMemcpyDeviceToHost, st));
     MLP_TRY(n, cudaStreamSynchronize(st));
+    return check_err(n);
   }
   return MOC_OK;
 }
@@ -482,10 +437,11 @@ int moc_mlp_gradients(moc_mlp *n, const float *x, const float *y, int64_t rows, 
   if (!n || rows < 1 || !x || !y || !grad) return MOC_ERR_ARG;
   cudaSetDevice(n->device);
   cudaStream_t st = (cudaStream_t)stream;
-  int rc = forward(n, x, rows, st);
+  int rc = forward(n, x, rows, nullptr, st);
   if (!rc) rc = backward(n, y, rows, st);
   if (rc) return rc;
   MLP_TRY(n, cudaStreamSynchronize(st));
+  if ((rc = check_err(n))) return rc;
   size_t o = 0;
   for (int l = 0; l < kLayers; ++l) {
     MLP_TRY(n, cudaMemcpy(grad + o, n->gW[l], wsize(n, l) * 4, cudaMemcpyDeviceToHost));
@@ -536,15 +492,6 @@ extern "C" int moc_mlp_forward_noalloc(moc_mlp *n, const float *x, float *y, int
   }
   cudaStream_t st = (cudaStream_t)stream;
   normalize_kernel<<<grid1(rows * n->dims[0]), 256, 0, st>>>(rows, n->dims[0], x, n->in_mean, n->in_std, Aw[0]);
-  for (int l = 0; l < kLayers; ++l) {
-    const int din = n->dims[l], dout = n->dims[l + 1];
-    gemm<false, true, __nv_bfloat16>((int)rows, dout, din, Aw[l], din, n->Wh[l], din, Zw[l], dout, st);
-    const bool act = l < kLayers - 1;
-    bias_act_kernel<<<grid1(rows * dout), 256, 0, st>>>(rows, dout, Zw[l], n->b[l], act ? Aw[l + 1] : nullptr,
-                                                        act ? 1 : 0);
-  }
-  const int dlast = n->dims[kLayers];
-  denorm_kernel<<<grid1(rows * dlast), 256, 0, st>>>(rows, dlast, Zw[kLayers - 1], n->out_mean, n->out_std, y);
   MLP_TRY(n, cudaGetLastError());
-  return MOC_OK;
+  return forward_layers(n, Aw, Zw, rows, y, st);
 }

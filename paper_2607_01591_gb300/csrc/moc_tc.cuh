@@ -1,0 +1,255 @@
+// Tensor-core GEMM of the warm-start network on sm_103a: tcgen05.mma with the accumulator in
+// tensor memory (TMEM), operands staged by the CTA's threads into shared memory in the canonical
+// K-major layout (no swizzle), one elected thread issuing the MMAs, completion signalled on an
+// mbarrier by tcgen05.commit, and the epilogue read back with tcgen05.ld.
+//
+// D[m][n] = sum_k A(m, k) B(n, k) over a 128-row tile of A and up to 256 columns. Operands in FP32
+// are split into bf16 pairs x = hi + lo (hi = bf16(x), lo = bf16(x - hi)), so the products keep
+// about 16 significant bits of every FP32 operand; bf16 operands (the network's weights) are used
+// as they are. Accumulation is FP32 in TMEM:
+//   A FP32, B bf16:  D = A_hi B + A_lo B                 (2 MMAs per k step)
+//   A FP32, B FP32:  D = A_hi B_hi + A_lo B_hi + A_hi B_lo (3 MMAs per k step)
+//
+// Every wait is bounded (about one second of the global timer); a wait that runs out sets *err,
+// skips the epilogue, and the CTA still frees its TMEM before it returns.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace mlp_tc {
+
+constexpr int kTileM = 128;   // rows of D per CTA: one TMEM lane per row
+constexpr int kMaxN = 256;    // columns of D (FP32 TMEM columns)
+constexpr int kKC = 64;       // k elements staged per round
+constexpr int kThreads = 256;
+
+// operand sources
+enum { SRC_F32 = 0,      // FP32, element (r, k) at p[r * ld + k]   (k contiguous)
+       SRC_F32_T = 1,    // FP32, element (r, k) at p[k * ld + r]   (r contiguous)
+       SRC_BF16 = 2,     // bf16, element (r, k) at p[r * ld + k]
+       SRC_BF16_T = 3 }; // bf16, element (r, k) at p[k * ld + r]
+
+// epilogues
+enum { EPI_ACT = 0,      // Z = D + bias; A_next = SiLU(Z)
+       EPI_LAST = 1,     // Z = D + bias; y = Z * out_sd + out_mean (when y != null)
+       EPI_DACT = 2,     // dZ = D * SiLU'(Zprev)
+       EPI_ATOMIC = 3 }; // C += D (atomically: split-k partial)
+
+struct TcArgs {
+  int M, N, K;            // D is M x N, reduction over K
+  const void *a;          // A source
+  int lda;
+  const void *b;          // B source
+  int ldb;
+  int k_per_cta;          // k range of one CTA (blockIdx.y splits K; EPI_ATOMIC only)
+  float *out;             // Z, dZ or C  [M][ldo]
+  int ldo;
+  float *out2;            // A_next (EPI_ACT) or y (EPI_LAST)
+  const float *bias;      // [N]
+  const float *aux;       // Zprev [M][ldo] (EPI_DACT)
+  const float *out_mean, *out_sd;  // EPI_LAST de-standardisation
+  int *err;               // set to 1 when a wait runs out
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// byte offset of element (r, k) of a tile with kc columns in the canonical K-major layout without
+// swizzle: 8 x 8 core matrices of 128 contiguous bytes (8 rows of 16 bytes), core matrices
+// adjacent in k 128 bytes apart (the leading byte offset), 8-row groups kc * 16 bytes apart (the
+// stride byte offset)
+__device__ __forceinline__ uint32_t kmaj_off(int r, int k, int kc) {
+  return (uint32_t)(((r >> 3) * (kc >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// shared-memory matrix descriptor: start address, leading and stride byte offsets (16-byte
+// units), descriptor version 1 (bits 46-47), no swizzle (layout 0 in bits 61-63)
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B bf16 (bits 7-9, 10-12 = 1),
+// both K-major (bits 15, 16 = 0), N >> 3 in bits 17-22, M >> 4 in bits 24-28
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// wait for the mbarrier phase with the given parity; false after about one second
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (global_ns() - t0 > 1000000000ull) return false;
+  }
+}
+
+__device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
+
+__device__ __forceinline__ float silu_grad(float z) {
+  const float s = 1.0f / (1.0f + __expf(-z));
+  return s * (1.0f + z * (1.0f - s));
+}
+
+template <int SRC> __device__ __forceinline__ float fetch(const void *p, int ld, int r, int k) {
+  if (SRC == SRC_F32) return static_cast<const float *>(p)[(size_t)r * ld + k];
+  if (SRC == SRC_F32_T) return static_cast<const float *>(p)[(size_t)k * ld + r];
+  if (SRC == SRC_BF16) return __bfloat162float(static_cast<const __nv_bfloat16 *>(p)[(size_t)r * ld + k]);
+  return __bfloat162float(static_cast<const __nv_bfloat16 *>(p)[(size_t)k * ld + r]);
+}
+
+// stage rows [r0, r0 + R) x k [k0, k0 + kKC) of a source into hi (and lo for FP32 sources) tiles;
+// out-of-range elements are zero. The loop order follows the source's contiguous index.
+template <int SRC>
+__device__ __forceinline__ void stage(unsigned char *hi, unsigned char *lo, const void *p, int ld, int r0, int R,
+                                      int rmax, int k0, int kmax) {
+  constexpr bool T = (SRC == SRC_F32_T || SRC == SRC_BF16_T);
+  constexpr bool F32 = (SRC == SRC_F32 || SRC == SRC_F32_T);
+  for (int e = threadIdx.x; e < R * kKC; e += kThreads) {
+    const int r = T ? (e % R) : (e / kKC);
+    const int k = T ? (e / R) : (e % kKC);
+    const int gr = r0 + r, gk = k0 + k;
+    const float v = (gr < rmax && gk < kmax) ? fetch<SRC>(p, ld, gr, gk) : 0.0f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const uint32_t o = kmaj_off(r, k, kKC);
+    *reinterpret_cast<__nv_bfloat16 *>(hi + o) = h;
+    if (F32) *reinterpret_cast<__nv_bfloat16 *>(lo + o) = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
+// One CTA: D tile rows [m0, m0 + 128) (blockIdx.x), columns [n0, n0 + 256) (blockIdx.z), k range
+// [kb, ke) (blockIdx.y).
+// Shared memory: A hi/lo (2 x 16 KB), B hi/lo (2 x 32 KB), mbarrier, TMEM address.
+template <int ASRC, int BSRC, int EPI>
+__global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs g) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  unsigned char *a_hi = sm, *a_lo = sm + kTileM * kKC * 2;
+  unsigned char *b_hi = a_lo + kTileM * kKC * 2, *b_lo = b_hi + kMaxN * kKC * 2;
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int failed;
+  constexpr bool A32 = (ASRC == SRC_F32 || ASRC == SRC_F32_T);
+  constexpr bool B32 = (BSRC == SRC_F32 || BSRC == SRC_F32_T);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kTileM, n0 = blockIdx.z * kMaxN;
+  const int kb = blockIdx.y * g.k_per_cta, ke = min(g.K, kb + g.k_per_cta);
+  const int Nt = min(kMaxN, g.N - n0);                // columns of this tile
+  const int Np = (Nt + 15) & ~15;                     // MMA N: a multiple of 16 (M = 128)
+  const uint32_t ncols = Np <= 32 ? 32 : Np <= 64 ? 64 : Np <= 128 ? 128 : 256;
+  if (threadIdx.x == 0) {
+    failed = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  const uint32_t idesc = idesc_bf16(kTileM, Np);
+  uint32_t parity = 0;
+  int first = 1;
+  for (int k0 = kb; k0 < ke; k0 += kKC) {
+    stage<ASRC>(a_hi, a_lo, g.a, g.lda, m0, kTileM, g.M, k0, ke);
+    stage<BSRC>(b_hi, b_lo, g.b, g.ldb, n0, Np, g.N, k0, ke);
+    // make the threads' shared-memory writes visible to the tensor core's (async) proxy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t sa = smem_u32(a_hi), sal = smem_u32(a_lo), sb = smem_u32(b_hi), sbl = smem_u32(b_lo);
+      const uint32_t lbo = 128, sbo = kKC * 16;
+#pragma unroll
+      for (int kk = 0; kk < kKC / 16; ++kk) {
+        const uint32_t step = kk * 2 * 128;  // 16 k = two core matrices
+        const uint64_t dah = smem_desc(sa + step, lbo, sbo), dbh = smem_desc(sb + step, lbo, sbo);
+        mma_bf16(tmem, dah, dbh, idesc, first ? 0u : 1u);
+        first = 0;
+        if (A32) mma_bf16(tmem, smem_desc(sal + step, lbo, sbo), dbh, idesc, 1u);
+        if (B32) mma_bf16(tmem, dah, smem_desc(sbl + step, lbo, sbo), idesc, 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&bar))
+                   : "memory");
+    }
+    first = 0;
+    // the MMAs read the staged tiles: wait for them before the next round overwrites them
+    if (!mbar_wait(smem_u32(&bar), parity)) failed = 1;
+    parity ^= 1u;
+    __syncthreads();
+    if (failed) break;
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (!failed && kb < ke) {
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows of D), column half w / 4
+    const int q = warp & 3, half = warp >> 2;
+    const int row = m0 + 32 * q + lane;
+    const int c_beg = half * (Np / 2), c_end = c_beg + Np / 2;
+    for (int c0 = c_beg; c0 < c_end; c0 += 8) {
+      uint32_t v[8];
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                   : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                   : "r"(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row < g.M) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int n = n0 + c0 + j;
+          if (c0 + j >= Nt) break;
+          const float d = __uint_as_float(v[j]);
+          const size_t o = (size_t)row * g.ldo + n;
+          if (EPI == EPI_ACT) {
+            const float z = d + g.bias[n];
+            g.out[o] = z;
+            g.out2[o] = silu(z);
+          } else if (EPI == EPI_LAST) {
+            const float z = d + g.bias[n];
+            g.out[o] = z;
+            if (g.out2) g.out2[o] = z * g.out_sd[n] + g.out_mean[n];
+          } else if (EPI == EPI_DACT) {
+            g.out[o] = d * silu_grad(g.aux[o]);
+          } else {
+            atomicAdd(g.out + o, d);
+          }
+        }
+      }
+    }
+  }
+  if (failed && threadIdx.x == 0) atomicExch(g.err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+  }
+}
+
+// dynamic shared memory of tc_gemm_kernel
+constexpr size_t kSmemBytes = (size_t)2 * kTileM * kKC * 2 + (size_t)2 * kMaxN * kKC * 2;
+
+}  // namespace mlp_tc

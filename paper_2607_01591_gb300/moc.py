@@ -91,6 +91,8 @@ def load_library(path: Optional[str] = None):
             "moc_get_work": (ctypes.c_int, [_vp, _i64, _i64, ctypes.POINTER(ctypes.c_int)]),
             "moc_synchronize": (ctypes.c_int, [_vp]),
             "moc_set_cmfd": (ctypes.c_int, [_vp, _i32, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double]),
+            "moc_set_cmfd_tolerance": (ctypes.c_int, [_vp, ctypes.c_double]),
+            "moc_get_cmfd_iterations": (ctypes.c_int, [_vp, _i64]),
             "moc_ws_features": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.c_int, _vp]),
             "moc_ws_apply": (ctypes.c_int, [_vp, _vp, _d]),
             "moc_mlp_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -388,6 +390,17 @@ class Moc:
         assert cell.size == self.n_regions
         self._check(self._lib.moc_set_cmfd(self._h, _p(cell, _i32), int(n_cells), int(n_outer), int(n_inner),
                                            float(omega)))
+
+    def set_cmfd_tolerance(self, tol: float):
+        """Stop each outer's coarse power iteration once k and the coarse fission source settle to
+        tol (0: the fixed count of set_cmfd)."""
+        self._check(self._lib.moc_set_cmfd_tolerance(self._h, float(tol)))
+
+    def cmfd_iterations(self) -> int:
+        """Coarse power iterations run since the last state reset, summed over outers."""
+        n = ctypes.c_int64()
+        self._check(self._lib.moc_get_cmfd_iterations(self._h, ctypes.byref(n)))
+        return n.value
 
     def set_axial(self, dz, mat3=None, bc=(0, 0)):
         """DGMOC on len(dz) axial planes (empty: back to the planar method): mat3 [nz][R] materials

@@ -253,11 +253,43 @@ def test_core_full_size_sampled_regions(precision):
     assert _rel(phig[sample], ref) <= tol, _rel(phig[sample], ref)
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 2e-5), ("fp32_plain", 2e-5)])
+def test_hex_core_full_size_sampled_regions(precision, tol):
+    """The 19-hexagon core at its benchmarked size (1.5M triangles, 33 groups, 48 azimuths, 0.02 cm:
+    1.3e8 segments; FP32 runs the four-group chunked sweep), vacuum everywhere: one fixed-source
+    outer from a random flux on the GPU, checked region by region against the oracle, which sweeps
+    only the rays crossing the sampled regions (each in-mesh chord with zero inflow)."""
+    prob = W.hex_core_problem()
+    xs = W.CrossSections(prob.xs.sigma_t, np.zeros_like(prob.xs.nu_sigma_f), prob.xs.chi, prob.xs.sigma_s)
+    R, G = prob.mesh.n_tri, xs.n_groups
+    rng = np.random.default_rng(23)
+    S = rng.uniform(0.0, 1.0, (R, G))
+    phi0 = rng.uniform(0.5, 1.5, (R, G))
+    m = moc.Moc.from_problem(prob, precision=precision, with_xs=False)
+    m.set_xs(xs)
+    m.set_fixed_source(S)
+    m.set_state(phi0, 1.0, None)
+    m.outer(1)
+    phig, _ = m.get_state()
+    m.close()
+    # regions of every material, the smallest ones and ones at the core's outer edge
+    by_mat = [rng.choice(np.nonzero(prob.mesh.mat == k)[0], 6, replace=False) for k in range(xs.n_mat)]
+    c = prob.mesh.centroids()
+    edge = np.argsort(-np.hypot(c[:, 0] - c[:, 0].mean(), c[:, 1] - c[:, 1].mean()))[:6]
+    sample = np.unique(np.concatenate(by_mat + [np.argsort(prob.mesh.areas())[:6], edge]))
+    ref, _ = oracle.sample_fixed_source(prob.mesh, prob.n_azim, prob.ray_spacing, prob.sin_theta, prob.polar_w,
+                                        xs, S, phi0, np.zeros((1, 2, 3, G)), sample)
+    err = _rel(phig[sample], ref)
+    print(precision, "sampled regions", sample.size, "max rel flux err", err)
+    assert err <= tol, err
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp32_plain"])
-@pytest.mark.parametrize("n_polar,G", [(1, 1), (2, 3), (4, 5), (3, 8), (3, 9)])
+@pytest.mark.parametrize("n_polar,G", [(1, 1), (2, 3), (4, 5), (3, 8), (3, 9), (3, 10), (3, 11), (3, 12), (3, 13)])
 def test_fp32_kernel_variants(precision, n_polar, G):
     """Every FP32 sweep variant (polar counts without the specialised kernel, group counts on both
-    sides of the 8-group chunk) against the oracle after 4 outers, mixed boundary conditions."""
+    sides of 8, and above it every remainder of G / 4: four-group lanes with tails of 1, 2, 3 or
+    no groups) against the oracle after 4 outers, mixed boundary conditions."""
     sin_t = {1: [0.8], 2: [0.3, 0.85], 3: list(W.TY3_SIN_THETA), 4: [0.1, 0.4, 0.7, 0.95]}[n_polar]
     wts = {1: [1.0], 2: [0.4, 0.6], 3: list(W.TY3_WEIGHT), 4: [0.1, 0.2, 0.3, 0.4]}[n_polar]
     mesh = W.lattice_mesh(3, guide_tubes=False, bc=(1, 0, 1, 1))
@@ -315,6 +347,30 @@ def test_cmfd_converges_to_the_unaccelerated_solution(precision):
     assert n < nr / 2, (n, nr)
     assert abs(k - kr) <= (1e-9 if precision == "fp64" else 2e-6) * kr
     assert _rel(m.get_state()[0], ref.get_state()[0]) <= (1e-7 if precision == "fp64" else 1e-4)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_cmfd_early_stop_reaches_the_same_solution(precision):
+    """The coarse power iteration stopped once k and the coarse source settle (a production mode):
+    the converged solution is still the unaccelerated one, and the coarse iterations run are far
+    fewer than the fixed count would run."""
+    prob = W.small_lattice_problem(5, bc=(1, 0, 1, 0), n_azim=16, ray_spacing=0.04)
+    cell, nc = W.grid_cells(prob.mesh, 1.26)
+    ref = moc.Moc.from_problem(prob, precision="fp64")
+    kr, _, _, cr = ref.power_iterate(1e-11, 1e-10, 50000, check_every=10)
+    m = moc.Moc.from_problem(prob, precision=precision)
+    m.set_cmfd(cell, nc, 60, 6)
+    m.set_cmfd_tolerance(1e-9 if precision == "fp64" else 1e-6)
+    m.set_state(None, 1.0)
+    tol = (1e-10, 1e-9) if precision == "fp64" else (1e-7, 1e-6)
+    k, n, _, c = m.power_iterate(tol[0], tol[1], 50000, check_every=1)
+    used = m.cmfd_iterations()
+    assert cr and c
+    assert used < 60 * n / 2, (used, n)
+    assert abs(k - kr) <= (1e-9 if precision == "fp64" else 2e-6) * kr
+    assert _rel(m.get_state()[0], ref.get_state()[0]) <= (1e-7 if precision == "fp64" else 1e-4)
+    with pytest.raises(moc.MocError):
+        m.set_cmfd_tolerance(-1.0)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
