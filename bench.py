@@ -212,7 +212,7 @@ def dg_cpu_baseline(nz: int = 8):
 # Per DGMOC update (segment x polar x group x plane x march), FP32: the algorithmic operations of the
 # closed-form 2x2 segment solution counted from its formulas (FMA = 1, the 1 - e^-x evaluation 13,
 # small-angle sin/cos 10, the reciprocal 1), and the thread instructions the plane-inner sweep
-# actually executes, from ncu on the extruded assembly (profiles/dg_sweep_assembly17x8.md)
+# actually executes, from an ncu capture of the plane-inner sweep on the extruded assembly
 DG_OPS_PER_UPDATE = 74
 DG_INST_PER_UPDATE = 110.4
 

@@ -402,7 +402,9 @@ template <typename Real> int upload_xs(moc_ctx *c, int n_mat, int G, const doubl
   const Geometry &g = c->geo;
   const int R = g.n_tri;
   c->G = G;
-  c->Gp = (G + 7) & ~7;
+  // padded group count of the region rows: 8 up to 8 groups (one 64/32-byte row per region for the
+  // group-per-thread sweep), a multiple of 4 beyond (the chunked sweep's 16-byte loads and atomics)
+  c->Gp = G <= 8 ? 8 : (G + 3) & ~3;
   c->M = n_mat;
   const int Gp = c->Gp;
   int rc;
@@ -553,10 +555,11 @@ template <typename Real> int launch_source(moc_ctx *c, cudaStream_t st) {
   const int R = c->geo.n_tri;
   if (lane_rows(c)) {
     const unsigned nb = (unsigned)((R + 31) / 32);
-    const size_t sm = (size_t)32 * c->Gp * sizeof(Real);
-    auto src = c->Gp == 40 ? source_lanes_kernel<Real, 5> : c->Gp == 16 ? source_lanes_kernel<Real, 2>
-             : c->Gp == 24 ? source_lanes_kernel<Real, 3> : c->Gp == 32 ? source_lanes_kernel<Real, 4>
-                           : source_lanes_kernel<Real, 0>;
+    const int gpl = (c->Gp + 7) / 8;
+    const size_t sm = (size_t)32 * 8 * gpl * sizeof(Real);  // 32 staged rows of 8 gpl groups
+    auto src = gpl == 5 ? source_lanes_kernel<Real, 5> : gpl == 2 ? source_lanes_kernel<Real, 2>
+             : gpl == 3 ? source_lanes_kernel<Real, 3> : gpl == 4 ? source_lanes_kernel<Real, 4>
+                        : source_lanes_kernel<Real, 0>;
     src<<<nb, 256, sm, st>>>(R, c->G, c->Gp, c->d_mat, (const Real *)c->d_sig_s, (const Real *)c->d_nsf,
                             (const Real *)c->d_chi, c->d_srange, c->d_ext, (Real *)c->d_phi,
                             (typename Pair<Real>::T *)c->d_xsq, c->d_fold, c->d_scal, c->eigen ? 1 : 0);
@@ -680,11 +683,12 @@ template <typename Real> int launch_finalize_reduce(moc_ctx *c, cudaStream_t st)
   if (lane_rows(c)) {
     const unsigned nb = (unsigned)((R + 31) / 32);
     const bool tm = tally_mode(c) == 1;
-    auto fin = c->Gp == 40 ? (tm ? finalize_lanes_kernel<Real, 1, 5> : finalize_lanes_kernel<Real, 0, 5>)
-             : c->Gp == 16 ? (tm ? finalize_lanes_kernel<Real, 1, 2> : finalize_lanes_kernel<Real, 0, 2>)
-             : c->Gp == 24 ? (tm ? finalize_lanes_kernel<Real, 1, 3> : finalize_lanes_kernel<Real, 0, 3>)
-             : c->Gp == 32 ? (tm ? finalize_lanes_kernel<Real, 1, 4> : finalize_lanes_kernel<Real, 0, 4>)
-                           : (tm ? finalize_lanes_kernel<Real, 1, 0> : finalize_lanes_kernel<Real, 0, 0>);
+    const int gpl = (c->Gp + 7) / 8;
+    auto fin = gpl == 5 ? (tm ? finalize_lanes_kernel<Real, 1, 5> : finalize_lanes_kernel<Real, 0, 5>)
+             : gpl == 2 ? (tm ? finalize_lanes_kernel<Real, 1, 2> : finalize_lanes_kernel<Real, 0, 2>)
+             : gpl == 3 ? (tm ? finalize_lanes_kernel<Real, 1, 3> : finalize_lanes_kernel<Real, 0, 3>)
+             : gpl == 4 ? (tm ? finalize_lanes_kernel<Real, 1, 4> : finalize_lanes_kernel<Real, 0, 4>)
+                        : (tm ? finalize_lanes_kernel<Real, 1, 0> : finalize_lanes_kernel<Real, 0, 0>);
     fin<<<nb, 256, 0, st>>>(R, c->G, c->Gp, c->d_mat, (const Real *)c->d_nsf, (const Real *)c->d_inv_ta,
                             (const typename Pair<Real>::T *)c->d_xsq, (Real *)c->d_tsum, (Real *)c->d_tcomp,
                             (Real *)c->d_phi, c->d_fold, c->d_area, c->d_part, c->d_ticket, c->d_scal,

@@ -113,7 +113,7 @@ __global__ void source_kernel(int R, int G, int Gp, int M, const int32_t *__rest
 }
 
 // Many groups (G > 8): eight consecutive threads per region, lane l owning the groups l, l + 8, ...
-// (GPL = Gp / 8 of them; 0: read from Gp at run time), 32 regions per block of 256. The block's
+// (GPL = ceil(Gp / 8) of them; 0: computed at run time), 32 regions per block of 256. The block's
 // normalised flux rows are staged in shared memory (one barrier), the fission rate is an 8-lane
 // shuffle sum, and each group visits only the nonzero band srange[m][g] = [first, last] source
 // group of column g of the material's scattering matrix (a downscatter-only matrix has half its
@@ -125,11 +125,11 @@ __global__ void __launch_bounds__(256) source_lanes_kernel(
     const double *__restrict__ ext, Real *__restrict__ phi, typename Pair<Real>::T *__restrict__ xsq,
     double *__restrict__ fold, const double *__restrict__ scal, int eigen) {
   extern __shared__ unsigned char smem_raw[];
-  const int gpl = GPL > 0 ? GPL : Gp / 8;
+  const int gpl = GPL > 0 ? GPL : (Gp + 7) / 8;
   const int rl = threadIdx.x >> 3, l = threadIdx.x & 7;
   const int r = blockIdx.x * 32 + rl;
   const bool live = r < R;
-  Real *row = reinterpret_cast<Real *>(smem_raw) + (size_t)rl * Gp;
+  Real *row = reinterpret_cast<Real *>(smem_raw) + (size_t)rl * 8 * gpl;
   const Real scale = eigen ? (Real)scal[S_SCALE] : (Real)1;
   const Real inv_k = eigen ? (Real)(1.0 / scal[S_K]) : (Real)0;
   const Real inv4pi = (Real)(1.0 / kFourPi);
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(256) source_lanes_kernel(
   }
 }
 
-// ----------------------------------------------------------------------------- state transfer// ----------------------------------------------------------------------------- state transfer// ----------------------------------------------------------------------------- state transfer
+// ----------------------------------------------------------------------------- state transfer
 // A caller's state read or written in place when its host arrays are addressable from the device
 // (pinned or registered memory, or pageable memory on a system whose GPU reads it coherently):
 // one kernel converts, pads and reorders instead of a host loop, a staging copy and a second
@@ -716,9 +716,9 @@ __global__ void __launch_bounds__(256) finalize8_kernel(
   }
 }
 
-// Many groups (G > 8): finalize8_kernel with GPL = Gp / 8 groups per lane (lane l owns l, l + 8,
-// ...; 0: read from Gp at run time): eight threads per region, 32 regions per block, the region's
-// fission rate an 8-lane shuffle sum, the last block to finish reducing all partials.
+// Many groups (G > 8): finalize8_kernel with GPL = ceil(Gp / 8) groups per lane (lane l owns l,
+// l + 8, ... below Gp; 0: computed at run time): eight threads per region, 32 regions per block,
+// the region's fission rate an 8-lane shuffle sum, the last block to finish reducing all partials.
 template <typename Real, int TM, int GPL>
 __global__ void __launch_bounds__(256) finalize_lanes_kernel(
     int R, int G, int Gp, const int32_t *__restrict__ mat, const Real *__restrict__ nsf,
@@ -729,7 +729,7 @@ __global__ void __launch_bounds__(256) finalize_lanes_kernel(
   __shared__ double l_sum[32];
   __shared__ Real l_min[32], l_max[32], l_res[32];
   __shared__ bool last;
-  const int gpl = GPL > 0 ? GPL : Gp / 8;
+  const int gpl = GPL > 0 ? GPL : (Gp + 7) / 8;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = tid >> 3, l = tid & 7;
   const bool live = r < R;
@@ -739,6 +739,7 @@ __global__ void __launch_bounds__(256) finalize_lanes_kernel(
 #pragma unroll 5
     for (int j = 0; j < gpl; ++j) {
       const int g = l + 8 * j;
+      if (g >= Gp) break;
       const size_t a = (size_t)r * Gp + g;
       const typename Pair<Real>::T v = xsq[a];
       Real t = tsum[a];
