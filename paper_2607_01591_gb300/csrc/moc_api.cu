@@ -32,6 +32,7 @@ struct moc_ctx {
   // problem sizes
   int G = 0, Gp = 0, P = 0, M = 0;
   int64_t T = 0, S = 0;
+  int order_mode = 0;         // internal track order: 0 longest first, 1 length classes (see upload_tracks)
   std::vector<int64_t> perm;  // internal track -> external track
   std::vector<int64_t> inv;   // external -> internal
   // device data
@@ -82,6 +83,8 @@ struct moc_ctx {
   unsigned *d_cticket = nullptr;
   void *h_stage = nullptr;    // pinned staging buffer for state transfers (grown on demand)
   size_t h_stage_bytes = 0;
+  double *d_ostage = nullptr;  // device staging of get_state into pinned host arrays (grown on demand)
+  size_t d_ostage_n = 0;
   // DGMOC (off unless moc_set_axial was called): nz planes, bottom/top condition
   int dg_nz = 0;
   int dg_bc[2] = {0, 0};
@@ -318,8 +321,13 @@ int stage(moc_ctx *c, size_t bytes, unsigned char *&out) {
   return MOC_OK;
 }
 
-// Upload tracks in the internal order: tracks sorted by segment count, longest first, so the
-// longest characteristic chains start first and neighbouring threads do similar work.
+// Upload tracks in the internal order, longest first so that the longest characteristic chains
+// start first and neighbouring threads do similar work. order_mode 0: sorted by segment count.
+// order_mode 1 (the four-group chunked sweep): sorted by length class, 8 classes per octave of
+// segment count, and within a class in laydown order (direction, then position across it), so the
+// threads of a warp sweep neighbouring parallel tracks that read and tally the same region rows at
+// about the same time (measured 5% faster on the 33-group hex core, 3% slower on the 7-group
+// assembly's group-per-thread sweep).
 template <typename Real> int upload_tracks(moc_ctx *c) {
   const Geometry &g = c->geo;
   const int64_t T = g.n_tracks(), S = g.n_segments();
@@ -328,9 +336,13 @@ template <typename Real> int upload_tracks(moc_ctx *c) {
   c->P = g.n_polar;
   c->perm.resize(T);
   std::iota(c->perm.begin(), c->perm.end(), 0);
-  std::stable_sort(c->perm.begin(), c->perm.end(), [&](int64_t a, int64_t b) {
-    return (g.seg_off[a + 1] - g.seg_off[a]) > (g.seg_off[b + 1] - g.seg_off[b]);
-  });
+  auto len = [&](int64_t t) { return g.seg_off[t + 1] - g.seg_off[t]; };
+  if (c->order_mode == 1) {
+    auto cls = [&](int64_t t) { return len(t) > 0 ? (int)std::floor(std::log2((double)len(t)) * 8.0) : -1; };
+    std::stable_sort(c->perm.begin(), c->perm.end(), [&](int64_t a, int64_t b) { return cls(a) > cls(b); });
+  } else {
+    std::stable_sort(c->perm.begin(), c->perm.end(), [&](int64_t a, int64_t b) { return len(a) > len(b); });
+  }
   c->inv.resize(T);
   for (int64_t i = 0; i < T; ++i) c->inv[c->perm[i]] = i;
   if (2 * T >= (int64_t)1 << 31) return fail(c, MOC_ERR_ARG, "too many tracks for 32-bit links");
@@ -1078,18 +1090,50 @@ template <typename Real> int state_in(moc_ctx *c, const double *dphi, const doub
   return MOC_OK;
 }
 
-template <typename Real> int state_out(moc_ctx *c, double *dphi, double *dpsi, double *s) {
+// The state written into the caller's host arrays (dphi, dpsi: their device views) by one kernel,
+// which also copies the scalars. Pinned arrays (pinned = 1) are written through a device staging
+// buffer and one copy each by the copy engine, which moves large states over the host link far
+// faster than the kernel's own stores to host memory; other device-addressable arrays are written
+// by the kernel directly.
+template <typename Real>
+int state_out(moc_ctx *c, double *dphi, double *dpsi, double *s, double *hphi, double *hpsi, bool pinned) {
   const int R = c->geo.n_tri;
-  const long long n = std::max<long long>(1, (dphi ? (long long)R * c->G : 0) + (dpsi ? c->T * 2 * c->P * c->G : 0));
+  const long long nphi = dphi ? (long long)R * c->G : 0, npsi = dpsi ? c->T * 2 * c->P * c->G : 0;
+  const long long n = std::max<long long>(1, nphi + npsi);
   double *hs = nullptr;
   CUDA_TRY(c, cudaHostGetDevicePointer((void **)&hs, c->h_scal, 0));
+  double *wphi = dphi, *wpsi = dpsi;
+  if (pinned) {
+    if ((size_t)n > c->d_ostage_n) {
+      dfree(c->d_ostage);
+      c->d_ostage_n = 0;
+      CUDA_TRY(c, cudaMalloc(&c->d_ostage, (size_t)n * sizeof(double)));
+      c->d_ostage_n = (size_t)n;
+    }
+    wphi = dphi ? c->d_ostage : nullptr;
+    wpsi = dpsi ? c->d_ostage + nphi : nullptr;
+  }
   state_out_kernel<Real><<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
       R, c->G, c->Gp, (long long)c->T, c->P, (const Real *)c->d_phi, (const Real *)c->d_psi[c->cur], c->d_inv,
-      c->d_scal, c->eigen ? 1 : 0, dphi, dpsi, hs);
+      c->d_scal, c->eigen ? 1 : 0, wphi, wpsi, hs);
   CUDA_TRY(c, cudaGetLastError());
+  if (pinned && hphi)
+    CUDA_TRY(c, cudaMemcpyAsync(hphi, wphi, (size_t)nphi * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (pinned && hpsi)
+    CUDA_TRY(c, cudaMemcpyAsync(hpsi, wpsi, (size_t)npsi * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   for (int i = 0; i < S_COUNT; ++i) s[i] = c->h_scal[i];
   return MOC_OK;
+}
+
+bool is_pinned(const void *p) {
+  if (!p) return true;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
 }
 
 }  // namespace
@@ -1369,6 +1413,7 @@ void moc_destroy(moc_ctx *c) {
     }
     free_tracks(c);
     dfree(c->d_scal);
+    dfree(c->d_ostage);
     if (c->h_stage) cudaFreeHost(c->h_stage);
     if (c->h_scal) cudaFreeHost(c->h_scal);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -1550,6 +1595,14 @@ int moc_set_xs(moc_ctx *c, int n_mat, int G, const double *st, const double *nsf
     }
   cudaSetDevice(c->device);
   free_problem(c);
+  // the sweep that will run decides the internal track order (re-uploaded when it changes)
+  const int order = (G > 8 && c->P == 3 && c->precision != MOC_FP64) ? 1 : 0;
+  if (order != c->order_mode) {
+    free_tracks(c);
+    c->order_mode = order;
+    rc = c->precision == MOC_FP64 ? upload_tracks<double>(c) : upload_tracks<float>(c);
+    if (rc) return rc;
+  }
   c->eigen = true;
   // the device tables hold the values rounded to the sweep's type; normalise with the same
   c->h_nsf.resize((size_t)n_mat * G);
@@ -1994,9 +2047,11 @@ int moc_get_state(moc_ctx *c, double *phi, double *k, double *psi) {
   double s[S_COUNT];
   void *vphi = (void *)host_view(c, phi), *vpsi = (void *)host_view(c, psi);
   if ((phi || psi) && (!phi || vphi) && (!psi || vpsi)) {
-    // written in place by one kernel, which also copies the scalars
-    rc = c->precision == MOC_FP64 ? state_out<double>(c, (double *)vphi, (double *)vpsi, s)
-                                  : state_out<float>(c, (double *)vphi, (double *)vpsi, s);
+    // written in place by one kernel, which also copies the scalars (pinned arrays through the
+    // copy engine)
+    const bool pinned = is_pinned(phi) && is_pinned(psi);
+    rc = c->precision == MOC_FP64 ? state_out<double>(c, (double *)vphi, (double *)vpsi, s, phi, psi, pinned)
+                                  : state_out<float>(c, (double *)vphi, (double *)vpsi, s, phi, psi, pinned);
     if (rc) return rc;
     if (k) *k = s[S_K];
     return MOC_OK;

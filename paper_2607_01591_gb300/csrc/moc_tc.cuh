@@ -119,13 +119,63 @@ template <int SRC> __device__ __forceinline__ float fetch(const void *p, int ld,
   return __bfloat162float(static_cast<const __nv_bfloat16 *>(p)[(size_t)k * ld + r]);
 }
 
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 a, __nv_bfloat16 b) {
+  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
 // stage rows [r0, r0 + R) x k [k0, k0 + kKC) of a source into hi (and lo for FP32 sources) tiles;
-// out-of-range elements are zero. The loop order follows the source's contiguous index.
+// out-of-range elements are zero. The loop order follows the source's contiguous index. Sources
+// with k contiguous and 16-byte aligned rows move 4 FP32 (or 8 bf16) values per thread step:
+// one 16-byte load, and 8 (16) contiguous bytes of one core-matrix row in shared memory.
 template <int SRC>
 __device__ __forceinline__ void stage(unsigned char *hi, unsigned char *lo, const void *p, int ld, int r0, int R,
                                       int rmax, int k0, int kmax) {
   constexpr bool T = (SRC == SRC_F32_T || SRC == SRC_BF16_T);
   constexpr bool F32 = (SRC == SRC_F32 || SRC == SRC_F32_T);
+  if (SRC == SRC_F32 && (ld & 3) == 0 && ((uintptr_t)p & 15) == 0) {
+    const float *q = static_cast<const float *>(p);
+    for (int e = threadIdx.x; e < R * (kKC / 4); e += kThreads) {
+      const int r = e / (kKC / 4), k = (e % (kKC / 4)) * 4;
+      const int gr = r0 + r, gk = k0 + k;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (gr < rmax) {
+        if (gk + 3 < kmax) {
+          v = *reinterpret_cast<const float4 *>(q + (size_t)gr * ld + gk);
+        } else {
+          if (gk < kmax) v.x = q[(size_t)gr * ld + gk];
+          if (gk + 1 < kmax) v.y = q[(size_t)gr * ld + gk + 1];
+          if (gk + 2 < kmax) v.z = q[(size_t)gr * ld + gk + 2];
+        }
+      }
+      const __nv_bfloat16 hx = __float2bfloat16_rn(v.x), hy = __float2bfloat16_rn(v.y), hz = __float2bfloat16_rn(v.z),
+                          hw = __float2bfloat16_rn(v.w);
+      const uint32_t o = kmaj_off(r, k, kKC);
+      *reinterpret_cast<uint2 *>(hi + o) = make_uint2(pack_bf16(hx, hy), pack_bf16(hz, hw));
+      *reinterpret_cast<uint2 *>(lo + o) = make_uint2(
+          pack_bf16(__float2bfloat16_rn(v.x - __bfloat162float(hx)), __float2bfloat16_rn(v.y - __bfloat162float(hy))),
+          pack_bf16(__float2bfloat16_rn(v.z - __bfloat162float(hz)), __float2bfloat16_rn(v.w - __bfloat162float(hw))));
+    }
+    return;
+  }
+  if (SRC == SRC_BF16 && (ld & 7) == 0 && ((uintptr_t)p & 15) == 0) {
+    const __nv_bfloat16 *q = static_cast<const __nv_bfloat16 *>(p);
+    for (int e = threadIdx.x; e < R * (kKC / 8); e += kThreads) {
+      const int r = e / (kKC / 8), k = (e % (kKC / 8)) * 8;
+      const int gr = r0 + r, gk = k0 + k;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (gr < rmax) {
+        if (gk + 7 < kmax) {
+          v = *reinterpret_cast<const uint4 *>(q + (size_t)gr * ld + gk);
+        } else {
+          __nv_bfloat16 t[8];
+          for (int j = 0; j < 8; ++j) t[j] = (gk + j < kmax) ? q[(size_t)gr * ld + gk + j] : __float2bfloat16_rn(0.f);
+          v = make_uint4(pack_bf16(t[0], t[1]), pack_bf16(t[2], t[3]), pack_bf16(t[4], t[5]), pack_bf16(t[6], t[7]));
+        }
+      }
+      *reinterpret_cast<uint4 *>(hi + kmaj_off(r, k, kKC)) = v;
+    }
+    return;
+  }
   for (int e = threadIdx.x; e < R * kKC; e += kThreads) {
     const int r = T ? (e % R) : (e / kKC);
     const int k = T ? (e / R) : (e % kKC);
@@ -142,7 +192,7 @@ __device__ __forceinline__ void stage(unsigned char *hi, unsigned char *lo, cons
 // [kb, ke) (blockIdx.y).
 // Shared memory: A hi/lo (2 x 16 KB), B hi/lo (2 x 32 KB), mbarrier, TMEM address.
 template <int ASRC, int BSRC, int EPI>
-__global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs g) {
+__global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(TcArgs g) {
   extern __shared__ __align__(1024) unsigned char sm[];
   unsigned char *a_hi = sm, *a_lo = sm + kTileM * kKC * 2;
   unsigned char *b_hi = a_lo + kTileM * kKC * 2, *b_lo = b_hi + kMaxN * kKC * 2;
