@@ -188,6 +188,73 @@ __device__ __forceinline__ void stage(unsigned char *hi, unsigned char *lo, cons
   }
 }
 
+// 32 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t *v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// the epilogue of NC columns c0 .. c0 + NC - 1 of the tile (local), for one row: groups of 4
+// columns that lie inside the tile and start 16-byte aligned in the output go out as float4
+template <int EPI, int NC>
+__device__ __forceinline__ void epilogue_cols(const TcArgs &g, const float *s_bias, const uint32_t *v, int row, int n0,
+                                              int c0, int Nt) {
+  if (row >= g.M) return;
+  const bool vec = (g.ldo & 3) == 0;
+#pragma unroll
+  for (int j0 = 0; j0 < NC; j0 += 4) {
+    const int cl = c0 + j0;
+    if (cl >= Nt) break;
+    const size_t o = (size_t)row * g.ldo + n0 + cl;
+    float d[4], z[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) d[j] = __uint_as_float(v[j0 + j]);
+    const bool full = vec && cl + 3 < Nt;
+    if (EPI == EPI_ATOMIC) {
+      for (int j = 0; j < 4 && cl + j < Nt; ++j) atomicAdd(g.out + o + j, d[j]);
+      continue;
+    }
+    if (EPI == EPI_DACT) {
+      float a[4];
+      if (full) {
+        const float4 t = *reinterpret_cast<const float4 *>(g.aux + o);
+        a[0] = t.x; a[1] = t.y; a[2] = t.z; a[3] = t.w;
+      } else {
+        for (int j = 0; j < 4; ++j) a[j] = (cl + j < Nt) ? g.aux[o + j] : 0.0f;
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) z[j] = d[j] * silu_grad(a[j]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) z[j] = d[j] + s_bias[cl + j];
+    }
+    if (full) {
+      *reinterpret_cast<float4 *>(g.out + o) = make_float4(z[0], z[1], z[2], z[3]);
+    } else {
+      for (int j = 0; j < 4 && cl + j < Nt; ++j) g.out[o + j] = z[j];
+    }
+    if (EPI == EPI_ACT || (EPI == EPI_LAST && g.out2)) {
+      float y[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        y[j] = (EPI == EPI_ACT) ? silu(z[j])
+                                : z[j] * g.out_sd[n0 + min(cl + j, Nt - 1)] + g.out_mean[n0 + min(cl + j, Nt - 1)];
+      if (full) {
+        *reinterpret_cast<float4 *>(g.out2 + o) = make_float4(y[0], y[1], y[2], y[3]);
+      } else {
+        for (int j = 0; j < 4 && cl + j < Nt; ++j) g.out2[o + j] = y[j];
+      }
+    }
+  }
+}
+
 // One CTA: D tile rows [m0, m0 + 128) (blockIdx.x), columns [n0, n0 + 256) (blockIdx.z), k range
 // [kb, ke) (blockIdx.y).
 // Shared memory: A hi/lo (2 x 16 KB), B hi/lo (2 x 32 KB), mbarrier, TMEM address.
@@ -199,6 +266,7 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(TcArgs g) {
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t tmem_base;
   __shared__ int failed;
+  __shared__ float s_bias[kMaxN];
   constexpr bool A32 = (ASRC == SRC_F32 || ASRC == SRC_F32_T);
   constexpr bool B32 = (BSRC == SRC_F32 || BSRC == SRC_F32_T);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -222,6 +290,9 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(TcArgs g) {
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
   const uint32_t idesc = idesc_bf16(kTileM, Np);
+  // the tile's bias values (read by the epilogue; made visible by the first round's barrier)
+  if (EPI == EPI_ACT || EPI == EPI_LAST)
+    for (int n = threadIdx.x; n < Nt; n += kThreads) s_bias[n] = g.bias[n0 + n];
   uint32_t parity = 0;
   int first = 1;
   for (int k0 = kb; k0 < ke; k0 += kKC) {
@@ -256,38 +327,25 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(TcArgs g) {
   }
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (!failed && kb < ke) {
-    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows of D), column half w / 4
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows of D), column half w / 4, 32
+    // columns per tcgen05.ld where the half allows (8 otherwise); results leave as float4 stores
     const int q = warp & 3, half = warp >> 2;
     const int row = m0 + 32 * q + lane;
     const int c_beg = half * (Np / 2), c_end = c_beg + Np / 2;
-    for (int c0 = c_beg; c0 < c_end; c0 += 8) {
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
+    int c0 = c_beg;
+    for (; c0 + 32 <= c_end; c0 += 32) {
+      uint32_t v[32];
+      tmem_ld32(lane_base + (uint32_t)c0, v);
+      epilogue_cols<EPI, 32>(g, s_bias, v, row, n0, c0, Nt);
+    }
+    for (; c0 < c_end; c0 += 8) {
       uint32_t v[8];
       asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-                   : "r"(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0));
+                   : "r"(lane_base + (uint32_t)c0));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (row < g.M) {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int n = n0 + c0 + j;
-          if (c0 + j >= Nt) break;
-          const float d = __uint_as_float(v[j]);
-          const size_t o = (size_t)row * g.ldo + n;
-          if (EPI == EPI_ACT) {
-            const float z = d + g.bias[n];
-            g.out[o] = z;
-            g.out2[o] = silu(z);
-          } else if (EPI == EPI_LAST) {
-            const float z = d + g.bias[n];
-            g.out[o] = z;
-            if (g.out2) g.out2[o] = z * g.out_sd[n] + g.out_mean[n];
-          } else if (EPI == EPI_DACT) {
-            g.out[o] = d * silu_grad(g.aux[o]);
-          } else {
-            atomicAdd(g.out + o, d);
-          }
-        }
-      }
+      epilogue_cols<EPI, 8>(g, s_bias, v, row, n0, c0, Nt);
     }
   }
   if (failed && threadIdx.x == 0) atomicExch(g.err, 1);
