@@ -207,7 +207,10 @@ template <int EPI, int NC>
 __device__ __forceinline__ void epilogue_cols(const TcArgs &g, const float *s_bias, const uint32_t *v, int row, int n0,
                                               int c0, int Nt) {
   if (row >= g.M) return;
-  const bool vec = (g.ldo & 3) == 0;
+  // float4 accesses need 16-byte aligned rows: the row pitch a multiple of 4 and every array's base
+  // aligned (a caller's workspace carved at arbitrary float offsets need not be)
+  const bool vec = (g.ldo & 3) == 0 && ((uintptr_t)g.out & 15) == 0 && ((uintptr_t)g.out2 & 15) == 0 &&
+                   ((uintptr_t)g.aux & 15) == 0;
 #pragma unroll
   for (int j0 = 0; j0 < NC; j0 += 4) {
     const int cl = c0 + j0;
