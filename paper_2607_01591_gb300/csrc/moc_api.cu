@@ -53,6 +53,8 @@ struct moc_ctx {
   void *d_inv_ta = nullptr;    // [R][Gp] 1/(Sigma_t A) in the sweep's type, 0 where the tracked area is 0
   unsigned *d_ticket = nullptr;  // finalize's last-block counter (back to 0 after each launch)
   int2 *d_srange = nullptr;      // [M][G] first and last source group of each scattering column
+  void *d_sig_sT = nullptr;      // FP32: [M][G][Gp4] the scattering matrix's columns as rows (many groups)
+  int Gp4 = 0;                   // G rounded up to a multiple of 4
   int n_sm = 0;                  // the device's multiprocessor count
   int cur = 0;          // psi buffer holding the incoming flux of the next sweep
   bool eigen = true;
@@ -264,6 +266,7 @@ void free_problem(moc_ctx *c) {
   dfree(c->d_chi);
   dfree(c->d_sig_s);
   dfree(c->d_srange);
+  dfree(c->d_sig_sT);
   c->xs_set = false;
 }
 
@@ -445,6 +448,18 @@ template <typename Real> int upload_xs(moc_ctx *c, int n_mat, int G, const doubl
         band[(size_t)m * G + g] = (hi < 0) ? make_int2(1, 0) : make_int2(lo, hi);
       }
     if ((rc = upload(c, c->d_srange, band.data(), band.size()))) return rc;
+    // FP32 many-group source: each column g (sources g' -> g) stored as a contiguous, 16-byte
+    // aligned row, zero-padded to a multiple of 4 groups
+    c->Gp4 = (G + 3) & ~3;
+    if (sizeof(Real) == 4 && G > 8) {
+      std::vector<Real> sT((size_t)n_mat * G * c->Gp4, (Real)0);
+      for (int m = 0; m < n_mat; ++m)
+        for (int g = 0; g < G; ++g)
+          for (int gp = 0; gp < G; ++gp) sT[((size_t)m * G + g) * c->Gp4 + gp] = vss[((size_t)m * G + gp) * G + g];
+      Real *dT = nullptr;
+      if ((rc = upload(c, dT, sT.data(), sT.size()))) return rc;
+      c->d_sig_sT = dT;
+    }
   }
   // region pairs {Sigma_t, q/Sigma_t}; padding groups get Sigma_t = 1, q = 0
   std::vector<typename Pair<Real>::T> xsq((size_t)R * Gp);
@@ -572,8 +587,8 @@ template <typename Real> int launch_source(moc_ctx *c, cudaStream_t st) {
     auto src = gpl == 5 ? source_lanes_kernel<Real, 5> : gpl == 2 ? source_lanes_kernel<Real, 2>
              : gpl == 3 ? source_lanes_kernel<Real, 3> : gpl == 4 ? source_lanes_kernel<Real, 4>
                         : source_lanes_kernel<Real, 0>;
-    src<<<nb, 256, sm, st>>>(R, c->G, c->Gp, c->d_mat, (const Real *)c->d_sig_s, (const Real *)c->d_nsf,
-                            (const Real *)c->d_chi, c->d_srange, c->d_ext, (Real *)c->d_phi,
+    src<<<nb, 256, sm, st>>>(R, c->G, c->Gp, c->d_mat, (const Real *)c->d_sig_s, (const Real *)c->d_sig_sT, c->Gp4,
+                            (const Real *)c->d_nsf, (const Real *)c->d_chi, c->d_srange, c->d_ext, (Real *)c->d_phi,
                             (typename Pair<Real>::T *)c->d_xsq, c->d_fold, c->d_scal, c->eigen ? 1 : 0);
     CUDA_TRY(c, cudaGetLastError());
     return MOC_OK;
@@ -693,7 +708,8 @@ template <typename Real> int launch_finalize_reduce(moc_ctx *c, cudaStream_t st)
     return MOC_OK;
   }
   if (lane_rows(c)) {
-    const unsigned nb = (unsigned)((R + 31) / 32);
+    // tiles of 32 regions, blocks striding over them: at most 8 blocks per multiprocessor
+    const unsigned nb = (unsigned)std::max(1, std::min((R + 31) / 32, 8 * std::max(c->n_sm, 1)));
     const bool tm = tally_mode(c) == 1;
     const int gpl = (c->Gp + 7) / 8;
     auto fin = gpl == 5 ? (tm ? finalize_lanes_kernel<Real, 1, 5> : finalize_lanes_kernel<Real, 0, 5>)

@@ -121,43 +121,86 @@ __global__ void source_kernel(int R, int G, int Gp, int M, const int32_t *__rest
 template <typename Real, int GPL>
 __global__ void __launch_bounds__(256) source_lanes_kernel(
     int R, int G, int Gp, const int32_t *__restrict__ mat, const Real *__restrict__ sig_s,
-    const Real *__restrict__ nsf, const Real *__restrict__ chi, const int2 *__restrict__ srange,
-    const double *__restrict__ ext, Real *__restrict__ phi, typename Pair<Real>::T *__restrict__ xsq,
-    double *__restrict__ fold, const double *__restrict__ scal, int eigen) {
-  extern __shared__ unsigned char smem_raw[];
+    const Real *__restrict__ sig_sT, int Gp4, const Real *__restrict__ nsf, const Real *__restrict__ chi,
+    const int2 *__restrict__ srange, const double *__restrict__ ext, Real *__restrict__ phi,
+    typename Pair<Real>::T *__restrict__ xsq, double *__restrict__ fold, const double *__restrict__ scal, int eigen) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int gpl = GPL > 0 ? GPL : (Gp + 7) / 8;
   const int rl = threadIdx.x >> 3, l = threadIdx.x & 7;
   const int r = blockIdx.x * 32 + rl;
   const bool live = r < R;
   Real *row = reinterpret_cast<Real *>(smem_raw) + (size_t)rl * 8 * gpl;
+  __shared__ Real s_inv_k;  // 1/k: one FP64 division per block (GB300's FP64 pipe is slow)
+  if (threadIdx.x == 0) s_inv_k = eigen ? (Real)(1.0 / scal[S_K]) : (Real)0;
   const Real scale = eigen ? (Real)scal[S_SCALE] : (Real)1;
-  const Real inv_k = eigen ? (Real)(1.0 / scal[S_K]) : (Real)0;
   const Real inv4pi = (Real)(1.0 / kFourPi);
   const int m = live ? mat[r] : 0;
   Real f = 0;
-#pragma unroll 5
-  for (int j = 0; j < gpl; ++j) {
-    const int g = l + 8 * j;
-    Real v = 0;
-    if (live && g < G) {
-      v = phi[(size_t)r * Gp + g] * scale;
-      phi[(size_t)r * Gp + g] = v;
-      f += nsf[m * G + g] * v;
+  if (GPL > 0) {
+    // all of the region's flux loads in flight together, then the scaled values stored
+    Real v[GPL > 0 ? GPL : 1], nf[GPL > 0 ? GPL : 1];
+#pragma unroll
+    for (int j = 0; j < GPL; ++j) {
+      const int g = l + 8 * j;
+      v[j] = nf[j] = 0;
+      if (live && g < G) {
+        v[j] = phi[(size_t)r * Gp + g];
+        nf[j] = nsf[m * G + g];
+      }
     }
-    row[g] = v;
+#pragma unroll
+    for (int j = 0; j < GPL; ++j) {
+      const int g = l + 8 * j;
+      const Real w = v[j] * scale;
+      if (live && g < G) {
+        phi[(size_t)r * Gp + g] = w;
+        f += nf[j] * w;
+      }
+      row[g] = (live && g < G) ? w : (Real)0;
+    }
+  } else {
+    for (int j = 0; j < gpl; ++j) {
+      const int g = l + 8 * j;
+      Real v = 0;
+      if (live && g < G) {
+        v = phi[(size_t)r * Gp + g] * scale;
+        phi[(size_t)r * Gp + g] = v;
+        f += nsf[m * G + g] * v;
+      }
+      row[g] = v;
+    }
   }
 #pragma unroll
   for (int o = 4; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
   if (eigen && live && l == 0) fold[r] = (double)f;
   __syncthreads();
   if (!live) return;
+  const Real inv_k = s_inv_k;
   for (int j = 0; j < gpl; ++j) {
     const int g = l + 8 * j;
     if (g >= G) break;
     const int2 band = srange[m * G + g];
-    const Real *ss = sig_s + (size_t)m * G * G + g;
     Real sc = 0;
-    for (int gp = band.x; gp <= band.y; ++gp) sc += ss[gp * G] * row[gp];
+    if constexpr (sizeof(Real) == 4) {
+      if (sig_sT) {
+        // FP32: column g of the scattering matrix as a contiguous row (sig_sT [M][G][Gp4], zero
+        // outside the matrix), four source groups per 16-byte load from both operands, summed in
+        // group order; the zeros outside the band add nothing
+        const float4 *ssr = reinterpret_cast<const float4 *>(sig_sT + ((size_t)m * G + g) * Gp4);
+        const float4 *rr = reinterpret_cast<const float4 *>(row);
+        for (int b4 = band.x >> 2; b4 <= (band.y >> 2); ++b4) {
+          const float4 a4 = ssr[b4], x4 = rr[b4];
+          sc = fmaf(a4.x, x4.x, sc);
+          sc = fmaf(a4.y, x4.y, sc);
+          sc = fmaf(a4.z, x4.z, sc);
+          sc = fmaf(a4.w, x4.w, sc);
+        }
+      }
+    }
+    if (sizeof(Real) != 4 || !sig_sT) {
+      const Real *ss = sig_s + (size_t)m * G * G + g;
+      for (int gp = band.x; gp <= band.y; ++gp) sc += ss[gp * G] * row[gp];
+    }
     Real src = sc + chi[m * G + g] * inv_k * f;
     if (ext) src += (Real)ext[(size_t)r * G + g];
     const size_t a = (size_t)r * Gp + g;
@@ -716,9 +759,13 @@ __global__ void __launch_bounds__(256) finalize8_kernel(
   }
 }
 
-// Many groups (G > 8): finalize8_kernel with GPL = ceil(Gp / 8) groups per lane (lane l owns l,
-// l + 8, ... below Gp; 0: computed at run time): eight threads per region, 32 regions per block,
-// the region's fission rate an 8-lane shuffle sum, the last block to finish reducing all partials.
+// Many groups (G > 8): eight threads per region (lane l owns groups l, l + 8, ... below Gp; GPL =
+// ceil(Gp / 8), 0: computed at run time), 32 regions per tile, the blocks striding over the tiles
+// (the grid is fixed by the launch: every sum has a fixed order). Each 8-lane group keeps running
+// FP64 partials of its own regions; the block adds its 32 groups' partials in order once at the
+// end, so there is one memory fence and one ticket per block, and the last block to finish
+// reduces all block partials. Per region and group the arithmetic is in the sweep's type, as in
+// finalize8_kernel; the region's fission rate is an 8-lane shuffle sum.
 template <typename Real, int TM, int GPL>
 __global__ void __launch_bounds__(256) finalize_lanes_kernel(
     int R, int G, int Gp, const int32_t *__restrict__ mat, const Real *__restrict__ nsf,
@@ -729,56 +776,101 @@ __global__ void __launch_bounds__(256) finalize_lanes_kernel(
   __shared__ double l_sum[32];
   __shared__ Real l_min[32], l_max[32], l_res[32];
   __shared__ bool last;
+  constexpr int NJ = GPL > 0 ? GPL : 1;
   const int gpl = GPL > 0 ? GPL : (Gp + 7) / 8;
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int r = tid >> 3, l = tid & 7;
-  const bool live = r < R;
-  Real f = 0, res = 0;
-  if (live) {
-    const int m = mat[r];
-#pragma unroll 5
-    for (int j = 0; j < gpl; ++j) {
-      const int g = l + 8 * j;
-      if (g >= Gp) break;
-      const size_t a = (size_t)r * Gp + g;
-      const typename Pair<Real>::T v = xsq[a];
-      Real t = tsum[a];
-      tsum[a] = (Real)0;
-      if (TM == 1) {
-        t += tcomp[a];
-        tcomp[a] = (Real)0;
-      }
-      if (g < G) {
-        const Real ph = fma(t, inv_ta[a], (Real)kFourPi * v.y);
-        if (!eigen) {
-          const Real old = phi[a];
-          if (ph > (Real)0) res = fmax(res, fabs(ph - old) / ph);
+  const int qg = threadIdx.x >> 3, l = threadIdx.x & 7;
+  const int ntile = (R + 31) / 32;
+  double g_sum = 0.0;
+  Real g_min = (Real)INFINITY, g_max = (Real)-INFINITY, g_res = 0;
+  for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+    const int r = tile * 32 + qg;
+    const bool live = r < R;
+    Real f = 0, res = 0;
+    if (live && GPL > 0) {
+      // every load of the region's groups first (independent, all in flight together), then the
+      // arithmetic and the stores
+      const int m = mat[r];
+      Real t[NJ], c[NJ], q[NJ], ita[NJ], nf[NJ], old[NJ];
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        const int g = l + 8 * j;
+        const size_t a = (size_t)r * Gp + g;
+        t[j] = c[j] = q[j] = ita[j] = nf[j] = old[j] = (Real)0;
+        if (g < Gp) {
+          t[j] = tsum[a];
+          if (TM == 1) c[j] = tcomp[a];
+          q[j] = xsq[a].y;
+          ita[j] = inv_ta[a];
+          if (g < G) nf[j] = nsf[m * G + g];
+          if (!eigen) old[j] = phi[a];
         }
-        phi[a] = ph;
-        f += nsf[m * G + g] * ph;
+      }
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        const int g = l + 8 * j;
+        const size_t a = (size_t)r * Gp + g;
+        if (g < Gp) {
+          tsum[a] = (Real)0;
+          if (TM == 1) tcomp[a] = (Real)0;
+        }
+        if (g < G) {
+          const Real ph = fma(TM == 1 ? t[j] + c[j] : t[j], ita[j], (Real)kFourPi * q[j]);
+          if (!eigen && ph > (Real)0) res = fmax(res, fabs(ph - old[j]) / ph);
+          phi[a] = ph;
+          f += nf[j] * ph;
+        }
+      }
+    } else if (live) {
+      const int m = mat[r];
+      for (int j = 0; j < gpl; ++j) {
+        const int g = l + 8 * j;
+        if (g >= Gp) break;
+        const size_t a = (size_t)r * Gp + g;
+        const typename Pair<Real>::T v = xsq[a];
+        Real t = tsum[a];
+        tsum[a] = (Real)0;
+        if (TM == 1) {
+          t += tcomp[a];
+          tcomp[a] = (Real)0;
+        }
+        if (g < G) {
+          const Real ph = fma(t, inv_ta[a], (Real)kFourPi * v.y);
+          if (!eigen) {
+            const Real old = phi[a];
+            if (ph > (Real)0) res = fmax(res, fabs(ph - old) / ph);
+          }
+          phi[a] = ph;
+          f += nsf[m * G + g] * ph;
+        }
       }
     }
-  }
 #pragma unroll
-  for (int o = 4; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
-  if (!eigen) {
+    for (int o = 4; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+    if (!eigen) {
 #pragma unroll
-    for (int o = 4; o > 0; o >>= 1) res = fmax(res, __shfl_xor_sync(0xffffffffu, res, o));
+      for (int o = 4; o > 0; o >>= 1) res = fmax(res, __shfl_xor_sync(0xffffffffu, res, o));
+    }
+    if (l == 0 && live) {
+      g_sum += area[r] * (double)f;
+      if (eigen && f > (Real)0) {
+        const Real rho = (Real)fold[r] / f;
+        g_min = fmin(g_min, rho);
+        g_max = fmax(g_max, rho);
+      }
+      g_res = fmax(g_res, res);
+    }
   }
   if (l == 0) {
-    const int q = threadIdx.x >> 3;
-    const bool fis = live && eigen && f > (Real)0;
-    const Real rho = fis ? (Real)fold[r] / f : (Real)0;
-    l_sum[q] = live ? area[r] * (double)f : 0.0;
-    l_min[q] = fis ? rho : (Real)INFINITY;
-    l_max[q] = fis ? rho : (Real)-INFINITY;
-    l_res[q] = res;
+    l_sum[qg] = g_sum;
+    l_min[qg] = g_min;
+    l_max[qg] = g_max;
+    l_res[qg] = g_res;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     double a = 0.0;
     Real mn = (Real)INFINITY, mx = (Real)-INFINITY, rs = 0;
-    for (int q = 0; q < (int)(blockDim.x >> 3); ++q) {
+    for (int q = 0; q < 32; ++q) {
       a += l_sum[q];
       mn = fmin(mn, l_min[q]);
       mx = fmax(mx, l_max[q]);
@@ -807,6 +899,8 @@ __device__ __forceinline__ void reduce_partials(int nb, const double *__restrict
                                                 int eigen) {
   __shared__ double s_sum[256], s_min[256], s_max[256], s_res[256];
   double a = 0.0, mn = INFINITY, mx = -INFINITY, rs = 0.0;
+  // unrolled so that many partials' loads are in flight at once (the sum's order is unchanged)
+#pragma unroll 8
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {
     a += part[4 * b];
     mn = fmin(mn, part[4 * b + 1]);
