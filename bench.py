@@ -65,8 +65,14 @@ IMPL_OPS_PER_UPDATE = 18
 # FP64 peak: the nominal 1.25 TFLOP/s of the part, i.e. 0.625e12 fused multiply-adds per second
 FP64_FMA_NOMINAL = 0.625e12
 # DRAM bytes (read + write) and L2 sector hit rate of one sweep launch, from ncu on the named
-# workload with the current kernel version; absent entries are reported as null.
-SWEEP_NCU = {}
+# workload with the current kernel versions (the hex core's DRAM counters are single-pass captures
+# of the full-size launch; its hit rate needs three passes, so it was captured on the seven-hexagon
+# case only); absent entries are reported as null.
+SWEEP_NCU = {
+    ("hexcore", "fp32"): {"dram_bytes": 36.32e9 + 17.49e9, "l2_hit_pct": None},
+    ("hexcore7", "fp32"): {"dram_bytes": 8.295e9 + 3.866e9, "l2_hit_pct": 58.4},
+    ("assembly", "fp32"): {"dram_bytes": 82.31e6 + 2.80e6, "l2_hit_pct": 73.5},
+}
 
 
 def measured_rates(device: int) -> dict:
