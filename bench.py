@@ -10,7 +10,8 @@ Prints one JSON line (rank 0). Under torchrun each rank runs an independent repl
 GPU (the sweep has no data-path exchange); value = all ranks' updates / max time. Beside the
 headline the line carries, for context: the FP64 mode with its own roofline, the time to a
 converged k (CMFD-accelerated, FP32 and FP64), the 17x17 assembly measured the same way with its
-plain and accelerated time to k, the learned warm start against the cold starts and the no-network
+plain and accelerated time to k and its FP64 rate, the 3x3-assembly core and the pin cell in FP32
+and FP64, the learned warm start against the cold starts and the no-network
 ablation on held-out assembly instances, a DGMOC block (the assembly extruded to `--axial` planes),
 host against device tracking, the hardware rate probes behind the roofline denominators and the
 CPU oracle timed on a bounded sample at one thread and at all host cores.
@@ -509,6 +510,19 @@ def workload_block(moc, prob, name, precision, local, stream, flush, steps, warm
     return out
 
 
+def fp64_block(moc, prob, name, local, stream, flush, steps, n_sm, rates):
+    """The FP64 mode of a workload: outers per second and the sweep's FP64 roofline."""
+    m = moc.Moc.from_problem(prob, device=local, precision="fp64", stream=stream.cuda_stream)
+    _, ups, _ = m.work()
+    timed_outers(m, stream, flush, 1)
+    ms = timed_outers(m, stream, flush, steps)
+    sw = sweep_seconds(m, stream, flush, 1)
+    out = {"value": ups * steps / (ms / 1e3), "ms_per_step": ms / steps,
+           "roofline": roofline(prob, m, "fp64", sw, ups, name, n_sm, rates)}
+    m.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -522,6 +536,8 @@ def main():
     ap.add_argument("--no-time-to-k", action="store_true")
     ap.add_argument("--no-tracking", action="store_true", help="skip the host vs device tracking timing")
     ap.add_argument("--no-assembly", action="store_true", help="skip the 17x17 assembly block")
+    ap.add_argument("--no-other-workloads", action="store_true",
+                    help="skip the core and pin-cell blocks (FP32 and FP64 outers of the other configurations)")
     ap.add_argument("--warm-eval", type=int, default=20, metavar="N",
                     help="held-out instances of the learned warm-start block (0 skips it)")
     ap.add_argument("--no-rates", action="store_true", help="skip the hardware rate probes")
@@ -649,6 +665,24 @@ def main():
         if not args.no_time_to_k:
             assembly["time_to_k"] = time_to_converged_k(moc, aprob, local, stream, cm_params("assembly"), plain=True)
 
+    # the other configurations of the scope table, FP32 and FP64: the 3x3-assembly core and the
+    # pin cell (the assembly block above has its FP64 rate too)
+    others = None
+    if extra and not args.no_other_workloads and not args.aniso and not args.cmfd:
+        others = {}
+        for name in ("core", "pin"):
+            if name == args.workload:
+                continue
+            oprob = make_problem(name)
+            blk = workload_block(moc, oprob, name, args.precision, local, stream, flush, args.steps, args.warmup,
+                                 n_sm, rates or {})
+            if args.fp64_steps > 0:
+                blk["fp64"] = fp64_block(moc, oprob, name, local, stream, flush, args.fp64_steps, n_sm, rates or {})
+            others[name] = blk
+    if assembly is not None and args.fp64_steps > 0:
+        assembly["fp64"] = fp64_block(moc, make_problem("assembly"), "assembly", local, stream, flush,
+                                      args.fp64_steps, n_sm, rates or {})
+
     # learned warm start on held-out assembly instances (the shipped network)
     warm = None
     if extra and args.warm_eval > 0 and not args.aniso and not args.cmfd:
@@ -714,6 +748,7 @@ def main():
         "fp64": fp64,
         "time_to_k": time_to_k,
         "assembly": assembly,
+        "other_workloads": others,
         "warm_start": warm,
         "tracking": tracking,
         "dgmoc": dgmoc,

@@ -50,8 +50,9 @@ typedef enum {
 /* Arithmetic of the sweep.
  *   MOC_FP64       : FP64 sweep, FP64 exponential, FP64 tallies.
  *   MOC_FP32       : FP32 sweep with the library's own FP32 evaluation of 1 - exp(-tau) and
- *                    compensated FP32 region tallies (a TwoSum error term per atomic update,
- *                    folded in FP64); FP64 source normalisation, k and norms.
+ *                    Kahan-compensated FP32 region tallies (the rounding error of every atomic
+ *                    update, x - (fl(old + x) - old), accumulated in a second array and folded
+ *                    in at the finalize); FP64 source normalisation, k and norms.
  *   MOC_FP32_PLAIN : as MOC_FP32 with plain FP32 atomic tallies (no compensation). */
 enum { MOC_FP64 = 0, MOC_FP32 = 1, MOC_FP32_PLAIN = 2 };
 

