@@ -180,3 +180,13 @@ def test_power_iterate_rejects_bad_arguments(lib, tol_k, tol_flux, max_outer, ch
     with pytest.raises(moc.MocError) as e:
         m.power_iterate(1e-6, 1e-6, 10, check_every=1)
     assert e.value.code == -4
+
+
+def test_rate_probe_rejects_unknown_kinds_and_devices(lib):
+    """The rate probes validate their arguments before touching a device."""
+    import ctypes
+
+    d = ctypes.c_double()
+    assert lib.moc_probe_rate(0, -1, ctypes.byref(d), None, None) == -1
+    assert lib.moc_probe_rate(0, len(moc.PROBES), ctypes.byref(d), None, None) == -1
+    assert lib.moc_probe_rate(-1, 0, ctypes.byref(d), None, None) == -1

@@ -117,3 +117,17 @@ def test_history_ring_keeps_the_last_4096_checks_in_order():
     assert h.shape == (4096, 4)
     np.testing.assert_array_equal(h[:, 0], np.arange(5, 4101, dtype=float))   # oldest first after wrapping
     assert np.array_equal(m.history(3), h[-3:])
+
+
+def test_rate_probes_measure_positive_rates():
+    """Every hardware rate probe runs, reports the device's multiprocessor count, positive lane
+    rates, and sector rates consistent with its access shape."""
+    for kind in moc.PROBES:
+        r = moc.probe_rate(kind, 0)
+        assert r["sm_count"] > 0
+        assert r["lane_ops_per_s"] > 0, kind
+        if kind in ("ffma", "dfma"):
+            assert r["sectors_per_s"] == 0.0
+        else:
+            per = {"red_f32x4_pair": 0.5, "red_f32_row8": 0.125}.get(kind, 1.0)
+            assert abs(r["sectors_per_s"] - per * r["lane_ops_per_s"]) <= 1e-9 * r["lane_ops_per_s"], kind
