@@ -1089,6 +1089,8 @@ const void *host_view(const moc_ctx *c, const void *p) {
 
 // The caller's state read in place by one kernel; in eigenvalue mode the kernel also sums the
 // fission source F of the state and sets the normalisation 1/F itself (no host pass over phi).
+// Pinned arrays are read by the kernel over the host link directly: staging them on the device
+// through the copy engine first was measured slower for the 0.55 GB state of the 199-assembly core.
 template <typename Real> int state_in(moc_ctx *c, const double *dphi, const double *dpsi, double k) {
   const int R = c->geo.n_tri;
   const long long n = std::max<long long>(1, (long long)R * c->Gp + c->T * 2 * c->P * c->G);

@@ -52,10 +52,14 @@ def test_state_round_trip(precision, memory):
     assert k2 == 1.234
     np.testing.assert_allclose(phi2, phi / F, rtol=tol)
     np.testing.assert_allclose(psi2, psi_exp, rtol=tol, atol=0)
-    # the same outers from pinned and from pageable copies of one state agree (up to the order
-    # of the sweep's atomic additions)
+    # the same outers from pinned and from pageable copies of one state agree up to the order
+    # of the sweep's atomic additions: in FP64 that order moves k by rounding only; in FP32 the
+    # compensated tally (one Fast2Sum step per addition) is exact only while the running sum
+    # outweighs the addend, so a different order leaves a residue near 2^-24 per region tally,
+    # about 1e-10 of k after two outers
     m.set_state(phi, 1.234, psi)
     k_a, _ = m.outer(2)
     m.set_state(np.array(phi), 1.234, np.array(psi))
     k_b, _ = m.outer(2)
-    assert abs(k_a - k_b) <= 1e-13 * k_a
+    rep = 1e-13 if precision == "fp64" else 1e-8
+    assert abs(k_a - k_b) <= rep * k_a
