@@ -333,6 +333,13 @@ int moc_ws_apply(moc_ctx *ctx, const float *pred_dev, double *k_out);
  * approximation error against an FP64 reference. Errors: MOC_ERR_ARG, MOC_ERR_CUDA. */
 int moc_eval_one_minus_exp_f32(int device, const float *tau, float *out, int64_t n);
 
+/* The same function in its packed form, two values per f32x2 multiply, add and fused multiply-add
+ * (as the FP32 sweeps evaluate it): each component is rounded as in the scalar form, so out equals
+ * moc_eval_one_minus_exp_f32's output bit for bit. Both ways the sweeps form the scale 2^-n (an
+ * integer multiply-add, or a shift and subtract) are evaluated; out[i] is NaN where they differ.
+ * Host buffers; synchronous. Errors: MOC_ERR_ARG, MOC_ERR_CUDA. */
+int moc_eval_one_minus_exp_f32x2(int device, const float *tau, float *out, int64_t n);
+
 /* Wait for all work enqueued on the context's stream. */
 int moc_synchronize(moc_ctx *ctx);
 

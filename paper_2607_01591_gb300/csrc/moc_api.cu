@@ -628,13 +628,13 @@ template <typename Real, int TM, bool CM> int launch_sweep_p(moc_ctx *c, cudaStr
   return MOC_OK;
 }
 
-// FP32 with 3 polar angles and G > 8: ceil(G / 4) four-group lanes per track end
-template <int TM> int launch_chunk(moc_ctx *c, cudaStream_t st) {
-  const int lanes = (c->G + 3) / 4;
+// FP32 with 3 polar angles: ceil(G / (2 NP)) lanes of NP group pairs per track end
+template <int TM, int NP = 2> int launch_chunk(moc_ctx *c, cudaStream_t st) {
+  const int lanes = (c->G + 2 * NP - 1) / (2 * NP);
   const long long n = (long long)c->T * 2 * lanes;
   PolarInv<3> is;
   for (int p = 0; p < 3; ++p) is.v[p] = (float)(1.0 / c->geo.sin_theta[p]);
-  sweep_chunk_kernel<3, TM><<<(unsigned)((n + 63) / 64), 64, 0, st>>>(
+  sweep_chunk_kernel<3, TM, NP><<<(unsigned)((n + 63) / 64), 64, 0, st>>>(
       c->d_trk, (const SegRec<float> *)c->d_seg, c->d_link, (const float *)c->d_wgt, is, (const float2 *)c->d_xsq,
       (float *)c->d_tsum, (float *)c->d_tcomp, (const float *)c->d_psi[c->cur], (float *)c->d_psi[c->cur ^ 1],
       c->d_scal, n, c->G, c->Gp, lanes);
@@ -2363,6 +2363,23 @@ int moc_eval_one_minus_exp_f32(int device, const float *tau, float *out, int64_t
   cudaError_t e = cudaMemcpy(d, tau, (size_t)n * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
     eval_exp_kernel<<<(unsigned)((n + 255) / 256), 256>>>(d, d + n, n);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(out, d + n, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  return e == cudaSuccess ? MOC_OK : MOC_ERR_CUDA;
+}
+
+int moc_eval_one_minus_exp_f32x2(int device, const float *tau, float *out, int64_t n) {
+  if (device < 0 || n < 0 || (n > 0 && (!tau || !out))) return MOC_ERR_ARG;
+  if (n == 0) return MOC_OK;
+  if (cudaSetDevice(device) != cudaSuccess) return MOC_ERR_CUDA;
+  float *d = nullptr;
+  if (cudaMalloc(&d, 2 * (size_t)n * sizeof(float)) != cudaSuccess) return MOC_ERR_OOM;
+  cudaError_t e = cudaMemcpy(d, tau, (size_t)n * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    const long long pairs = (n + 1) / 2;
+    eval_exp2_kernel<<<(unsigned)((pairs + 255) / 256), 256>>>(d, d + n, n);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemcpy(out, d + n, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost);

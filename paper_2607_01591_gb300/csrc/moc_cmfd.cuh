@@ -340,7 +340,10 @@ __global__ void __launch_bounds__(1024, 1) cmfd_solve_cluster_kernel(CmfdTopo t,
     return m;
   };
   double kc = scal[S_K];
-  // 2. coarse power iteration
+  // 2. coarse power iteration. The fission sum that ends an iteration is, operation for operation,
+  // the one that starts the next (same cells, same threads, same order), so it is carried over
+  // instead of reduced again.
+  double F_carry = 0.0;
   for (int it = 0; it < n_outer; ++it) {
     double fsum = 0.0;
     for (int li = threadIdx.x; li < nc; li += blockDim.x) {
@@ -350,7 +353,7 @@ __global__ void __launch_bounds__(1024, 1) cmfd_solve_cluster_kernel(CmfdTopo t,
       fis[i] = f;
       fsum += (double)f;
     }
-    const double F_old = cluster_sum(fsum);
+    const double F_old = it == 0 ? cluster_sum(fsum) : F_carry;
     const Real inv_k = (Real)(1.0 / kc);
     for (int g = 0; g < G; ++g) {
       for (int li = threadIdx.x; li < nc; li += blockDim.x) {
@@ -380,8 +383,10 @@ __global__ void __launch_bounds__(1024, 1) cmfd_solve_cluster_kernel(CmfdTopo t,
           cluster.sync();
         }
       }
+      // no barrier here: the last colour sweep's barrier already ended every remote read of this
+      // group's iterate, and each thread reads back (next group's staging, the fission sums) only
+      // the owned cells it writes itself
       for (int li = threadIdx.x; li < nc; li += blockDim.x) phic[(size_t)g * N + own[li]] = s_x[li];
-      cluster.sync();  // remote readers are done with this group's iterate; phic written
     }
     fsum = 0.0;
     for (int li = threadIdx.x; li < nc; li += blockDim.x) {
@@ -391,6 +396,7 @@ __global__ void __launch_bounds__(1024, 1) cmfd_solve_cluster_kernel(CmfdTopo t,
       fsum += (double)f;
     }
     const double F_new = cluster_sum(fsum);
+    F_carry = F_new;
     const double k_prev = kc;
     if (F_new > 0.0 && F_old > 0.0) kc = kc * F_new / F_old;
     if (tol > 0.0 && F_new > 0.0 && F_old > 0.0) {

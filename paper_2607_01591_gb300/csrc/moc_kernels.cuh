@@ -57,17 +57,64 @@ __device__ __forceinline__ float one_minus_exp(float tau) {
   const float r = fmaf(n, -0.693147182464599609375f, tau);
   const float h = fmaf(fmaf(fmaf(fmaf(MOC_EXP_H4, r, MOC_EXP_H3), r, MOC_EXP_H2), r, MOC_EXP_H1), r, MOC_EXP_H0);
   const float p = fmaf(r * r, h, r);                   // 1 - exp(-r)
-  // 2^-n from the bits of t (0x4B400000 + n): 0x3F800000 - n * 2^23 as one unsigned (wrapping)
-  // multiply-add: (0x4B400000 + n) * (2^32 - 2^23) = -n * 2^23 modulo 2^32
-  const float sc = __uint_as_float((unsigned)__float_as_int(t) * 0xFF800000u + 0x3F800000u);
+  // 2^-n from the bits of t (0x4B400000 + n): 0x3F800000 - n * 2^23, where n * 2^23 modulo 2^32
+  // is the bits of t shifted left by 23 (the shift drops 0x4B400000); a funnel shift and an
+  // integer subtract, both on the ALU pipe, which leaves the FMA pipe to the arithmetic
+  const float sc = __uint_as_float(0x3F800000u - __funnelshift_l(0u, __float_as_uint(t), 23));
   return fmaf(sc, p, 1.0f - sc);
 }
 
 __device__ __forceinline__ double one_minus_exp(double tau) { return -expm1(-tau); }
 
+// Packed FP32 pairs: the f32x2 multiply, add and fused multiply-add of sm_100 and later round each
+// component exactly as the scalar instruction does, so a pair of updates computed this way gives
+// the scalar results bit for bit in half the issue slots. a - b is formed as fma(b, -1, a), which
+// rounds a - b once, like the scalar subtraction.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }
+
+// one_minus_exp on a pair, step for step the scalar evaluation above. 2^-n comes either from one
+// integer multiply-add per lane (ALU_SCALE = false): (0x4B400000 + n) * (2^32 - 2^23) + 0x3F800000
+// = 0x3F800000 - n * 2^23 modulo 2^32; or from the scalar form's funnel shift and subtract on the
+// ALU pipe (true). The bits are the same; which balances the pipes better depends on the kernel
+// around it (measured: the many-group sweep prefers the multiply-add, the polar-pair sweep the
+// shift).
+template <bool ALU_SCALE> __device__ __forceinline__ float2 one_minus_exp(float2 tau) {
+  tau.x = fminf(tau.x, 80.0f);
+  tau.y = fminf(tau.y, 80.0f);
+  const float2 t = fma2(tau, f2(1.44269504088896341f), f2(12582912.0f));
+  const float2 n = add2(t, f2(-12582912.0f));
+  const float2 r = fma2(n, f2(-0.693147182464599609375f), tau);
+  const float2 h =
+      fma2(fma2(fma2(fma2(f2(MOC_EXP_H4), r, f2(MOC_EXP_H3)), r, f2(MOC_EXP_H2)), r, f2(MOC_EXP_H1)), r, f2(MOC_EXP_H0));
+  const float2 p = fma2(mul2(r, r), h, r);
+  float2 sc;
+  if constexpr (ALU_SCALE) {
+    sc = make_float2(__uint_as_float(0x3F800000u - __funnelshift_l(0u, __float_as_uint(t.x), 23)),
+                     __uint_as_float(0x3F800000u - __funnelshift_l(0u, __float_as_uint(t.y), 23)));
+  } else {
+    sc = make_float2(__uint_as_float((unsigned)__float_as_int(t.x) * 0xFF800000u + 0x3F800000u),
+                     __uint_as_float((unsigned)__float_as_int(t.y) * 0xFF800000u + 0x3F800000u));
+  }
+  return fma2(sc, p, sub2(f2(1.0f), sc));
+}
+
 __global__ void eval_exp_kernel(const float *__restrict__ tau, float *__restrict__ out, long long n) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = one_minus_exp(tau[i]);
+}
+
+__global__ void eval_exp2_kernel(const float *__restrict__ tau, float *__restrict__ out, long long n) {
+  const long long i = 2 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+  if (i >= n) return;
+  const float2 a = make_float2(tau[i], i + 1 < n ? tau[i + 1] : 0.0f);
+  const float2 v = one_minus_exp<false>(a), u = one_minus_exp<true>(a);
+  // the two ways of forming 2^-n must agree bit for bit; a difference is reported as NaN
+  out[i] = __float_as_uint(v.x) == __float_as_uint(u.x) ? v.x : __uint_as_float(0x7FC00000u);
+  if (i + 1 < n) out[i + 1] = __float_as_uint(v.y) == __float_as_uint(u.y) ? v.y : __uint_as_float(0x7FC00000u);
 }
 
 // ----------------------------------------------------------------------------- source update
@@ -471,12 +518,34 @@ __global__ void __launch_bounds__(128, CM ? 8 : 9) sweep_kernel(
     const typename Pair<Real>::T xq2 = xsq[(size_t)s2.r * Gp + g];
     const Real tau0 = xq0.x * s0.l;
     Real acc = 0;
+    if constexpr (sizeof(Real) == 4) {
+      // FP32: polar angles p, p + 1 as the two lanes of packed f32x2 operations (the same
+      // roundings as the scalar loop, so the same results), an odd last angle alone
 #pragma unroll
-    for (int p = 0; p < P; ++p) {
-      const Real F = one_minus_exp(tau0 * is[p]);
-      const Real dl = (psi[p] - xq0.y) * F;
-      psi[p] -= dl;
-      acc = fma(w[p], dl, acc);
+      for (int p = 0; p + 1 < P; p += 2) {
+        const float2 F = one_minus_exp<true>(mul2(f2(tau0), make_float2(is[p], is[p + 1])));
+        const float2 ps = make_float2(psi[p], psi[p + 1]);
+        const float2 dl = mul2(sub2(ps, f2(xq0.y)), F);
+        const float2 pn = sub2(ps, dl);
+        psi[p] = pn.x;
+        psi[p + 1] = pn.y;
+        acc = fmaf(w[p], dl.x, acc);
+        acc = fmaf(w[p + 1], dl.y, acc);
+      }
+      if constexpr ((P & 1) != 0) {
+        const float F = one_minus_exp(tau0 * is[P - 1]);
+        const float dl = (psi[P - 1] - xq0.y) * F;
+        psi[P - 1] -= dl;
+        acc = fmaf(w[P - 1], dl, acc);
+      }
+    } else {
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const Real F = one_minus_exp(tau0 * is[p]);
+        const Real dl = (psi[p] - xq0.y) * F;
+        psi[p] -= dl;
+        acc = fma(w[p], dl, acc);
+      }
     }
     tally.add(tsum, tcomp, (unsigned)(s0.r * Gp + g), acc);
     if (CM && n == xt) {
@@ -511,102 +580,140 @@ __global__ void __launch_bounds__(128, CM ? 8 : 9) sweep_kernel(
   }
 }
 
-// FP32 sweep for many groups (G > 8): one thread per (track, sense, chunk of four groups), the
-// chunk fastest, so the ceil(G / 4) threads of a track end sit side by side in a warp and read one
-// region row together. All P polar angles stay in registers; region rows are read as two 128-bit
-// loads of {Sigma_t, q/Sigma_t} pairs and the tallies are added with one float4 atomic, so the
-// per-segment cost (segment record, addresses, loop, atomics) is shared by 4 P updates. The last
-// chunk of a G that is not a multiple of 4 carries padding groups (Sigma_t = 1, q = 0, no inflow),
-// whose updates are zero. The segment array carries kSegPad padding records at each end, so the
-// two-ahead prefetch never needs a bounds test. 1/sin(theta_p) arrive as kernel parameters
-// (uniform over the grid, no registers or loads).
+// FP32 sweep with packed pairs of groups: one thread per (track, sense, chunk of 2 NP groups), the
+// chunk fastest, so the threads of a track end sit side by side in a warp and read one region row
+// together. All P polar angles stay in registers; each pair of groups is one f32x2 lane of every
+// operation, region rows are read as 128-bit loads of {Sigma_t, q/Sigma_t} pairs and the tallies
+// are added with one float4 (NP = 2) or float2 (NP = 1) atomic, so the per-segment cost (segment
+// record, addresses, loop, atomics) is shared by 2 NP P updates. The last chunk of a G that is not
+// a multiple of 2 NP carries padding groups (Sigma_t = 1, q = 0, no inflow), whose updates are
+// zero. The segment array carries kSegPad padding records at each end, so the two-ahead prefetch
+// never needs a bounds test. 1/sin(theta_p) arrive as kernel parameters (uniform over the grid,
+// no registers or loads).
 // Kahan's compensation step (Dekker's Fast2Sum) per lane: the rounding error (old + x) -
 // fl(old + x) of the atomic add, exact whenever |old| >= |x| (see Tally<1, float>).
 __device__ __forceinline__ float add_err(float o, float x) { return x - ((o + x) - o); }
 
+__device__ __forceinline__ float2 add_err(float2 o, float2 x) { return sub2(x, sub2(add2(o, x), o)); }
+
 __device__ __forceinline__ float4 add_err(float4 o, float4 x) {
-  return make_float4(add_err(o.x, x.x), add_err(o.y, x.y), add_err(o.z, x.z), add_err(o.w, x.w));
+  const float2 lo = add_err(make_float2(o.x, o.y), make_float2(x.x, x.y));
+  const float2 hi = add_err(make_float2(o.z, o.w), make_float2(x.z, x.w));
+  return make_float4(lo.x, lo.y, hi.x, hi.y);
 }
 
 template <int P> struct PolarInv {
   float v[P];
 };
 
-template <int P, int TM>
+// The tally vector of NP group pairs: one float4 (NP = 2) or one float2 (NP = 1) per lane.
+template <int NP> struct PairVec;
+template <> struct PairVec<2> {
+  using T = float4;
+  __device__ __forceinline__ static T make(const float2 (&a)[2]) { return make_float4(a[0].x, a[0].y, a[1].x, a[1].y); }
+  __device__ __forceinline__ static T zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+};
+template <> struct PairVec<1> {
+  using T = float2;
+  __device__ __forceinline__ static T make(const float2 (&a)[1]) { return a[0]; }
+  __device__ __forceinline__ static T zero() { return make_float2(0.f, 0.f); }
+};
+
+template <int P, int TM, int NP>
 __global__ void __launch_bounds__(64, 16) sweep_chunk_kernel(
     const TrackRec *__restrict__ trk, const SegRec<float> *__restrict__ seg, const int32_t *__restrict__ link,
     const float *__restrict__ wgt, const PolarInv<P> is, const float2 *__restrict__ xsq, float *__restrict__ tsum,
     float *__restrict__ tcomp, const float *__restrict__ psi_in, float *__restrict__ psi_out,
     const double *__restrict__ scal, long long n_threads, int G, int Gp, int lanes) {
+  using V = typename PairVec<NP>::T;
+  constexpr int GPT = 2 * NP;  // groups per thread
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n_threads) return;
   const long long td = idx / lanes;
-  const int g0 = (int)(idx - td * lanes) * 4;
+  const int g0 = (int)(idx - td * lanes) * GPT;
   const TrackRec tr = trk[td >> 1];
   const int d = (int)(td & 1);
   const float scale = (float)scal[S_SCALE];
-  float psi[4][P], w[P];
+  // pair j holds groups g0 + 2j and g0 + 2j + 1
+  float2 psi[NP][P];
+  float w[P];
 #pragma unroll
   for (int p = 0; p < P; ++p) {
     w[p] = wgt[tr.dir * P + p];
+    const float *src = psi_in + (td * P + p) * G + g0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) psi[k][p] = (g0 + k < G) ? psi_in[(td * P + p) * G + g0 + k] * scale : 0.0f;
+    for (int j = 0; j < NP; ++j)
+      psi[j][p] = make_float2((g0 + 2 * j < G) ? src[2 * j] * scale : 0.0f,
+                              (g0 + 2 * j + 1 < G) ? src[2 * j + 1] * scale : 0.0f);
   }
   const int step = d ? -1 : 1;
   const SegRec<float> *sp = seg + (d ? tr.off + tr.n - 1 : tr.off);
   const float4 *rows = reinterpret_cast<const float4 *>(xsq + g0);
   const int rstride = Gp / 2;  // float4 per region row
   SegRec<float> s0 = sp[0], s1 = sp[step];
-  float4 r0a = rows[(size_t)s0.r * rstride], r0b = rows[(size_t)s0.r * rstride + 1];
-  float4 *tsum4 = reinterpret_cast<float4 *>(tsum + g0);
-  float4 *tcomp4 = reinterpret_cast<float4 *>(tcomp + g0);
-  const int tstride = Gp / 4;
+  float4 r0[NP];
+#pragma unroll
+  for (int j = 0; j < NP; ++j) r0[j] = rows[(size_t)s0.r * rstride + j];
+  V *tsumv = reinterpret_cast<V *>(tsum + g0);
+  V *tcompv = reinterpret_cast<V *>(tcomp + g0);
+  const int tstride = Gp / GPT;
   // compensated mode: the old values returned by this segment's atomic become rounding errors one
   // segment later, so the atomic's latency overlaps the next segment's arithmetic
-  float4 p_old = make_float4(0.f, 0.f, 0.f, 0.f), p_x = p_old;
+  V p_old = PairVec<NP>::zero(), p_x = p_old;
   size_t p_a = (size_t)s0.r * tstride;
   for (int n = 0; n < tr.n; ++n) {
     const SegRec<float> s2 = sp[2 * step];
-    const float4 r1a = rows[(size_t)s1.r * rstride], r1b = rows[(size_t)s1.r * rstride + 1];
-    const float sig[4] = {r0a.x, r0a.z, r0b.x, r0b.z}, qr[4] = {r0a.y, r0a.w, r0b.y, r0b.w};
-    float acc[4];
+    float4 r1[NP];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const float tau0 = sig[k] * s0.l;
-      acc[k] = 0.0f;
+    for (int j = 0; j < NP; ++j) r1[j] = rows[(size_t)s1.r * rstride + j];
+    // a region row holds {Sigma_t, q/Sigma_t} per group: pair the two groups of each float4
+    const float2 l2 = f2(s0.l);
+    float2 tau[NP], q[NP], acc[NP];
 #pragma unroll
-      for (int p = 0; p < P; ++p) {
-        const float F = one_minus_exp(tau0 * is.v[p]);
-        const float dl = (psi[k][p] - qr[k]) * F;
-        psi[k][p] -= dl;
-        acc[k] = fmaf(w[p], dl, acc[k]);
+    for (int j = 0; j < NP; ++j) {
+      tau[j] = mul2(make_float2(r0[j].x, r0[j].z), l2);
+      q[j] = make_float2(r0[j].y, r0[j].w);
+      acc[j] = f2(0.0f);
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        const float2 F = one_minus_exp<false>(mul2(tau[j], f2(is.v[p])));
+        const float2 dl = mul2(sub2(psi[j][p], q[j]), F);
+        psi[j][p] = sub2(psi[j][p], dl);
+        acc[j] = fma2(f2(w[p]), dl, acc[j]);
       }
     }
     const size_t a = (size_t)s0.r * tstride;
-    const float4 x = make_float4(acc[0], acc[1], acc[2], acc[3]);
+    const V x = PairVec<NP>::make(acc);
     if (TM == 1) {
-      const float4 o = atomicAdd(tsum4 + a, x);
-      atomicAdd(tcomp4 + p_a, add_err(p_old, p_x));
+      const V o = atomicAdd(tsumv + a, x);
+      atomicAdd(tcompv + p_a, add_err(p_old, p_x));
       p_old = o;
       p_x = x;
     } else {
-      atomicAdd(tsum4 + a, x);
+      atomicAdd(tsumv + a, x);
     }
     p_a = a;
     s0 = s1;
     s1 = s2;
-    r0a = r1a;
-    r0b = r1b;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) r0[j] = r1[j];
     sp += step;
   }
-  if (TM == 1) atomicAdd(tcomp4 + p_a, add_err(p_old, p_x));
+  if (TM == 1) atomicAdd(tcompv + p_a, add_err(p_old, p_x));
   const int e = link[td];
   if (e >= 0) {
 #pragma unroll
-    for (int p = 0; p < P; ++p)
+    for (int p = 0; p < P; ++p) {
+      float *dst = psi_out + ((long long)e * P + p) * G + g0;
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if (g0 + k < G) psi_out[((long long)e * P + p) * G + g0 + k] = psi[k][p];
+      for (int j = 0; j < NP; ++j) {
+        if (g0 + 2 * j < G) dst[2 * j] = psi[j][p].x;
+        if (g0 + 2 * j + 1 < G) dst[2 * j + 1] = psi[j][p].y;
+      }
+    }
   }
 }
 

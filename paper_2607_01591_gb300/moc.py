@@ -111,6 +111,8 @@ def load_library(path: Optional[str] = None):
             "moc_mlp_forward_noalloc": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, _vp]),
             "moc_eval_one_minus_exp_f32": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_float),
                                                           ctypes.POINTER(ctypes.c_float), ctypes.c_int64]),
+            "moc_eval_one_minus_exp_f32x2": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_float),
+                                                            ctypes.POINTER(ctypes.c_float), ctypes.c_int64]),
             "moc_probe_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _d, _d, ctypes.POINTER(ctypes.c_int)]),
         }
         for name, (res, args) in sig.items():
@@ -213,15 +215,16 @@ class Mlp:
         return g, loss.value
 
 
-def eval_one_minus_exp_f32(tau: np.ndarray, device: int = 0) -> np.ndarray:
-    """The library's FP32 1 - exp(-tau) evaluated on the GPU."""
+def eval_one_minus_exp_f32(tau: np.ndarray, device: int = 0, packed: bool = False) -> np.ndarray:
+    """The library's FP32 1 - exp(-tau) evaluated on the GPU (packed: its f32x2 form)."""
     lib = load_library()
     tau = np.ascontiguousarray(tau, dtype=np.float32)
     out = np.empty_like(tau)
     fp = ctypes.POINTER(ctypes.c_float)
-    rc = lib.moc_eval_one_minus_exp_f32(int(device), tau.ctypes.data_as(fp), out.ctypes.data_as(fp), tau.size)
+    name = "moc_eval_one_minus_exp_f32x2" if packed else "moc_eval_one_minus_exp_f32"
+    rc = getattr(lib, name)(int(device), tau.ctypes.data_as(fp), out.ctypes.data_as(fp), tau.size)
     if rc != 0:
-        raise MocError(rc, "moc_eval_one_minus_exp_f32 failed")
+        raise MocError(rc, name + " failed")
     return out
 
 

@@ -177,7 +177,12 @@ def test_fp32_exponential_exhaustive():
     for start in range(lo, hi + 1, chunk):
         bits = np.arange(start, min(start + chunk, hi + 1), dtype=np.int32)
         tau = bits.view(np.float32)
-        got = moc.eval_one_minus_exp_f32(tau).astype(np.float64)
+        got32 = moc.eval_one_minus_exp_f32(tau)
+        # the packed form (two values per f32x2 instruction, the many-group sweep's) is the same
+        # function bit for bit
+        np.testing.assert_array_equal(moc.eval_one_minus_exp_f32(tau, packed=True).view(np.int32),
+                                      got32.view(np.int32))
+        got = got32.astype(np.float64)
         ref = -np.expm1(-tau.astype(np.float64))
         nz = ref > 0
         err = np.abs(got[nz] - ref[nz]) / ref[nz]
