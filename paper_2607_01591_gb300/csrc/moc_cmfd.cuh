@@ -119,6 +119,47 @@ __device__ __forceinline__ double block_max_1024(double v, double *red32) {
 // by the context. SMEM: the per-group working set (source, 1/diagonal, iterate, coefficients,
 // offsets and neighbour ids of type Idx) lives in dynamic shared memory; otherwise in the global
 // scratch.
+// Per-cell sums over the groups, in group order (the same additions as a plain loop), read in
+// batches of 8 predicated loads so that a thread waits for one round trip per batch instead of
+// one per group.
+template <typename Real>
+__device__ __forceinline__ Real cell_fission(const Real *__restrict__ FV, const Real *__restrict__ phic, int G, int N,
+                                             int i) {
+  Real f = 0;
+  for (int g0 = 0; g0 < G; g0 += 8) {
+    Real a[8], b[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const bool in = g0 + u < G;
+      a[u] = in ? FV[(size_t)(g0 + u) * N + i] : (Real)0;
+      b[u] = in ? phic[(size_t)(g0 + u) * N + i] : (Real)0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (g0 + u < G) f += a[u] * b[u];
+  }
+  return f;
+}
+
+// rhs + sum over h != g of Sigma_s(h -> g) V phi_h, in h order, batched as above
+template <typename Real>
+__device__ __forceinline__ Real cell_inscatter(const Real *__restrict__ SV, const Real *__restrict__ phic, int g,
+                                               int G, int N, int i, Real rhs) {
+  for (int h0 = 0; h0 < G; h0 += 8) {
+    Real a[8], b[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const bool in = h0 + u < G && h0 + u != g;
+      a[u] = in ? SV[((size_t)g * G + h0 + u) * N + i] : (Real)0;
+      b[u] = in ? phic[(size_t)(h0 + u) * N + i] : (Real)0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (h0 + u < G && h0 + u != g) rhs += a[u] * b[u];
+  }
+  return rhs;
+}
+
 template <typename Real, bool SMEM, typename Idx>
 __global__ void __launch_bounds__(1024, 1) cmfd_solve_kernel(CmfdTopo t, double *__restrict__ cur, double *__restrict__ leak,
                                                              const Real *__restrict__ cphi, const Real *__restrict__ TV,
@@ -180,8 +221,7 @@ __global__ void __launch_bounds__(1024, 1) cmfd_solve_kernel(CmfdTopo t, double 
   for (int it = 0; it < n_outer; ++it) {
     double fsum = 0.0;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
-      Real f = 0;
-      for (int g = 0; g < G; ++g) f += FV[(size_t)g * N + i] * phic[(size_t)g * N + i];
+      const Real f = cell_fission(FV, phic, G, N, i);
       fis[i] = f;
       fsum += (double)f;
     }
@@ -192,8 +232,7 @@ __global__ void __launch_bounds__(1024, 1) cmfd_solve_kernel(CmfdTopo t, double 
       // coefficients, staged once per group
       for (int i = threadIdx.x; i < N; i += blockDim.x) {
         Real rhs = CHI[(size_t)g * N + i] * fis[i] * inv_k;
-        for (int h = 0; h < G; ++h)
-          if (h != g) rhs += SV[((size_t)g * G + h) * N + i] * phic[(size_t)h * N + i];
+        rhs = cell_inscatter(SV, phic, g, G, N, i, rhs);
         s_src[i] = rhs;
         const Real dg = diag[(size_t)g * N + i];
         s_rd[i] = (dg > (Real)0) ? (Real)1 / dg : (Real)0;
@@ -219,8 +258,7 @@ __global__ void __launch_bounds__(1024, 1) cmfd_solve_kernel(CmfdTopo t, double 
     }
     fsum = 0.0;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
-      Real f = 0;
-      for (int g = 0; g < G; ++g) f += FV[(size_t)g * N + i] * phic[(size_t)g * N + i];
+      const Real f = cell_fission(FV, phic, G, N, i);
       fsum += (double)f;
     }
     const double F_new = block_sum_1024(fsum, red32);
@@ -230,8 +268,7 @@ __global__ void __launch_bounds__(1024, 1) cmfd_solve_kernel(CmfdTopo t, double 
       // stop once k and the normalised coarse fission source have settled to tol
       double dmax = 0.0;
       for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        Real f = 0;
-        for (int g = 0; g < G; ++g) f += FV[(size_t)g * N + i] * phic[(size_t)g * N + i];
+        const Real f = cell_fission(FV, phic, G, N, i);
         if (f > (Real)0) dmax = fmax(dmax, fabs(1.0 - ((double)fis[i] / F_old) * (F_new / (double)f)));
       }
       const double dm = block_max_1024(dmax, red32);
@@ -348,8 +385,7 @@ __global__ void __launch_bounds__(1024, 1) cmfd_solve_cluster_kernel(CmfdTopo t,
     double fsum = 0.0;
     for (int li = threadIdx.x; li < nc; li += blockDim.x) {
       const int i = own[li];
-      Real f = 0;
-      for (int g = 0; g < G; ++g) f += FV[(size_t)g * N + i] * phic[(size_t)g * N + i];
+      const Real f = cell_fission(FV, phic, G, N, i);
       fis[i] = f;
       fsum += (double)f;
     }
@@ -359,8 +395,7 @@ __global__ void __launch_bounds__(1024, 1) cmfd_solve_cluster_kernel(CmfdTopo t,
       for (int li = threadIdx.x; li < nc; li += blockDim.x) {
         const int i = own[li];
         Real rhs = CHI[(size_t)g * N + i] * fis[i] * inv_k;
-        for (int h = 0; h < G; ++h)
-          if (h != g) rhs += SV[((size_t)g * G + h) * N + i] * phic[(size_t)h * N + i];
+        rhs = cell_inscatter(SV, phic, g, G, N, i, rhs);
         s_src[li] = rhs;
         const Real dg = diag[(size_t)g * N + i];
         s_rd[li] = (dg > (Real)0) ? (Real)1 / dg : (Real)0;
@@ -391,8 +426,7 @@ __global__ void __launch_bounds__(1024, 1) cmfd_solve_cluster_kernel(CmfdTopo t,
     fsum = 0.0;
     for (int li = threadIdx.x; li < nc; li += blockDim.x) {
       const int i = own[li];
-      Real f = 0;
-      for (int g = 0; g < G; ++g) f += FV[(size_t)g * N + i] * phic[(size_t)g * N + i];
+      const Real f = cell_fission(FV, phic, G, N, i);
       fsum += (double)f;
     }
     const double F_new = cluster_sum(fsum);
@@ -405,8 +439,7 @@ __global__ void __launch_bounds__(1024, 1) cmfd_solve_cluster_kernel(CmfdTopo t,
       double dmax = 0.0;
       for (int li = threadIdx.x; li < nc; li += blockDim.x) {
         const int i = own[li];
-        Real f = 0;
-        for (int g = 0; g < G; ++g) f += FV[(size_t)g * N + i] * phic[(size_t)g * N + i];
+        const Real f = cell_fission(FV, phic, G, N, i);
         if (f > (Real)0) dmax = fmax(dmax, fabs(1.0 - ((double)fis[i] / F_old) * (F_new / (double)f)));
       }
       const double dm = cluster_max(dmax);
