@@ -1913,7 +1913,7 @@ int moc_set_cmfd(moc_ctx *c, const int32_t *cell_in, int n_cells, int n_outer, i
       }
     }
     for (int b = 0; b < C; ++b) ccoff[(size_t)b * (ncol + 1) + ncol] = (int32_t)own[b].size();
-    std::vector<int32_t> cbase(C + 1, 0), ebase(C + 1, 0), own_cell, eoff, ent, loc;
+    std::vector<int32_t> cbase(C + 1, 0), ebase(C + 1, 0), own_cell, eoff, loc;
     size_t need_max = 0;
     bool fits = true;
     for (int b = 0; b < C; ++b) {
@@ -1924,7 +1924,6 @@ int moc_set_cmfd(moc_ctx *c, const int32_t *cell_in, int n_cells, int n_outer, i
         own_cell.push_back(i);
         for (int q = cif_off[i]; q < cif_off[i + 1]; ++q) {
           const int j = nbr[q];
-          ent.push_back(q);
           loc.push_back((owner[j] << 16) | local[j]);
           ++ne;
         }
@@ -1938,7 +1937,7 @@ int moc_set_cmfd(moc_ctx *c, const int32_t *cell_in, int n_cells, int n_outer, i
       for (int b = 0; b < C; ++b) ncmax = std::max(ncmax, own[b].size());
       for (int b = 0; b < C; ++b) {
         const size_t ne = (size_t)(ebase[b + 1] - ebase[b]);
-        need_max = std::max(need_max, (3 * ncmax + ne) * rs + ne * 4 + (ncmax + 1) * 4);
+        need_max = std::max(need_max, (4 * ncmax + ne) * rs + (ncmax + 1) * 4 + 8 + ne * sizeof(void *));
       }
     }
     int dev_max = 0;
@@ -1964,16 +1963,16 @@ int moc_set_cmfd(moc_ctx *c, const int32_t *cell_in, int n_cells, int n_outer, i
         n_cl = 0;
       }
       if (n_cl >= 1) {
-        // one allocation: cbase | own_cell | ccoff | ebase | eoff | ent | loc
+        // one allocation: cbase | own_cell | ccoff | ebase | eoff | loc
         std::vector<int32_t> all;
         std::vector<size_t> at_off;
-        for (const std::vector<int32_t> *v : {&cbase, &own_cell, &ccoff, &ebase, &eoff, &ent, &loc}) {
+        for (const std::vector<int32_t> *v : {&cbase, &own_cell, &ccoff, &ebase, &eoff, &loc}) {
           at_off.push_back(all.size());
           all.insert(all.end(), v->begin(), v->end());
         }
         if ((rc = upload(c, c->d_cl, all.data(), all.size()))) return rc;
         c->cl = CmfdCluster{c->d_cl + at_off[0], c->d_cl + at_off[1], c->d_cl + at_off[2], c->d_cl + at_off[3],
-                            c->d_cl + at_off[4], c->d_cl + at_off[5], c->d_cl + at_off[6]};
+                            c->d_cl + at_off[4], c->d_cl + at_off[5]};
         c->cm_cluster = C;
         c->cm_cl_smem = need_max;
       }

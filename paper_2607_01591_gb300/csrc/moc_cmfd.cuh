@@ -301,7 +301,6 @@ struct CmfdCluster {
   const int32_t *ccoff;    // [C][n_colors+1] local offsets of each colour within a CTA's cells
   const int32_t *ebase;    // [C+1] owned entries of CTA b
   const int32_t *eoff;     // [sum of cells + C] local entry offsets per owned cell (per CTA)
-  const int32_t *ent;      // [entries] global entry index (for din)
   const int32_t *loc;      // [entries] neighbour's owner CTA << 16 | its local index there
 };
 
@@ -318,7 +317,7 @@ __global__ void __launch_bounds__(1024, 1) cmfd_solve_cluster_kernel(CmfdTopo t,
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks(), b = (int)cluster.block_rank();
   __shared__ double red32[32];
-  __shared__ double s_part;
+  __shared__ double s_part[2];
   const int N = t.N, G = t.G, Gp = t.Gp, NE = t.n_entries;
   const int c0 = cl.cbase[b], nc = cl.cbase[b + 1] - c0;
   const int e0 = cl.ebase[b], ne = cl.ebase[b + 1] - e0;
@@ -326,17 +325,26 @@ __global__ void __launch_bounds__(1024, 1) cmfd_solve_cluster_kernel(CmfdTopo t,
   const int32_t *eoff = cl.eoff + c0 + b;  // nc + 1 local offsets
   const int32_t *coff = cl.ccoff + (size_t)b * (t.n_colors + 1);
   // the iterate sits at the same shared-memory offset in every CTA (sized by the largest slice),
-  // so a neighbour's value is read at its owner's copy of that offset
+  // so a neighbour's value is read at its owner's copy of that offset; two copies (s_x and
+  // s_x + ncmax) alternate from group to group, so the next group is staged while other CTAs may
+  // still read the current one
   int ncmax = 0;
   for (int r = 0; r < C; ++r) ncmax = max(ncmax, cl.cbase[r + 1] - cl.cbase[r]);
   extern __shared__ unsigned char dyn[];
   Real *s_x = reinterpret_cast<Real *>(dyn);
-  Real *s_src = s_x + ncmax;
+  Real *s_src = s_x + 2 * ncmax;
   Real *s_rd = s_src + ncmax;
   Real *s_din = s_rd + ncmax;
-  int32_t *s_loc = reinterpret_cast<int32_t *>(s_din + ne);
-  int32_t *s_eoff = s_loc + ne;
-  for (int q = threadIdx.x; q < ne; q += blockDim.x) s_loc[q] = cl.loc[e0 + q];
+  int32_t *s_eoff = reinterpret_cast<int32_t *>(s_din + ne);
+  // each entry's neighbour iterate as one generic address (this CTA's shared memory or another's
+  // through distributed shared memory), resolved once, so a colour sweep loads it without a branch
+  uintptr_t np_at = reinterpret_cast<uintptr_t>(s_eoff + nc + 1);
+  np_at = (np_at + 7) & ~(uintptr_t)7;
+  const Real **s_np = reinterpret_cast<const Real **>(np_at);
+  for (int q = threadIdx.x; q < ne; q += blockDim.x) {
+    const int l = cl.loc[e0 + q], r = l >> 16, k = l & 0xffff;
+    s_np[q] = (r == b) ? s_x + k : cluster.map_shared_rank(s_x + k, r);
+  }
   for (int i = threadIdx.x; i <= nc; i += blockDim.x) s_eoff[i] = eoff[i];
   // 1. coefficients of the owned cells from the tallied currents (FP64 leakage terms)
   for (int x = threadIdx.x; x < nc * G; x += blockDim.x) {
@@ -345,12 +353,16 @@ __global__ void __launch_bounds__(1024, 1) cmfd_solve_cluster_kernel(CmfdTopo t,
     const Real pi = cphi[xi];
     const double inv_pi = (pi > (Real)0) ? 1.0 / (double)pi : 0.0;
     double out = leak[(size_t)i * Gp + g];
-    for (int q = t.cif_off[i]; q < t.cif_off[i + 1]; ++q) {
+    // coefficients stored in this CTA's entry order (its slice e0 .. e0 + ne of each group's
+    // row), so the per-group staging below reads them contiguously
+    const int q_base = t.cif_off[i];
+    Real *drow = din + (size_t)g * NE + e0 + eoff[li];
+    for (int q = q_base; q < t.cif_off[i + 1]; ++q) {
       const int e = t.cif[q] >> 1, side = t.cif[q] & 1;
       const int j = t.if_cells[2 * e + (side ^ 1)];
       const Real pj = cphi[(size_t)g * N + j];
       out += cur[(size_t)(2 * e + side) * Gp + g];
-      din[(size_t)g * NE + q] = (pj > (Real)0) ? (Real)(cur[(size_t)(2 * e + (side ^ 1)) * Gp + g] / (double)pj) : (Real)0;
+      drow[q - q_base] = (pj > (Real)0) ? (Real)(cur[(size_t)(2 * e + (side ^ 1)) * Gp + g] / (double)pj) : (Real)0;
     }
     diag[xi] = TV[xi] - SV[((size_t)g * G + g) * N + i] + (Real)(out * inv_pi);
     phic[xi] = pi;
@@ -358,24 +370,43 @@ __global__ void __launch_bounds__(1024, 1) cmfd_solve_cluster_kernel(CmfdTopo t,
   cluster.sync();  // every CTA's currents read before any are cleared
   for (int x = b * blockDim.x + threadIdx.x; x < NE * Gp; x += C * blockDim.x) cur[x] = 0.0;
   for (int x = b * blockDim.x + threadIdx.x; x < N * Gp; x += C * blockDim.x) leak[x] = 0.0;
+  // cluster-wide reductions publish each CTA's partial in one of two slots, alternately: a slot is
+  // written again only after the next reduction's barrier, which no CTA passes before every CTA
+  // has finished reading the slot, so one barrier per reduction suffices
+  int sp = 0;
   auto cluster_sum = [&](double v) {
     const double p = block_sum_1024(v, red32);
-    if (threadIdx.x == 0) s_part = p;
+    if (threadIdx.x == 0) s_part[sp] = p;
     cluster.sync();
     double tot = 0.0;
-    for (int r = 0; r < C; ++r) tot += *cluster.map_shared_rank(&s_part, r);
-    cluster.sync();  // s_part is not overwritten before every CTA has read it
+    for (int r = 0; r < C; ++r) tot += *cluster.map_shared_rank(&s_part[sp], r);
+    sp ^= 1;
     return tot;
   };
   auto cluster_max = [&](double v) {
     const double p = block_max_1024(v, red32);
-    if (threadIdx.x == 0) s_part = p;
+    if (threadIdx.x == 0) s_part[sp] = p;
     cluster.sync();
     double m = 0.0;
-    for (int r = 0; r < C; ++r) m = fmax(m, *cluster.map_shared_rank(&s_part, r));
-    cluster.sync();
+    for (int r = 0; r < C; ++r) m = fmax(m, *cluster.map_shared_rank(&s_part[sp], r));
+    sp ^= 1;
     return m;
   };
+  // the group's fixed source, 1/diagonal, coefficients and iterate (into copy `to` of s_x)
+  auto stage = [&](int g, Real inv_k, int to) {
+    Real *sx = s_x + to * ncmax;
+    for (int li = threadIdx.x; li < nc; li += blockDim.x) {
+      const int i = own[li];
+      Real rhs = CHI[(size_t)g * N + i] * fis[i] * inv_k;
+      rhs = cell_inscatter(SV, phic, g, G, N, i, rhs);
+      s_src[li] = rhs;
+      const Real dg = diag[(size_t)g * N + i];
+      s_rd[li] = (dg > (Real)0) ? (Real)1 / dg : (Real)0;
+      sx[li] = phic[(size_t)g * N + i];
+    }
+    for (int q = threadIdx.x; q < ne; q += blockDim.x) s_din[q] = din[(size_t)g * NE + e0 + q];
+  };
+  int xb = 0;  // the copy of s_x that holds the current group
   double kc = scal[S_K];
   // 2. coarse power iteration. The fission sum that ends an iteration is, operation for operation,
   // the one that starts the next (same cells, same threads, same order), so it is carried over
@@ -391,37 +422,50 @@ __global__ void __launch_bounds__(1024, 1) cmfd_solve_cluster_kernel(CmfdTopo t,
     }
     const double F_old = it == 0 ? cluster_sum(fsum) : F_carry;
     const Real inv_k = (Real)(1.0 / kc);
+    // the first group is staged after the fission sum's barrier, which every CTA passes only once
+    // its last colour sweep of the previous iteration is done
+    xb ^= 1;
+    stage(0, inv_k, xb);
+    cluster.sync();  // every CTA's iterate staged before any is read remotely
     for (int g = 0; g < G; ++g) {
-      for (int li = threadIdx.x; li < nc; li += blockDim.x) {
-        const int i = own[li];
-        Real rhs = CHI[(size_t)g * N + i] * fis[i] * inv_k;
-        rhs = cell_inscatter(SV, phic, g, G, N, i, rhs);
-        s_src[li] = rhs;
-        const Real dg = diag[(size_t)g * N + i];
-        s_rd[li] = (dg > (Real)0) ? (Real)1 / dg : (Real)0;
-        s_x[li] = phic[(size_t)g * N + i];
-      }
-      for (int q = threadIdx.x; q < ne; q += blockDim.x) s_din[q] = din[(size_t)g * NE + cl.ent[e0 + q]];
-      cluster.sync();  // every CTA's iterate staged before any is read remotely
+      Real *sx = s_x + xb * ncmax;
+      const int xo = xb * ncmax;
       for (int j = 0; j < n_inner; ++j) {
         for (int c = 0; c < t.n_colors; ++c) {
           for (int li = coff[c] + threadIdx.x; li < coff[c + 1]; li += blockDim.x) {
             Real rhs = s_src[li];
-            for (int q = s_eoff[li]; q < s_eoff[li + 1]; ++q) {
-              const int l = s_loc[q], r = l >> 16, k = l & 0xffff;
-              const Real xn = (r == b) ? s_x[k] : *cluster.map_shared_rank(s_x + k, r);
-              rhs += s_din[q] * xn;
+            const int q0 = s_eoff[li], q1 = s_eoff[li + 1];
+            // neighbours in batches of 8: the (local or remote) loads first, then the additions
+            // in entry order
+            for (int qb = q0; qb < q1; qb += 8) {
+              Real xv[8], dv[8];
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                const bool in = qb + u < q1;
+                xv[u] = in ? s_np[qb + u][xo] : (Real)0;
+                dv[u] = in ? s_din[qb + u] : (Real)0;
+              }
+#pragma unroll
+              for (int u = 0; u < 8; ++u)
+                if (qb + u < q1) rhs += dv[u] * xv[u];
             }
             const Real rd = s_rd[li];
-            if (rd > (Real)0) s_x[li] = fma(omega, rhs * rd - s_x[li], s_x[li]);
+            if (rd > (Real)0) sx[li] = fma(omega, rhs * rd - sx[li], sx[li]);
           }
-          cluster.sync();
+          // the group's last colour sweep ends with the next group's staging barrier instead
+          if (j + 1 < n_inner || c + 1 < t.n_colors) cluster.sync();
         }
       }
-      // no barrier here: the last colour sweep's barrier already ended every remote read of this
-      // group's iterate, and each thread reads back (next group's staging, the fission sums) only
-      // the owned cells it writes itself
-      for (int li = threadIdx.x; li < nc; li += blockDim.x) phic[(size_t)g * N + own[li]] = s_x[li];
+      // this CTA's sweeps are done (its own reads of the staged source, diagonal and
+      // coefficients; its own iterate final); other CTAs may still read this copy of the iterate
+      __syncthreads();
+      for (int li = threadIdx.x; li < nc; li += blockDim.x) phic[(size_t)g * N + own[li]] = sx[li];
+      if (g + 1 < G) {
+        // each thread stages only owned cells whose other-group values it wrote itself
+        xb ^= 1;
+        stage(g + 1, inv_k, xb);
+        cluster.sync();  // every CTA's last colour sweep of g done and group g + 1 staged
+      }
     }
     fsum = 0.0;
     for (int li = threadIdx.x; li < nc; li += blockDim.x) {
