@@ -532,7 +532,9 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_plain", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2)
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=None, choices=sorted(WORKLOADS),
+                    help=f"default: {DEFAULT_WORKLOAD} (with --dgmoc-only: the assembly, whose extruded "
+                         "stack the default line's DGMOC block measures)")
     ap.add_argument("--no-time-to-k", action="store_true")
     ap.add_argument("--no-tracking", action="store_true", help="skip the host vs device tracking timing")
     ap.add_argument("--no-assembly", action="store_true", help="skip the 17x17 assembly block")
@@ -557,6 +559,8 @@ def main():
                     help="stop each outer's coarse power iteration once k and the coarse source settle "
                          "to this (0: the fixed count)")
     args = ap.parse_args()
+    if args.workload is None:
+        args.workload = "assembly" if args.dgmoc_only else DEFAULT_WORKLOAD
     cm_defaults = {"assembly": "1.26,6,6,1.0", "core": "1.26,80,3,1.5", "hexcore": "2.52,10,5,1.0",
                    "hexcore7": "2.52,10,5,1.0", "hexcore1": "2.52,10,5,1.0", "pin": "0.63,6,6,1.0"}
 
