@@ -588,8 +588,9 @@ template <typename Real> int launch_source(moc_ctx *c, cudaStream_t st) {
              : gpl == 3 ? source_lanes_kernel<Real, 3> : gpl == 4 ? source_lanes_kernel<Real, 4>
                         : source_lanes_kernel<Real, 0>;
     src<<<nb, 256, sm, st>>>(R, c->G, c->Gp, c->d_mat, (const Real *)c->d_sig_s, (const Real *)c->d_sig_sT, c->Gp4,
-                            (const Real *)c->d_nsf, (const Real *)c->d_chi, c->d_srange, c->d_ext, (Real *)c->d_phi,
-                            (typename Pair<Real>::T *)c->d_xsq, c->d_fold, c->d_scal, c->eigen ? 1 : 0);
+                            (const Real *)c->d_nsf, (const Real *)c->d_chi, c->d_srange, c->d_ext,
+                            (const Real *)c->d_sig_t, (Real *)c->d_phi, (typename Pair<Real>::T *)c->d_xsq,
+                            c->d_fold, c->d_scal, c->eigen ? 1 : 0);
     CUDA_TRY(c, cudaGetLastError());
     return MOC_OK;
   }
@@ -689,6 +690,39 @@ int launch_sweep(moc_ctx *c, cudaStream_t st) {
   return launch_sweep_p<float, 0, false>(c, st);
 }
 
+template <int TM, int GPL> int launch_finalize_bulk_t(moc_ctx *c, cudaStream_t st) {
+  const int R = c->geo.n_tri;
+  const size_t sm = 2 * (size_t)finalize_bulk_stage_floats(c->Gp, TM, c->eigen ? 1 : 0) * sizeof(float);
+  auto fn = finalize_bulk_kernel<TM, GPL>;
+  // the opt-in covers dynamic memory beyond what the default leaves next to the static reduction buffers
+  CUDA_TRY(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  int per_sm = 0;
+  CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, sm));
+  per_sm = std::max(1, std::min(per_sm, 8));
+  const unsigned nb = (unsigned)std::max(1, std::min((R + 31) / 32, per_sm * std::max(c->n_sm, 1)));
+  fn<<<nb, 256, sm, st>>>(R, c->G, c->Gp, c->d_mat, (const float *)c->d_nsf, (const float *)c->d_inv_ta,
+                          (const float2 *)c->d_xsq, (float *)c->d_tsum, (float *)c->d_tcomp, (float *)c->d_phi,
+                          c->d_fold, c->d_area, c->d_part, c->d_ticket, c->d_scal, c->eigen ? 1 : 0);
+  CUDA_TRY(c, cudaGetLastError());
+  return MOC_OK;
+}
+
+template <int TM> int launch_finalize_bulk_tm(moc_ctx *c, cudaStream_t st) {
+  switch ((c->Gp + 7) / 8) {
+    case 2: return launch_finalize_bulk_t<TM, 2>(c, st);
+    case 3: return launch_finalize_bulk_t<TM, 3>(c, st);
+    case 4: return launch_finalize_bulk_t<TM, 4>(c, st);
+    case 5: return launch_finalize_bulk_t<TM, 5>(c, st);
+    case 6: return launch_finalize_bulk_t<TM, 6>(c, st);
+    case 7: return launch_finalize_bulk_t<TM, 7>(c, st);
+    default: return launch_finalize_bulk_t<TM, 8>(c, st);
+  }
+}
+
+int launch_finalize_bulk(moc_ctx *c, cudaStream_t st) {
+  return tally_mode(c) == 1 ? launch_finalize_bulk_tm<1>(c, st) : launch_finalize_bulk_tm<0>(c, st);
+}
+
 template <typename Real> int launch_finalize_reduce(moc_ctx *c, cudaStream_t st) {
   const int R = c->geo.n_tri;
   if (c->Gp == 8) {
@@ -706,6 +740,11 @@ template <typename Real> int launch_finalize_reduce(moc_ctx *c, cudaStream_t st)
           c->d_scal, c->eigen ? 1 : 0);
     CUDA_TRY(c, cudaGetLastError());
     return MOC_OK;
+  }
+  if (lane_rows(c) && sizeof(Real) == 4 && c->Gp <= 64) {
+    // FP32, rows of up to 64 groups: tiles of 32 regions staged by bulk copies, double-buffered,
+    // as many blocks as fit on the device (at most 8 per multiprocessor)
+    if constexpr (sizeof(Real) == 4) return launch_finalize_bulk(c, st);
   }
   if (lane_rows(c)) {
     // tiles of 32 regions, blocks striding over them: at most 8 blocks per multiprocessor
@@ -2110,6 +2149,7 @@ int moc_outer(moc_ctx *c, int n, double *k_out, double *resid_out) {
     if (n > 0) record_history(c, s);
     if (k_out) *k_out = s[S_K];
     if (resid_out) *resid_out = s[S_RESID];
+    if (s[S_STATUS] == 2.0) return fail(c, MOC_ERR_CUDA, "outer: a bulk copy of the finalize did not complete");
     if (s[S_STATUS] != 0.0) return fail(c, MOC_ERR_NONFINITE, "outer: k or the residual is not finite");
   }
   return MOC_OK;
@@ -2218,6 +2258,8 @@ int moc_power_iterate(moc_ctx *c, double tol_k, double tol_flux, int max_outer, 
     n += m;
     if ((rc = read_scalars(c, s))) return rc;
     record_history(c, s);
+    if (s[S_STATUS] == 2.0)
+      return fail(c, MOC_ERR_CUDA, "power_iterate: a bulk copy of the finalize did not complete");
     if (s[S_STATUS] != 0.0) return fail(c, MOC_ERR_NONFINITE, "power_iterate: k or the residual is not finite");
     bool ok_k = !c->eigen || std::fabs(s[S_K] - s[S_KPREV]) <= tol_k;
     if (ok_k && s[S_RESID] <= tol_flux) {

@@ -169,8 +169,9 @@ template <typename Real, int GPL>
 __global__ void __launch_bounds__(256) source_lanes_kernel(
     int R, int G, int Gp, const int32_t *__restrict__ mat, const Real *__restrict__ sig_s,
     const Real *__restrict__ sig_sT, int Gp4, const Real *__restrict__ nsf, const Real *__restrict__ chi,
-    const int2 *__restrict__ srange, const double *__restrict__ ext, Real *__restrict__ phi,
-    typename Pair<Real>::T *__restrict__ xsq, double *__restrict__ fold, const double *__restrict__ scal, int eigen) {
+    const int2 *__restrict__ srange, const double *__restrict__ ext, const Real *__restrict__ sig_t,
+    Real *__restrict__ phi, typename Pair<Real>::T *__restrict__ xsq, double *__restrict__ fold,
+    const double *__restrict__ scal, int eigen) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int gpl = GPL > 0 ? GPL : (Gp + 7) / 8;
   const int rl = threadIdx.x >> 3, l = threadIdx.x & 7;
@@ -250,10 +251,10 @@ __global__ void __launch_bounds__(256) source_lanes_kernel(
     }
     Real src = sc + chi[m * G + g] * inv_k * f;
     if (ext) src += (Real)ext[(size_t)r * G + g];
+    // only the q/Sigma_t half of the region's pair is written; Sigma_t (the pair's other half,
+    // the same value) comes from the material table, so the pair is not read
     const size_t a = (size_t)r * Gp + g;
-    typename Pair<Real>::T v = xsq[a];
-    v.y = src * inv4pi / v.x;
-    xsq[a] = v;
+    reinterpret_cast<Real *>(xsq)[2 * a + 1] = src * inv4pi / sig_t[m * G + g];
   }
 }
 
@@ -980,6 +981,203 @@ __global__ void __launch_bounds__(256) finalize_lanes_kernel(
       mn = fmin(mn, l_min[q]);
       mx = fmax(mx, l_max[q]);
       rs = fmax(rs, l_res[q]);
+    }
+    part[4 * blockIdx.x + 0] = a;
+    part[4 * blockIdx.x + 1] = (double)mn;
+    part[4 * blockIdx.x + 2] = (double)mx;
+    part[4 * blockIdx.x + 3] = (double)rs;
+    __threadfence();
+    last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    reduce_partials(gridDim.x, part, scal, eigen);
+    if (threadIdx.x == 0) *ticket = 0u;
+  }
+}
+
+// ----------------------------------------------------------------------------- finalize, bulk
+// FP32 finalize for many groups with its inputs staged by the copy engine's bulk path: a tile's 32
+// region rows of tsum, tcomp, 1/(Sigma_t A), the old flux (fixed-source mode) and the {Sigma_t,
+// q/Sigma_t} pairs are contiguous, so each is one cp.async.bulk copy into shared memory, completed
+// on an mbarrier. Tiles are double-buffered: the copies of a block's next tile are in flight while
+// it computes the current one, so many bytes are outstanding per SM without registers to hold
+// them. The arithmetic, the stores and the fixed-order reduction are those of
+// finalize_lanes_kernel, so the results are the same bit for bit. A wait that has not completed
+// after about a second sets S_STATUS = 2 (the host reports an error), waits (again bounded) for the
+// block's copies still in flight, and leaves the loop.
+__device__ __forceinline__ uint32_t bulk_smem(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bulk_expect(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bulk_smem(bar)), "r"(bytes) : "memory");
+}
+
+// global -> shared, bytes a multiple of 16, both addresses 16-byte aligned
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   bulk_smem(dst)),
+               "l"(src), "r"(bytes), "r"(bulk_smem(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ uint64_t bulk_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// wait for the mbarrier phase of the given parity; false after about one second
+__device__ __forceinline__ bool bulk_wait(uint64_t *bar, uint32_t parity) {
+  const uint32_t a = bulk_smem(bar);
+  const uint64_t t0 = bulk_ns();
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (bulk_ns() - t0 > 1000000000ull) return false;
+  }
+}
+
+// Shared memory per stage (floats): tsum | tcomp (TM = 1) | 1/(Sigma_t A) | old flux (fixed
+// source) | pairs (2 per element), each 32 * Gp long.
+__host__ __device__ constexpr int finalize_bulk_stage_floats(int Gp, int TM, int eigen) {
+  return 32 * Gp * (2 + TM + (eigen ? 0 : 1) + 2);
+}
+
+template <int TM, int GPL>
+__global__ void __launch_bounds__(256) finalize_bulk_kernel(
+    int R, int G, int Gp, const int32_t *__restrict__ mat, const float *__restrict__ nsf,
+    const float *__restrict__ inv_ta, const float2 *__restrict__ xsq, float *__restrict__ tsum,
+    float *__restrict__ tcomp, float *__restrict__ phi, const double *__restrict__ fold,
+    const double *__restrict__ area, double *__restrict__ part, unsigned *__restrict__ ticket,
+    double *__restrict__ scal, int eigen) {
+  extern __shared__ __align__(16) float fb_dyn[];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ double l_sum[32];
+  __shared__ float l_min[32], l_max[32], l_res[32];
+  __shared__ bool last;
+  __shared__ int s_fail;
+  const int qg = threadIdx.x >> 3, l = threadIdx.x & 7;
+  const int ntile = (R + 31) / 32;
+  const int tf = 32 * Gp, stage_f = finalize_bulk_stage_floats(Gp, TM, eigen);
+  auto st_t = [&](int st) { return fb_dyn + st * stage_f; };
+  auto st_c = [&](int st) { return fb_dyn + st * stage_f + tf; };
+  auto st_i = [&](int st) { return fb_dyn + st * stage_f + tf * (1 + TM); };
+  auto st_o = [&](int st) { return fb_dyn + st * stage_f + tf * (2 + TM); };
+  auto st_q = [&](int st) { return fb_dyn + st * stage_f + tf * (2 + TM + (eigen ? 0 : 1)); };
+  // thread 0: every copy of one tile into one stage, the byte count announced first
+  auto issue = [&](int tile, int st) {
+    const int r0 = tile * 32, nr = min(32, R - r0);
+    const size_t off = (size_t)r0 * Gp;
+    const uint32_t n4 = (uint32_t)(nr * Gp) * 4u;
+    const uint32_t total = n4 * (2u + (uint32_t)TM + (eigen ? 0u : 1u)) + 2u * n4;
+    bulk_expect(&bar[st], total);
+    bulk_g2s(st_t(st), tsum + off, n4, &bar[st]);
+    if (TM == 1) bulk_g2s(st_c(st), tcomp + off, n4, &bar[st]);
+    bulk_g2s(st_i(st), inv_ta + off, n4, &bar[st]);
+    if (!eigen) bulk_g2s(st_o(st), phi + off, n4, &bar[st]);
+    bulk_g2s(st_q(st), xsq + off, 2u * n4, &bar[st]);
+  };
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bulk_smem(&bar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bulk_smem(&bar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    s_fail = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && (int)blockIdx.x < ntile) issue(blockIdx.x, 0);
+  double g_sum = 0.0;
+  float g_min = INFINITY, g_max = -INFINITY, g_res = 0.f;
+  int k = 0, tile = blockIdx.x;
+  for (; tile < ntile; tile += gridDim.x, ++k) {
+    const int st = k & 1;
+    const int nxt = tile + (int)gridDim.x;
+    if (threadIdx.x == 0 && nxt < ntile) {
+      // the stage was last read before the barrier that ended the previous iteration
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(nxt, st ^ 1);
+    }
+    const int r = tile * 32 + qg;
+    const bool live = r < R;
+    // per-region inputs that are not staged, loaded while the tile's copies complete
+    int m = 0;
+    double ar = 0.0, fo = 0.0;
+    if (live) {
+      m = mat[r];
+      if (l == 0) {
+        ar = area[r];
+        if (eigen) fo = fold[r];
+      }
+    }
+    if (!bulk_wait(&bar[st], (uint32_t)(k >> 1) & 1u)) s_fail = 1;
+    float f = 0.f, res = 0.f;
+    if (live) {
+      const float *t_ = st_t(st), *c_ = st_c(st), *i_ = st_i(st), *o_ = st_o(st), *q_ = st_q(st);
+      const int base = qg * Gp;
+#pragma unroll
+      for (int j = 0; j < GPL; ++j) {
+        const int g = l + 8 * j;
+        if (g < Gp) {
+          const size_t a = (size_t)r * Gp + g;
+          const float t = t_[base + g];
+          const float c = TM == 1 ? c_[base + g] : 0.f;
+          tsum[a] = 0.f;
+          if (TM == 1) tcomp[a] = 0.f;
+          if (g < G) {
+            const float ph = fmaf(TM == 1 ? t + c : t, i_[base + g], (float)kFourPi * q_[2 * (base + g) + 1]);
+            if (!eigen && ph > 0.f) res = fmaxf(res, fabsf(ph - o_[base + g]) / ph);
+            phi[a] = ph;
+            f += nsf[m * G + g] * ph;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+    if (!eigen) {
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) res = fmaxf(res, __shfl_xor_sync(0xffffffffu, res, o));
+    }
+    if (l == 0 && live) {
+      g_sum += ar * (double)f;
+      if (eigen && f > 0.f) {
+        const float rho = (float)fo / f;
+        g_min = fminf(g_min, rho);
+        g_max = fmaxf(g_max, rho);
+      }
+      g_res = fmaxf(g_res, res);
+    }
+    __syncthreads();  // every read of this stage done before the next iteration refills it
+    if (s_fail) break;
+  }
+  if (s_fail && threadIdx.x == 0) {
+    // the stage that timed out and the next tile's copies, if issued, may still be in flight
+    bulk_wait(&bar[k & 1], (uint32_t)(k >> 1) & 1u);
+    if (tile + (int)gridDim.x < ntile) bulk_wait(&bar[(k + 1) & 1], (uint32_t)((k + 1) >> 1) & 1u);
+    scal[S_STATUS] = 2.0;
+  }
+  if (l == 0) {
+    l_sum[qg] = g_sum;
+    l_min[qg] = g_min;
+    l_max[qg] = g_max;
+    l_res[qg] = g_res;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    float mn = INFINITY, mx = -INFINITY, rs = 0.f;
+    for (int q = 0; q < 32; ++q) {
+      a += l_sum[q];
+      mn = fminf(mn, l_min[q]);
+      mx = fmaxf(mx, l_max[q]);
+      rs = fmaxf(rs, l_res[q]);
     }
     part[4 * blockIdx.x + 0] = a;
     part[4 * blockIdx.x + 1] = (double)mn;
