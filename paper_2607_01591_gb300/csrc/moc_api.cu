@@ -709,6 +709,7 @@ template <int TM, int GPL> int launch_finalize_bulk_t(moc_ctx *c, cudaStream_t s
 
 template <int TM> int launch_finalize_bulk_tm(moc_ctx *c, cudaStream_t st) {
   switch ((c->Gp + 7) / 8) {
+    case 1: return launch_finalize_bulk_t<TM, 1>(c, st);
     case 2: return launch_finalize_bulk_t<TM, 2>(c, st);
     case 3: return launch_finalize_bulk_t<TM, 3>(c, st);
     case 4: return launch_finalize_bulk_t<TM, 4>(c, st);
@@ -725,6 +726,10 @@ int launch_finalize_bulk(moc_ctx *c, cudaStream_t st) {
 
 template <typename Real> int launch_finalize_reduce(moc_ctx *c, cudaStream_t st) {
   const int R = c->geo.n_tri;
+  if (c->Gp == 8 && sizeof(Real) == 4) {
+    // FP32, one group per lane: the bulk-staged finalize
+    if constexpr (sizeof(Real) == 4) return launch_finalize_bulk(c, st);
+  }
   if (c->Gp == 8) {
     // 8 lanes per region, 32 regions per block of 256 threads; the last block also reduces
     const int nb8 = (R + 31) / 32;
@@ -742,7 +747,7 @@ template <typename Real> int launch_finalize_reduce(moc_ctx *c, cudaStream_t st)
     return MOC_OK;
   }
   if (lane_rows(c) && sizeof(Real) == 4 && c->Gp <= 64) {
-    // FP32, rows of up to 64 groups: tiles of 32 regions staged by bulk copies, double-buffered,
+    // FP32, rows of 12 to 64 groups: tiles of 32 regions staged by bulk copies, double-buffered,
     // as many blocks as fit on the device (at most 8 per multiprocessor)
     if constexpr (sizeof(Real) == 4) return launch_finalize_bulk(c, st);
   }
